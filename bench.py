@@ -1,0 +1,303 @@
+"""Benchmark of the D3Q7 reactive-diffusion LBM hot path on one GB300.
+
+Workload: the 256^3 Pt catalyst layer at 2 nm (seeded QSGS: pore 45 %,
+ionomer 18.87 %, solid 36.13 %; Knudsen diffusivity from the 13-direction
+pore length at 353 K; 5 % of the carbon-pore faces catalytic with
+k = 1e-3 m/s; gas reservoir plane at x = 0 with a fixed concentration,
+zero-flux outlet; periodic in y and z).
+
+One bench step = one check interval of the solver: `--check-every` fused
+collide-stream steps (the last with the fused FP64 reduction), replayed as
+one CUDA graph, plus the host read of the readouts.  The metric is MLUPS
+over all box cells.  The population buffers (2 x 7 x 4 B x 16.8 M cells)
+are far larger than the 129 MB L2, so no flush is needed between steps.
+
+Rank r of N solves its own structure (seed 1 + r): weak scaling with no
+data-path collective.
+
+`--impl reference` times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pt_cl_256"
+WORKLOAD_DESC = ("256^3 Pt catalyst layer, 2 nm voxels, seeded QSGS (pore 0.45, ionomer 0.1887), "
+                 "Knudsen D (353 K, M 0.032), 5% catalytic carbon-pore faces k=1e-3 m/s, "
+                 "reservoir plane + fixed C inlet, zero-flux outlet, periodic y,z")
+
+
+def bytes_per_cell(storage: str) -> tuple[float, float]:
+    """Algorithmic DRAM bytes of one fused step: (per active cell, per box cell).
+
+    Active cell: 7 populations read + 7 written (4 B each) + omega (4 B);
+    every box cell: its 2 B link mask."""
+    if storage == "fp32":
+        return 7 * 4 * 2 + 4, 2
+    # C (4 B) + 6 deviations (2 B) read and written, omega 4 B
+    return (4 + 6 * 2) * 2 + 4, 2
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(ph, react, params, budget_s: float = 20.0):
+    """The FP64 oracle on the host cores: set-up, then as many whole steps as
+    fit the budget (at least one).  Returns MLUPS and what was sampled."""
+    import oracle
+    t0 = time.perf_counter()
+    o = oracle.OracleLBM(ph, react=react, **params)
+    t_setup = time.perf_counter() - t0
+    n = ph.size
+    steps = 0
+    t1 = time.perf_counter()
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t1
+        if el * (steps + 1) / steps > budget_s:
+            break
+    mlups = n * steps / el / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 steps of the full {ph.shape[2]}x{ph.shape[1]}x{ph.shape[0]} workload "
+                      f"({el:.1f} s; oracle set-up {t_setup:.1f} s not counted)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle, as it stands, on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from paper_1410_1914_gb300 import inputs
+    import oracle
+    ph, react, params = inputs.make_workload(WORKLOAD, shape=args.shape)
+    o = oracle.OracleLBM(ph, react=react, **params)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(args.ref_steps_per_step)
+    el = time.perf_counter() - t0
+    n = ph.size
+    value = n * args.steps * args.ref_steps_per_step / el / 1e6
+    line = {
+        "impl": "reference", "metric": "MLUPS (D3Q7 fused collide-stream, all box cells)", "value": value,
+        "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "shape_zyx": list(ph.shape),
+                   "lbm_steps_per_bench_step": args.ref_steps_per_step},
+        "cpu_baseline": {"value": value, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{args.steps} x {args.ref_steps_per_step} FP64 steps of the full workload"},
+        "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16dev"])
+    ap.add_argument("--check-every", type=int, default=100)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-lbm-steps", type=int, default=1000)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-steps-per-step", type=int, default=1)
+    ap.add_argument("--shape", type=int, nargs=3, default=None, help="override (nz ny nx)")
+    args = ap.parse_args()
+    if args.shape:
+        args.shape = tuple(args.shape)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1410_1914_gb300 import Solver, inputs
+    from paper_1410_1914_gb300 import _lib as L
+
+    ph, react, params = inputs.make_workload(WORKLOAD, shape=args.shape, seed=1 + rank)
+    n_cells = ph.size
+    K = args.check_every
+    stream = torch.cuda.current_stream()
+    s = Solver(ph.shape, storage=args.storage, stream=int(stream.cuda_stream), check_every=K, **params)
+    t0 = time.perf_counter()
+    s.set_structure(ph, react)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    info = s.info()
+
+    for _ in range(args.warmup):
+        s.solve_budget(K)
+    torch.cuda.synchronize()
+
+    # ---------------------------------------------------------- timed region
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        last = None
+        for _ in range(args.steps):
+            last = s.solve_budget(K)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_updates = n_cells * K * args.steps * world
+    mlups = total_updates / (elapsed_ms * 1e-3) / 1e6
+    ms_per_step = elapsed_ms / args.steps
+
+    # roofline of the fused step kernel (average launch = interval time / K)
+    per_active, per_cell = bytes_per_cell(args.storage)
+    launch_bytes = per_active * info["n_active"] + per_cell * n_cells
+    launch_s = ms_per_step * 1e-3 / K
+    peak, peak_kind = measured_peak_gbs()
+    achieved = launch_bytes / launch_s / 1e9
+
+    # ---------------------------------------------------------- end to end
+    # Through the public API with host buffers: pinned host structure ->
+    # set_structure -> e2e_lbm_steps steps -> reaction rate to the host.
+    e2e = None
+    if args.e2e_steps > 0:
+        ph_pin = torch.from_numpy(ph).pin_memory()
+        re_pin = torch.from_numpy(react).pin_memory() if react is not None else None
+        E = max(K, (args.e2e_lbm_steps // K) * K)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            L.cl_lbm_set_structure(s.h, ph_pin, re_pin, n_cells)
+            s.solve_budget(E)
+            R_tot, prof_R, prof_C = s.reaction_rate()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": n_cells * E * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(ph.nbytes + (react.nbytes if react is not None else 0)),
+               "d2h_bytes_per_step": int(8 + 2 * 8 * ph.shape[2]),
+               "lbm_steps_per_e2e_step": E, "includes": "structure upload + GPU set-up + steps + readout"}
+
+    line = {
+        "metric": "MLUPS (D3Q7 fused collide-stream, all box cells)",
+        "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_DESC, "shape_zyx": list(ph.shape), "storage": args.storage,
+                   "lbm_steps_per_bench_step": K, "active_fraction": info["n_active"] / n_cells,
+                   "l2": "inputs larger than L2 (population buffers 2 x %.0f MB)" % (7 * 4 * n_cells / 1e6),
+                   "parallelism": f"replicas x{world}", "setup_s": setup_s},
+        "active_mlups": mlups * info["n_active"] / n_cells,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_kind": f"{peak_kind} hbm_gbs",
+                     "algorithmic_bytes_per_launch": launch_bytes, "kernel": "k_step_fp32"},
+        "gpu_launches": args.steps * (K + 1),
+        "clocks": clocks.summary(),
+        "e2e": e2e,
+        "last_check": {k: last[k] for k in ("J_in", "J_out", "R", "flux_balance", "resid")},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(ph, react, params, args.cpu_budget)
+    s.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,236 @@
+/*
+ * cl_lbm.h -- C ABI of the GB300 (sm_103a) reactive-diffusion lattice
+ * Boltzmann library for catalyst-layer structures, after Chen et al.,
+ * arXiv:1410.1914 ("Nanoscale study of reactive transport in catalyst layer
+ * of PEM fuel cells with precious and non-precious catalysts using LBM").
+ *
+ * The library solves, on one GPU, the steady O2 transport of Eq. 6 / Eq. 15
+ * in the transport phase of a voxelised catalyst layer:
+ *   - per-voxel diffusivity: Eq. 7 (bulk), Eq. 8 (Knudsen, from the
+ *     13-direction local pore length of Sec. 2.1.3), Eq. 9 (Bosanquet);
+ *   - relaxation time per voxel from Eq. 24, here on the D3Q7 lattice
+ *     (weights 1/4 rest, 1/8 axis; cs^2 = 1/4; D = (tau - 1/2) dx^2 / (4 dt));
+ *   - BGK evolution Eq. 21 with equilibrium w_i C (Eq. 23);
+ *   - boundaries of Sec. 3.5: fixed concentration (Eq. 19 setup, Eq. 20b)
+ *     or zero flux (Eq. 20a) at the x faces, periodic in y and z,
+ *     bounce-back on solid faces, and a first-order surface sink on
+ *     catalyst faces (the uniform-potential Tafel rate of Eq. 17b placed as a
+ *     flux k*C on the face rather than the volumetric source of Eq. 18a);
+ *   - readouts: D_eff of Eq. 19 and the total / per-plane reaction rate
+ *     (left side of Eq. 25 divided by 4F).
+ *
+ * Conventions shared by every call:
+ *   - Arrays are x-fastest: index = x + nx*(y + ny*z).
+ *   - Phase codes: 0 pore, 1 solid (carbon/Pt/catalyst), 2 ionomer,
+ *     3 micropore (transports like pore, never reactive).
+ *   - Direction codes d = 1..6 are +x, -x, +y, -y, +z, -z.
+ *   - A pointer argument documented "host or device" is read or written with
+ *     cudaMemcpyAsync on the handle's stream; `ptr_is_device` says which.
+ *   - Calls are ordered on the handle's CUDA stream.  Calls that return
+ *     values to host memory synchronise that stream before returning.
+ *   - Every call returns a cl_status; no call throws or aborts.  On
+ *     CL_ERR_ARG nothing was changed.  After CL_ERR_CUDA the handle should
+ *     be destroyed.
+ *   - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef CL_LBM_H
+#define CL_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cl_lbm* cl_handle;
+
+typedef enum {
+    CL_OK = 0,
+    CL_ERR_ARG = 1,           /* invalid argument (size, pointer, parameter) */
+    CL_ERR_OOM = 2,           /* device allocation failed */
+    CL_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    CL_ERR_STATE = 4,         /* call out of order (e.g. solve before set_structure) */
+    CL_ERR_DIVERGED = 5,      /* NaN/Inf in the readouts */
+    CL_ERR_NOT_CONVERGED = 6, /* max_steps reached before the stopping rule */
+    CL_ERR_NO_PATH = 7,       /* no transport cell is connected to the inlet plane */
+    CL_ERR_TIMEOUT = 8        /* a bounded device-side wait gave up */
+} cl_status;
+
+typedef enum { CL_BC_DIRICHLET = 0, CL_BC_ZERO_FLUX = 1 } cl_bc;
+
+typedef enum {
+    CL_STORE_FP32 = 0,   /* 7 x f32 populations per cell */
+    CL_STORE_FP16DEV = 1 /* C as f32 + 6 post-collision deviations from w_i C as scaled f16 */
+} cl_storage;
+
+typedef enum {
+    CL_REACT_GIVEN = 0,   /* reactive faces from the mask given to set_structure (NULL: none) */
+    CL_REACT_ALL_PORE_SOLID = 1 /* every face between a pore (0) and a solid (1) cell */
+} cl_react_rule;
+
+/* Optional device allocator (e.g. a framework's caching allocator).  Both
+   NULL: the library uses cudaMallocAsync / cudaFreeAsync on its stream. */
+typedef void* (*cl_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*cl_free_fn)(void* ptr, size_t bytes, void* stream, void* ctx);
+
+typedef struct {
+    int nx, ny, nz;        /* box in voxels, each >= 1; nx*ny*nz < 2^31 */
+    double dx_m;           /* voxel edge [m] */
+    double T_K;            /* temperature [K] (Eq. 7, Eq. 8) */
+    double p_atm;          /* pressure [atm] (Eq. 7) */
+    double M_kgmol;        /* O2 molar mass [kg/mol] (Eq. 8) */
+    double D_bulk;         /* bulk diffusivity [m^2/s]; <= 0: Eq. 7 */
+    double D_ionomer;      /* > 0: ionomer (phase 2) transports with this D; 0: impermeable */
+    double k_ms;           /* first-order surface rate constant [m/s] */
+    int knudsen;           /* 1: Eq. 8 + Eq. 9 in pore cells; 0: D = D_b */
+    int bc_in, bc_out;     /* cl_bc at x = 0 and x = L */
+    double c_in, c_out;    /* boundary concentrations (any unit; readouts carry it) */
+    double tau_ref;        /* relaxation time of the most diffusive active cell (> 0.5) */
+    int storage;           /* cl_storage */
+    int react_rule;        /* cl_react_rule */
+    int check_every;       /* steps between convergence checks in cl_lbm_solve (even, >= 2) */
+    double tol_flux;       /* |J_in - J_out - R| / |J_in| below this ... */
+    double tol_rel;        /* ... and the extrapolated relative error of the tracked readout
+                              (D_eff, or R for zero-flux outlets) below this: converged */
+    long long max_steps;   /* step budget of cl_lbm_solve */
+    void* cuda_stream;     /* cudaStream_t; NULL = legacy default stream */
+    cl_alloc_fn alloc;     /* optional, see above */
+    cl_free_fn free;
+    void* alloc_ctx;
+} cl_params;
+
+/* Fills the defaults: T 353 K, 1 atm, M 0.032, dx 1 nm, Dirichlet both ends,
+   c_in 1, c_out 0, tau_ref 1, FP32, check_every 1000, tol_flux 1e-4,
+   tol_rel 1e-4, max_steps 10^7; sizes 0. */
+void cl_params_default(cl_params* p);
+
+typedef struct {
+    long long n_cells;        /* nx*ny*nz */
+    long long n_transport;    /* transport-phase cells */
+    long long n_active;       /* transport cells 6-connected to the inlet plane */
+    long long n_wall_links;   /* active-cell faces toward inactive cells */
+    long long n_react_links;  /* of those, reactive */
+    double D_b;               /* bulk diffusivity used [m^2/s] */
+    double D_max;             /* largest active-cell diffusivity [m^2/s] */
+    double dt_s;              /* lattice time step [s] (Eq. 24 at tau_ref) */
+    double k_lu;              /* k dt / dx */
+    double mean_pore_diameter_m; /* mean 13-direction length over pore cells (Sec. 2.1.3) */
+} cl_structure_info;
+
+typedef struct {
+    long long steps;       /* steps taken by this call */
+    int converged;         /* 1 if the stopping rule fired */
+    double J_in, J_out, R; /* lattice-unit fluxes at the last check (see cl_lbm_fluxes) */
+    double flux_balance;   /* |J_in - J_out - R| / |J_in| at the last check */
+    double rel_change;     /* extrapolated relative error of the tracked readout */
+    double resid;          /* sum|C(t) - C(t-K)| / sum|C(t)| over the last interval */
+    double seconds;        /* wall time of the call */
+} cl_solve_info;
+
+/* Create a solver for a box of p->nx * p->ny * p->nz voxels.  Allocates all
+   device buffers (through p->alloc if given).  *out is set only on CL_OK.
+   Errors: CL_ERR_ARG (bad sizes/parameters), CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_lbm_create(cl_handle* out, const cl_params* p);
+
+/* Free every buffer of the handle (NULL is ignored). */
+void cl_lbm_destroy(cl_handle h);
+
+/* Load a structure (Sec. 2 reconstruction output) and run the set-up on
+   the GPU: transport set, cells reachable from the inlet plane (Sec. 2.1.3
+   connectivity), 13-direction pore lengths (Sec. 2.1.3), per-cell D
+   (Eq. 7-9), tau/omega (Eq. 24), link masks, then the linear initial field.
+     phase:          nx*ny*nz bytes of phase codes (host or device); copied.
+     reactive_faces: nx*ny*nz bytes, bit d-1 = face toward x + c_d is
+                     catalytic, or NULL (no reaction unless react_rule says
+                     otherwise); copied.  A face reacts only if it is marked,
+                     belongs to an active cell and its neighbour is solid (1).
+   Errors: CL_ERR_ARG (phase code > 3), CL_ERR_NO_PATH, CL_ERR_CUDA. */
+cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t* reactive_faces,
+                               int ptr_is_device);
+
+/* Replace the Eq. 7-9 diffusivities of the active cells by D [m^2/s]
+   (nx*ny*nz doubles, host or device; values of inactive cells ignored; each
+   active value must be > 0) and re-derive tau, omega and dt, then re-apply
+   the linear initial field.  For layered closed-form cases and for callers
+   with their own diffusivity model.  Errors: CL_ERR_STATE, CL_ERR_ARG. */
+cl_status cl_lbm_set_diffusivity(cl_handle h, const double* D, int ptr_is_device);
+
+/* Initial field: populations at equilibrium w_i C (Eq. 23).  C0 (nx*ny*nz
+   floats, host or device) or NULL for the linear ramp C_in -> C_out between
+   the half-way faces x = 0 and x = L.  Resets the step counter. */
+cl_status cl_lbm_init(cl_handle h, const float* C0, int ptr_is_device);
+
+/* Advance exactly nsteps time steps (Eq. 21 with the boundaries above). */
+cl_status cl_lbm_step(cl_handle h, long long nsteps);
+
+/* Advance until the stopping rule fires or p->max_steps more steps are
+   taken: every check_every steps the fused reduction gives J_in, J_out, R
+   and sum|dC|; converged when the flux balance is below tol_flux and the
+   geometric-series extrapolation of the tracked readout's remaining change
+   (D_eff for a Dirichlet outlet, R otherwise) is below tol_rel of it.
+   Returns CL_ERR_NOT_CONVERGED at the budget, CL_ERR_DIVERGED on NaN/Inf.
+   info may be NULL. */
+cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info);
+
+/* cl_lbm_solve with an explicit step budget instead of p->max_steps (whole
+   check intervals only; a budget below check_every runs no step).  Each call
+   restarts the stopping rule's history, so a budget of one interval always
+   returns CL_ERR_NOT_CONVERGED with that interval's readouts in info. */
+cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* info);
+
+/* Lattice-unit fluxes of the current state, FP64 sums:
+   out[0] J_in  net amount entering through x = 0 per step,
+   out[1] J_out net amount leaving through x = L per step,
+   out[2] R     amount consumed on reactive faces per step,
+   out[3] sum of C over active cells,
+   out[4] number of active cells.
+   Per step: sum C(t+1) - sum C(t) = J_in - J_out - R. */
+cl_status cl_lbm_fluxes(cl_handle h, double out[5]);
+
+/* Eq. 19 from the outlet flux: D_eff [m^2/s] and D_eff / D_b.  Needs
+   Dirichlet at both ends and c_in != c_out (else CL_ERR_STATE).
+   Either pointer may be NULL. */
+cl_status cl_lbm_effective_diffusivity(cl_handle h, double* d_eff_m2s, double* d_eff_over_db);
+
+/* Reaction rate: total = sum over reactive faces of k C_wall dx^2, in
+   (concentration unit) * m^3 / s (mol/s for C in mol/m^3).  profile_R
+   (nullable, nx doubles, host): the same per x-plane.  profile_C
+   (nullable, nx doubles, host): mean C over the active cells of each plane
+   (0 where none). */
+cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, double* profile_C);
+
+/* Current concentration C = sum_i g_i (nx*ny*nz floats, host or device; 0 on
+   inactive cells). */
+cl_status cl_lbm_get_field(cl_handle h, float* C, int ptr_is_device);
+
+/* Current post-collision populations as f32, layout [7][nz][ny][nx], host
+   or device (decoded from FP16 storage if used; 0 on inactive cells). */
+cl_status cl_lbm_get_populations(cl_handle h, float* g, int ptr_is_device);
+
+/* Set-up products: active (nx*ny*nz bytes, 0/1), omega (nx*ny*nz floats,
+   1/tau; 0 on inactive cells), chord (nx*ny*nz*13 int32: run length in cells
+   of pore cells in each of the 13 directions of Sec. 2.1.3, 0 for non-pore
+   cells), link mask (nx*ny*nz uint16: bits 0-5 face d closed, 6-11 face d
+   reactive, 12 active).  Any pointer may be NULL; all are host or device. */
+cl_status cl_lbm_get_setup(cl_handle h, uint8_t* active, float* omega, int32_t* chord,
+                           uint16_t* link_mask, int ptr_is_device);
+
+cl_status cl_lbm_get_info(cl_handle h, cl_structure_info* info);
+
+/* Step counter since the last init. */
+cl_status cl_lbm_get_step(cl_handle h, long long* step);
+
+const char* cl_status_str(cl_status s);
+
+/* Text of the last error raised on the calling thread ("" if none). */
+const char* cl_last_error_message(void);
+
+/* Library version string. */
+const char* cl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CL_LBM_H */

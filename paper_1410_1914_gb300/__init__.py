@@ -1,0 +1,20 @@
+"""GB300-native D3Q7 reactive-diffusion lattice Boltzmann for catalyst layers
+(after Chen et al., arXiv:1410.1914).
+
+The solver is the CUDA library behind include/cl_lbm.h; ``Solver`` and the
+``cl_*`` functions of ``_lib`` are its Python binding.  ``inputs`` generates
+seeded synthetic structures.  Submodules load lazily so that importing the
+package never needs a GPU.
+"""
+
+__all__ = ["Solver", "inputs", "build"]
+
+
+def __getattr__(name):
+    if name == "Solver":
+        from .solver import Solver
+        return Solver
+    if name in ("inputs", "build", "_lib", "solver"):
+        import importlib
+        return importlib.import_module(f".{name}", __name__)
+    raise AttributeError(name)

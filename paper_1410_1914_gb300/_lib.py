@@ -1,0 +1,315 @@
+"""Thin ctypes binding of the C ABI in include/cl_lbm.h.
+
+Argument marshalling only: every step of the solver runs in libcllbm.so.
+Functions keep the C names.  Array arguments may be numpy arrays (host) or
+torch tensors (host or CUDA); the device flag of the C call is derived from
+the tensor.  A failed call raises ClError with the library's message.  If
+the CUDA library is not built the import of any entry point raises: there
+is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libcllbm.so")
+HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "cl_lbm.h")
+
+CL_OK, CL_ERR_ARG, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_STATE = 0, 1, 2, 3, 4
+CL_ERR_DIVERGED, CL_ERR_NOT_CONVERGED, CL_ERR_NO_PATH, CL_ERR_TIMEOUT = 5, 6, 7, 8
+CL_BC_DIRICHLET, CL_BC_ZERO_FLUX = 0, 1
+CL_STORE_FP32, CL_STORE_FP16DEV = 0, 1
+CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID = 0, 1
+
+cl_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+cl_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class cl_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("dx_m", ctypes.c_double), ("T_K", ctypes.c_double), ("p_atm", ctypes.c_double),
+        ("M_kgmol", ctypes.c_double), ("D_bulk", ctypes.c_double), ("D_ionomer", ctypes.c_double),
+        ("k_ms", ctypes.c_double),
+        ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
+        ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
+        ("storage", ctypes.c_int), ("react_rule", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("tol_flux", ctypes.c_double), ("tol_rel", ctypes.c_double),
+        ("max_steps", ctypes.c_longlong),
+        ("cuda_stream", ctypes.c_void_p),
+        ("alloc", cl_alloc_fn), ("free", cl_free_fn), ("alloc_ctx", ctypes.c_void_p),
+    ]
+
+
+class cl_structure_info(ctypes.Structure):
+    _fields_ = [
+        ("n_cells", ctypes.c_longlong), ("n_transport", ctypes.c_longlong),
+        ("n_active", ctypes.c_longlong), ("n_wall_links", ctypes.c_longlong),
+        ("n_react_links", ctypes.c_longlong),
+        ("D_b", ctypes.c_double), ("D_max", ctypes.c_double), ("dt_s", ctypes.c_double),
+        ("k_lu", ctypes.c_double), ("mean_pore_diameter_m", ctypes.c_double),
+    ]
+
+
+class cl_solve_info(ctypes.Structure):
+    _fields_ = [
+        ("steps", ctypes.c_longlong), ("converged", ctypes.c_int),
+        ("J_in", ctypes.c_double), ("J_out", ctypes.c_double), ("R", ctypes.c_double),
+        ("flux_balance", ctypes.c_double), ("rel_change", ctypes.c_double),
+        ("resid", ctypes.c_double), ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_S = ctypes.c_int  # cl_status
+_H = ctypes.c_void_p  # cl_handle
+
+SIGNATURES = {
+    "cl_params_default": (None, [ctypes.POINTER(cl_params)]),
+    "cl_lbm_create": (_S, [ctypes.POINTER(_H), ctypes.POINTER(cl_params)]),
+    "cl_lbm_destroy": (None, [_H]),
+    "cl_lbm_set_structure": (_S, [_H, _P, _P, _I]),
+    "cl_lbm_set_diffusivity": (_S, [_H, _P, _I]),
+    "cl_lbm_init": (_S, [_H, _P, _I]),
+    "cl_lbm_step": (_S, [_H, ctypes.c_longlong]),
+    "cl_lbm_solve": (_S, [_H, ctypes.POINTER(cl_solve_info)]),
+    "cl_lbm_solve_budget": (_S, [_H, ctypes.c_longlong, ctypes.POINTER(cl_solve_info)]),
+    "cl_lbm_fluxes": (_S, [_H, _P]),
+    "cl_lbm_effective_diffusivity": (_S, [_H, _P, _P]),
+    "cl_lbm_reaction_rate": (_S, [_H, _P, _P, _P]),
+    "cl_lbm_get_field": (_S, [_H, _P, _I]),
+    "cl_lbm_get_populations": (_S, [_H, _P, _I]),
+    "cl_lbm_get_setup": (_S, [_H, _P, _P, _P, _P, _I]),
+    "cl_lbm_get_info": (_S, [_H, ctypes.POINTER(cl_structure_info)]),
+    "cl_lbm_get_step": (_S, [_H, ctypes.POINTER(ctypes.c_longlong)]),
+    "cl_status_str": (ctypes.c_char_p, [_I]),
+    "cl_last_error_message": (ctypes.c_char_p, []),
+    "cl_version": (ctypes.c_char_p, []),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class ClError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        self.status = status
+        super().__init__(f"{where}: {status_str(status)} ({msg})")
+
+
+def load() -> ctypes.CDLL:
+    """Load libcllbm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                                   "(run __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def status_str(s: int) -> str:
+    return load().cl_status_str(int(s)).decode()
+
+
+def last_error_message() -> str:
+    return load().cl_last_error_message().decode()
+
+
+def version() -> str:
+    return load().cl_version().decode()
+
+
+def _check(status: int, where: str):
+    if status != CL_OK:
+        raise ClError(status, where, last_error_message())
+
+
+def _arr(x, dtype, n=None, writable=False):
+    """(pointer, is_device, keepalive) for a numpy array or torch tensor."""
+    if x is None:
+        return None, 0, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            tdt = {np.uint8: torch.uint8, np.float32: torch.float32, np.float64: torch.float64,
+                   np.int32: torch.int32, np.uint16: None}[dtype]
+            if tdt is not None and x.dtype != tdt:
+                raise TypeError(f"tensor dtype {x.dtype}, expected {tdt}")
+            if not x.is_contiguous():
+                raise ValueError("tensor must be contiguous")
+            if n is not None and x.numel() < n:
+                raise ValueError(f"tensor has {x.numel()} elements, need {n}")
+            return ctypes.c_void_p(x.data_ptr()), int(x.is_cuda), x
+    except ImportError:
+        pass
+    if not isinstance(x, np.ndarray):
+        raise TypeError("expected a numpy array or torch tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"array dtype {x.dtype}, expected {np.dtype(dtype)}")
+    if not x.flags.c_contiguous:
+        raise ValueError("array must be C-contiguous")
+    if writable and not x.flags.writeable:
+        raise ValueError("array must be writable")
+    if n is not None and x.size < n:
+        raise ValueError(f"array has {x.size} elements, need {n}")
+    return x.ctypes.data_as(ctypes.c_void_p), 0, x
+
+
+def cl_params_default(**overrides) -> cl_params:
+    p = cl_params()
+    load().cl_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def current_torch_stream() -> int:
+    """cudaStream_t of torch's current stream, or 0."""
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return 0
+
+
+class TorchAllocator:
+    """Routes the library's device allocations through torch's caching allocator."""
+
+    def __init__(self, device: int = 0):
+        import torch
+        self._torch = torch
+        self.device = device
+
+        def _alloc(nbytes, stream, ctx):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, int(stream or 0)))
+            except Exception:  # the C side reports CL_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, stream, ctx):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = cl_alloc_fn(_alloc)
+        self.free = cl_free_fn(_free)
+
+
+# ------------------------------------------------------------ ABI mirrors
+def cl_lbm_create(params: cl_params) -> int:
+    h = ctypes.c_void_p()
+    _check(load().cl_lbm_create(ctypes.byref(h), ctypes.byref(params)), "cl_lbm_create")
+    return h.value
+
+
+def cl_lbm_destroy(h: int) -> None:
+    load().cl_lbm_destroy(h)
+
+
+def cl_lbm_set_structure(h: int, phase, reactive_faces=None, n: int | None = None) -> None:
+    pp, dev, _k1 = _arr(phase, np.uint8, n)
+    rp, rdev, _k2 = _arr(reactive_faces, np.uint8, n)
+    if reactive_faces is not None and rdev != dev:
+        raise ValueError("phase and reactive_faces must both be host or both be device")
+    _check(load().cl_lbm_set_structure(h, pp, rp, dev), "cl_lbm_set_structure")
+
+
+def cl_lbm_set_diffusivity(h: int, D, n: int | None = None) -> None:
+    p, dev, _k = _arr(D, np.float64, n)
+    _check(load().cl_lbm_set_diffusivity(h, p, dev), "cl_lbm_set_diffusivity")
+
+
+def cl_lbm_init(h: int, C0=None, n: int | None = None) -> None:
+    p, dev, _k = _arr(C0, np.float32, n)
+    _check(load().cl_lbm_init(h, p, dev), "cl_lbm_init")
+
+
+def cl_lbm_step(h: int, nsteps: int) -> None:
+    _check(load().cl_lbm_step(h, int(nsteps)), "cl_lbm_step")
+
+
+def cl_lbm_solve(h: int, raise_on_not_converged: bool = False) -> tuple[int, cl_solve_info]:
+    info = cl_solve_info()
+    s = load().cl_lbm_solve(h, ctypes.byref(info))
+    if s not in (CL_OK, CL_ERR_NOT_CONVERGED) or (raise_on_not_converged and s != CL_OK):
+        _check(s, "cl_lbm_solve")
+    return s, info
+
+
+def cl_lbm_solve_budget(h: int, max_steps: int) -> tuple[int, cl_solve_info]:
+    info = cl_solve_info()
+    s = load().cl_lbm_solve_budget(h, int(max_steps), ctypes.byref(info))
+    if s not in (CL_OK, CL_ERR_NOT_CONVERGED):
+        _check(s, "cl_lbm_solve_budget")
+    return s, info
+
+
+def cl_lbm_fluxes(h: int) -> np.ndarray:
+    out = np.zeros(5)
+    _check(load().cl_lbm_fluxes(h, out.ctypes.data_as(ctypes.c_void_p)), "cl_lbm_fluxes")
+    return out
+
+
+def cl_lbm_effective_diffusivity(h: int) -> tuple[float, float]:
+    d = ctypes.c_double()
+    r = ctypes.c_double()
+    _check(load().cl_lbm_effective_diffusivity(h, ctypes.byref(d), ctypes.byref(r)),
+           "cl_lbm_effective_diffusivity")
+    return d.value, r.value
+
+
+def cl_lbm_reaction_rate(h: int, nx: int) -> tuple[float, np.ndarray, np.ndarray]:
+    tot = ctypes.c_double()
+    pr = np.zeros(nx)
+    pc = np.zeros(nx)
+    _check(load().cl_lbm_reaction_rate(h, ctypes.byref(tot), pr.ctypes.data_as(ctypes.c_void_p),
+                                       pc.ctypes.data_as(ctypes.c_void_p)), "cl_lbm_reaction_rate")
+    return tot.value, pr, pc
+
+
+def cl_lbm_get_field(h: int, out) -> None:
+    p, dev, _k = _arr(out, np.float32, writable=True)
+    _check(load().cl_lbm_get_field(h, p, dev), "cl_lbm_get_field")
+
+
+def cl_lbm_get_populations(h: int, out) -> None:
+    p, dev, _k = _arr(out, np.float32, writable=True)
+    _check(load().cl_lbm_get_populations(h, p, dev), "cl_lbm_get_populations")
+
+
+def cl_lbm_get_setup(h: int, active=None, omega=None, chord=None, link_mask=None) -> None:
+    a, d1, _k1 = _arr(active, np.uint8, writable=True)
+    o, d2, _k2 = _arr(omega, np.float32, writable=True)
+    c, d3, _k3 = _arr(chord, np.int32, writable=True)
+    m, d4, _k4 = _arr(link_mask, np.uint16, writable=True)
+    devs = {d for d, x in ((d1, active), (d2, omega), (d3, chord), (d4, link_mask)) if x is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must all be host or all be device")
+    _check(load().cl_lbm_get_setup(h, a, o, c, m, devs.pop() if devs else 0), "cl_lbm_get_setup")
+
+
+def cl_lbm_get_info(h: int) -> cl_structure_info:
+    info = cl_structure_info()
+    _check(load().cl_lbm_get_info(h, ctypes.byref(info)), "cl_lbm_get_info")
+    return info
+
+
+def cl_lbm_get_step(h: int) -> int:
+    s = ctypes.c_longlong()
+    _check(load().cl_lbm_get_step(h, ctypes.byref(s)), "cl_lbm_get_step")
+    return s.value

@@ -1,0 +1,588 @@
+// Host implementation of the C ABI declared in include/cl_lbm.h.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <chrono>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace cl;
+
+namespace {
+
+thread_local char g_msg[512] = "";
+
+void set_msg(const char* where, cudaError_t e) {
+    snprintf(g_msg, sizeof(g_msg), "%s: %s", where, cudaGetErrorString(e));
+}
+void set_msg_txt(const char* txt) { snprintf(g_msg, sizeof(g_msg), "%s", txt); }
+
+cl_status from_cuda(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA;
+}
+
+#define CK(call)                                  \
+    do {                                          \
+        cudaError_t e_ = (call);                  \
+        if (e_ != cudaSuccess) {                  \
+            set_msg(#call, e_);                   \
+            return from_cuda(e_);                 \
+        }                                         \
+    } while (0)
+
+#define CKS(stmt)                                 \
+    do {                                          \
+        cl_status s_ = (stmt);                    \
+        if (s_ != CL_OK) return s_;               \
+    } while (0)
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int parity = -1;
+    long long K = 0;
+    bool reduce = false;
+};
+
+}  // namespace
+
+struct cl_lbm {
+    cl_params p;
+    int nx, ny, nz;
+    long long N;
+    cudaStream_t s = nullptr;    // stream every call is ordered on
+    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    std::vector<std::pair<void*, size_t>> allocs;
+
+    uint8_t *phase = nullptr, *react = nullptr, *active = nullptr, *touch = nullptr;
+    int* labels = nullptr;
+    int* d_err = nullptr;
+    double *D = nullptr, *dp = nullptr;
+    float* omega = nullptr;
+    uint16_t* mask = nullptr;
+    float* pop[2] = {nullptr, nullptr};
+    int cur = 0;
+    float* Csnap = nullptr;
+    float* fbuf = nullptr;
+    double* partials = nullptr;
+    int nblk_step = 0, nblk_stats = 0;
+    double* d_red = nullptr;    // [16]
+    double* d_plane = nullptr;  // [5 * nx]
+    double* h_red = nullptr;    // pinned [16 + 5 * nx]
+    bool have_react = false;
+    bool have_structure = false;
+    long long step = 0;
+    double D_b = 0, D_max = 0, dt = 0, k_lu = 0;
+    cl_structure_info info;
+    Graph graphs[4];
+};
+
+namespace {
+
+cl_status dalloc(cl_lbm* h, void** out, size_t bytes) {
+    void* ptr = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (h->p.alloc) {
+        ptr = h->p.alloc(bytes, (void*)h->s, h->p.alloc_ctx);
+        if (!ptr) { set_msg_txt("allocator callback returned NULL"); return CL_ERR_OOM; }
+    } else {
+        cudaError_t e = cudaMallocAsync(&ptr, bytes, h->s);
+        if (e != cudaSuccess) { set_msg("cudaMallocAsync", e); return from_cuda(e); }
+    }
+    h->allocs.emplace_back(ptr, bytes);
+    *out = ptr;
+    return CL_OK;
+}
+
+template <class T>
+cl_status dalloc_n(cl_lbm* h, T** out, long long n) {
+    return dalloc(h, (void**)out, sizeof(T) * (size_t)n);
+}
+
+cudaMemcpyKind kind_in(int ptr_is_device) { return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int ptr_is_device) { return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+StepArgs make_args(cl_lbm* h) {
+    StepArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.N = h->N;
+    a.mask = h->mask;
+    a.omega = h->omega;
+    const double w = 0.125;
+    a.rfac = (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
+    a.abb_in = (float)(2.0 * w * h->p.c_in);
+    a.abb_out = (float)(2.0 * w * h->p.c_out);
+    a.w_cin = (float)(w * h->p.c_in);
+    a.w_cout = (float)(w * h->p.c_out);
+    a.bc_in = h->p.bc_in;
+    a.bc_out = h->p.bc_out;
+    a.Csnap = h->Csnap;
+    a.partials = h->partials;
+    return a;
+}
+
+void drop_graphs(cl_lbm* h) {
+    for (auto& g : h->graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g = Graph();
+    }
+}
+
+// Enqueue `n` steps (the last one with the fused reduction if `reduce`) on stream s.
+cl_status enqueue_steps(cl_lbm* h, long long n, bool reduce, cudaStream_t s, int* parity) {
+    StepArgs a = make_args(h);
+    for (long long i = 0; i < n; ++i) {
+        const bool red = reduce && i == n - 1;
+        CK(launch_step_fp32(h->pop[*parity], h->pop[*parity ^ 1], a, red, s));
+        *parity ^= 1;
+    }
+    if (reduce) CK(launch_finalize(h->partials, h->nblk_step, RED_N, h->d_red, s));
+    return CL_OK;
+}
+
+// A graph of K steps (K even, so the buffer parity returns) starting at the
+// current parity; cached.
+cl_status get_graph(cl_lbm* h, long long K, bool reduce, cudaGraphExec_t* out) {
+    for (auto& g : h->graphs)
+        if (g.exec && g.parity == h->cur && g.K == K && g.reduce == reduce) { *out = g.exec; return CL_OK; }
+    Graph* slot = nullptr;
+    for (auto& g : h->graphs) if (!g.exec) { slot = &g; break; }
+    if (!slot) { drop_graphs(h); slot = &h->graphs[0]; }
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int par = h->cur;
+    cl_status st = enqueue_steps(h, K, reduce, h->cap, &par);
+    if (st == CL_OK && reduce) {
+        cudaError_t e = cudaMemcpyAsync(h->h_red, h->d_red, sizeof(double) * RED_N, cudaMemcpyDeviceToHost, h->cap);
+        if (e != cudaSuccess) { set_msg("capture memcpy", e); st = from_cuda(e); }
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(h->cap, &graph);
+    if (st != CL_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (e != cudaSuccess) { set_msg("cudaStreamEndCapture", e); return from_cuda(e); }
+    e = cudaGraphInstantiate(&slot->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) { set_msg("cudaGraphInstantiate", e); slot->exec = nullptr; return from_cuda(e); }
+    slot->parity = h->cur;
+    slot->K = K;
+    slot->reduce = reduce;
+    *out = slot->exec;
+    return CL_OK;
+}
+
+cl_status need_structure(cl_lbm* h) {
+    if (!h) { set_msg_txt("NULL handle"); return CL_ERR_ARG; }
+    if (!h->have_structure) { set_msg_txt("no structure loaded"); return CL_ERR_STATE; }
+    return CL_OK;
+}
+
+cl_status check_err_flag(cl_lbm* h) {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (herr & 1) { set_msg_txt("phase code outside 0..3"); return CL_ERR_ARG; }
+    if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
+    if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
+    return CL_OK;
+}
+
+// stats + dt + omega + init, shared by set_structure and set_diffusivity
+cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
+    double* stat_out = h->d_red + 8;  // 7 slots
+    CK(launch_stats(h->phase, h->mask, h->D, with_dp ? h->dp : nullptr, h->N, h->nx, h->p.D_ionomer > 0,
+                    h->partials, h->nblk_stats, stat_out, h->s));
+    double st[7];
+    CK(cudaMemcpyAsync(st, stat_out, sizeof(st), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->info.n_cells = h->N;
+    h->info.n_transport = (long long)st[0];
+    h->info.n_active = (long long)st[1];
+    h->info.n_wall_links = (long long)st[2];
+    h->info.n_react_links = (long long)st[3];
+    if (with_dp) h->info.mean_pore_diameter_m = st[5] > 0 ? st[4] / st[5] : 0.0;
+    if (h->info.n_active == 0) { set_msg_txt("no transport cell is connected to the inlet plane"); return CL_ERR_NO_PATH; }
+    h->D_max = st[6];
+    if (!(h->D_max > 0) || !isfinite(h->D_max)) { set_msg_txt("largest diffusivity is not positive"); return CL_ERR_ARG; }
+    // Eq. 24 on D3Q7 (cs^2 = 1/4): D = (tau - 1/2) dx^2 / (4 dt); tau_ref at D_max.
+    h->dt = (h->p.tau_ref - 0.5) * 0.25 * h->p.dx_m * h->p.dx_m / h->D_max;
+    h->k_lu = h->p.k_ms * h->dt / h->p.dx_m;
+    h->info.D_b = h->D_b;
+    h->info.D_max = h->D_max;
+    h->info.dt_s = h->dt;
+    h->info.k_lu = h->k_lu;
+    CK(launch_omega(h->active, h->D, h->N, h->p.tau_ref, stat_out + 6, h->omega, h->s));
+    drop_graphs(h);  // the reactive factor is baked into captured kernel arguments
+    return CL_OK;
+}
+
+cl_status do_init(cl_lbm* h, const float* C0dev) {
+    h->cur = 0;
+    CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)h->N, h->s));
+    CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap, h->s));
+    h->step = 0;
+    return CL_OK;
+}
+
+cl_status plane_readout(cl_lbm* h, double* tot /* [5] */) {
+    StepArgs a = make_args(h);
+    CK(launch_readout_fp32(h->pop[h->cur], a, h->d_plane, h->s));
+    double* hp = h->h_red + 16;
+    CK(cudaMemcpyAsync(hp, h->d_plane, sizeof(double) * 5 * h->nx, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    for (int k = 0; k < 5; ++k) tot[k] = 0.0;
+    for (int x = 0; x < h->nx; ++x)
+        for (int k = 0; k < 5; ++k) tot[k] += hp[5 * x + k];
+    return CL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cl_params_default(cl_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dx_m = 1e-9;
+    p->T_K = 353.0;
+    p->p_atm = 1.0;
+    p->M_kgmol = 0.032;
+    p->bc_in = CL_BC_DIRICHLET;
+    p->bc_out = CL_BC_DIRICHLET;
+    p->c_in = 1.0;
+    p->c_out = 0.0;
+    p->tau_ref = 1.0;
+    p->storage = CL_STORE_FP32;
+    p->react_rule = CL_REACT_GIVEN;
+    p->check_every = 1000;
+    p->tol_flux = 1e-4;
+    p->tol_rel = 1e-4;
+    p->max_steps = 10000000;
+}
+
+const char* cl_status_str(cl_status s) {
+    switch (s) {
+        case CL_OK: return "CL_OK";
+        case CL_ERR_ARG: return "CL_ERR_ARG";
+        case CL_ERR_OOM: return "CL_ERR_OOM";
+        case CL_ERR_CUDA: return "CL_ERR_CUDA";
+        case CL_ERR_STATE: return "CL_ERR_STATE";
+        case CL_ERR_DIVERGED: return "CL_ERR_DIVERGED";
+        case CL_ERR_NOT_CONVERGED: return "CL_ERR_NOT_CONVERGED";
+        case CL_ERR_NO_PATH: return "CL_ERR_NO_PATH";
+        case CL_ERR_TIMEOUT: return "CL_ERR_TIMEOUT";
+    }
+    return "CL_ERR_UNKNOWN";
+}
+
+const char* cl_last_error_message(void) { return g_msg; }
+
+const char* cl_version(void) { return "cl_lbm 0.1 (D3Q7, sm_103a)"; }
+
+cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
+    if (!out || !p) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    const long long N = (long long)p->nx * p->ny * p->nz;
+    if (p->nx < 1 || p->ny < 1 || p->nz < 1 || N >= (1LL << 31)) { set_msg_txt("box size out of range"); return CL_ERR_ARG; }
+    if (p->ny > 65535 || p->nz > 65535) { set_msg_txt("ny and nz must be <= 65535"); return CL_ERR_ARG; }
+    if (!(p->dx_m > 0) || !(p->tau_ref > 0.5) || !(p->T_K > 0) || !(p->M_kgmol > 0)) { set_msg_txt("dx_m, T_K, M_kgmol must be > 0 and tau_ref > 0.5"); return CL_ERR_ARG; }
+    if (p->D_bulk <= 0 && !(p->p_atm > 0)) { set_msg_txt("p_atm must be > 0 when D_bulk comes from Eq. 7"); return CL_ERR_ARG; }
+    if (p->D_ionomer < 0 || p->k_ms < 0) { set_msg_txt("D_ionomer and k_ms must be >= 0"); return CL_ERR_ARG; }
+    if ((p->bc_in != 0 && p->bc_in != 1) || (p->bc_out != 0 && p->bc_out != 1)) { set_msg_txt("bad boundary type"); return CL_ERR_ARG; }
+    if (p->storage != CL_STORE_FP32) { set_msg_txt("storage mode not available"); return CL_ERR_ARG; }
+    if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
+    if (p->check_every < 2 || (p->check_every & 1)) { set_msg_txt("check_every must be even and >= 2"); return CL_ERR_ARG; }
+    if ((p->alloc == nullptr) != (p->free == nullptr)) { set_msg_txt("alloc and free must both be set or both NULL"); return CL_ERR_ARG; }
+
+    cl_lbm* h = new cl_lbm();
+    h->p = *p;
+    h->nx = p->nx; h->ny = p->ny; h->nz = p->nz; h->N = N;
+    h->s = (cudaStream_t)p->cuda_stream;
+    memset(&h->info, 0, sizeof(h->info));
+    cl_status st = CL_OK;
+    auto fail = [&](cl_status s) { cl_lbm_destroy(h); return s; };
+    cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
+
+    StepArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+    h->nblk_step = step_fp32_blocks(a);
+    h->nblk_stats = 152 * 4;
+    const long long npart = (long long)h->nblk_step * RED_N > (long long)h->nblk_stats * 8
+                                ? (long long)h->nblk_step * RED_N : (long long)h->nblk_stats * 8;
+    if ((st = dalloc_n(h, &h->phase, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->react, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->active, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->touch, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->labels, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->d_err, 4)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->D, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->dp, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->omega, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->mask, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->pop[0], 7 * N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->pop[1], 7 * N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->Csnap, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->fbuf, N)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->partials, npart)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->d_red, 16)) != CL_OK) return fail(st);
+    if ((st = dalloc_n(h, &h->d_plane, 5LL * h->nx)) != CL_OK) return fail(st);
+    e = cudaMallocHost(&h->h_red, sizeof(double) * (16 + 5 * (size_t)h->nx));
+    if (e != cudaSuccess) { set_msg("cudaMallocHost", e); return fail(from_cuda(e)); }
+    e = cudaMemsetAsync(h->pop[0], 0, sizeof(float) * 7 * (size_t)N, h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)N, h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->mask, 0, sizeof(uint16_t) * (size_t)N, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    if (e != cudaSuccess) { set_msg("initial memset", e); return fail(from_cuda(e)); }
+    *out = h;
+    return CL_OK;
+}
+
+void cl_lbm_destroy(cl_handle h) {
+    if (!h) return;
+    drop_graphs(h);
+    if (h->s || true) cudaStreamSynchronize(h->s);
+    for (auto& pr : h->allocs) {
+        if (h->p.free) h->p.free(pr.first, pr.second, (void*)h->s, h->p.alloc_ctx);
+        else cudaFreeAsync(pr.first, h->s);
+    }
+    cudaStreamSynchronize(h->s);
+    if (h->h_red) cudaFreeHost(h->h_red);
+    if (h->cap) cudaStreamDestroy(h->cap);
+    delete h;
+}
+
+cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t* reactive_faces, int ptr_is_device) {
+    if (!h || !phase) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    const size_t N = (size_t)h->N;
+    CK(cudaMemcpyAsync(h->phase, phase, N, kind_in(ptr_is_device), h->s));
+    h->have_react = reactive_faces != nullptr;
+    if (reactive_faces) CK(cudaMemcpyAsync(h->react, reactive_faces, N, kind_in(ptr_is_device), h->s));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(launch_validate(h->phase, h->N, h->d_err, h->s));
+    CKS(check_err_flag(h));
+    h->have_structure = false;
+    const int ion = h->p.D_ionomer > 0;
+    CK(launch_percolation(h->phase, h->nx, h->ny, h->nz, ion, h->labels, h->touch, h->active, h->d_err, h->s));
+    CKS(check_err_flag(h));
+    // Eq. 7 unless the bulk value is given
+    h->D_b = h->p.D_bulk > 0 ? h->p.D_bulk : 0.22e-4 * pow(h->p.T_K / 293.2, 1.5) / h->p.p_atm;
+    CK(launch_diffusivity(h->phase, h->active, h->nx, h->ny, h->nz, h->p.dx_m, h->p.T_K, h->p.M_kgmol, h->D_b,
+                          h->p.D_ionomer, h->p.knudsen, nullptr, h->D, h->dp, nullptr, h->s));
+    CK(launch_masks(h->phase, h->active, h->have_react ? h->react : nullptr, h->p.react_rule, h->nx, h->ny,
+                    h->nz, h->mask, h->s));
+    CKS(derive_relaxation(h, true));
+    CKS(do_init(h, nullptr));
+    CK(cudaStreamSynchronize(h->s));
+    h->have_structure = true;
+    return CL_OK;
+}
+
+cl_status cl_lbm_set_diffusivity(cl_handle h, const double* D, int ptr_is_device) {
+    CKS(need_structure(h));
+    if (!D) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    CK(cudaMemcpyAsync(h->dp, D, sizeof(double) * (size_t)h->N, kind_in(ptr_is_device), h->s));
+    CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+    CK(launch_diffusivity(h->phase, h->active, h->nx, h->ny, h->nz, h->p.dx_m, h->p.T_K, h->p.M_kgmol, h->D_b,
+                          h->p.D_ionomer, h->p.knudsen, h->dp, h->D, nullptr, nullptr, h->s));
+    CK(launch_check_positive(h->active, h->D, h->N, h->d_err, h->s));
+    CKS(check_err_flag(h));
+    CKS(derive_relaxation(h, false));
+    CKS(do_init(h, nullptr));
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_init(cl_handle h, const float* C0, int ptr_is_device) {
+    CKS(need_structure(h));
+    const float* src = nullptr;
+    if (C0) {
+        if (ptr_is_device) src = C0;
+        else {
+            CK(cudaMemcpyAsync(h->fbuf, C0, sizeof(float) * (size_t)h->N, cudaMemcpyHostToDevice, h->s));
+            src = h->fbuf;
+        }
+    }
+    CKS(do_init(h, src));
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_step(cl_handle h, long long nsteps) {
+    CKS(need_structure(h));
+    if (nsteps < 0) { set_msg_txt("nsteps < 0"); return CL_ERR_ARG; }
+    const long long G = 64;  // steps per captured graph (even)
+    long long left = nsteps;
+    if (left >= G) {
+        cudaGraphExec_t g;
+        CKS(get_graph(h, G, false, &g));
+        while (left >= G) {
+            CK(cudaGraphLaunch(g, h->s));
+            left -= G;
+        }
+    }
+    int par = h->cur;
+    CKS(enqueue_steps(h, left, false, h->s, &par));
+    h->cur = par;
+    h->step += nsteps;
+    CK(cudaGetLastError());
+    return CL_OK;
+}
+
+cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info) {
+    if (!h) { set_msg_txt("NULL handle"); return CL_ERR_ARG; }
+    return cl_lbm_solve_budget(h, h->p.max_steps, info);
+}
+
+cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* info) {
+    CKS(need_structure(h));
+    if (max_steps < 0) { set_msg_txt("max_steps < 0"); return CL_ERR_ARG; }
+    auto t0 = std::chrono::steady_clock::now();
+    const long long K = h->p.check_every;
+    cudaGraphExec_t g;
+    CKS(get_graph(h, K, true, &g));
+    const bool track_deff = h->p.bc_in == CL_BC_DIRICHLET && h->p.bc_out == CL_BC_DIRICHLET && h->p.c_in != h->p.c_out;
+    double q_prev = NAN, dq_prev = NAN;
+    int nchecks = 0;
+    cl_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    inf.rel_change = INFINITY;
+    cl_status result = CL_ERR_NOT_CONVERGED;
+    while (inf.steps + K <= max_steps) {
+        CK(cudaGraphLaunch(g, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        inf.steps += K;
+        h->step += K;
+        const double* r = h->h_red;
+        inf.J_in = r[RED_JIN];
+        inf.J_out = r[RED_JOUT];
+        inf.R = r[RED_R];
+        inf.resid = r[RED_ABSC] > 0 ? r[RED_DC] / r[RED_ABSC] : 0.0;
+        if (r[RED_NONFINITE] > 0 || !isfinite(inf.J_in) || !isfinite(inf.J_out) || !isfinite(inf.R)) {
+            result = CL_ERR_DIVERGED;
+            set_msg_txt("non-finite concentration");
+            break;
+        }
+        inf.flux_balance = fabs(inf.J_in - inf.J_out - inf.R) / fmax(fabs(inf.J_in), 1e-300);
+        const double q = track_deff ? inf.J_out : inf.R;
+        const double dq = q - q_prev;
+        double est = INFINITY;
+        if (nchecks >= 2) {
+            const double rho = dq / dq_prev;
+            if (rho >= 1.0) est = INFINITY;
+            else if (rho > 0.0) est = fabs(dq) * rho / (1.0 - rho);
+            else est = fabs(dq);
+        }
+        inf.rel_change = q != 0 ? est / fabs(q) : INFINITY;
+        q_prev = q;
+        dq_prev = dq;
+        ++nchecks;
+        if (nchecks >= 3 && inf.flux_balance < h->p.tol_flux && inf.rel_change < h->p.tol_rel) {
+            result = CL_OK;
+            inf.converged = 1;
+            break;
+        }
+    }
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return result;
+}
+
+cl_status cl_lbm_fluxes(cl_handle h, double out[5]) {
+    CKS(need_structure(h));
+    if (!out) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    double t[5];
+    CKS(plane_readout(h, t));
+    out[0] = t[3];
+    out[1] = t[4];
+    out[2] = t[2];
+    out[3] = t[0];
+    out[4] = t[1];
+    return CL_OK;
+}
+
+cl_status cl_lbm_effective_diffusivity(cl_handle h, double* d_eff_m2s, double* d_eff_over_db) {
+    CKS(need_structure(h));
+    if (h->p.bc_in != CL_BC_DIRICHLET || h->p.bc_out != CL_BC_DIRICHLET || h->p.c_in == h->p.c_out) {
+        set_msg_txt("D_eff needs fixed, different concentrations at both x faces");
+        return CL_ERR_STATE;
+    }
+    double t[5];
+    CKS(plane_readout(h, t));
+    // Eq. 19: mean outlet flux density over (C_in - C_out) / L_x, lattice units
+    const double jd = t[4] / ((double)h->ny * h->nz);
+    const double dlu = jd * h->nx / (h->p.c_in - h->p.c_out);
+    const double d = dlu * h->p.dx_m * h->p.dx_m / h->dt;
+    if (d_eff_m2s) *d_eff_m2s = d;
+    if (d_eff_over_db) *d_eff_over_db = d / h->D_b;
+    return CL_OK;
+}
+
+cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, double* profile_C) {
+    CKS(need_structure(h));
+    double t[5];
+    CKS(plane_readout(h, t));
+    const double scale = h->p.dx_m * h->p.dx_m * h->p.dx_m / h->dt;
+    const double* hp = h->h_red + 16;
+    if (total) *total = t[2] * scale;
+    for (int x = 0; x < h->nx; ++x) {
+        if (profile_R) profile_R[x] = hp[5 * x + 2] * scale;
+        if (profile_C) profile_C[x] = hp[5 * x + 1] > 0 ? hp[5 * x] / hp[5 * x + 1] : 0.0;
+    }
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_field(cl_handle h, float* C, int ptr_is_device) {
+    CKS(need_structure(h));
+    if (!C) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    float* dstp = ptr_is_device ? C : h->fbuf;
+    CK(launch_field_fp32(h->pop[h->cur], h->mask, h->N, dstp, h->s));
+    if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * (size_t)h->N, cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_populations(cl_handle h, float* g, int ptr_is_device) {
+    CKS(need_structure(h));
+    if (!g) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    CK(cudaMemcpyAsync(g, h->pop[h->cur], sizeof(float) * 7 * (size_t)h->N, kind_out(ptr_is_device), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_setup(cl_handle h, uint8_t* active, float* omega, int32_t* chord, uint16_t* link_mask,
+                           int ptr_is_device) {
+    CKS(need_structure(h));
+    const size_t N = (size_t)h->N;
+    if (active) CK(cudaMemcpyAsync(active, h->active, N, kind_out(ptr_is_device), h->s));
+    if (omega) CK(cudaMemcpyAsync(omega, h->omega, N * sizeof(float), kind_out(ptr_is_device), h->s));
+    if (link_mask) CK(cudaMemcpyAsync(link_mask, h->mask, N * sizeof(uint16_t), kind_out(ptr_is_device), h->s));
+    if (chord) {
+        int32_t* dchord = chord;
+        void* tmp = nullptr;
+        if (!ptr_is_device) {
+            CK(cudaMallocAsync(&tmp, N * 13 * sizeof(int32_t), h->s));
+            dchord = (int32_t*)tmp;
+        }
+        cudaError_t e = launch_chords13(h->phase, h->nx, h->ny, h->nz, dchord, h->s);
+        if (e == cudaSuccess && !ptr_is_device)
+            e = cudaMemcpyAsync(chord, dchord, N * 13 * sizeof(int32_t), cudaMemcpyDeviceToHost, h->s);
+        if (tmp) cudaFreeAsync(tmp, h->s);
+        if (e != cudaSuccess) { set_msg("chords", e); return from_cuda(e); }
+    }
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_info(cl_handle h, cl_structure_info* info) {
+    CKS(need_structure(h));
+    if (!info) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    *info = h->info;
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_step(cl_handle h, long long* step) {
+    CKS(need_structure(h));
+    if (!step) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    *step = h->step;
+    return CL_OK;
+}
+
+}  // extern "C"

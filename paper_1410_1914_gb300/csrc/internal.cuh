@@ -1,0 +1,74 @@
+// Internal declarations of the CUDA library (not part of the public ABI).
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "cl_lbm.h"
+
+namespace cl {
+
+// D3Q7: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z.  w0 = 1/4, w1..6 = 1/8.
+constexpr float kW0 = 0.25f;
+constexpr float kW1 = 0.125f;
+
+// Link-mask bits per active cell.
+constexpr uint16_t kClosedShift = 0;   // bit d-1: face toward x + c_d closed
+constexpr uint16_t kReactShift = 6;    // bit 6 + d-1: that face is a catalytic sink
+constexpr uint16_t kActiveBit = 1u << 12;
+
+// Reduction slots of the fused check (FP64 per block, then a fixed-order sum).
+enum RedSlot { RED_JIN = 0, RED_JOUT, RED_R, RED_SUMC, RED_DC, RED_ABSC, RED_NONFINITE, RED_N };
+
+struct StepArgs {
+    int nx, ny, nz;
+    long long N;
+    const uint16_t* __restrict__ mask;
+    const float* __restrict__ omega;
+    float rfac;          // (2w - k_lu) / (2w + k_lu), w = 1/8 on every axis link
+    float abb_in;        // 2 w C_in
+    float abb_out;       // 2 w C_out
+    float w_cin, w_cout; // w C_in, w C_out (reduction)
+    int bc_in, bc_out;   // cl_bc
+    float* Csnap;        // C at the previous check (reduction)
+    double* partials;    // [blocks][RED_N] (reduction)
+};
+
+// ---- setup (kernels.cu) ----
+cudaError_t launch_validate(const uint8_t* phase, long long N, int* d_err, cudaStream_t s);
+cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
+                               int* labels, uint8_t* touch, uint8_t* active, int* d_err,
+                               cudaStream_t s);
+cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int nx, int ny, int nz,
+                               double dx, double T, double M, double D_b, double D_ionomer,
+                               int knudsen, const double* D_override, double* D, double* dp,
+                               int32_t* chord13, cudaStream_t s);
+cudaError_t launch_chords13(const uint8_t* phase, int nx, int ny, int nz, int32_t* chord13,
+                            cudaStream_t s);
+cudaError_t launch_check_positive(const uint8_t* active, const double* D, long long N, int* d_err,
+                                  cudaStream_t s);
+cudaError_t launch_omega(const uint8_t* active, const double* D, long long N, double tau_ref,
+                         const double* d_Dmax, float* omega, cudaStream_t s);
+cudaError_t launch_masks(const uint8_t* phase, const uint8_t* active, const uint8_t* react_in,
+                         int react_rule, int nx, int ny, int nz, uint16_t* mask, cudaStream_t s);
+// stats: out[0] n_transport, [1] n_active, [2] wall links, [3] react links,
+//        [4] sum d_p over pore cells, [5] pore cells, [6] D_max (max)
+cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const double* D,
+                         const double* dp, long long N, int nx, int ionomer_transport,
+                         double* partials, int nblocks, double* out, cudaStream_t s);
+
+// ---- FP32 solver (kernels.cu) ----
+cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, int nx, int ny,
+                             int nz, double c_in, double c_out, float* Csnap, cudaStream_t s);
+cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce,
+                             cudaStream_t s);
+int step_fp32_blocks(const StepArgs& a);
+cudaError_t launch_finalize(const double* partials, int nblocks, int nslots, double* out,
+                            cudaStream_t s);
+cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C,
+                              cudaStream_t s);
+// per-plane readout: out[5*nx]: sumC, count, R, J_in part, J_out part
+cudaError_t launch_readout_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s);
+
+}  // namespace cl

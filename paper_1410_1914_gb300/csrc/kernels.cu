@@ -1,0 +1,597 @@
+// Set-up kernels and the FP32 fused collide-stream kernel of the D3Q7
+// reactive-diffusion LBM (arXiv:1410.1914, Sec. 2.1.3, Eq. 7-9, 19, 21-24).
+#include <math.h>
+
+#include "internal.cuh"
+
+namespace cl {
+
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ bool is_pore(uint8_t p) { return p == 0 || p == 3; }
+__device__ __forceinline__ bool is_transport(uint8_t p, int ion) {
+    return p == 0 || p == 3 || (p == 2 && ion);
+}
+__device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+template <int NV>
+__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+}
+
+// Block-wide sum of NV doubles in a fixed order; thread 0 writes out[0..NV).
+// Requires blockDim a multiple of 32, at most 1024 threads.
+template <int NV>
+__device__ void block_sum_store(double (&v)[NV], double* out) {
+    __shared__ double sh[32][NV];
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
+    const int lane = tid & 31, warp = tid >> 5, nwarps = (nthreads + 31) >> 5;
+    warp_sum<NV>(v);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) v[k] = lane < nwarps ? sh[lane][k] : 0.0;
+        warp_sum<NV>(v);
+        if (lane == 0)
+#pragma unroll
+            for (int k = 0; k < NV; ++k) out[k] = v[k];
+    }
+}
+
+// ------------------------------------------------------------ validation
+__global__ void k_validate(const uint8_t* __restrict__ phase, long long N, int* err) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        if (phase[c] > 3) atomicOr(err, 1);
+}
+
+cudaError_t launch_validate(const uint8_t* phase, long long N, int* d_err, cudaStream_t s) {
+    k_validate<<<1024, 256, 0, s>>>(phase, N, d_err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------ percolation (union-find)
+// Transport cells 6-connected (y, z periodic) to the inlet plane x = 0.
+// Lock-free union-find: a root is only ever linked to a smaller index, so
+// parent chains strictly decrease and every find terminates; each failed
+// CAS means another thread linked that root, so the retry loop makes
+// global progress.  Both loops still carry an iteration cap that raises
+// an error bit instead of spinning.
+constexpr int kUfMaxIter = 1 << 24;
+
+__device__ int uf_find(volatile int* L, int a, int* err) {
+    int it = 0;
+    int p = L[a];
+    while (p != a) {
+        a = p;
+        p = L[a];
+        if (++it > kUfMaxIter) { atomicOr(err, 2); break; }
+    }
+    return a;
+}
+
+__device__ void uf_union(int* L, int a, int b, int* err) {
+    for (int it = 0; it < kUfMaxIter; ++it) {
+        a = uf_find(L, a, err);
+        b = uf_find(L, b, err);
+        if (a == b) return;
+        if (a < b) { int t = a; a = b; b = t; }
+        int old = atomicCAS(L + a, a, b);
+        if (old == a) return;
+    }
+    atomicOr(err, 2);
+}
+
+__global__ void k_uf_init(const uint8_t* __restrict__ phase, long long N, int ion, int* L,
+                          uint8_t* touch) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        L[c] = is_transport(phase[c], ion) ? (int)c : -1;
+        touch[c] = 0;
+    }
+}
+
+__global__ void k_uf_merge(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ion, int* L,
+                           int* err) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (!is_transport(phase[c], ion)) continue;
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        if (x > 0 && is_transport(phase[c - 1], ion)) uf_union(L, (int)c, (int)(c - 1), err);
+        long long n = x + (long long)nx * (wrapi(y - 1, ny) + (long long)ny * z);
+        if (n != c && is_transport(phase[n], ion)) uf_union(L, (int)c, (int)n, err);
+        n = x + (long long)nx * (y + (long long)ny * wrapi(z - 1, nz));
+        if (n != c && is_transport(phase[n], ion)) uf_union(L, (int)c, (int)n, err);
+    }
+}
+
+__global__ void k_uf_flatten(long long N, int* L, int* err) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        if (L[c] >= 0) L[c] = uf_find(L, (int)c, err);
+}
+
+__global__ void k_uf_touch(int nx, long long N, const int* __restrict__ L, uint8_t* touch) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        if (c % nx == 0 && L[c] >= 0) touch[L[c]] = 1;
+}
+
+__global__ void k_uf_active(long long N, const int* __restrict__ L, const uint8_t* __restrict__ touch,
+                            uint8_t* active) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        active[c] = (L[c] >= 0 && touch[L[c]]) ? 1 : 0;
+}
+
+cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int ion, int* labels,
+                               uint8_t* touch, uint8_t* active, int* d_err, cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    const int g = 152 * 8, b = 256;
+    k_uf_init<<<g, b, 0, s>>>(phase, N, ion, labels, touch);
+    k_uf_merge<<<g, b, 0, s>>>(phase, nx, ny, nz, ion, labels, d_err);
+    k_uf_flatten<<<g, b, 0, s>>>(N, labels, d_err);
+    k_uf_touch<<<g, b, 0, s>>>(nx, N, labels, touch);
+    k_uf_active<<<g, b, 0, s>>>(N, labels, touch, active);
+    return cudaGetLastError();
+}
+
+// ------------------------------------- 13-direction pore length + D (Eq. 7-9)
+__constant__ int c_dir13[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                                   {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                                   {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+
+__device__ long long gcd_ll(long long a, long long b) {
+    while (b) { long long t = a % b; a = b; b = t; }
+    return a;
+}
+
+// Run length (cells) of pore cells through (x,y,z) along direction d.  y, z
+// periodic; x bounded; a line with no x component is a loop of period P and
+// its run is capped at P.  Every loop is bounded by nx or by P.
+__device__ int chord_run(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int x, int y, int z,
+                         int d) {
+    const int ex = c_dir13[d][0], ey = c_dir13[d][1], ez = c_dir13[d][2];
+    long long period = -1;
+    if (ex == 0) {
+        long long py = ey ? ny : 1, pz = ez ? nz : 1;
+        period = py / gcd_ll(py, pz) * pz;
+    }
+    long long run = 1;
+    for (int sgn = 1; sgn >= -1; sgn -= 2) {
+        int px = x, py = y, pz = z;
+        for (;;) {
+            if (period > 0 && run >= period) break;
+            const int qx = px + sgn * ex;
+            if (qx < 0 || qx >= nx) break;
+            const int qy = wrapi(py + sgn * ey, ny), qz = wrapi(pz + sgn * ez, nz);
+            if (!is_pore(__ldg(phase + qx + (long long)nx * (qy + (long long)ny * qz)))) break;
+            px = qx; py = qy; pz = qz;
+            ++run;
+        }
+    }
+    return (int)run;
+}
+
+__global__ void k_diffusivity(const uint8_t* __restrict__ phase, const uint8_t* __restrict__ active, int nx,
+                              int ny, int nz, double dx, double T, double M, double D_b, double D_ion,
+                              int knudsen, const double* __restrict__ D_override, double* D, double* dp,
+                              int32_t* chord13) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint8_t ph = phase[c];
+        const bool act = active[c] != 0;
+        double dcell = 0.0, dpc = 0.0;
+        const bool need_chords = is_pore(ph) && (chord13 != nullptr || dp != nullptr || (act && knudsen && !D_override));
+        if (need_chords) {
+            const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+            long long s1 = 0, s2 = 0, s3 = 0;  // axis, face-diagonal, body-diagonal sums
+            for (int d = 0; d < 13; ++d) {
+                const int r = chord_run(phase, nx, ny, nz, x, y, z, d);
+                if (chord13) chord13[c * 13 + d] = r;
+                if (d < 3) s1 += r; else if (d < 9) s2 += r; else s3 += r;
+            }
+            dpc = ((double)s1 + sqrt(2.0) * (double)s2 + sqrt(3.0) * (double)s3) * dx / 13.0;
+        } else if (chord13) {
+#pragma unroll
+            for (int d = 0; d < 13; ++d) chord13[c * 13 + d] = 0;
+        }
+        if (act) {
+            if (D_override) dcell = D_override[c];
+            else if (ph == 2) dcell = D_ion;
+            else if (knudsen) {
+                const double R = 8.314462618;
+                const double D_kn = dpc / 3.0 * sqrt(8.0 * R * T / (M_PI * M));  // Eq. 8
+                dcell = 1.0 / (1.0 / D_kn + 1.0 / D_b);                           // Eq. 9
+            } else dcell = D_b;
+        }
+        D[c] = dcell;
+        if (dp) dp[c] = dpc;
+    }
+}
+
+cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int nx, int ny, int nz,
+                               double dx, double T, double M, double D_b, double D_ionomer, int knudsen,
+                               const double* D_override, double* D, double* dp, int32_t* chord13,
+                               cudaStream_t s) {
+    k_diffusivity<<<152 * 16, 128, 0, s>>>(phase, active, nx, ny, nz, dx, T, M, D_b, D_ionomer, knudsen,
+                                           D_override, D, dp, chord13);
+    return cudaGetLastError();
+}
+
+// 13-direction run lengths only (diagnostic export of the Sec. 2.1.3 lengths)
+__global__ void k_chords13(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int32_t* chord13) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        if (!is_pore(phase[c])) {
+            for (int d = 0; d < 13; ++d) chord13[c * 13 + d] = 0;
+            continue;
+        }
+        const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+        for (int d = 0; d < 13; ++d) chord13[c * 13 + d] = chord_run(phase, nx, ny, nz, x, y, z, d);
+    }
+}
+
+cudaError_t launch_chords13(const uint8_t* phase, int nx, int ny, int nz, int32_t* chord13, cudaStream_t s) {
+    k_chords13<<<152 * 16, 128, 0, s>>>(phase, nx, ny, nz, chord13);
+    return cudaGetLastError();
+}
+
+__global__ void k_check_positive(const uint8_t* __restrict__ active, const double* __restrict__ D, long long N,
+                                 int* err) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        if (active[c] && !(D[c] > 0.0 && D[c] < INFINITY)) atomicOr(err, 4);
+}
+
+cudaError_t launch_check_positive(const uint8_t* active, const double* D, long long N, int* d_err, cudaStream_t s) {
+    k_check_positive<<<152 * 4, 256, 0, s>>>(active, D, N, d_err);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------- omega (Eq. 24, D3Q7)
+// tau = 1/2 + (tau_ref - 1/2) D / D_max  (dt fixed by tau_ref at D_max)
+__global__ void k_omega(const uint8_t* __restrict__ active, const double* __restrict__ D, long long N,
+                        double tau_ref, const double* __restrict__ Dmax, float* omega) {
+    const double dmax = *Dmax;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        float om = 0.f;
+        if (active[c]) {
+            const double tau = 0.5 + (tau_ref - 0.5) * D[c] / dmax;
+            om = (float)(1.0 / tau);
+        }
+        omega[c] = om;
+    }
+}
+
+cudaError_t launch_omega(const uint8_t* active, const double* D, long long N, double tau_ref,
+                         const double* d_Dmax, float* omega, cudaStream_t s) {
+    k_omega<<<152 * 8, 256, 0, s>>>(active, D, N, tau_ref, d_Dmax, omega);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- link masks
+__global__ void k_masks(const uint8_t* __restrict__ phase, const uint8_t* __restrict__ active,
+                        const uint8_t* __restrict__ react_in, int rule, int nx, int ny, int nz,
+                        uint16_t* mask) {
+    const long long N = (long long)nx * ny * nz;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        uint16_t m = 0;
+        if (active[c]) {
+            m = kActiveBit;
+            const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+            const int dx[6] = {1, -1, 0, 0, 0, 0}, dy[6] = {0, 0, 1, -1, 0, 0}, dz[6] = {0, 0, 0, 0, 1, -1};
+            for (int d = 0; d < 6; ++d) {
+                const int qx = x + dx[d];
+                if (qx < 0 || qx >= nx) { m |= (uint16_t)(1u << (kClosedShift + d)); continue; }
+                const long long n = qx + (long long)nx * (wrapi(y + dy[d], ny) + (long long)ny * wrapi(z + dz[d], nz));
+                if (active[n]) continue;
+                m |= (uint16_t)(1u << (kClosedShift + d));
+                bool react = false;
+                if (phase[n] == 1) {
+                    if (rule == CL_REACT_ALL_PORE_SOLID) react = phase[c] == 0;
+                    else if (react_in) react = (react_in[c] >> d) & 1;
+                }
+                if (react) m |= (uint16_t)(1u << (kReactShift + d));
+            }
+        }
+        mask[c] = m;
+    }
+}
+
+cudaError_t launch_masks(const uint8_t* phase, const uint8_t* active, const uint8_t* react_in, int rule,
+                         int nx, int ny, int nz, uint16_t* mask, cudaStream_t s) {
+    k_masks<<<152 * 8, 256, 0, s>>>(phase, active, react_in, rule, nx, ny, nz, mask);
+    return cudaGetLastError();
+}
+
+// -------------------------------------------------------------------- stats
+constexpr int kStatN = 7;
+__global__ void k_stats(const uint8_t* __restrict__ phase, const uint16_t* __restrict__ mask,
+                        const double* __restrict__ D, const double* __restrict__ dp, long long N, int nx,
+                        int ion, double* partials) {
+    double v[kStatN] = {0, 0, 0, 0, 0, 0, 0};
+    double dmax = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint8_t ph = phase[c];
+        const uint16_t m = mask[c];
+        v[0] += is_transport(ph, ion) ? 1.0 : 0.0;
+        if (m & kActiveBit) {
+            v[1] += 1.0;
+            const int x = (int)(c % nx);
+            unsigned closed = m & 0x3fu;
+            if (x == 0) closed &= ~2u;       // -x face on the inlet plane
+            if (x == nx - 1) closed &= ~1u;  // +x face on the outlet plane
+            v[2] += __popc(closed);
+            v[3] += __popc((m >> kReactShift) & 0x3fu);
+            dmax = fmax(dmax, D[c]);
+        }
+        if (dp && is_pore(ph)) { v[4] += dp[c]; v[5] += 1.0; }
+    }
+    // sums for 0..5, max for 6 (max via the same tree with fmax)
+    __shared__ double shm[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+    if (lane == 0) shm[warp] = dmax;
+    __syncthreads();
+    if (warp == 0) {
+        dmax = lane < nw ? shm[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_down_sync(0xffffffffu, dmax, o));
+    }
+    __syncthreads();
+    v[6] = 0.0;
+    block_sum_store<kStatN>(v, partials + (long long)blockIdx.x * kStatN);
+    if (threadIdx.x == 0) partials[(long long)blockIdx.x * kStatN + 6] = dmax;
+}
+
+// Fixed-order reduction of partials[nblocks][nslots] -> out[nslots]; slot k
+// uses max instead of sum when bit k of max_mask is set.
+__global__ void k_finalize(const double* __restrict__ partials, int nblocks, int nslots, unsigned max_mask,
+                           double* out) {
+    const int slot = blockIdx.x;
+    const bool is_max = (max_mask >> slot) & 1u;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double v = partials[(long long)b * nslots + slot];
+        acc = is_max ? fmax(acc, v) : acc + v;
+    }
+    __shared__ double sh[1024];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = is_max ? fmax(sh[threadIdx.x], sh[threadIdx.x + w])
+                                                      : sh[threadIdx.x] + sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[slot] = sh[0];
+}
+
+cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const double* D, const double* dp,
+                            long long N, int nx, int ion, double* partials, int nblocks, double* out,
+                            cudaStream_t s) {
+    k_stats<<<nblocks, 256, 0, s>>>(phase, mask, D, dp, N, nx, ion, partials);
+    k_finalize<<<kStatN, 1024, 0, s>>>(partials, nblocks, kStatN, 1u << 6, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const double* partials, int nblocks, int nslots, double* out, cudaStream_t s) {
+    k_finalize<<<nslots, 1024, 0, s>>>(partials, nblocks, nslots, 0u, out);
+    return cudaGetLastError();
+}
+
+// ====================================================== FP32 solver kernels
+__global__ void k_init_fp32(float* __restrict__ pop, const uint16_t* __restrict__ mask,
+                            const float* __restrict__ C0, int nx, long long N, double c_in, double c_out,
+                            float* __restrict__ Csnap) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        float C = 0.f;
+        const bool act = (mask[c] & kActiveBit) != 0;
+        if (act) {
+            if (C0) C = C0[c];
+            else {
+                const int x = (int)(c % nx);
+                C = (float)(c_in + (c_out - c_in) * (x + 0.5) / nx);
+            }
+        }
+        pop[c] = act ? kW0 * C : 0.f;
+#pragma unroll
+        for (int i = 1; i < 7; ++i) pop[(long long)i * N + c] = act ? kW1 * C : 0.f;
+        if (Csnap) Csnap[c] = C;
+    }
+}
+
+cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, int nx, int ny, int nz,
+                             double c_in, double c_out, float* Csnap, cudaStream_t s) {
+    const long long N = (long long)nx * ny * nz;
+    k_init_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, C0, nx, N, c_in, c_out, Csnap);
+    return cudaGetLastError();
+}
+
+// Fused pull-stream + BGK collide (Eq. 21) for one cell per thread.
+// Pull: g_i(x) = g*_i(x - c_i) when that face is open; across a closed face
+// the cell's own opposite post-collision population comes back:
+//   inlet  (x = 0,  i = +x): -g*_{-x} + 2 w C_in  (Dirichlet, anti-bounce-back) or g*_{-x}
+//   outlet (x = L,  i = -x): -g*_{+x} + 2 w C_out or g*_{+x}
+//   wall:  g*_{opp}(x) times (2w - k)/(2w + k) if catalytic, else 1.
+// Collide: C = sum g_i, g*_i = g_i - omega (g_i - w_i C).
+template <bool REDUCE>
+__global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src, float* __restrict__ dst,
+                                                   StepArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const long long N = a.N;
+    double rv[RED_N];
+    if (REDUCE)
+#pragma unroll
+        for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+    if (x < nx) {
+        const long long plane = (long long)nx * ny;
+        const long long c = x + (long long)nx * y + plane * z;
+        const uint16_t m = a.mask[c];
+        if (m & kActiveBit) {
+            const float* s0 = src;
+            const float* s1 = src + N;
+            const float* s2 = src + 2 * N;
+            const float* s3 = src + 3 * N;
+            const float* s4 = src + 4 * N;
+            const float* s5 = src + 5 * N;
+            const float* s6 = src + 6 * N;
+            const float rf = a.rfac;
+            float g0 = s0[c];
+            float g1, g2, g3, g4, g5, g6;
+            // +x population arrives from x-1 through the -x face (d = 2, bit 1)
+            if (m & (1u << 1)) {
+                const float o = s2[c];
+                if (x == 0) g1 = a.bc_in == CL_BC_DIRICHLET ? a.abb_in - o : o;
+                else g1 = (m & (1u << (kReactShift + 1))) ? rf * o : o;
+            } else g1 = s1[c - 1];
+            // -x population from x+1 through the +x face (d = 1, bit 0)
+            if (m & (1u << 0)) {
+                const float o = s1[c];
+                if (x == nx - 1) g2 = a.bc_out == CL_BC_DIRICHLET ? a.abb_out - o : o;
+                else g2 = (m & (1u << (kReactShift + 0))) ? rf * o : o;
+            } else g2 = s2[c + 1];
+            // +y from y-1 through the -y face (d = 4, bit 3)
+            if (m & (1u << 3)) { const float o = s4[c]; g3 = (m & (1u << (kReactShift + 3))) ? rf * o : o; }
+            else g3 = s3[y == 0 ? c + (long long)(ny - 1) * nx : c - nx];
+            // -y from y+1 through the +y face (d = 3, bit 2)
+            if (m & (1u << 2)) { const float o = s3[c]; g4 = (m & (1u << (kReactShift + 2))) ? rf * o : o; }
+            else g4 = s4[y == ny - 1 ? c - (long long)(ny - 1) * nx : c + nx];
+            // +z from z-1 through the -z face (d = 6, bit 5)
+            if (m & (1u << 5)) { const float o = s6[c]; g5 = (m & (1u << (kReactShift + 5))) ? rf * o : o; }
+            else g5 = s5[z == 0 ? c + (long long)(nz - 1) * plane : c - plane];
+            // -z from z+1 through the +z face (d = 5, bit 4)
+            if (m & (1u << 4)) { const float o = s5[c]; g6 = (m & (1u << (kReactShift + 4))) ? rf * o : o; }
+            else g6 = s6[z == nz - 1 ? c - (long long)(nz - 1) * plane : c + plane];
+
+            const float C = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6);
+            const float om = a.omega[c];
+            const float e0 = kW0 * C, e1 = kW1 * C;
+            const float h0 = g0 - om * (g0 - e0);
+            const float h1 = g1 - om * (g1 - e1);
+            const float h2 = g2 - om * (g2 - e1);
+            const float h3 = g3 - om * (g3 - e1);
+            const float h4 = g4 - om * (g4 - e1);
+            const float h5 = g5 - om * (g5 - e1);
+            const float h6 = g6 - om * (g6 - e1);
+            dst[c] = h0;
+            dst[N + c] = h1;
+            dst[2 * N + c] = h2;
+            dst[3 * N + c] = h3;
+            dst[4 * N + c] = h4;
+            dst[5 * N + c] = h5;
+            dst[6 * N + c] = h6;
+            if (REDUCE) {
+                if (x == 0 && a.bc_in == CL_BC_DIRICHLET) rv[RED_JIN] = 2.0 * ((double)a.w_cin - (double)h2);
+                if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h1 - (double)a.w_cout);
+                const unsigned rb = (m >> kReactShift) & 0x3fu;
+                if (rb) {
+                    const double sink = 1.0 - (double)rf;
+                    double r = 0.0;
+                    if (rb & 1u) r += h1;
+                    if (rb & 2u) r += h2;
+                    if (rb & 4u) r += h3;
+                    if (rb & 8u) r += h4;
+                    if (rb & 16u) r += h5;
+                    if (rb & 32u) r += h6;
+                    rv[RED_R] = sink * r;
+                }
+                const double Cd = C;
+                rv[RED_SUMC] = Cd;
+                rv[RED_DC] = fabs(Cd - (double)a.Csnap[c]);
+                rv[RED_ABSC] = fabs(Cd);
+                rv[RED_NONFINITE] = isfinite(C) ? 0.0 : 1.0;
+                a.Csnap[c] = C;
+            }
+        }
+    }
+    if (REDUCE) {
+        const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        block_sum_store<RED_N>(rv, a.partials + blk * RED_N);
+    }
+}
+
+static dim3 step_grid(const StepArgs& a) { return dim3((a.nx + 127) / 128, a.ny, a.nz); }
+
+int step_fp32_blocks(const StepArgs& a) {
+    dim3 g = step_grid(a);
+    return (int)(g.x * g.y * g.z);
+}
+
+cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce, cudaStream_t s) {
+    const dim3 g = step_grid(a);
+    if (reduce) k_step_fp32<true><<<g, 128, 0, s>>>(src, dst, a);
+    else k_step_fp32<false><<<g, 128, 0, s>>>(src, dst, a);
+    return cudaGetLastError();
+}
+
+__global__ void k_field_fp32(const float* __restrict__ pop, const uint16_t* __restrict__ mask, long long N,
+                             float* __restrict__ C) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        if (mask[c] & kActiveBit) {
+            v = pop[c];
+#pragma unroll
+            for (int i = 1; i < 7; ++i) v += pop[(long long)i * N + c];
+        }
+        C[c] = v;
+    }
+}
+
+cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C, cudaStream_t s) {
+    k_field_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, N, C);
+    return cudaGetLastError();
+}
+
+// Per-plane readouts from the stored post-collision populations: one block
+// per x-plane, fixed-order sums.  out[5*x + k]: sum C, active count, R,
+// J_in part, J_out part.
+__global__ void k_readout_fp32(const float* __restrict__ pop, StepArgs a, double* out) {
+    const int x = blockIdx.x;
+    const long long N = a.N;
+    const long long nyz = (long long)a.ny * a.nz;
+    double v[5] = {0, 0, 0, 0, 0};
+    const double sink = 1.0 - (double)a.rfac;
+    for (long long j = threadIdx.x; j < nyz; j += blockDim.x) {
+        const long long c = x + (long long)a.nx * j;
+        const uint16_t m = a.mask[c];
+        if (!(m & kActiveBit)) continue;
+        double C = 0.0;
+        float h[7];
+#pragma unroll
+        for (int i = 0; i < 7; ++i) { h[i] = pop[(long long)i * N + c]; }
+        C = (double)(((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + h[6]));
+        v[0] += C;
+        v[1] += 1.0;
+        const unsigned rb = (m >> kReactShift) & 0x3fu;
+        double r = 0.0;
+        for (int d = 0; d < 6; ++d)
+            if (rb & (1u << d)) r += h[d + 1];
+        v[2] += sink * r;
+        if (x == 0 && a.bc_in == CL_BC_DIRICHLET) v[3] += 2.0 * ((double)a.w_cin - (double)h[2]);
+        if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) v[4] += 2.0 * ((double)h[1] - (double)a.w_cout);
+    }
+    block_sum_store<5>(v, out + 5LL * x);
+}
+
+cudaError_t launch_readout_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s) {
+    k_readout_fp32<<<a.nx, 256, 0, s>>>(pop, a, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cl

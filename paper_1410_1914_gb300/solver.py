@@ -1,0 +1,113 @@
+"""Object wrapper over one cl_lbm handle (argument marshalling only)."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib as L
+
+_STORAGE = {"fp32": L.CL_STORE_FP32, "fp16dev": L.CL_STORE_FP16DEV}
+
+
+class Solver:
+    """One D3Q7 solver on one box.  Parameters are the cl_params fields.
+
+    ``shape`` is (nz, ny, nx).  ``stream``: a cudaStream_t (int); default is
+    torch's current stream when torch has initialised CUDA, else the legacy
+    default stream.  ``torch_alloc``: route device allocations through torch's
+    caching allocator.
+    """
+
+    def __init__(self, shape, storage: str = "fp32", stream: int | None = None,
+                 torch_alloc: bool = False, **params):
+        nz, ny, nx = (int(v) for v in shape)
+        self.shape = (nz, ny, nx)
+        self.n = nx * ny * nz
+        p = L.cl_params_default(nx=nx, ny=ny, nz=nz)
+        p.storage = _STORAGE[storage]
+        for k, v in params.items():
+            setattr(p, k, v)
+        p.cuda_stream = L.current_torch_stream() if stream is None else stream
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = L.TorchAllocator()
+            p.alloc = self._alloc.alloc
+            p.free = self._alloc.free
+        self.params = p
+        self.h = L.cl_lbm_create(p)
+
+    def close(self):
+        if getattr(self, "h", None):
+            L.cl_lbm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------ set-up
+    def set_structure(self, phase, reactive_faces=None):
+        L.cl_lbm_set_structure(self.h, phase, reactive_faces, self.n)
+
+    def set_diffusivity(self, D):
+        L.cl_lbm_set_diffusivity(self.h, D, self.n)
+
+    def init(self, C0=None):
+        L.cl_lbm_init(self.h, C0, self.n)
+
+    # ------------------------------------------------------------ stepping
+    def step(self, n: int = 1):
+        L.cl_lbm_step(self.h, n)
+
+    def solve(self, raise_on_not_converged: bool = False):
+        status, info = L.cl_lbm_solve(self.h, raise_on_not_converged)
+        d = info.as_dict()
+        d["status"] = L.status_str(status)
+        return d
+
+    def solve_budget(self, max_steps: int):
+        status, info = L.cl_lbm_solve_budget(self.h, max_steps)
+        d = info.as_dict()
+        d["status"] = L.status_str(status)
+        return d
+
+    # ------------------------------------------------------------ readouts
+    def fluxes(self):
+        f = L.cl_lbm_fluxes(self.h)
+        return dict(J_in=f[0], J_out=f[1], R=f[2], sum_C=f[3], n_active=int(f[4]))
+
+    def effective_diffusivity(self):
+        return L.cl_lbm_effective_diffusivity(self.h)
+
+    def reaction_rate(self):
+        return L.cl_lbm_reaction_rate(self.h, self.shape[2])
+
+    def field(self):
+        out = np.zeros(self.shape, dtype=np.float32)
+        L.cl_lbm_get_field(self.h, out)
+        return out
+
+    def populations(self):
+        out = np.zeros((7,) + self.shape, dtype=np.float32)
+        L.cl_lbm_get_populations(self.h, out)
+        return out
+
+    def setup(self, chord: bool = False):
+        active = np.zeros(self.shape, dtype=np.uint8)
+        omega = np.zeros(self.shape, dtype=np.float32)
+        mask = np.zeros(self.shape, dtype=np.uint16)
+        ch = np.zeros(self.shape + (13,), dtype=np.int32) if chord else None
+        L.cl_lbm_get_setup(self.h, active, omega, ch, mask)
+        return dict(active=active, omega=omega, chord=ch, mask=mask)
+
+    def info(self):
+        i = L.cl_lbm_get_info(self.h)
+        return {k: getattr(i, k) for k, _ in i._fields_}
+
+    @property
+    def steps(self):
+        return L.cl_lbm_get_step(self.h)

@@ -1,0 +1,106 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/*.h declares, the ctypes structures match the C layout, and argument
+validation answers before any device work."""
+import ctypes
+import glob
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1410_1914_gb300 import _lib, build
+    build.build_cuda()
+    return _lib.load()
+
+
+def declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(cl_\w+)\s*\(", text, flags=re.M):
+            if not text[m.start():m.end()].lstrip().startswith("typedef"):
+                names.add(m.group(1))
+    return sorted(names)
+
+
+def test_header_declares_the_entry_points():
+    names = declared_functions()
+    for required in ("cl_lbm_create", "cl_lbm_set_structure", "cl_lbm_solve", "cl_lbm_effective_diffusivity",
+                     "cl_lbm_reaction_rate", "cl_lbm_destroy"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    from paper_1410_1914_gb300 import _lib
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    # the binding mirrors every declared function
+    assert set(declared_functions()) <= set(_lib.SIGNATURES), set(declared_functions()) - set(_lib.SIGNATURES)
+
+
+def test_struct_layouts_match_c(tmp_path):
+    from paper_1410_1914_gb300 import _lib
+    structs = {"cl_params": _lib.cl_params, "cl_structure_info": _lib.cl_structure_info,
+               "cl_solve_info": _lib.cl_solve_info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cl_lbm.h"', "int main(void){"]
+    for sname, cls in structs.items():
+        lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{sname} {f} %zu\\n", offsetof({sname}, {f}));')
+    lines.append("return 0;}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    for ln in out:
+        if not ln:
+            continue
+        sname, field, val = ln.split()
+        cls = structs[sname]
+        if field == "sizeof":
+            assert ctypes.sizeof(cls) == int(val), sname
+        else:
+            assert getattr(cls, field).offset == int(val), (sname, field)
+
+
+def test_defaults_and_strings(lib):
+    from paper_1410_1914_gb300 import _lib
+    p = _lib.cl_params_default()
+    assert p.tau_ref == 1.0 and p.c_in == 1.0 and p.c_out == 0.0 and p.check_every == 1000
+    assert p.storage == _lib.CL_STORE_FP32 and p.max_steps == 10_000_000
+    assert _lib.status_str(_lib.CL_ERR_NO_PATH) == "CL_ERR_NO_PATH"
+    assert "D3Q7" in _lib.version()
+
+
+@pytest.mark.parametrize("field,value", [("nx", 0), ("tau_ref", 0.5), ("check_every", 3), ("bc_in", 7),
+                                         ("storage", 9), ("dx_m", -1.0), ("k_ms", -1.0)])
+def test_create_rejects_bad_parameters_before_device_work(lib, field, value):
+    from paper_1410_1914_gb300 import _lib
+    p = _lib.cl_params_default(nx=8, ny=8, nz=8)
+    setattr(p, field, value)
+    with pytest.raises(_lib.ClError) as e:
+        _lib.cl_lbm_create(p)
+    assert e.value.status == _lib.CL_ERR_ARG
+
+
+def test_oversized_box_rejected(lib):
+    from paper_1410_1914_gb300 import _lib
+    p = _lib.cl_params_default(nx=2048, ny=2048, nz=1024)
+    with pytest.raises(_lib.ClError) as e:
+        _lib.cl_lbm_create(p)
+    assert e.value.status == _lib.CL_ERR_ARG
+
+
+def test_null_handle_calls(lib):
+    from paper_1410_1914_gb300 import _lib
+    info = _lib.cl_solve_info()
+    assert lib.cl_lbm_solve(None, ctypes.byref(info)) == _lib.CL_ERR_ARG
+    lib.cl_lbm_destroy(None)  # ignored
