@@ -60,8 +60,14 @@ typedef enum {
 typedef enum { CL_BC_DIRICHLET = 0, CL_BC_ZERO_FLUX = 1 } cl_bc;
 
 typedef enum {
-    CL_STORE_FP32 = 0,   /* 7 x f32 populations per cell */
-    CL_STORE_FP16DEV = 1 /* C as f32 + 6 post-collision deviations from w_i C as scaled f16 */
+    /* C as a double-float (two f32) + 6 post-collision deviations from w_i C
+       as f32; FP32 arithmetic on small quantities only */
+    CL_STORE_FP32 = 0,
+    /* C as f32 + a scaled f16 low word, deviations as scaled f16; FP32 arithmetic */
+    CL_STORE_FP16DEV = 1,
+    /* plain 7 x f32 populations per cell (reference layout; its steady state
+       carries an FP32 rounding floor that grows with the box) */
+    CL_STORE_FP32POP = 2
 } cl_storage;
 
 typedef enum {

@@ -22,7 +22,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_PKG), "include", "cl_lbm.h")
 CL_OK, CL_ERR_ARG, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_STATE = 0, 1, 2, 3, 4
 CL_ERR_DIVERGED, CL_ERR_NOT_CONVERGED, CL_ERR_NO_PATH, CL_ERR_TIMEOUT = 5, 6, 7, 8
 CL_BC_DIRICHLET, CL_BC_ZERO_FLUX = 0, 1
-CL_STORE_FP32, CL_STORE_FP16DEV = 0, 1
+CL_STORE_FP32, CL_STORE_FP16DEV, CL_STORE_FP32POP = 0, 1, 2
 CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID = 0, 1
 
 cl_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

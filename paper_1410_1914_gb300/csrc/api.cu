@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "march.cuh"
 
 using namespace cl;
 
@@ -19,23 +20,21 @@ void set_msg(const char* where, cudaError_t e) {
 }
 void set_msg_txt(const char* txt) { snprintf(g_msg, sizeof(g_msg), "%s", txt); }
 
-cl_status from_cuda(cudaError_t e) {
-    return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA;
-}
+cl_status from_cuda(cudaError_t e) { return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA; }
 
-#define CK(call)                                  \
-    do {                                          \
-        cudaError_t e_ = (call);                  \
-        if (e_ != cudaSuccess) {                  \
-            set_msg(#call, e_);                   \
-            return from_cuda(e_);                 \
-        }                                         \
+#define CK(call)                    \
+    do {                            \
+        cudaError_t e_ = (call);    \
+        if (e_ != cudaSuccess) {    \
+            set_msg(#call, e_);     \
+            return from_cuda(e_);   \
+        }                           \
     } while (0)
 
-#define CKS(stmt)                                 \
-    do {                                          \
-        cl_status s_ = (stmt);                    \
-        if (s_ != CL_OK) return s_;               \
+#define CKS(stmt)                   \
+    do {                            \
+        cl_status s_ = (stmt);      \
+        if (s_ != CL_OK) return s_; \
     } while (0)
 
 struct Graph {
@@ -45,14 +44,43 @@ struct Graph {
     bool reduce = false;
 };
 
+// cuTensorMapEncodeTiled, fetched from the driver through the runtime
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    }
+    return fn;
+}
+
+// One time level of the (C, delta) state, padded rows and two ghost rows per plane.
+struct MState {
+    float* chi = nullptr;
+    void* clo = nullptr;
+    void* d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
 }  // namespace
 
 struct cl_lbm {
     cl_params p;
     int nx, ny, nz;
     long long N;
-    cudaStream_t s = nullptr;    // stream every call is ordered on
-    cudaStream_t cap = nullptr;  // private stream used only to capture graphs
+    bool march = true;  // (C, delta) storage; false: 7 f32 populations
+    int px = 0;         // padded row pitch
+    long long NP = 0;   // padded, ghosted cell count
+    int el = 4;         // bytes per stored deviation
+    cudaStream_t s = nullptr;
+    cudaStream_t cap = nullptr;
     std::vector<std::pair<void*, size_t>> allocs;
 
     uint8_t *phase = nullptr, *react = nullptr, *active = nullptr, *touch = nullptr;
@@ -61,9 +89,20 @@ struct cl_lbm {
     double *D = nullptr, *dp = nullptr;
     float* omega = nullptr;
     uint16_t* mask = nullptr;
+    // population layout
     float* pop[2] = {nullptr, nullptr};
-    int cur = 0;
     float* Csnap = nullptr;
+    // (C, delta) layout
+    MState st[2];
+    uint16_t* mask_p = nullptr;
+    float* omega_p = nullptr;
+    float* Csnap_p = nullptr;
+    MarchMaps maps[2];
+    dim3 mgrid;
+    int z_chunk = 0;
+    float s_lo = 1.f, s_d = 1.f;
+
+    int cur = 0;
     float* fbuf = nullptr;
     double* partials = nullptr;
     int nblk_step = 0, nblk_stats = 0;
@@ -100,8 +139,13 @@ cl_status dalloc_n(cl_lbm* h, T** out, long long n) {
     return dalloc(h, (void**)out, sizeof(T) * (size_t)n);
 }
 
-cudaMemcpyKind kind_in(int ptr_is_device) { return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
-cudaMemcpyKind kind_out(int ptr_is_device) { return ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+cudaMemcpyKind kind_in(int dev) { return dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int dev) { return dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+float reactive_factor(const cl_lbm* h) {
+    const double w = 0.125;
+    return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
+}
 
 StepArgs make_args(cl_lbm* h) {
     StepArgs a;
@@ -109,7 +153,7 @@ StepArgs make_args(cl_lbm* h) {
     a.mask = h->mask;
     a.omega = h->omega;
     const double w = 0.125;
-    a.rfac = (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
+    a.rfac = reactive_factor(h);
     a.abb_in = (float)(2.0 * w * h->p.c_in);
     a.abb_out = (float)(2.0 * w * h->p.c_out);
     a.w_cin = (float)(w * h->p.c_in);
@@ -121,6 +165,95 @@ StepArgs make_args(cl_lbm* h) {
     return a;
 }
 
+MarchArgs make_margs(cl_lbm* h, int dst) {
+    MarchArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
+    a.z_chunk = h->z_chunk;
+    a.chi = h->st[dst].chi;
+    a.clo = h->st[dst].clo;
+    for (int i = 0; i < 6; ++i) a.d[i] = h->st[dst].d[i];
+    a.rfac = reactive_factor(h);
+    a.c_in = (float)h->p.c_in;
+    a.c_out = (float)h->p.c_out;
+    a.bc_in = h->p.bc_in;
+    a.bc_out = h->p.bc_out;
+    a.s_lo = h->s_lo;
+    a.inv_lo = 1.0f / h->s_lo;
+    a.s_d = h->s_d;
+    a.inv_d = 1.0f / h->s_d;
+    a.Csnap = h->Csnap_p;
+    a.partials = h->partials;
+    a.err = h->d_err;
+    return a;
+}
+
+cl_status make_map(CUtensorMap* m, CUtensorMapDataType dt, int el, void* ptr, int px, int rows, int nz, int bx,
+                   int by) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) { set_msg_txt("cuTensorMapEncodeTiled unavailable"); return CL_ERR_CUDA; }
+    cuuint64_t dims[3] = {(cuuint64_t)px, (cuuint64_t)rows, (cuuint64_t)nz};
+    cuuint64_t strides[2] = {(cuuint64_t)px * el, (cuuint64_t)px * rows * el};
+    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(m, dt, 3, ptr, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        snprintf(g_msg, sizeof(g_msg), "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        return CL_ERR_CUDA;
+    }
+    return CL_OK;
+}
+
+cl_status build_maps(cl_lbm* h) {
+    const CUtensorMapDataType tT = h->el == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUtensorMapDataType tF = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const int R = h->ny + 2, px = h->px, nz = h->nz, el = h->el;
+    const int hxl = 16 / el;
+    for (int b = 0; b < 2; ++b) {
+        MarchMaps& m = h->maps[b];
+        MState& s = h->st[b];
+        CKS(make_map(&m.chi, tF, 4, s.chi, px, R, nz, kBX, kBY + 2));
+        CKS(make_map(&m.clo, tT, el, s.clo, px, R, nz, kBX, kBY + 2));
+        CKS(make_map(&m.d3, tT, el, s.d[2], px, R, nz, kBX, kBY + 2));
+        CKS(make_map(&m.d4, tT, el, s.d[3], px, R, nz, kBX, kBY + 2));
+        CKS(make_map(&m.d1, tT, el, s.d[0], px, R, nz, kBX, kBY));
+        CKS(make_map(&m.d2, tT, el, s.d[1], px, R, nz, kBX, kBY));
+        CKS(make_map(&m.d5, tT, el, s.d[4], px, R, nz, kBX, kBY));
+        CKS(make_map(&m.d6, tT, el, s.d[5], px, R, nz, kBX, kBY));
+        CKS(make_map(&m.om, tF, 4, h->omega_p, px, R, nz, kBX, kBY));
+        CKS(make_map(&m.mk, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->mask_p, px, R, nz, kBX, kBY));
+        CKS(make_map(&m.chi_h, tF, 4, s.chi, px, R, nz, 4, kBY));
+        CKS(make_map(&m.clo_h, tT, el, s.clo, px, R, nz, hxl, kBY));
+        CKS(make_map(&m.d1_h, tT, el, s.d[0], px, R, nz, hxl, kBY));
+        CKS(make_map(&m.d2_h, tT, el, s.d[1], px, R, nz, hxl, kBY));
+    }
+    return CL_OK;
+}
+
+// Blocks per z-column chosen so that the grid fills whole waves of resident
+// blocks while keeping at least 8 planes per block.
+void choose_march_grid(cl_lbm* h) {
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int resident = nsm * march_blocks_per_sm(h->p.storage);
+    const int tiles = (h->px / kBX) * ((h->ny + kBY - 1) / kBY);
+    int best_gz = 1;
+    double best = 1e30;
+    const int gz_max = h->nz < 8 ? 1 : h->nz / 8;
+    for (int gz = 1; gz <= gz_max && gz <= 4096; ++gz) {
+        const int zc = (h->nz + gz - 1) / gz;
+        const int g = (h->nz + zc - 1) / zc;
+        const double blocks = (double)tiles * g;
+        const double waves = ceil(blocks / resident);
+        // time ~ waves * (planes per block + 2 halo planes)
+        const double cost = waves * (zc + 2.0);
+        if (cost < best - 1e-9) { best = cost; best_gz = g; }
+    }
+    h->z_chunk = (h->nz + best_gz - 1) / best_gz;
+    h->mgrid = dim3(h->px / kBX, (h->ny + kBY - 1) / kBY, (h->nz + h->z_chunk - 1) / h->z_chunk);
+}
+
 void drop_graphs(cl_lbm* h) {
     for (auto& g : h->graphs) {
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -128,13 +261,22 @@ void drop_graphs(cl_lbm* h) {
     }
 }
 
-// Enqueue `n` steps (the last one with the fused reduction if `reduce`) on stream s.
+// Enqueue `n` steps (the last one with the fused reduction if `reduce`).
 cl_status enqueue_steps(cl_lbm* h, long long n, bool reduce, cudaStream_t s, int* parity) {
-    StepArgs a = make_args(h);
-    for (long long i = 0; i < n; ++i) {
-        const bool red = reduce && i == n - 1;
-        CK(launch_step_fp32(h->pop[*parity], h->pop[*parity ^ 1], a, red, s));
-        *parity ^= 1;
+    if (h->march) {
+        for (long long i = 0; i < n; ++i) {
+            const bool red = reduce && i == n - 1;
+            MarchArgs a = make_margs(h, *parity ^ 1);
+            CK(launch_march(h->p.storage, red, h->maps[*parity], a, h->mgrid, s));
+            *parity ^= 1;
+        }
+    } else {
+        StepArgs a = make_args(h);
+        for (long long i = 0; i < n; ++i) {
+            const bool red = reduce && i == n - 1;
+            CK(launch_step_fp32(h->pop[*parity], h->pop[*parity ^ 1], a, red, s));
+            *parity ^= 1;
+        }
     }
     if (reduce) CK(launch_finalize(h->partials, h->nblk_step, RED_N, h->d_red, s));
     return CL_OK;
@@ -146,7 +288,8 @@ cl_status get_graph(cl_lbm* h, long long K, bool reduce, cudaGraphExec_t* out) {
     for (auto& g : h->graphs)
         if (g.exec && g.parity == h->cur && g.K == K && g.reduce == reduce) { *out = g.exec; return CL_OK; }
     Graph* slot = nullptr;
-    for (auto& g : h->graphs) if (!g.exec) { slot = &g; break; }
+    for (auto& g : h->graphs)
+        if (!g.exec) { slot = &g; break; }
     if (!slot) { drop_graphs(h); slot = &h->graphs[0]; }
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
     int par = h->cur;
@@ -182,10 +325,11 @@ cl_status check_err_flag(cl_lbm* h) {
     if (herr & 1) { set_msg_txt("phase code outside 0..3"); return CL_ERR_ARG; }
     if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
     if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
+    if (herr & 8) { set_msg_txt("a plane load of the step kernel did not arrive within its wait bound"); return CL_ERR_TIMEOUT; }
     return CL_OK;
 }
 
-// stats + dt + omega + init, shared by set_structure and set_diffusivity
+// stats + dt + omega, shared by set_structure and set_diffusivity
 cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
     double* stat_out = h->d_red + 8;  // 7 slots
     CK(launch_stats(h->phase, h->mask, h->D, with_dp ? h->dp : nullptr, h->N, h->nx, h->p.D_ionomer > 0,
@@ -210,21 +354,59 @@ cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
     h->info.dt_s = h->dt;
     h->info.k_lu = h->k_lu;
     CK(launch_omega(h->active, h->D, h->N, h->p.tau_ref, stat_out + 6, h->omega, h->s));
+    if (h->march)
+        CK(launch_pad_static(h->mask, h->omega, h->nx, h->ny, h->nz, h->px, h->mask_p, h->omega_p, h->s));
     drop_graphs(h);  // the reactive factor is baked into captured kernel arguments
     return CL_OK;
 }
 
+// FP16 scales from the largest concentration magnitude (C < 2^E):
+// low word scaled by 2^(38 - E), deviations by 2^(14 - E).
+void set_scales(cl_lbm* h, double cmax) {
+    if (h->p.storage != CL_STORE_FP16DEV) { h->s_lo = h->s_d = 1.f; return; }
+    int E = 0;
+    frexp(cmax > 0 ? cmax : 1.0, &E);  // cmax < 2^E
+    h->s_lo = ldexpf(1.f, 38 - E);
+    h->s_d = ldexpf(1.f, 14 - E);
+}
+
 cl_status do_init(cl_lbm* h, const float* C0dev) {
     h->cur = 0;
-    CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)h->N, h->s));
-    CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap, h->s));
+    double cmax = fmax(fabs(h->p.c_in), fabs(h->p.c_out));
+    if (C0dev) {
+        double* out = h->d_red + 15;
+        CK(launch_absmax(C0dev, h->N, h->partials, h->nblk_stats, out, h->s));
+        double m = 0;
+        CK(cudaMemcpyAsync(&m, out, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        cmax = fmax(cmax, m);
+    }
+    if (h->march) {
+        set_scales(h, cmax);
+        drop_graphs(h);
+        // the other time level must hold zeros on inactive slots: the kernel never writes them
+        const MState& o = h->st[1];
+        CK(cudaMemsetAsync(o.chi, 0, sizeof(float) * h->NP, h->s));
+        CK(cudaMemsetAsync(o.clo, 0, (size_t)h->el * h->NP, h->s));
+        for (int i = 0; i < 6; ++i) CK(cudaMemsetAsync(o.d[i], 0, (size_t)h->el * h->NP, h->s));
+        MarchArgs a = make_margs(h, 0);
+        CK(launch_state_init(h->p.storage, a, h->mask_p, C0dev, h->s));
+    } else {
+        CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)h->N, h->s));
+        CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap, h->s));
+    }
     h->step = 0;
     return CL_OK;
 }
 
 cl_status plane_readout(cl_lbm* h, double* tot /* [5] */) {
-    StepArgs a = make_args(h);
-    CK(launch_readout_fp32(h->pop[h->cur], a, h->d_plane, h->s));
+    if (h->march) {
+        MarchArgs a = make_margs(h, h->cur);
+        CK(launch_state_readout(h->p.storage, a, h->mask_p, h->d_plane, h->s));
+    } else {
+        StepArgs a = make_args(h);
+        CK(launch_readout_fp32(h->pop[h->cur], a, h->d_plane, h->s));
+    }
     double* hp = h->h_red + 16;
     CK(cudaMemcpyAsync(hp, h->d_plane, sizeof(double) * 5 * h->nx, cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
@@ -275,7 +457,7 @@ const char* cl_status_str(cl_status s) {
 
 const char* cl_last_error_message(void) { return g_msg; }
 
-const char* cl_version(void) { return "cl_lbm 0.1 (D3Q7, sm_103a)"; }
+const char* cl_version(void) { return "cl_lbm 0.2 (D3Q7, sm_103a)"; }
 
 cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (!out || !p) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
@@ -286,14 +468,17 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (p->D_bulk <= 0 && !(p->p_atm > 0)) { set_msg_txt("p_atm must be > 0 when D_bulk comes from Eq. 7"); return CL_ERR_ARG; }
     if (p->D_ionomer < 0 || p->k_ms < 0) { set_msg_txt("D_ionomer and k_ms must be >= 0"); return CL_ERR_ARG; }
     if ((p->bc_in != 0 && p->bc_in != 1) || (p->bc_out != 0 && p->bc_out != 1)) { set_msg_txt("bad boundary type"); return CL_ERR_ARG; }
-    if (p->storage != CL_STORE_FP32) { set_msg_txt("storage mode not available"); return CL_ERR_ARG; }
+    if (p->storage != CL_STORE_FP32 && p->storage != CL_STORE_FP16DEV && p->storage != CL_STORE_FP32POP) { set_msg_txt("bad storage mode"); return CL_ERR_ARG; }
     if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
     if (p->check_every < 2 || (p->check_every & 1)) { set_msg_txt("check_every must be even and >= 2"); return CL_ERR_ARG; }
     if ((p->alloc == nullptr) != (p->free == nullptr)) { set_msg_txt("alloc and free must both be set or both NULL"); return CL_ERR_ARG; }
+    if (!(fabs(p->c_in) < 1e30) || !(fabs(p->c_out) < 1e30)) { set_msg_txt("boundary concentrations must be finite"); return CL_ERR_ARG; }
 
     cl_lbm* h = new cl_lbm();
     h->p = *p;
     h->nx = p->nx; h->ny = p->ny; h->nz = p->nz; h->N = N;
+    h->march = p->storage != CL_STORE_FP32POP;
+    h->el = p->storage == CL_STORE_FP16DEV ? 2 : 4;
     h->s = (cudaStream_t)p->cuda_stream;
     memset(&h->info, 0, sizeof(h->info));
     cl_status st = CL_OK;
@@ -301,9 +486,16 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
 
-    StepArgs a;
-    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
-    h->nblk_step = step_fp32_blocks(a);
+    if (h->march) {
+        h->px = (h->nx + kBX - 1) / kBX * kBX;
+        h->NP = (long long)h->px * (h->ny + 2) * h->nz;
+        choose_march_grid(h);
+        h->nblk_step = (int)(h->mgrid.x * h->mgrid.y * h->mgrid.z);
+    } else {
+        StepArgs a;
+        a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
+        h->nblk_step = step_fp32_blocks(a);
+    }
     h->nblk_stats = 152 * 4;
     const long long npart = (long long)h->nblk_step * RED_N > (long long)h->nblk_stats * 8
                                 ? (long long)h->nblk_step * RED_N : (long long)h->nblk_stats * 8;
@@ -317,18 +509,35 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if ((st = dalloc_n(h, &h->dp, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->omega, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->mask, N)) != CL_OK) return fail(st);
-    if ((st = dalloc_n(h, &h->pop[0], 7 * N)) != CL_OK) return fail(st);
-    if ((st = dalloc_n(h, &h->pop[1], 7 * N)) != CL_OK) return fail(st);
-    if ((st = dalloc_n(h, &h->Csnap, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->fbuf, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->partials, npart)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->d_red, 16)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->d_plane, 5LL * h->nx)) != CL_OK) return fail(st);
+    if (h->march) {
+        for (int b = 0; b < 2; ++b) {
+            if ((st = dalloc_n(h, &h->st[b].chi, h->NP)) != CL_OK) return fail(st);
+            if ((st = dalloc(h, &h->st[b].clo, (size_t)h->el * h->NP)) != CL_OK) return fail(st);
+            for (int i = 0; i < 6; ++i)
+                if ((st = dalloc(h, &h->st[b].d[i], (size_t)h->el * h->NP)) != CL_OK) return fail(st);
+        }
+        if ((st = dalloc_n(h, &h->mask_p, h->NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->omega_p, h->NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->Csnap_p, h->NP)) != CL_OK) return fail(st);
+        if ((st = build_maps(h)) != CL_OK) return fail(st);
+        e = cudaMemsetAsync(h->mask_p, 0, sizeof(uint16_t) * h->NP, h->s);
+        if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
+    } else {
+        if ((st = dalloc_n(h, &h->pop[0], 7 * N)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->pop[1], 7 * N)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->Csnap, N)) != CL_OK) return fail(st);
+        e = cudaMemsetAsync(h->pop[0], 0, sizeof(float) * 7 * (size_t)N, h->s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)N, h->s);
+        if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
+    }
     e = cudaMallocHost(&h->h_red, sizeof(double) * (16 + 5 * (size_t)h->nx));
     if (e != cudaSuccess) { set_msg("cudaMallocHost", e); return fail(from_cuda(e)); }
-    e = cudaMemsetAsync(h->pop[0], 0, sizeof(float) * 7 * (size_t)N, h->s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)N, h->s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->mask, 0, sizeof(uint16_t) * (size_t)N, h->s);
+    e = cudaMemsetAsync(h->mask, 0, sizeof(uint16_t) * (size_t)N, h->s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
     if (e != cudaSuccess) { set_msg("initial memset", e); return fail(from_cuda(e)); }
     *out = h;
@@ -338,7 +547,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
 void cl_lbm_destroy(cl_handle h) {
     if (!h) return;
     drop_graphs(h);
-    if (h->s || true) cudaStreamSynchronize(h->s);
+    cudaStreamSynchronize(h->s);
     for (auto& pr : h->allocs) {
         if (h->p.free) h->p.free(pr.first, pr.second, (void*)h->s, h->p.alloc_ctx);
         else cudaFreeAsync(pr.first, h->s);
@@ -480,6 +689,10 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
             break;
         }
     }
+    if (h->march) {
+        cl_status es = check_err_flag(h);
+        if (es != CL_OK) result = es;
+    }
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return result;
@@ -529,22 +742,45 @@ cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, do
     return CL_OK;
 }
 
+static cl_status state_out(cl_lbm* h, float* C, float* g, int ptr_is_device) {
+    const size_t N = (size_t)h->N;
+    if (h->march) {
+        MarchArgs a = make_margs(h, h->cur);
+        if (ptr_is_device) {
+            CK(launch_state_out(h->p.storage, a, h->mask_p, C, g, h->s));
+        } else if (C) {
+            CK(launch_state_out(h->p.storage, a, h->mask_p, h->fbuf, nullptr, h->s));
+            CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * N, cudaMemcpyDeviceToHost, h->s));
+        } else {
+            void* tmp = nullptr;
+            CK(cudaMallocAsync(&tmp, sizeof(float) * 7 * N, h->s));
+            cudaError_t e = launch_state_out(h->p.storage, a, h->mask_p, nullptr, (float*)tmp, h->s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(g, tmp, sizeof(float) * 7 * N, cudaMemcpyDeviceToHost, h->s);
+            cudaFreeAsync(tmp, h->s);
+            if (e != cudaSuccess) { set_msg("populations", e); return from_cuda(e); }
+        }
+    } else {
+        if (C) {
+            float* dstp = ptr_is_device ? C : h->fbuf;
+            CK(launch_field_fp32(h->pop[h->cur], h->mask, h->N, dstp, h->s));
+            if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * N, cudaMemcpyDeviceToHost, h->s));
+        }
+        if (g) CK(cudaMemcpyAsync(g, h->pop[h->cur], sizeof(float) * 7 * N, kind_out(ptr_is_device), h->s));
+    }
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
 cl_status cl_lbm_get_field(cl_handle h, float* C, int ptr_is_device) {
     CKS(need_structure(h));
     if (!C) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
-    float* dstp = ptr_is_device ? C : h->fbuf;
-    CK(launch_field_fp32(h->pop[h->cur], h->mask, h->N, dstp, h->s));
-    if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * (size_t)h->N, cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    return CL_OK;
+    return state_out(h, C, nullptr, ptr_is_device);
 }
 
 cl_status cl_lbm_get_populations(cl_handle h, float* g, int ptr_is_device) {
     CKS(need_structure(h));
     if (!g) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
-    CK(cudaMemcpyAsync(g, h->pop[h->cur], sizeof(float) * 7 * (size_t)h->N, kind_out(ptr_is_device), h->s));
-    CK(cudaStreamSynchronize(h->s));
-    return CL_OK;
+    return state_out(h, nullptr, g, ptr_is_device);
 }
 
 cl_status cl_lbm_get_setup(cl_handle h, uint8_t* active, float* omega, int32_t* chord, uint16_t* link_mask,

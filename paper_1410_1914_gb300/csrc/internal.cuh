@@ -64,6 +64,8 @@ cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, 
 cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce,
                              cudaStream_t s);
 int step_fp32_blocks(const StepArgs& a);
+cudaError_t launch_absmax(const float* v, long long N, double* partials, int nblocks, double* out,
+                          cudaStream_t s);
 cudaError_t launch_finalize(const double* partials, int nblocks, int nslots, double* out,
                             cudaStream_t s);
 cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C,

@@ -2,6 +2,7 @@
 // reactive-diffusion LBM (arXiv:1410.1914, Sec. 2.1.3, Eq. 7-9, 19, 21-24).
 #include <math.h>
 
+#include "device_util.cuh"
 #include "internal.cuh"
 
 namespace cl {
@@ -12,37 +13,6 @@ __device__ __forceinline__ bool is_transport(uint8_t p, int ion) {
     return p == 0 || p == 3 || (p == 2 && ion);
 }
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
-
-template <int NV>
-__device__ __forceinline__ void warp_sum(double (&v)[NV]) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k)
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-}
-
-// Block-wide sum of NV doubles in a fixed order; thread 0 writes out[0..NV).
-// Requires blockDim a multiple of 32, at most 1024 threads.
-template <int NV>
-__device__ void block_sum_store(double (&v)[NV], double* out) {
-    __shared__ double sh[32][NV];
-    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
-    const int nthreads = blockDim.x * blockDim.y * blockDim.z;
-    const int lane = tid & 31, warp = tid >> 5, nwarps = (nthreads + 31) >> 5;
-    warp_sum<NV>(v);
-    if (lane == 0)
-#pragma unroll
-        for (int k = 0; k < NV; ++k) sh[warp][k] = v[k];
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) v[k] = lane < nwarps ? sh[lane][k] : 0.0;
-        warp_sum<NV>(v);
-        if (lane == 0)
-#pragma unroll
-            for (int k = 0; k < NV; ++k) out[k] = v[k];
-    }
-}
 
 // ------------------------------------------------------------ validation
 __global__ void k_validate(const uint8_t* __restrict__ phase, long long N, int* err) {
@@ -383,6 +353,27 @@ cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const doubl
                             cudaStream_t s) {
     k_stats<<<nblocks, 256, 0, s>>>(phase, mask, D, dp, N, nx, ion, partials);
     k_finalize<<<kStatN, 1024, 0, s>>>(partials, nblocks, kStatN, 1u << 6, out);
+    return cudaGetLastError();
+}
+
+__global__ void k_absmax(const float* __restrict__ v, long long N, double* partials) {
+    double m = 0.0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        m = fmax(m, fabs((double)v[c]));
+    __shared__ double sh[1024];
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + w]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+cudaError_t launch_absmax(const float* v, long long N, double* partials, int nblocks, double* out, cudaStream_t s) {
+    k_absmax<<<nblocks, 256, 0, s>>>(v, N, partials);
+    k_finalize<<<1, 1024, 0, s>>>(partials, nblocks, 1, 1u, out);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,566 @@
+// z-marching fused D3Q7 collide-stream kernel on the (C, delta) state.
+//
+// State per active cell after step t (post-collision, Eq. 21 with the
+// equilibrium w_i C of Eq. 23):
+//     g*_i = w_i C + delta_i,   i = 1..6,   delta_0 = -(delta_1 + ... + delta_6)
+// C is kept as an unevaluated sum hi + lo of two floats (hi f32; lo f32, or
+// f16 scaled by s_lo), the deviations as f32 (or f16 scaled by s_d).  Every
+// arithmetic step works on small quantities: with a_i the incoming
+// population minus w C(x),
+//     open face:   a_i = w (C(x - c_i) - C(x)) + delta_i(x - c_i)
+//     wall:        a_i = r delta_opp(x) - (1 - r) w C(x)      (r = 1 inert,
+//                  (2w - k)/(2w + k) catalytic; the half-way first-order sink)
+//     Dirichlet:   a_i = 2 w (C_bc - C(x)) - delta_opp(x)     (anti-bounce-back)
+//     zero flux:   a_i = delta_opp(x)
+//     dC = sum_i a_i + delta_0(x),  C' = C + dC,
+//     delta'_i = (1 - omega) (a_i - w dC)
+// which is the BGK step of Eq. 21 rewritten exactly; C' is accumulated in
+// double-float so that increments far below ulp(C) are not lost.
+//
+// Each thread block owns a BX x BY column of cells and marches along z
+// through a chunk of planes.  Planes are staged into shared memory by TMA
+// (cp.async.bulk.tensor.3d) into a ring of S slots guarded by mbarriers;
+// the producer thread keeps S - 2 planes in flight.  Arrays carry two ghost
+// rows (copies of rows ny-1 and 0 above and below) so the y-halo of a tile
+// is one in-bounds box; x-halo columns come from 16-byte boxes just left and
+// right of the tile.  Outputs go straight to global memory.
+#include <cuda.h>
+#include <math.h>
+
+#include "device_util.cuh"
+#include "internal.cuh"
+#include "march.cuh"
+
+namespace cl {
+
+// ------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for one phase of an mbarrier; gives up after ~1 s of SM clock and
+// raises bit 8 of the error word instead of spinning forever.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            atomicOr(err, 8);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// ------------------------------------------------------- storage formats
+struct StoreF32 {
+    using T = float;
+    static __device__ __forceinline__ float ld(T v, float inv) { return v; }
+    static __device__ __forceinline__ T st(float v, float s) { return v; }
+};
+struct StoreF16 {
+    using T = __half;
+    static __device__ __forceinline__ float ld(T v, float inv) { return __half2float(v) * inv; }
+    static __device__ __forceinline__ T st(float v, float s) { return __float2half_rn(v * s); }
+};
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// (hi, lo) + d, renormalised
+__device__ __forceinline__ void df_add(float hi, float lo, float d, float& ho, float& lo_out) {
+    float s, e;
+    two_sum(hi, d, s, e);
+    e += lo;
+    ho = s + e;
+    lo_out = e - (ho - s);
+}
+
+// ------------------------------------------------------- shared layout
+template <class S>
+struct SlotLayout {
+    using T = typename S::T;
+    static constexpr int EL = sizeof(T);
+    static constexpr int HXL = 16 / EL;  // width of a 16-byte x-halo box in elements of T
+    static constexpr int HXF = 4;        // same for f32 arrays
+    static constexpr int R2 = kBY + 2;
+    static constexpr int al(int b) { return (b + 127) & ~127; }
+    static constexpr int o_chi = 0;
+    static constexpr int o_clo = o_chi + al(R2 * kBX * 4);
+    static constexpr int o_d3 = o_clo + al(R2 * kBX * EL);
+    static constexpr int o_d4 = o_d3 + al(R2 * kBX * EL);
+    static constexpr int o_d1 = o_d4 + al(R2 * kBX * EL);
+    static constexpr int o_d2 = o_d1 + al(kBY * kBX * EL);
+    static constexpr int o_d5 = o_d2 + al(kBY * kBX * EL);
+    static constexpr int o_d6 = o_d5 + al(kBY * kBX * EL);
+    static constexpr int o_om = o_d6 + al(kBY * kBX * EL);
+    static constexpr int o_mk = o_om + al(kBY * kBX * 4);
+    static constexpr int o_chiL = o_mk + al(kBY * kBX * 2);
+    static constexpr int o_chiR = o_chiL + al(kBY * HXF * 4);
+    static constexpr int o_cloL = o_chiR + al(kBY * HXF * 4);
+    static constexpr int o_cloR = o_cloL + al(kBY * HXL * EL);
+    static constexpr int o_d1L = o_cloR + al(kBY * HXL * EL);
+    static constexpr int o_d2R = o_d1L + al(kBY * HXL * EL);
+    static constexpr int bytes = o_d2R + al(kBY * HXL * EL);
+    // bytes delivered by the TMA loads of one plane (full boxes)
+    static constexpr uint32_t tx = R2 * kBX * 4 + 3 * R2 * kBX * EL + 4 * kBY * kBX * EL + kBY * kBX * 4 +
+                                   kBY * kBX * 2 + 2 * kBY * HXF * 4 + 4 * kBY * HXL * EL;
+};
+
+int march_slot_bytes(int storage) {
+    return storage == CL_STORE_FP16DEV ? SlotLayout<StoreF16>::bytes : SlotLayout<StoreF32>::bytes;
+}
+
+int march_smem_bytes(int storage) { return 256 + kStages * march_slot_bytes(storage); }
+
+// ------------------------------------------------------------- the kernel
+template <class S, bool REDUCE>
+__global__ void __launch_bounds__(kBX* kBY) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
+    using T = typename S::T;
+    using L = SlotLayout<S>;
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(base);
+    unsigned char* slots = base + 128;
+
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = tx + kBX * ty;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
+    const int x = x0 + tx, y = y0 + ty;
+    const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
+    const int zs = blockIdx.z * a.z_chunk;
+    const int ze = min(nz, zs + a.z_chunk);
+    const int nplanes = (ze - zs) + 2;  // zs-1 .. ze
+    const bool valid = x < nx && y < ny;
+    const long long pstride = (long long)px * (ny + 2);
+
+    double rv[RED_N];
+    if (REDUCE)
+#pragma unroll
+        for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    auto issue = [&](int k) {  // plane number k of this block's sequence
+        const int s = k % kStages;
+        unsigned char* sl = slots + s * L::bytes;
+        int z = zs - 1 + k;
+        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+        uint64_t* bar = &bars[s];
+        fence_proxy_async();
+        mbar_expect_tx(bar, L::tx);
+        tma_load_3d(sl + L::o_chi, &maps.chi, bar, x0, y0, z);
+        tma_load_3d(sl + L::o_clo, &maps.clo, bar, x0, y0, z);
+        tma_load_3d(sl + L::o_d3, &maps.d3, bar, x0, y0, z);
+        tma_load_3d(sl + L::o_d4, &maps.d4, bar, x0, y0, z);
+        tma_load_3d(sl + L::o_d1, &maps.d1, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_d2, &maps.d2, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_d5, &maps.d5, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_d6, &maps.d6, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_om, &maps.om, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_mk, &maps.mk, bar, x0, y0 + 1, z);
+        tma_load_3d(sl + L::o_chiL, &maps.chi_h, bar, x0 - L::HXF, y0 + 1, z);
+        tma_load_3d(sl + L::o_chiR, &maps.chi_h, bar, x0 + kBX, y0 + 1, z);
+        tma_load_3d(sl + L::o_cloL, &maps.clo_h, bar, x0 - L::HXL, y0 + 1, z);
+        tma_load_3d(sl + L::o_cloR, &maps.clo_h, bar, x0 + kBX, y0 + 1, z);
+        tma_load_3d(sl + L::o_d1L, &maps.d1_h, bar, x0 - L::HXL, y0 + 1, z);
+        tma_load_3d(sl + L::o_d2R, &maps.d2_h, bar, x0 + kBX, y0 + 1, z);
+    };
+
+    int issued = 0, waited = 1;  // planes issued; highest plane index waited for
+    if (tid == 0)
+        for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
+
+    bool ok = true;
+    ok &= mbar_wait_bounded(&bars[0], 0, a.err);  // plane zs-1
+    ok &= mbar_wait_bounded(&bars[1 % kStages], (1 / kStages) & 1, a.err);  // plane zs
+
+    const float w = kW1;
+    const float inv_lo = a.inv_lo, inv_d = a.inv_d, s_lo = a.s_lo, s_d = a.s_d;
+    const int r_own = (ty + 1) * kBX + tx;  // ghosted arrays
+    const int r_plain = ty * kBX + tx;       // plain arrays
+
+    for (int z = zs; z < ze; ++z) {
+        const int k = z - zs + 1;  // sequence number of plane z
+        ok &= mbar_wait_bounded(&bars[(k + 1) % kStages], ((k + 1) / kStages) & 1, a.err);
+        waited = k + 1;
+        const unsigned char* sc = slots + (k % kStages) * L::bytes;
+        const unsigned char* sm = slots + ((k - 1) % kStages) * L::bytes;
+        const unsigned char* sp = slots + ((k + 1) % kStages) * L::bytes;
+        const int gz = z;
+        const uint16_t m = valid ? reinterpret_cast<const uint16_t*>(sc + L::o_mk)[r_plain] : 0;
+        if (m & kActiveBit) {
+            const float* chi_c = reinterpret_cast<const float*>(sc + L::o_chi);
+            const T* clo_c = reinterpret_cast<const T*>(sc + L::o_clo);
+            const float hx = chi_c[r_own];
+            const float lx = S::ld(clo_c[r_own], inv_lo);
+            const float Cx = hx + lx;
+            float dd[6];
+            dd[0] = S::ld(reinterpret_cast<const T*>(sc + L::o_d1)[r_plain], inv_d);
+            dd[1] = S::ld(reinterpret_cast<const T*>(sc + L::o_d2)[r_plain], inv_d);
+            dd[2] = S::ld(reinterpret_cast<const T*>(sc + L::o_d3)[r_own], inv_d);
+            dd[3] = S::ld(reinterpret_cast<const T*>(sc + L::o_d4)[r_own], inv_d);
+            dd[4] = S::ld(reinterpret_cast<const T*>(sc + L::o_d5)[r_plain], inv_d);
+            dd[5] = S::ld(reinterpret_cast<const T*>(sc + L::o_d6)[r_plain], inv_d);
+            const float om = reinterpret_cast<const float*>(sc + L::o_om)[r_plain];
+            const float rf = a.rfac;
+            float av[6];
+            // wall / boundary value of the population arriving through closed face `bit`,
+            // whose own opposite deviation is `dopp`
+            auto closed_val = [&](float dopp, int face_bit) -> float {
+                const float r = (m & (1u << (kReactShift + face_bit))) ? rf : 1.0f;
+                return r * dopp - (1.0f - r) * w * Cx;
+            };
+            // i = 1 (+x), from x-1 through face -x (bit 1); opposite deviation delta_2
+            if (!(m & 2u)) {
+                float hn, ln, dn;
+                if (tx > 0) {
+                    hn = chi_c[r_own - 1];
+                    ln = S::ld(clo_c[r_own - 1], inv_lo);
+                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d1)[r_plain - 1], inv_d);
+                } else {
+                    hn = reinterpret_cast<const float*>(sc + L::o_chiL)[ty * L::HXF + L::HXF - 1];
+                    ln = S::ld(reinterpret_cast<const T*>(sc + L::o_cloL)[ty * L::HXL + L::HXL - 1], inv_lo);
+                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d1L)[ty * L::HXL + L::HXL - 1], inv_d);
+                }
+                av[0] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else if (x == 0) {
+                av[0] = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dd[1] : dd[1];
+            } else {
+                av[0] = closed_val(dd[1], 1);
+            }
+            // i = 2 (-x), from x+1 through face +x (bit 0); opposite delta_1
+            if (!(m & 1u)) {
+                float hn, ln, dn;
+                if (tx < kBX - 1) {
+                    hn = chi_c[r_own + 1];
+                    ln = S::ld(clo_c[r_own + 1], inv_lo);
+                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d2)[r_plain + 1], inv_d);
+                } else {
+                    hn = reinterpret_cast<const float*>(sc + L::o_chiR)[ty * L::HXF];
+                    ln = S::ld(reinterpret_cast<const T*>(sc + L::o_cloR)[ty * L::HXL], inv_lo);
+                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d2R)[ty * L::HXL], inv_d);
+                }
+                av[1] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else if (x == nx - 1) {
+                av[1] = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dd[0] : dd[0];
+            } else {
+                av[1] = closed_val(dd[0], 0);
+            }
+            // i = 3 (+y), from y-1 through face -y (bit 3); opposite delta_4
+            if (!(m & 8u)) {
+                const float hn = chi_c[r_own - kBX];
+                const float ln = S::ld(clo_c[r_own - kBX], inv_lo);
+                const float dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d3)[r_own - kBX], inv_d);
+                av[2] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else {
+                av[2] = closed_val(dd[3], 3);
+            }
+            // i = 4 (-y), from y+1 through face +y (bit 2); opposite delta_3
+            if (!(m & 4u)) {
+                const float hn = chi_c[r_own + kBX];
+                const float ln = S::ld(clo_c[r_own + kBX], inv_lo);
+                const float dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d4)[r_own + kBX], inv_d);
+                av[3] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else {
+                av[3] = closed_val(dd[2], 2);
+            }
+            // i = 5 (+z), from z-1 through face -z (bit 5); opposite delta_6
+            if (!(m & 32u)) {
+                const float hn = reinterpret_cast<const float*>(sm + L::o_chi)[r_own];
+                const float ln = S::ld(reinterpret_cast<const T*>(sm + L::o_clo)[r_own], inv_lo);
+                const float dn = S::ld(reinterpret_cast<const T*>(sm + L::o_d5)[r_plain], inv_d);
+                av[4] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else {
+                av[4] = closed_val(dd[5], 5);
+            }
+            // i = 6 (-z), from z+1 through face +z (bit 4); opposite delta_5
+            if (!(m & 16u)) {
+                const float hn = reinterpret_cast<const float*>(sp + L::o_chi)[r_own];
+                const float ln = S::ld(reinterpret_cast<const T*>(sp + L::o_clo)[r_own], inv_lo);
+                const float dn = S::ld(reinterpret_cast<const T*>(sp + L::o_d6)[r_plain], inv_d);
+                av[5] = w * ((hn - hx) + (ln - lx)) + dn;
+            } else {
+                av[5] = closed_val(dd[4], 4);
+            }
+
+            const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
+                             ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
+            float hnew, lnew;
+            df_add(hx, lx, dC, hnew, lnew);
+            const float om1 = 1.0f - om;
+            float dn[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
+
+            // stores (padded, ghosted layout)
+            const long long gi = x + (long long)px * (y + 1) + pstride * gz;
+            a.chi[gi] = hnew;
+            T* clo = reinterpret_cast<T*>(a.clo);
+            clo[gi] = S::st(lnew, s_lo);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) reinterpret_cast<T*>(a.d[i])[gi] = S::st(dn[i], s_d);
+            if (y == ny - 1) {  // ghost row above row 0
+                const long long gg = x + pstride * gz;
+                a.chi[gg] = hnew;
+                clo[gg] = S::st(lnew, s_lo);
+                reinterpret_cast<T*>(a.d[2])[gg] = S::st(dn[2], s_d);
+            }
+            if (y == 0) {  // ghost row below row ny-1
+                const long long gg = x + (long long)px * (ny + 1) + pstride * gz;
+                a.chi[gg] = hnew;
+                clo[gg] = S::st(lnew, s_lo);
+                reinterpret_cast<T*>(a.d[3])[gg] = S::st(dn[3], s_d);
+            }
+            if (REDUCE) {
+                const double Cn = (double)hnew + (double)lnew;
+                if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
+                    rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
+                if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET)
+                    rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
+                const unsigned rb = (m >> kReactShift) & 0x3fu;
+                if (rb) {
+                    double r = 0.0;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d)
+                        if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
+                    rv[RED_R] += (1.0 - (double)rf) * r;
+                }
+                rv[RED_SUMC] += Cn;
+                rv[RED_DC] += fabs(Cn - (double)a.Csnap[gi]);
+                rv[RED_ABSC] += fabs(Cn);
+                rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
+                a.Csnap[gi] = (float)Cn;
+            }
+        }
+        // every thread is done with plane z-1's slot before it is refilled
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        if (tid == 0 && issued < nplanes) {
+            issue(issued);
+            ++issued;
+        }
+    }
+    if (!ok && tid == 0) {
+        // let copies still in flight land before the block's shared memory is released
+        for (int k = waited + 1; k < issued; ++k) mbar_wait_bounded(&bars[k % kStages], (k / kStages) & 1, a.err);
+    }
+    if (REDUCE) {
+        const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        block_sum_store<RED_N>(rv, a.partials + blk * RED_N);
+    }
+}
+
+// ----------------------------------------------------------- host launch
+template <class S, bool R>
+static cudaError_t launch_one(const MarchMaps& maps, const MarchArgs& a, dim3 grid, int smem, cudaStream_t s) {
+    static bool attr_set = false;  // per template instance
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_march<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    k_march<S, R><<<grid, dim3(kBX, kBY, 1), smem, s>>>(maps, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
+                         cudaStream_t s) {
+    const int smem = march_smem_bytes(storage);
+    if (storage == CL_STORE_FP16DEV)
+        return reduce ? launch_one<StoreF16, true>(maps, a, grid, smem, s)
+                      : launch_one<StoreF16, false>(maps, a, grid, smem, s);
+    return reduce ? launch_one<StoreF32, true>(maps, a, grid, smem, s)
+                  : launch_one<StoreF32, false>(maps, a, grid, smem, s);
+}
+
+int march_blocks_per_sm(int storage) {
+    const int smem = march_smem_bytes(storage);
+    int nb = 0;
+    if (storage == CL_STORE_FP16DEV) {
+        cudaFuncSetAttribute(k_march<StoreF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF16, true>, kBX * kBY, smem);
+    } else {
+        cudaFuncSetAttribute(k_march<StoreF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF32, true>, kBX * kBY, smem);
+    }
+    return nb > 0 ? nb : 1;
+}
+
+// ====================================================== state utilities
+// Stored row yr in [0, ny+2) -> actual row (ghost rows wrap).
+__device__ __forceinline__ int actual_row(int yr, int ny) { return yr == 0 ? ny - 1 : (yr == ny + 1 ? 0 : yr - 1); }
+
+template <class S>
+__global__ void k_state_init(MarchArgs a, const uint16_t* __restrict__ mask_p, const float* __restrict__ C0) {
+    using T = typename S::T;
+    const long long pstride = (long long)a.px * (a.ny + 2);
+    const long long total = pstride * a.nz;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(gi % a.px);
+        const int yr = (int)((gi / a.px) % (a.ny + 2));
+        const int z = (int)(gi / pstride);
+        const int y = actual_row(yr, a.ny);
+        const long long gm = x + (long long)a.px * (y + 1) + pstride * z;  // owner's slot
+        float hi = 0.f, lo = 0.f;
+        if (x < a.nx && (mask_p[gm] & kActiveBit)) {
+            double C;
+            if (C0) C = C0[x + (long long)a.nx * (y + (long long)a.ny * z)];
+            else C = (double)a.c_in + ((double)a.c_out - (double)a.c_in) * (x + 0.5) / a.nx;
+            hi = (float)C;
+            lo = (float)(C - (double)hi);
+        }
+        a.chi[gi] = hi;
+        reinterpret_cast<T*>(a.clo)[gi] = S::st(lo, a.s_lo);
+        for (int i = 0; i < 6; ++i) reinterpret_cast<T*>(a.d[i])[gi] = S::st(0.f, a.s_d);
+        if (a.Csnap) a.Csnap[gi] = hi + lo;
+    }
+}
+
+// unpadded outputs: C (N floats) and/or g* (7 x N floats)
+template <class S>
+__global__ void k_state_out(MarchArgs a, const uint16_t* __restrict__ mask_p, float* __restrict__ C,
+                            float* __restrict__ g) {
+    using T = typename S::T;
+    const long long N = (long long)a.nx * a.ny * a.nz;
+    const long long pstride = (long long)a.px * (a.ny + 2);
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(c % a.nx), y = (int)((c / a.nx) % a.ny), z = (int)(c / ((long long)a.nx * a.ny));
+        const long long gi = x + (long long)a.px * (y + 1) + pstride * z;
+        const bool act = (mask_p[gi] & kActiveBit) != 0;
+        float Cv = 0.f, d[6] = {0, 0, 0, 0, 0, 0};
+        if (act) {
+            Cv = a.chi[gi] + S::ld(reinterpret_cast<const T*>(a.clo)[gi], a.inv_lo);
+            for (int i = 0; i < 6; ++i) d[i] = S::ld(reinterpret_cast<const T*>(a.d[i])[gi], a.inv_d);
+        }
+        if (C) C[c] = Cv;
+        if (g) {
+            const float d0 = -(((d[0] + d[1]) + (d[2] + d[3])) + (d[4] + d[5]));
+            g[c] = act ? kW0 * Cv + d0 : 0.f;
+            for (int i = 0; i < 6; ++i) g[(long long)(i + 1) * N + c] = act ? kW1 * Cv + d[i] : 0.f;
+        }
+    }
+}
+
+// per-plane readouts (one block per x-plane): sum C, count, R, J_in part, J_out part
+template <class S>
+__global__ void k_state_readout(MarchArgs a, const uint16_t* __restrict__ mask_p, double* out) {
+    using T = typename S::T;
+    const int x = blockIdx.x;
+    const long long nyz = (long long)a.ny * a.nz;
+    const long long pstride = (long long)a.px * (a.ny + 2);
+    const double w = kW1;
+    double v[5] = {0, 0, 0, 0, 0};
+    for (long long j = threadIdx.x; j < nyz; j += blockDim.x) {
+        const int y = (int)(j % a.ny), z = (int)(j / a.ny);
+        const long long gi = x + (long long)a.px * (y + 1) + pstride * z;
+        const uint16_t m = mask_p[gi];
+        if (!(m & kActiveBit)) continue;
+        const double C = (double)a.chi[gi] + (double)S::ld(reinterpret_cast<const T*>(a.clo)[gi], a.inv_lo);
+        double d[6];
+        for (int i = 0; i < 6; ++i) d[i] = S::ld(reinterpret_cast<const T*>(a.d[i])[gi], a.inv_d);
+        v[0] += C;
+        v[1] += 1.0;
+        const unsigned rb = (m >> kReactShift) & 0x3fu;
+        double r = 0.0;
+        for (int dd = 0; dd < 6; ++dd)
+            if (rb & (1u << dd)) r += w * C + d[dd];
+        v[2] += (1.0 - (double)a.rfac) * r;
+        if (x == 0 && a.bc_in == CL_BC_DIRICHLET) v[3] += 2.0 * w * ((double)a.c_in - C) - 2.0 * d[1];
+        if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) v[4] += 2.0 * w * (C - (double)a.c_out) + 2.0 * d[0];
+    }
+    block_sum_store<5>(v, out + 5LL * x);
+}
+
+cudaError_t launch_state_init(int storage, const MarchArgs& a, const uint16_t* mask_p, const float* C0,
+                              cudaStream_t s) {
+    if (storage == CL_STORE_FP16DEV) k_state_init<StoreF16><<<152 * 8, 256, 0, s>>>(a, mask_p, C0);
+    else k_state_init<StoreF32><<<152 * 8, 256, 0, s>>>(a, mask_p, C0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_out(int storage, const MarchArgs& a, const uint16_t* mask_p, float* C, float* g,
+                             cudaStream_t s) {
+    if (storage == CL_STORE_FP16DEV) k_state_out<StoreF16><<<152 * 8, 256, 0, s>>>(a, mask_p, C, g);
+    else k_state_out<StoreF32><<<152 * 8, 256, 0, s>>>(a, mask_p, C, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_readout(int storage, const MarchArgs& a, const uint16_t* mask_p, double* out,
+                                 cudaStream_t s) {
+    if (storage == CL_STORE_FP16DEV) k_state_readout<StoreF16><<<a.nx, 256, 0, s>>>(a, mask_p, out);
+    else k_state_readout<StoreF32><<<a.nx, 256, 0, s>>>(a, mask_p, out);
+    return cudaGetLastError();
+}
+
+// unpadded -> padded (ghosted) copy of the static per-cell arrays
+__global__ void k_pad_static(const uint16_t* __restrict__ mask, const float* __restrict__ omega, int nx, int ny,
+                             int nz, int px, uint16_t* __restrict__ mask_p, float* __restrict__ omega_p) {
+    const long long pstride = (long long)px * (ny + 2);
+    const long long total = pstride * nz;
+    for (long long gi = blockIdx.x * (long long)blockDim.x + threadIdx.x; gi < total;
+         gi += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(gi % px);
+        const int yr = (int)((gi / px) % (ny + 2));
+        const int z = (int)(gi / pstride);
+        const int y = actual_row(yr, ny);
+        uint16_t m = 0;
+        float o = 0.f;
+        if (x < nx) {
+            const long long c = x + (long long)nx * (y + (long long)ny * z);
+            m = mask[c];
+            o = omega[c];
+        }
+        mask_p[gi] = m;
+        omega_p[gi] = o;
+    }
+}
+
+cudaError_t launch_pad_static(const uint16_t* mask, const float* omega, int nx, int ny, int nz, int px,
+                              uint16_t* mask_p, float* omega_p, cudaStream_t s) {
+    k_pad_static<<<152 * 8, 256, 0, s>>>(mask, omega, nx, ny, nz, px, mask_p, omega_p);
+    return cudaGetLastError();
+}
+
+}  // namespace cl

@@ -1,0 +1,50 @@
+// z-marching (C, delta) kernel: shared declarations.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cl {
+
+constexpr int kBX = 32;     // tile width in x (one warp)
+constexpr int kBY = 8;      // tile height in y (warps per block)
+constexpr int kStages = 5;  // planes resident per block: z-1, z, z+1 and two in flight
+
+// TMA descriptors of one source time level (main boxes and 16-byte x-halo boxes)
+struct MarchMaps {
+    CUtensorMap chi, clo, d1, d2, d3, d4, d5, d6, om, mk;
+    CUtensorMap chi_h, clo_h, d1_h, d2_h;
+};
+
+struct MarchArgs {
+    int nx, ny, nz, px;  // px: padded row pitch (multiple of kBX)
+    int z_chunk;         // planes per block
+    // destination time level (padded, two ghost rows per plane)
+    float* chi;
+    void* clo;
+    void* d[6];
+    float rfac;
+    float c_in, c_out;
+    int bc_in, bc_out;
+    float s_lo, inv_lo, s_d, inv_d;  // FP16 scales (1 for FP32 storage)
+    float* Csnap;
+    double* partials;
+    int* err;
+};
+
+int march_slot_bytes(int storage);
+int march_smem_bytes(int storage);
+int march_blocks_per_sm(int storage);
+cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
+                         cudaStream_t s);
+cudaError_t launch_state_init(int storage, const MarchArgs& a, const uint16_t* mask_p, const float* C0,
+                              cudaStream_t s);
+cudaError_t launch_state_out(int storage, const MarchArgs& a, const uint16_t* mask_p, float* C, float* g,
+                             cudaStream_t s);
+cudaError_t launch_state_readout(int storage, const MarchArgs& a, const uint16_t* mask_p, double* out,
+                                 cudaStream_t s);
+cudaError_t launch_pad_static(const uint16_t* mask, const float* omega, int nx, int ny, int nz, int px,
+                              uint16_t* mask_p, float* omega_p, cudaStream_t s);
+
+}  // namespace cl

@@ -5,7 +5,7 @@ import numpy as np
 
 from . import _lib as L
 
-_STORAGE = {"fp32": L.CL_STORE_FP32, "fp16dev": L.CL_STORE_FP16DEV}
+_STORAGE = {"fp32": L.CL_STORE_FP32, "fp16dev": L.CL_STORE_FP16DEV, "fp32pop": L.CL_STORE_FP32POP}
 
 
 class Solver:
