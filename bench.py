@@ -38,15 +38,15 @@ WORKLOAD_DESC = ("256^3 Pt catalyst layer, 2 nm voxels, seeded QSGS (pore 0.45, 
                  "reservoir plane + fixed C inlet, zero-flux outlet, periodic y,z")
 
 
-def bytes_per_cell(storage: str) -> tuple[float, float]:
-    """Algorithmic DRAM bytes of one fused step: (per active cell, per box cell).
-
-    Active cell: 7 populations read + 7 written (4 B each) + omega (4 B);
-    every box cell: its 2 B link mask."""
-    if storage == "fp32":
-        return 7 * 4 * 2 + 4, 2
-    # C (4 B) + 6 deviations (2 B) read and written, omega 4 B
-    return (4 + 6 * 2) * 2 + 4, 2
+def bytes_per_cell(storage: str) -> float:
+    """Algorithmic DRAM bytes of one fused step per box cell: the cell's state
+    read once and written once, plus its relaxation rate (f32, 4 B) and link
+    mask (u16, 2 B).
+      fp32     C as two f32 + 6 f32 deviations: 32 B state -> 2*32 + 6 = 70 B
+      fp16dev  C f32 + f16 low word + 6 f16 deviations: 18 B -> 2*18 + 6 = 42 B
+      fp32pop  7 f32 populations: 28 B -> 2*28 + 6 = 62 B"""
+    state = {"fp32": 32, "fp16dev": 18, "fp32pop": 28}[storage]
+    return 2 * state + 6
 
 
 class ClockSampler:
@@ -174,7 +174,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16dev"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16dev", "fp32pop"])
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-lbm-steps", type=int, default=1000)
@@ -243,8 +243,7 @@ def main():
     ms_per_step = elapsed_ms / args.steps
 
     # roofline of the fused step kernel (average launch = interval time / K)
-    per_active, per_cell = bytes_per_cell(args.storage)
-    launch_bytes = per_active * info["n_active"] + per_cell * n_cells
+    launch_bytes = bytes_per_cell(args.storage) * n_cells
     launch_s = ms_per_step * 1e-3 / K
     peak, peak_kind = measured_peak_gbs()
     achieved = launch_bytes / launch_s / 1e9
@@ -283,7 +282,8 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_kind": f"{peak_kind} hbm_gbs",
-                     "algorithmic_bytes_per_launch": launch_bytes, "kernel": "k_step_fp32"},
+                     "algorithmic_bytes_per_launch": launch_bytes,
+                     "kernel": "k_step_fp32" if args.storage == "fp32pop" else "k_march"},
         "gpu_launches": args.steps * (K + 1),
         "clocks": clocks.summary(),
         "e2e": e2e,

@@ -150,24 +150,32 @@ int march_slot_bytes(int storage) {
 int march_smem_bytes(int storage) { return 256 + kStages * march_slot_bytes(storage); }
 
 // ------------------------------------------------------------- the kernel
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Warp roles: warps 0..kBY-1 each own one row of the tile and compute; warp
+// kBY is the producer and issues the TMA loads of one plane per slot.
+// full[s] completes when a plane has landed in slot s; empty[s] when all
+// consumer warps have released it.  A consumer keeps the z-1 values it needs
+// (its own previous cell) in registers, so a slot is live only while its
+// plane is the current one or the next one.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kBX* kBY) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
     using T = typename S::T;
     using L = SlotLayout<S>;
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(base);
+    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    uint64_t* empty = full + kStages;
     unsigned char* slots = base + 128;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = tx + kBX * ty;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
-    const int x = x0 + tx, y = y0 + ty;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
     const int zs = blockIdx.z * a.z_chunk;
     const int ze = min(nz, zs + a.z_chunk);
     const int nplanes = (ze - zs) + 2;  // zs-1 .. ze
-    const bool valid = x < nx && y < ny;
     const long long pstride = (long long)px * (ny + 2);
 
     double rv[RED_N];
@@ -175,214 +183,186 @@ __global__ void __launch_bounds__(kBX* kBY) k_march(const __grid_constant__ Marc
 #pragma unroll
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
 
-    if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+    if (tx == 0 && ty == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kBY);
+        }
         fence_mbar_init();
     }
     __syncthreads();
 
-    auto issue = [&](int k) {  // plane number k of this block's sequence
-        const int s = k % kStages;
-        unsigned char* sl = slots + s * L::bytes;
-        int z = zs - 1 + k;
-        z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-        uint64_t* bar = &bars[s];
-        fence_proxy_async();
-        mbar_expect_tx(bar, L::tx);
-        tma_load_3d(sl + L::o_chi, &maps.chi, bar, x0, y0, z);
-        tma_load_3d(sl + L::o_clo, &maps.clo, bar, x0, y0, z);
-        tma_load_3d(sl + L::o_d3, &maps.d3, bar, x0, y0, z);
-        tma_load_3d(sl + L::o_d4, &maps.d4, bar, x0, y0, z);
-        tma_load_3d(sl + L::o_d1, &maps.d1, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_d2, &maps.d2, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_d5, &maps.d5, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_d6, &maps.d6, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_om, &maps.om, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_mk, &maps.mk, bar, x0, y0 + 1, z);
-        tma_load_3d(sl + L::o_chiL, &maps.chi_h, bar, x0 - L::HXF, y0 + 1, z);
-        tma_load_3d(sl + L::o_chiR, &maps.chi_h, bar, x0 + kBX, y0 + 1, z);
-        tma_load_3d(sl + L::o_cloL, &maps.clo_h, bar, x0 - L::HXL, y0 + 1, z);
-        tma_load_3d(sl + L::o_cloR, &maps.clo_h, bar, x0 + kBX, y0 + 1, z);
-        tma_load_3d(sl + L::o_d1L, &maps.d1_h, bar, x0 - L::HXL, y0 + 1, z);
-        tma_load_3d(sl + L::o_d2R, &maps.d2_h, bar, x0 + kBX, y0 + 1, z);
-    };
+    if (ty == kBY) {
+        // ------------------------------------------------------ producer
+        if (tx == 0) {
+            int k = 0;
+            bool ok = true;
+            for (; k < nplanes && ok; ++k) {
+                const int s = k % kStages, u = k / kStages;
+                if (u > 0) ok = mbar_wait_bounded(&empty[s], (u - 1) & 1, a.err);
+                if (!ok) break;
+                unsigned char* sl = slots + s * L::bytes;
+                int z = zs - 1 + k;
+                z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+                uint64_t* bar = &full[s];
+                fence_proxy_async();
+                mbar_expect_tx(bar, L::tx);
+                tma_load_3d(sl + L::o_chi, &maps.chi, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_clo, &maps.clo, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d3, &maps.d3, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d4, &maps.d4, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d1, &maps.d1, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d2, &maps.d2, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d5, &maps.d5, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d6, &maps.d6, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_om, &maps.om, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_mk, &maps.mk, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_chiL, &maps.chi_h, bar, x0 - L::HXF, y0 + 1, z);
+                tma_load_3d(sl + L::o_chiR, &maps.chi_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_cloL, &maps.clo_h, bar, x0 - L::HXL, y0 + 1, z);
+                tma_load_3d(sl + L::o_cloR, &maps.clo_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_d1L, &maps.d1_h, bar, x0 - L::HXL, y0 + 1, z);
+                tma_load_3d(sl + L::o_d2R, &maps.d2_h, bar, x0 + kBX, y0 + 1, z);
+            }
+            if (!ok) {
+                // the loads still in flight land before shared memory is released
+                for (int j = k - 1; j >= 0 && j >= k - kStages; --j)
+                    mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, a.err);
+            }
+        }
+    } else {
+        // ------------------------------------------------------ consumers
+        const int x = x0 + tx, y = y0 + ty;
+        const bool valid = x < nx && y < ny;
+        const int r_own = (ty + 1) * kBX + tx;  // ghosted arrays
+        const int r_plain = ty * kBX + tx;       // plain arrays
+        const float w = kW1;
+        const float inv_lo = a.inv_lo, inv_d = a.inv_d, s_lo = a.s_lo, s_d = a.s_d;
+        const float rf = a.rfac;
+        const bool lane_l = tx == 0, lane_r = tx == kBX - 1;
+        // addresses of the x-neighbour values: row neighbours or halo boxes
+        const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (r_own - 1);
+        const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (r_own + 1);
+        const int xl_lo = lane_l ? L::o_cloL + L::EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + L::EL * (r_own - 1);
+        const int xr_lo = lane_r ? L::o_cloR + L::EL * (ty * L::HXL) : L::o_clo + L::EL * (r_own + 1);
+        const int xl_d1 = lane_l ? L::o_d1L + L::EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + L::EL * (r_plain - 1);
+        const int xr_d2 = lane_r ? L::o_d2R + L::EL * (ty * L::HXL) : L::o_d2 + L::EL * (r_plain + 1);
 
-    int issued = 0, waited = 1;  // planes issued; highest plane index waited for
-    if (tid == 0)
-        for (; issued < kStages && issued < nplanes; ++issued) issue(issued);
+        auto ldf = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
+        auto ldt = [&](const unsigned char* sl, int off, float inv) {
+            return S::ld(*reinterpret_cast<const T*>(sl + off), inv);
+        };
 
-    bool ok = true;
-    ok &= mbar_wait_bounded(&bars[0], 0, a.err);  // plane zs-1
-    ok &= mbar_wait_bounded(&bars[1 % kStages], (1 / kStages) & 1, a.err);  // plane zs
+        bool ok = mbar_wait_bounded(&full[0], 0, a.err);  // plane zs-1
+        float ph = ldf(slots, L::o_chi + 4 * r_own);       // own cell one plane below
+        float pl = ldt(slots, L::o_clo + L::EL * r_own, inv_lo);
+        float pd5 = ldt(slots, L::o_d5 + L::EL * r_plain, inv_d);
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[0]);
+        ok &= mbar_wait_bounded(&full[1 % kStages], (1 / kStages) & 1, a.err);  // plane zs
 
-    const float w = kW1;
-    const float inv_lo = a.inv_lo, inv_d = a.inv_d, s_lo = a.s_lo, s_d = a.s_d;
-    const int r_own = (ty + 1) * kBX + tx;  // ghosted arrays
-    const int r_plain = ty * kBX + tx;       // plain arrays
-
-    for (int z = zs; z < ze; ++z) {
-        const int k = z - zs + 1;  // sequence number of plane z
-        ok &= mbar_wait_bounded(&bars[(k + 1) % kStages], ((k + 1) / kStages) & 1, a.err);
-        waited = k + 1;
-        const unsigned char* sc = slots + (k % kStages) * L::bytes;
-        const unsigned char* sm = slots + ((k - 1) % kStages) * L::bytes;
-        const unsigned char* sp = slots + ((k + 1) % kStages) * L::bytes;
-        const int gz = z;
-        const uint16_t m = valid ? reinterpret_cast<const uint16_t*>(sc + L::o_mk)[r_plain] : 0;
-        if (m & kActiveBit) {
-            const float* chi_c = reinterpret_cast<const float*>(sc + L::o_chi);
-            const T* clo_c = reinterpret_cast<const T*>(sc + L::o_clo);
-            const float hx = chi_c[r_own];
-            const float lx = S::ld(clo_c[r_own], inv_lo);
-            const float Cx = hx + lx;
+        for (int z = zs; z < ze && ok; ++z) {
+            const int k = z - zs + 1;
+            ok &= mbar_wait_bounded(&full[(k + 1) % kStages], ((k + 1) / kStages) & 1, a.err);
+            const unsigned char* sc = slots + (k % kStages) * L::bytes;
+            const unsigned char* sp = slots + ((k + 1) % kStages) * L::bytes;
+            const uint16_t m = valid ? *reinterpret_cast<const uint16_t*>(sc + L::o_mk + 2 * r_plain) : 0;
+            const float hx = ldf(sc, L::o_chi + 4 * r_own);
+            const float lx = ldt(sc, L::o_clo + L::EL * r_own, inv_lo);
             float dd[6];
-            dd[0] = S::ld(reinterpret_cast<const T*>(sc + L::o_d1)[r_plain], inv_d);
-            dd[1] = S::ld(reinterpret_cast<const T*>(sc + L::o_d2)[r_plain], inv_d);
-            dd[2] = S::ld(reinterpret_cast<const T*>(sc + L::o_d3)[r_own], inv_d);
-            dd[3] = S::ld(reinterpret_cast<const T*>(sc + L::o_d4)[r_own], inv_d);
-            dd[4] = S::ld(reinterpret_cast<const T*>(sc + L::o_d5)[r_plain], inv_d);
-            dd[5] = S::ld(reinterpret_cast<const T*>(sc + L::o_d6)[r_plain], inv_d);
-            const float om = reinterpret_cast<const float*>(sc + L::o_om)[r_plain];
-            const float rf = a.rfac;
-            float av[6];
-            // wall / boundary value of the population arriving through closed face `bit`,
-            // whose own opposite deviation is `dopp`
-            auto closed_val = [&](float dopp, int face_bit) -> float {
-                const float r = (m & (1u << (kReactShift + face_bit))) ? rf : 1.0f;
-                return r * dopp - (1.0f - r) * w * Cx;
-            };
-            // i = 1 (+x), from x-1 through face -x (bit 1); opposite deviation delta_2
-            if (!(m & 2u)) {
-                float hn, ln, dn;
-                if (tx > 0) {
-                    hn = chi_c[r_own - 1];
-                    ln = S::ld(clo_c[r_own - 1], inv_lo);
-                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d1)[r_plain - 1], inv_d);
-                } else {
-                    hn = reinterpret_cast<const float*>(sc + L::o_chiL)[ty * L::HXF + L::HXF - 1];
-                    ln = S::ld(reinterpret_cast<const T*>(sc + L::o_cloL)[ty * L::HXL + L::HXL - 1], inv_lo);
-                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d1L)[ty * L::HXL + L::HXL - 1], inv_d);
+            dd[0] = ldt(sc, L::o_d1 + L::EL * r_plain, inv_d);
+            dd[1] = ldt(sc, L::o_d2 + L::EL * r_plain, inv_d);
+            dd[2] = ldt(sc, L::o_d3 + L::EL * r_own, inv_d);
+            dd[3] = ldt(sc, L::o_d4 + L::EL * r_own, inv_d);
+            dd[4] = ldt(sc, L::o_d5 + L::EL * r_plain, inv_d);
+            dd[5] = ldt(sc, L::o_d6 + L::EL * r_plain, inv_d);
+            if (m & kActiveBit) {
+                const float Cx = hx + lx;
+                const float om = ldf(sc, L::o_om + 4 * r_plain);
+                // neighbour C (hi, lo) and the deviation travelling toward this cell
+                float nh[6], nl[6], nd[6];
+                nh[0] = ldf(sc, xl_f);  nl[0] = ldt(sc, xl_lo, inv_lo);  nd[0] = ldt(sc, xl_d1, inv_d);
+                nh[1] = ldf(sc, xr_f);  nl[1] = ldt(sc, xr_lo, inv_lo);  nd[1] = ldt(sc, xr_d2, inv_d);
+                nh[2] = ldf(sc, L::o_chi + 4 * (r_own - kBX));
+                nl[2] = ldt(sc, L::o_clo + L::EL * (r_own - kBX), inv_lo);
+                nd[2] = ldt(sc, L::o_d3 + L::EL * (r_own - kBX), inv_d);
+                nh[3] = ldf(sc, L::o_chi + 4 * (r_own + kBX));
+                nl[3] = ldt(sc, L::o_clo + L::EL * (r_own + kBX), inv_lo);
+                nd[3] = ldt(sc, L::o_d4 + L::EL * (r_own + kBX), inv_d);
+                nh[4] = ph;  nl[4] = pl;  nd[4] = pd5;
+                nh[5] = ldf(sp, L::o_chi + 4 * r_own);
+                nl[5] = ldt(sp, L::o_clo + L::EL * r_own, inv_lo);
+                nd[5] = ldt(sp, L::o_d6 + L::EL * r_plain, inv_d);
+                // population i arrives through face opp(i): bits 1,0,3,2,5,4; own opposite deviation dd[opp]
+                const int fbit[6] = {1, 0, 3, 2, 5, 4};
+                float av[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    const float dopp = dd[fbit[i]];
+                    const float a_open = w * ((nh[i] - hx) + (nl[i] - lx)) + nd[i];
+                    const float r = (m >> (kReactShift + fbit[i])) & 1u ? rf : 1.0f;
+                    float a_closed = r * dopp - (1.0f - r) * w * Cx;
+                    if (i == 0 && x == 0)
+                        a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dopp : dopp;
+                    if (i == 1 && x == nx - 1)
+                        a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dopp : dopp;
+                    av[i] = (m >> fbit[i]) & 1u ? a_closed : a_open;
                 }
-                av[0] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else if (x == 0) {
-                av[0] = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dd[1] : dd[1];
-            } else {
-                av[0] = closed_val(dd[1], 1);
-            }
-            // i = 2 (-x), from x+1 through face +x (bit 0); opposite delta_1
-            if (!(m & 1u)) {
-                float hn, ln, dn;
-                if (tx < kBX - 1) {
-                    hn = chi_c[r_own + 1];
-                    ln = S::ld(clo_c[r_own + 1], inv_lo);
-                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d2)[r_plain + 1], inv_d);
-                } else {
-                    hn = reinterpret_cast<const float*>(sc + L::o_chiR)[ty * L::HXF];
-                    ln = S::ld(reinterpret_cast<const T*>(sc + L::o_cloR)[ty * L::HXL], inv_lo);
-                    dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d2R)[ty * L::HXL], inv_d);
-                }
-                av[1] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else if (x == nx - 1) {
-                av[1] = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dd[0] : dd[0];
-            } else {
-                av[1] = closed_val(dd[0], 0);
-            }
-            // i = 3 (+y), from y-1 through face -y (bit 3); opposite delta_4
-            if (!(m & 8u)) {
-                const float hn = chi_c[r_own - kBX];
-                const float ln = S::ld(clo_c[r_own - kBX], inv_lo);
-                const float dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d3)[r_own - kBX], inv_d);
-                av[2] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else {
-                av[2] = closed_val(dd[3], 3);
-            }
-            // i = 4 (-y), from y+1 through face +y (bit 2); opposite delta_3
-            if (!(m & 4u)) {
-                const float hn = chi_c[r_own + kBX];
-                const float ln = S::ld(clo_c[r_own + kBX], inv_lo);
-                const float dn = S::ld(reinterpret_cast<const T*>(sc + L::o_d4)[r_own + kBX], inv_d);
-                av[3] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else {
-                av[3] = closed_val(dd[2], 2);
-            }
-            // i = 5 (+z), from z-1 through face -z (bit 5); opposite delta_6
-            if (!(m & 32u)) {
-                const float hn = reinterpret_cast<const float*>(sm + L::o_chi)[r_own];
-                const float ln = S::ld(reinterpret_cast<const T*>(sm + L::o_clo)[r_own], inv_lo);
-                const float dn = S::ld(reinterpret_cast<const T*>(sm + L::o_d5)[r_plain], inv_d);
-                av[4] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else {
-                av[4] = closed_val(dd[5], 5);
-            }
-            // i = 6 (-z), from z+1 through face +z (bit 4); opposite delta_5
-            if (!(m & 16u)) {
-                const float hn = reinterpret_cast<const float*>(sp + L::o_chi)[r_own];
-                const float ln = S::ld(reinterpret_cast<const T*>(sp + L::o_clo)[r_own], inv_lo);
-                const float dn = S::ld(reinterpret_cast<const T*>(sp + L::o_d6)[r_plain], inv_d);
-                av[5] = w * ((hn - hx) + (ln - lx)) + dn;
-            } else {
-                av[5] = closed_val(dd[4], 4);
-            }
+                const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
+                                 ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
+                float hnew, lnew;
+                df_add(hx, lx, dC, hnew, lnew);
+                const float om1 = 1.0f - om;
+                float dn[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
 
-            const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
-                             ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
-            float hnew, lnew;
-            df_add(hx, lx, dC, hnew, lnew);
-            const float om1 = 1.0f - om;
-            float dn[6];
+                const long long gi = x + (long long)px * (y + 1) + pstride * z;
+                T* clo = reinterpret_cast<T*>(a.clo);
+                a.chi[gi] = hnew;
+                clo[gi] = S::st(lnew, s_lo);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
-
-            // stores (padded, ghosted layout)
-            const long long gi = x + (long long)px * (y + 1) + pstride * gz;
-            a.chi[gi] = hnew;
-            T* clo = reinterpret_cast<T*>(a.clo);
-            clo[gi] = S::st(lnew, s_lo);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) reinterpret_cast<T*>(a.d[i])[gi] = S::st(dn[i], s_d);
-            if (y == ny - 1) {  // ghost row above row 0
-                const long long gg = x + pstride * gz;
-                a.chi[gg] = hnew;
-                clo[gg] = S::st(lnew, s_lo);
-                reinterpret_cast<T*>(a.d[2])[gg] = S::st(dn[2], s_d);
-            }
-            if (y == 0) {  // ghost row below row ny-1
-                const long long gg = x + (long long)px * (ny + 1) + pstride * gz;
-                a.chi[gg] = hnew;
-                clo[gg] = S::st(lnew, s_lo);
-                reinterpret_cast<T*>(a.d[3])[gg] = S::st(dn[3], s_d);
-            }
-            if (REDUCE) {
-                const double Cn = (double)hnew + (double)lnew;
-                if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
-                    rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
-                if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET)
-                    rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
-                const unsigned rb = (m >> kReactShift) & 0x3fu;
-                if (rb) {
-                    double r = 0.0;
-#pragma unroll
-                    for (int d = 0; d < 6; ++d)
-                        if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
-                    rv[RED_R] += (1.0 - (double)rf) * r;
+                for (int i = 0; i < 6; ++i) reinterpret_cast<T*>(a.d[i])[gi] = S::st(dn[i], s_d);
+                if (y == ny - 1) {  // ghost row above row 0
+                    const long long gg = x + pstride * z;
+                    a.chi[gg] = hnew;
+                    clo[gg] = S::st(lnew, s_lo);
+                    reinterpret_cast<T*>(a.d[2])[gg] = S::st(dn[2], s_d);
                 }
-                rv[RED_SUMC] += Cn;
-                rv[RED_DC] += fabs(Cn - (double)a.Csnap[gi]);
-                rv[RED_ABSC] += fabs(Cn);
-                rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
-                a.Csnap[gi] = (float)Cn;
+                if (y == 0) {  // ghost row below row ny-1
+                    const long long gg = x + (long long)px * (ny + 1) + pstride * z;
+                    a.chi[gg] = hnew;
+                    clo[gg] = S::st(lnew, s_lo);
+                    reinterpret_cast<T*>(a.d[3])[gg] = S::st(dn[3], s_d);
+                }
+                if (REDUCE) {
+                    const double Cn = (double)hnew + (double)lnew;
+                    if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
+                        rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
+                    if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET)
+                        rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
+                    const unsigned rb = (m >> kReactShift) & 0x3fu;
+                    if (rb) {
+                        double r = 0.0;
+#pragma unroll
+                        for (int d = 0; d < 6; ++d)
+                            if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
+                        rv[RED_R] += (1.0 - (double)rf) * r;
+                    }
+                    rv[RED_SUMC] += Cn;
+                    rv[RED_DC] += fabs(Cn - (double)a.Csnap[gi]);
+                    rv[RED_ABSC] += fabs(Cn);
+                    rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
+                    a.Csnap[gi] = (float)Cn;
+                }
             }
+            // this plane becomes the z-1 neighbour of the next one
+            ph = hx;
+            pl = lx;
+            pd5 = dd[4];
+            __syncwarp();
+            if (tx == 0) mbar_arrive(&empty[k % kStages]);
         }
-        // every thread is done with plane z-1's slot before it is refilled
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        if (tid == 0 && issued < nplanes) {
-            issue(issued);
-            ++issued;
-        }
-    }
-    if (!ok && tid == 0) {
-        // let copies still in flight land before the block's shared memory is released
-        for (int k = waited + 1; k < issued; ++k) mbar_wait_bounded(&bars[k % kStages], (k / kStages) & 1, a.err);
     }
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
@@ -399,7 +379,7 @@ static cudaError_t launch_one(const MarchMaps& maps, const MarchArgs& a, dim3 gr
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_march<S, R><<<grid, dim3(kBX, kBY, 1), smem, s>>>(maps, a);
+    k_march<S, R><<<grid, dim3(kBX, kBY + 1, 1), smem, s>>>(maps, a);
     return cudaGetLastError();
 }
 
@@ -416,12 +396,13 @@ cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const 
 int march_blocks_per_sm(int storage) {
     const int smem = march_smem_bytes(storage);
     int nb = 0;
+    // the plain step variant sets the grid; the reduction variant runs once per check
     if (storage == CL_STORE_FP16DEV) {
-        cudaFuncSetAttribute(k_march<StoreF16, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF16, true>, kBX * kBY, smem);
+        cudaFuncSetAttribute(k_march<StoreF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF16, false>, kThreads, smem);
     } else {
-        cudaFuncSetAttribute(k_march<StoreF32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF32, true>, kBX * kBY, smem);
+        cudaFuncSetAttribute(k_march<StoreF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF32, false>, kThreads, smem);
     }
     return nb > 0 ? nb : 1;
 }

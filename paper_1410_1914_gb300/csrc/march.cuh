@@ -8,8 +8,9 @@
 namespace cl {
 
 constexpr int kBX = 32;     // tile width in x (one warp)
-constexpr int kBY = 8;      // tile height in y (warps per block)
-constexpr int kStages = 5;  // planes resident per block: z-1, z, z+1 and two in flight
+constexpr int kBY = 8;      // tile height in y (consumer warps per block)
+constexpr int kStages = 4;  // plane slots per block: z, z+1 in use, two in flight
+constexpr int kThreads = kBX * (kBY + 1);  // plus one producer warp
 
 // TMA descriptors of one source time level (main boxes and 16-byte x-halo boxes)
 struct MarchMaps {

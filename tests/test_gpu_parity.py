@@ -3,8 +3,11 @@
 Integer set-up products (connectivity, 13-direction lengths, link masks) must
 match bit for bit; floating-point results within the bounds stated per
 storage mode:
-  fp32     C as double-float, deviations f32: a few 1e-9 of O(1) values;
-  fp16dev  deviations as scaled f16 (11-bit significand): 5e-5 after 150 steps;
+  fp32     C as double-float, deviations f32: the f32 rounding of the
+           returned O(1) field (1e-7);
+  fp16dev  deviations as scaled f16 (11-bit significand): 2^-11 of the
+           largest deviation, up to ~0.15 in the first steps next to strongly
+           reactive walls (8e-5);
   fp32pop  7 plain f32 populations: ulps of O(1) values per step.
 Sizes span several 32-wide x tiles and 8-row y tiles with ragged tails.
 """
@@ -29,7 +32,7 @@ def _solver(shape, storage="fp32", **params):
 
 
 def _tol(storage, steps):
-    return {"fp32": 1e-8 + 1e-10 * steps, "fp16dev": 2e-6 + 3e-7 * steps,
+    return {"fp32": 1e-7 + 1e-10 * steps, "fp16dev": 8e-5 + 1e-7 * steps,
             "fp32pop": 2e-6 + 1e-7 * steps}[storage]
 
 
@@ -38,7 +41,7 @@ CASES = {
     "pt_ragged": ("pt_cl_256", (13, 17, 291), 21, dict(k_ms=2e4)),
     "pt_deff": ("pt_cl_48", (19, 23, 37), 22, {}),
     "npmc": ("npmc_cl_400", (24, 20, 150), 23, dict(k_ms=5e3)),
-    "thin": ("pt_cl_48", (3, 5, 40), 24, {}),
+    "thin": ("pt_cl_256", (3, 5, 40), 24, dict(k_ms=2e4)),
 }
 
 
@@ -99,10 +102,13 @@ def test_trajectory(cuda_lib, storage, name, steps):
     fg, fo = s.fluxes(), o.fluxes()
     scale = max(abs(fo["J_in"]), 1e-30)
     ftol = {"fp32": 1e-6, "fp16dev": 5e-4, "fp32pop": 2e-5}[storage]
+    # absolute floor: one rounding of an O(0.1) stored value per boundary term
+    nyz = ph.shape[0] * ph.shape[1]
+    floor = {"fp32": 1e-9, "fp16dev": 2e-6, "fp32pop": 6e-8}[storage] * nyz + 1e-7
     assert fg["n_active"] == fo["n_active"]
-    assert abs(fg["J_in"] - fo["J_in"]) <= ftol * scale + 1e-7
-    assert abs(fg["J_out"] - fo["J_out"]) <= ftol * scale + 1e-7
-    assert abs(fg["R"] - fo["R"]) <= ftol * max(abs(fo["R"]), 1e-30) + 1e-7 * scale
+    assert abs(fg["J_in"] - fo["J_in"]) <= ftol * scale + floor
+    assert abs(fg["J_out"] - fo["J_out"]) <= ftol * scale + floor
+    assert abs(fg["R"] - fo["R"]) <= ftol * max(abs(fo["R"]), 1e-30) + floor
     assert fg["sum_C"] == pytest.approx(fo["sum_C"], rel=max(ftol, 1e-6))
     tg, pRg, pCg = s.reaction_rate()
     to, pRo, pCo = o.reaction_rate()
