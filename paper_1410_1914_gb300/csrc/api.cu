@@ -1,6 +1,7 @@
 // Host implementation of the C ABI declared in include/cl_lbm.h.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -100,6 +101,7 @@ struct cl_lbm {
     MarchMaps maps[2];
     dim3 mgrid;
     int z_chunk = 0;
+    int prefetch = kPrefetchDefault;
     float s_lo = 1.f, s_d = 1.f;
 
     int cur = 0;
@@ -169,6 +171,7 @@ MarchArgs make_margs(cl_lbm* h, int dst) {
     MarchArgs a;
     a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
     a.z_chunk = h->z_chunk;
+    a.prefetch = h->prefetch;
     a.chi = h->st[dst].chi;
     a.clo = h->st[dst].clo;
     for (int i = 0; i < 6; ++i) a.d[i] = h->st[dst].d[i];
@@ -326,6 +329,7 @@ cl_status check_err_flag(cl_lbm* h) {
     if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
     if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
     if (herr & 8) { set_msg_txt("a plane load of the step kernel did not arrive within its wait bound"); return CL_ERR_TIMEOUT; }
+    if (herr & 16) { set_msg_txt("dynamic shared memory of the step kernel is not 128-byte aligned"); return CL_ERR_CUDA; }
     return CL_OK;
 }
 
@@ -488,6 +492,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
 
     if (h->march) {
         h->px = (h->nx + kBX - 1) / kBX * kBX;
+        if (const char* e = getenv("CL_LBM_PREFETCH")) h->prefetch = atoi(e);  // tuning override
         h->NP = (long long)h->px * (h->ny + 2) * h->nz;
         choose_march_grid(h);
         h->nblk_step = (int)(h->mgrid.x * h->mgrid.y * h->mgrid.z);

@@ -81,6 +81,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
@@ -147,28 +154,112 @@ int march_slot_bytes(int storage) {
     return storage == CL_STORE_FP16DEV ? SlotLayout<StoreF16>::bytes : SlotLayout<StoreF32>::bytes;
 }
 
-int march_smem_bytes(int storage) { return 256 + kStages * march_slot_bytes(storage); }
+int march_smem_bytes(int storage) { return 128 + kStages * march_slot_bytes(storage); }
 
 // ------------------------------------------------------------- the kernel
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Warp roles: warps 0..kBY-1 each own one row of the tile and compute; warp
-// kBY is the producer and issues the TMA loads of one plane per slot.
-// full[s] completes when a plane has landed in slot s; empty[s] when all
-// consumer warps have released it.  A consumer keeps the z-1 values it needs
-// (its own previous cell) in registers, so a slot is live only while its
-// plane is the current one or the next one.
+// Per-cell update on the (C, delta) state; nh/nl/nd: neighbour hi, lo and the
+// deviation travelling toward this cell, for i = 1..6 (+x, -x, +y, -y, +z, -z).
+// Population i arrives through face opp(i); mask bits of those faces are
+// 1, 0, 3, 2, 5, 4 and the own opposite deviations dd[1], dd[0], dd[3], ...
+template <bool REDUCE>
+__device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, float om, float hx, float lx,
+                                            const float (&dd)[6], const float (&nh)[6], const float (&nl)[6],
+                                            const float (&nd)[6], int x, float& hnew, float& lnew, float (&dn)[6],
+                                            double (&rv)[RED_N], float csnap, float& csnap_out) {
+    const float w = kW1;
+    const float rf = a.rfac;
+    const float Cx = hx + lx;
+    float av[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        const int fb = i ^ 1;  // face bit of population i, also the index of its opposite deviation
+        const float dopp = dd[fb];
+        const float a_open = w * ((nh[i] - hx) + (nl[i] - lx)) + nd[i];
+        const float r = (m & (1u << (kReactShift + fb))) ? rf : 1.0f;
+        float a_closed = r * dopp - (1.0f - r) * w * Cx;
+        if (i == 0 && x == 0)
+            a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dopp : dopp;
+        if (i == 1 && x == a.nx - 1)
+            a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dopp : dopp;
+        av[i] = (m & (1u << fb)) ? a_closed : a_open;
+    }
+    const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
+                     ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
+    df_add(hx, lx, dC, hnew, lnew);
+    const float om1 = 1.0f - om;
+#pragma unroll
+    for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
+    if (REDUCE) {
+        const double Cn = (double)hnew + (double)lnew;
+        if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
+            rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
+        if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET)
+            rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
+        const unsigned rb = (m >> kReactShift) & 0x3fu;
+        if (rb) {
+            double r = 0.0;
+#pragma unroll
+            for (int d = 0; d < 6; ++d)
+                if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
+            rv[RED_R] += (1.0 - (double)rf) * r;
+        }
+        rv[RED_SUMC] += Cn;
+        rv[RED_DC] += fabs(Cn - (double)csnap);
+        rv[RED_ABSC] += fabs(Cn);
+        rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
+        csnap_out = (float)Cn;
+    }
+}
+
+// Pair loads/stores of two adjacent cells of one array (f32 or f16)
+template <class S>
+struct Pair;
+template <>
+struct Pair<StoreF32> {
+    static __device__ __forceinline__ float2 ld(const unsigned char* p, float) {
+        return *reinterpret_cast<const float2*>(p);
+    }
+    static __device__ __forceinline__ void st(void* p, float a, float b, float) {
+        *reinterpret_cast<float2*>(p) = make_float2(a, b);
+    }
+};
+template <>
+struct Pair<StoreF16> {
+    static __device__ __forceinline__ float2 ld(const unsigned char* p, float inv) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
+        return make_float2(v.x * inv, v.y * inv);
+    }
+    static __device__ __forceinline__ void st(void* p, float a, float b, float s) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * s, b * s);
+    }
+};
+
+// Warp roles: warps 0..kBY-1 each own one row of the tile (two cells per
+// lane) and compute; warp kBY is the producer and issues the TMA loads of
+// one plane per slot.  full[s] completes when a plane has landed in slot s,
+// empty[s] when every consumer warp has released it.  A consumer keeps the
+// z-1 values it needs (its own cells one plane below) in registers, so a
+// slot is live only while its plane is the current or the next one.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, REDUCE ? 1 : 2) k_march(const __grid_constant__ MarchMaps maps,
+                                                                     const MarchArgs a) {
     using T = typename S::T;
     using L = SlotLayout<S>;
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
-    uint64_t* full = reinterpret_cast<uint64_t*>(base);
+    using P = Pair<S>;
+    // Addressed directly (no integer round trip) so that every slot access
+    // compiles to a shared-memory load.
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + kStages;
-    unsigned char* slots = base + 128;
+    unsigned char* slots = smem_raw + 128;
+    if (smem_u32(smem_raw) & 127u) {  // TMA destinations need this alignment
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.err, 16);
+        return;
+    }
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
@@ -179,9 +270,8 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid
     const long long pstride = (long long)px * (ny + 2);
 
     double rv[RED_N];
-    if (REDUCE)
 #pragma unroll
-        for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+    for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
 
     if (tx == 0 && ty == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -223,6 +313,20 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid
                 tma_load_3d(sl + L::o_cloR, &maps.clo_h, bar, x0 + kBX, y0 + 1, z);
                 tma_load_3d(sl + L::o_d1L, &maps.d1_h, bar, x0 - L::HXL, y0 + 1, z);
                 tma_load_3d(sl + L::o_d2R, &maps.d2_h, bar, x0 + kBX, y0 + 1, z);
+                if (a.prefetch > 0 && k + a.prefetch < nplanes) {
+                    int zp = zs - 1 + k + a.prefetch;
+                    zp = zp >= nz ? zp - nz : zp;
+                    tma_prefetch_3d(&maps.chi, x0, y0, zp);
+                    tma_prefetch_3d(&maps.clo, x0, y0, zp);
+                    tma_prefetch_3d(&maps.d3, x0, y0, zp);
+                    tma_prefetch_3d(&maps.d4, x0, y0, zp);
+                    tma_prefetch_3d(&maps.d1, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps.d2, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps.d5, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps.d6, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps.om, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps.mk, x0, y0 + 1, zp);
+                }
             }
             if (!ok) {
                 // the loads still in flight land before shared memory is released
@@ -232,31 +336,31 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid
         }
     } else {
         // ------------------------------------------------------ consumers
-        const int x = x0 + tx, y = y0 + ty;
-        const bool valid = x < nx && y < ny;
-        const int r_own = (ty + 1) * kBX + tx;  // ghosted arrays
-        const int r_plain = ty * kBX + tx;       // plain arrays
-        const float w = kW1;
+        const int xa = x0 + 2 * tx;  // this lane's cells: xa, xa + 1
+        const int y = y0 + ty;
+        const bool row_ok = y < ny;
+        const int c_own = (ty + 1) * kBX + 2 * tx;  // element index, ghosted arrays
+        const int c_pl = ty * kBX + 2 * tx;         // element index, plain arrays
         const float inv_lo = a.inv_lo, inv_d = a.inv_d, s_lo = a.s_lo, s_d = a.s_d;
-        const float rf = a.rfac;
-        const bool lane_l = tx == 0, lane_r = tx == kBX - 1;
-        // addresses of the x-neighbour values: row neighbours or halo boxes
-        const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (r_own - 1);
-        const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (r_own + 1);
-        const int xl_lo = lane_l ? L::o_cloL + L::EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + L::EL * (r_own - 1);
-        const int xr_lo = lane_r ? L::o_cloR + L::EL * (ty * L::HXL) : L::o_clo + L::EL * (r_own + 1);
-        const int xl_d1 = lane_l ? L::o_d1L + L::EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + L::EL * (r_plain - 1);
-        const int xr_d2 = lane_r ? L::o_d2R + L::EL * (ty * L::HXL) : L::o_d2 + L::EL * (r_plain + 1);
-
-        auto ldf = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
-        auto ldt = [&](const unsigned char* sl, int off, float inv) {
+        constexpr int EL = L::EL;
+        auto f1 = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
+        auto t1 = [&](const unsigned char* sl, int off, float inv) {
             return S::ld(*reinterpret_cast<const T*>(sl + off), inv);
         };
+        // x-halo neighbours: left of xa, right of xa + 1
+        const bool lane_l = tx == 0, lane_r = tx == 31;
+        const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (c_own - 1);
+        const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (c_own + 2);
+        const int xl_lo = lane_l ? L::o_cloL + EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + EL * (c_own - 1);
+        const int xr_lo = lane_r ? L::o_cloR + EL * (ty * L::HXL) : L::o_clo + EL * (c_own + 2);
+        const int xl_d1 = lane_l ? L::o_d1L + EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
+        const int xr_d2 = lane_r ? L::o_d2R + EL * (ty * L::HXL) : L::o_d2 + EL * (c_pl + 2);
 
         bool ok = mbar_wait_bounded(&full[0], 0, a.err);  // plane zs-1
-        float ph = ldf(slots, L::o_chi + 4 * r_own);       // own cell one plane below
-        float pl = ldt(slots, L::o_clo + L::EL * r_own, inv_lo);
-        float pd5 = ldt(slots, L::o_d5 + L::EL * r_plain, inv_d);
+        // own cells one plane below
+        float2 ph = *reinterpret_cast<const float2*>(slots + L::o_chi + 4 * c_own);
+        float2 pl = P::ld(slots + L::o_clo + EL * c_own, inv_lo);
+        float2 pd5 = P::ld(slots + L::o_d5 + EL * c_pl, inv_d);
         __syncwarp();
         if (tx == 0) mbar_arrive(&empty[0]);
         ok &= mbar_wait_bounded(&full[1 % kStages], (1 / kStages) & 1, a.err);  // plane zs
@@ -266,100 +370,78 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 2 : 4) k_march(const __grid
             ok &= mbar_wait_bounded(&full[(k + 1) % kStages], ((k + 1) / kStages) & 1, a.err);
             const unsigned char* sc = slots + (k % kStages) * L::bytes;
             const unsigned char* sp = slots + ((k + 1) % kStages) * L::bytes;
-            const uint16_t m = valid ? *reinterpret_cast<const uint16_t*>(sc + L::o_mk + 2 * r_plain) : 0;
-            const float hx = ldf(sc, L::o_chi + 4 * r_own);
-            const float lx = ldt(sc, L::o_clo + L::EL * r_own, inv_lo);
-            float dd[6];
-            dd[0] = ldt(sc, L::o_d1 + L::EL * r_plain, inv_d);
-            dd[1] = ldt(sc, L::o_d2 + L::EL * r_plain, inv_d);
-            dd[2] = ldt(sc, L::o_d3 + L::EL * r_own, inv_d);
-            dd[3] = ldt(sc, L::o_d4 + L::EL * r_own, inv_d);
-            dd[4] = ldt(sc, L::o_d5 + L::EL * r_plain, inv_d);
-            dd[5] = ldt(sc, L::o_d6 + L::EL * r_plain, inv_d);
-            if (m & kActiveBit) {
-                const float Cx = hx + lx;
-                const float om = ldf(sc, L::o_om + 4 * r_plain);
-                // neighbour C (hi, lo) and the deviation travelling toward this cell
-                float nh[6], nl[6], nd[6];
-                nh[0] = ldf(sc, xl_f);  nl[0] = ldt(sc, xl_lo, inv_lo);  nd[0] = ldt(sc, xl_d1, inv_d);
-                nh[1] = ldf(sc, xr_f);  nl[1] = ldt(sc, xr_lo, inv_lo);  nd[1] = ldt(sc, xr_d2, inv_d);
-                nh[2] = ldf(sc, L::o_chi + 4 * (r_own - kBX));
-                nl[2] = ldt(sc, L::o_clo + L::EL * (r_own - kBX), inv_lo);
-                nd[2] = ldt(sc, L::o_d3 + L::EL * (r_own - kBX), inv_d);
-                nh[3] = ldf(sc, L::o_chi + 4 * (r_own + kBX));
-                nl[3] = ldt(sc, L::o_clo + L::EL * (r_own + kBX), inv_lo);
-                nd[3] = ldt(sc, L::o_d4 + L::EL * (r_own + kBX), inv_d);
-                nh[4] = ph;  nl[4] = pl;  nd[4] = pd5;
-                nh[5] = ldf(sp, L::o_chi + 4 * r_own);
-                nl[5] = ldt(sp, L::o_clo + L::EL * r_own, inv_lo);
-                nd[5] = ldt(sp, L::o_d6 + L::EL * r_plain, inv_d);
-                // population i arrives through face opp(i): bits 1,0,3,2,5,4; own opposite deviation dd[opp]
-                const int fbit[6] = {1, 0, 3, 2, 5, 4};
-                float av[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) {
-                    const float dopp = dd[fbit[i]];
-                    const float a_open = w * ((nh[i] - hx) + (nl[i] - lx)) + nd[i];
-                    const float r = (m >> (kReactShift + fbit[i])) & 1u ? rf : 1.0f;
-                    float a_closed = r * dopp - (1.0f - r) * w * Cx;
-                    if (i == 0 && x == 0)
-                        a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dopp : dopp;
-                    if (i == 1 && x == nx - 1)
-                        a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dopp : dopp;
-                    av[i] = (m >> fbit[i]) & 1u ? a_closed : a_open;
-                }
-                const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
-                                 ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
-                float hnew, lnew;
-                df_add(hx, lx, dC, hnew, lnew);
-                const float om1 = 1.0f - om;
-                float dn[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
+            const uint32_t mm = row_ok ? *reinterpret_cast<const uint32_t*>(sc + L::o_mk + 2 * c_pl) : 0u;
+            const uint32_t ma = mm & 0xffffu, mb = mm >> 16;
+            if ((ma | mb) & kActiveBit) {
+                // own pair
+                const float2 hx = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * c_own);
+                const float2 lx = P::ld(sc + L::o_clo + EL * c_own, inv_lo);
+                float2 dp[6];
+                dp[0] = P::ld(sc + L::o_d1 + EL * c_pl, inv_d);
+                dp[1] = P::ld(sc + L::o_d2 + EL * c_pl, inv_d);
+                dp[2] = P::ld(sc + L::o_d3 + EL * c_own, inv_d);
+                dp[3] = P::ld(sc + L::o_d4 + EL * c_own, inv_d);
+                dp[4] = P::ld(sc + L::o_d5 + EL * c_pl, inv_d);
+                dp[5] = P::ld(sc + L::o_d6 + EL * c_pl, inv_d);
+                const float2 om = *reinterpret_cast<const float2*>(sc + L::o_om + 4 * c_pl);
+                // y and z neighbours of both cells
+                const float2 hym = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own - kBX));
+                const float2 lym = P::ld(sc + L::o_clo + EL * (c_own - kBX), inv_lo);
+                const float2 dym = P::ld(sc + L::o_d3 + EL * (c_own - kBX), inv_d);
+                const float2 hyp = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own + kBX));
+                const float2 lyp = P::ld(sc + L::o_clo + EL * (c_own + kBX), inv_lo);
+                const float2 dyp = P::ld(sc + L::o_d4 + EL * (c_own + kBX), inv_d);
+                const float2 hzp = *reinterpret_cast<const float2*>(sp + L::o_chi + 4 * c_own);
+                const float2 lzp = P::ld(sp + L::o_clo + EL * c_own, inv_lo);
+                const float2 dzp = P::ld(sp + L::o_d6 + EL * c_pl, inv_d);
+                // outer x neighbours
+                const float hxl = f1(sc, xl_f), lxl = t1(sc, xl_lo, inv_lo), dxl = t1(sc, xl_d1, inv_d);
+                const float hxr = f1(sc, xr_f), lxr = t1(sc, xr_lo, inv_lo), dxr = t1(sc, xr_d2, inv_d);
 
-                const long long gi = x + (long long)px * (y + 1) + pstride * z;
-                T* clo = reinterpret_cast<T*>(a.clo);
-                a.chi[gi] = hnew;
-                clo[gi] = S::st(lnew, s_lo);
+                const long long gi = xa + (long long)px * (y + 1) + pstride * z;
+                float2 cs = make_float2(0.f, 0.f), cso = cs;
+                if (REDUCE) cs = *reinterpret_cast<const float2*>(a.Csnap + gi);
+
+                float hA = 0.f, lA = 0.f, hB = 0.f, lB = 0.f, dA[6], dB[6];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) reinterpret_cast<T*>(a.d[i])[gi] = S::st(dn[i], s_d);
+                for (int i = 0; i < 6; ++i) { dA[i] = 0.f; dB[i] = 0.f; }
+                if (ma & kActiveBit) {
+                    const float dd[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
+                    const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
+                    const float nl[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
+                    const float nd[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
+                    cell_update<REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
+                }
+                if (mb & kActiveBit) {
+                    const float dd[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
+                    const float nh[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
+                    const float nl[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
+                    const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
+                    cell_update<REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+                }
+                // inactive cells of the pair get zeros, which they already hold
+                *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
+                P::st(reinterpret_cast<T*>(a.clo) + gi, lA, lB, s_lo);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) P::st(reinterpret_cast<T*>(a.d[i]) + gi, dA[i], dB[i], s_d);
                 if (y == ny - 1) {  // ghost row above row 0
-                    const long long gg = x + pstride * z;
-                    a.chi[gg] = hnew;
-                    clo[gg] = S::st(lnew, s_lo);
-                    reinterpret_cast<T*>(a.d[2])[gg] = S::st(dn[2], s_d);
+                    const long long gg = xa + pstride * z;
+                    *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+                    P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                    P::st(reinterpret_cast<T*>(a.d[2]) + gg, dA[2], dB[2], s_d);
                 }
                 if (y == 0) {  // ghost row below row ny-1
-                    const long long gg = x + (long long)px * (ny + 1) + pstride * z;
-                    a.chi[gg] = hnew;
-                    clo[gg] = S::st(lnew, s_lo);
-                    reinterpret_cast<T*>(a.d[3])[gg] = S::st(dn[3], s_d);
+                    const long long gg = xa + (long long)px * (ny + 1) + pstride * z;
+                    *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+                    P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                    P::st(reinterpret_cast<T*>(a.d[3]) + gg, dA[3], dB[3], s_d);
                 }
-                if (REDUCE) {
-                    const double Cn = (double)hnew + (double)lnew;
-                    if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
-                        rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
-                    if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET)
-                        rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
-                    const unsigned rb = (m >> kReactShift) & 0x3fu;
-                    if (rb) {
-                        double r = 0.0;
-#pragma unroll
-                        for (int d = 0; d < 6; ++d)
-                            if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
-                        rv[RED_R] += (1.0 - (double)rf) * r;
-                    }
-                    rv[RED_SUMC] += Cn;
-                    rv[RED_DC] += fabs(Cn - (double)a.Csnap[gi]);
-                    rv[RED_ABSC] += fabs(Cn);
-                    rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
-                    a.Csnap[gi] = (float)Cn;
-                }
+                if (REDUCE) *reinterpret_cast<float2*>(a.Csnap + gi) = cso;
+                // this plane becomes the z-1 neighbour of the next one
+                ph = hx;
+                pl = lx;
+                pd5 = dp[4];
             }
-            // this plane becomes the z-1 neighbour of the next one
-            ph = hx;
-            pl = lx;
-            pd5 = dd[4];
             __syncwarp();
             if (tx == 0) mbar_arrive(&empty[k % kStages]);
         }
@@ -379,7 +461,7 @@ static cudaError_t launch_one(const MarchMaps& maps, const MarchArgs& a, dim3 gr
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_march<S, R><<<grid, dim3(kBX, kBY + 1, 1), smem, s>>>(maps, a);
+    k_march<S, R><<<grid, dim3(32, kBY + 1, 1), smem, s>>>(maps, a);
     return cudaGetLastError();
 }
 

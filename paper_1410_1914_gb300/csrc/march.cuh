@@ -7,10 +7,11 @@
 
 namespace cl {
 
-constexpr int kBX = 32;     // tile width in x (one warp)
+constexpr int kBX = 64;     // tile width in x (cells; two per lane of a warp)
 constexpr int kBY = 8;      // tile height in y (consumer warps per block)
 constexpr int kStages = 4;  // plane slots per block: z, z+1 in use, two in flight
-constexpr int kThreads = kBX * (kBY + 1);  // plus one producer warp
+constexpr int kPrefetchDefault = 0;  // planes beyond the TMA load pulled into L2
+constexpr int kThreads = 32 * (kBY + 1);  // one warp per row plus one producer warp
 
 // TMA descriptors of one source time level (main boxes and 16-byte x-halo boxes)
 struct MarchMaps {
@@ -21,6 +22,7 @@ struct MarchMaps {
 struct MarchArgs {
     int nx, ny, nz, px;  // px: padded row pitch (multiple of kBX)
     int z_chunk;         // planes per block
+    int prefetch;        // L2 prefetch distance in planes (0: none)
     // destination time level (padded, two ghost rows per plane)
     float* chi;
     void* clo;
