@@ -492,6 +492,8 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
 
     if (h->march) {
         h->px = (h->nx + kBX - 1) / kBX * kBX;
+        // L2 prefetch pays off for the FP32 state (memory-latency bound), not for FP16 (issue bound)
+        h->prefetch = p->storage == CL_STORE_FP32 ? 2 : 0;
         if (const char* e = getenv("CL_LBM_PREFETCH")) h->prefetch = atoi(e);  // tuning override
         h->NP = (long long)h->px * (h->ny + 2) * h->nz;
         choose_march_grid(h);

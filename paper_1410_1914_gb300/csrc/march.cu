@@ -161,50 +161,60 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Per-cell update on the (C, delta) state; nh/nl/nd: neighbour hi, lo and the
-// deviation travelling toward this cell, for i = 1..6 (+x, -x, +y, -y, +z, -z).
-// Population i arrives through face opp(i); mask bits of those faces are
-// 1, 0, 3, 2, 5, 4 and the own opposite deviations dd[1], dd[0], dd[3], ...
-template <bool REDUCE>
-__device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, float om, float hx, float lx,
-                                            const float (&dd)[6], const float (&nh)[6], const float (&nl)[6],
-                                            const float (&nd)[6], int x, float& hnew, float& lnew, float (&dn)[6],
-                                            double (&rv)[RED_N], float csnap, float& csnap_out) {
+// Per-cell update on the (C, delta) state, in storage units: deviations
+// scaled by s_d and low words by s_lo (both 1 for FP32 storage), so that no
+// value is rescaled on its way in or out.  nh/nls/nds: neighbour hi, low word
+// and the deviation travelling toward this cell, for i = 1..6 (+x, -x, +y,
+// -y, +z, -z).  Population i arrives through face opp(i), whose mask bit and
+// own opposite deviation index are both i ^ 1.
+template <class S, bool REDUCE>
+__device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, float om, float hx, float lxs,
+                                            const float (&dds)[6], const float (&nh)[6], const float (&nls)[6],
+                                            const float (&nds)[6], int x, float& hnew, float& lnew_s,
+                                            float (&dns)[6], double (&rv)[RED_N], float csnap, float& csnap_out) {
+    constexpr bool HALF = sizeof(typename S::T) == 2;
+    const float inv_lo = HALF ? a.inv_lo : 1.0f, s_lo = HALF ? a.s_lo : 1.0f;
+    const float s_d = HALF ? a.s_d : 1.0f, inv_d = HALF ? a.inv_d : 1.0f;
     const float w = kW1;
+    const float ws = w * s_d;
     const float rf = a.rfac;
+    const float lx = lxs * inv_lo;
     const float Cx = hx + lx;
     float av[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
-        const int fb = i ^ 1;  // face bit of population i, also the index of its opposite deviation
-        const float dopp = dd[fb];
-        const float a_open = w * ((nh[i] - hx) + (nl[i] - lx)) + nd[i];
+        const int fb = i ^ 1;
+        const float dopp = dds[fb];
+        const float a_open = ws * ((nh[i] - hx) + (nls[i] - lxs) * inv_lo) + nds[i];
         const float r = (m & (1u << (kReactShift + fb))) ? rf : 1.0f;
-        float a_closed = r * dopp - (1.0f - r) * w * Cx;
+        float a_closed = r * dopp - (1.0f - r) * ws * Cx;
         if (i == 0 && x == 0)
-            a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_in - hx) - lx) - dopp : dopp;
+            a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_in - hx) - lx) - dopp : dopp;
         if (i == 1 && x == a.nx - 1)
-            a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * w * ((a.c_out - hx) - lx) - dopp : dopp;
+            a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_out - hx) - lx) - dopp : dopp;
         av[i] = (m & (1u << fb)) ? a_closed : a_open;
     }
-    const float dC = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
-                     ((dd[0] + dd[1]) + (dd[2] + dd[3]) + (dd[4] + dd[5]));
-    df_add(hx, lx, dC, hnew, lnew);
+    const float dCs = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
+                      ((dds[0] + dds[1]) + (dds[2] + dds[3]) + (dds[4] + dds[5]));
+    float lnew;
+    df_add(hx, lx, dCs * inv_d, hnew, lnew);
+    lnew_s = lnew * s_lo;
     const float om1 = 1.0f - om;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dn[i] = om1 * (av[i] - w * dC);
+    for (int i = 0; i < 6; ++i) dns[i] = om1 * (av[i] - w * dCs);
     if (REDUCE) {
         const double Cn = (double)hnew + (double)lnew;
+        const double id = inv_d;
         if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
-            rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dn[1];
+            rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dns[1] * id;
         if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET)
-            rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dn[0];
+            rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dns[0] * id;
         const unsigned rb = (m >> kReactShift) & 0x3fu;
         if (rb) {
             double r = 0.0;
 #pragma unroll
             for (int d = 0; d < 6; ++d)
-                if (rb & (1u << d)) r += (double)w * Cn + (double)dn[d];
+                if (rb & (1u << d)) r += (double)w * Cn + (double)dns[d] * id;
             rv[RED_R] += (1.0 - (double)rf) * r;
         }
         rv[RED_SUMC] += Cn;
@@ -229,12 +239,11 @@ struct Pair<StoreF32> {
 };
 template <>
 struct Pair<StoreF16> {
-    static __device__ __forceinline__ float2 ld(const unsigned char* p, float inv) {
-        const float2 v = __half22float2(*reinterpret_cast<const __half2*>(p));
-        return make_float2(v.x * inv, v.y * inv);
+    static __device__ __forceinline__ float2 ld(const unsigned char* p, float) {
+        return __half22float2(*reinterpret_cast<const __half2*>(p));
     }
-    static __device__ __forceinline__ void st(void* p, float a, float b, float s) {
-        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a * s, b * s);
+    static __device__ __forceinline__ void st(void* p, float a, float b, float) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
     }
 };
 
@@ -245,7 +254,7 @@ struct Pair<StoreF16> {
 // z-1 values it needs (its own cells one plane below) in registers, so a
 // slot is live only while its plane is the current or the next one.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, REDUCE ? 1 : 2) k_march(const __grid_constant__ MarchMaps maps,
+__global__ void __launch_bounds__(kThreads, 1) k_march(const __grid_constant__ MarchMaps maps,
                                                                      const MarchArgs a) {
     using T = typename S::T;
     using L = SlotLayout<S>;
@@ -341,7 +350,8 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 1 : 2) k_march(const __grid
         const bool row_ok = y < ny;
         const int c_own = (ty + 1) * kBX + 2 * tx;  // element index, ghosted arrays
         const int c_pl = ty * kBX + 2 * tx;         // element index, plain arrays
-        const float inv_lo = a.inv_lo, inv_d = a.inv_d, s_lo = a.s_lo, s_d = a.s_d;
+        // values stay in storage units; cell_update applies the scales
+        const float inv_lo = 1.0f, inv_d = 1.0f, s_lo = 1.0f, s_d = 1.0f;
         constexpr int EL = L::EL;
         auto f1 = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
         auto t1 = [&](const unsigned char* sl, int off, float inv) {
@@ -410,14 +420,14 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 1 : 2) k_march(const __grid
                     const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
                     const float nl[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
                     const float nd[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
-                    cell_update<REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
+                    cell_update<S, REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
                 }
                 if (mb & kActiveBit) {
                     const float dd[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
                     const float nh[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
                     const float nl[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
                     const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
-                    cell_update<REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+                    cell_update<S, REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
                 }
                 // inactive cells of the pair get zeros, which they already hold
                 *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
