@@ -232,6 +232,26 @@ const char* cl_status_str(cl_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* cl_last_error_message(void);
 
+/* Cells of the transport phase 6-connected to the inlet plane x = 0 (y, z
+   periodic), computed without allocating any device memory; for callers
+   that cannot call cudaMalloc when they need it (a host application that
+   owns all device allocations, or a pipeline that forbids allocation after
+   start-up).  The paper has no counterpart: it is the same answer as the
+   `active` output of cl_lbm_get_setup, obtained without a handle.
+     phase:  nx*ny*nz phase codes, DEVICE pointer (read only).
+     active: nx*ny*nz bytes, DEVICE pointer, written with 0/1.
+     ionomer_transport: nonzero counts ionomer (2) as transport phase.
+     cuda_stream: cudaStream_t or NULL; the call synchronises it.
+   Limit: nx*ny*nz <= 4,194,304 cells (CL_ERR_ARG beyond).  Scratch space is
+   a static device array of about 20 MiB that every GPU loading the library
+   keeps until exit; all calls share it, so calls must not overlap on the
+   GPU.  The first call on a device looks up the array's device address
+   (make it before any stream capture).  Allocates nothing.
+   Errors: CL_ERR_ARG (NULL pointer, size, phase code > 3), CL_ERR_CUDA,
+   CL_ERR_TIMEOUT (labelling iteration bound). */
+cl_status cl_active_mask_noalloc(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
+                                 uint8_t* active, void* cuda_stream);
+
 /* Library version string. */
 const char* cl_version(void);
 

@@ -93,6 +93,7 @@ SIGNATURES = {
     "cl_status_str": (ctypes.c_char_p, [_I]),
     "cl_last_error_message": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_char_p, []),
+    "cl_active_mask_noalloc": (_S, [_P, _I, _I, _I, _I, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -307,6 +308,19 @@ def cl_lbm_get_info(h: int) -> cl_structure_info:
     info = cl_structure_info()
     _check(load().cl_lbm_get_info(h, ctypes.byref(info)), "cl_lbm_get_info")
     return info
+
+
+def cl_active_mask_noalloc(phase, active, ionomer_transport: bool = False, stream: int | None = None) -> None:
+    """Inlet-connected transport cells without device allocation.  `phase`
+    (uint8) and `active` (uint8, written) are CUDA tensors of shape (nz, ny, nx)."""
+    nz, ny, nx = (int(v) for v in phase.shape)
+    pp, pdev, _k1 = _arr(phase, np.uint8, nx * ny * nz)
+    ap, adev, _k2 = _arr(active, np.uint8, nx * ny * nz, writable=True)
+    if not (pdev and adev):
+        raise ValueError("phase and active must be device tensors")
+    st = current_torch_stream() if stream is None else stream
+    _check(load().cl_active_mask_noalloc(pp, nx, ny, nz, int(bool(ionomer_transport)), ap, st),
+           "cl_active_mask_noalloc")
 
 
 def cl_lbm_get_step(h: int) -> int:
