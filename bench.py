@@ -27,9 +27,13 @@ import sys
 import threading
 import time
 
+import hashlib
+
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+KERNEL_SRC = os.path.join(ROOT, "paper_1410_1914_gb300", "csrc", "march.cu")
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "pt_cl_256"
@@ -105,6 +109,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def measured_traffic(storage: str, n_cells: int):
+    """DRAM bytes per launch of the step kernel from the committed ncu capture
+    (profiles/traffic.json), scaled by the cells processed; None when the
+    kernel source changed since the capture or no capture exists."""
+    try:
+        with open(TRAFFIC_JSON) as fh:
+            rec = json.load(fh)[storage]
+        with open(KERNEL_SRC, "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
+        return None, "no capture"
+    if rec.get("src_sha256") != sha:
+        return None, "kernel changed since the capture"
+    return rec["dram_bytes_per_cell"] * n_cells, rec["case"]
+
+
 def measured_peak_gbs():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -154,7 +174,7 @@ def run_reference(args):
     n = ph.size
     value = n * args.steps * args.ref_steps_per_step / el / 1e6
     line = {
-        "impl": "reference", "metric": "MLUPS (D3Q7 fused collide-stream, all box cells)", "value": value,
+        "impl": "reference", "metric": "MLUPS (D3Q7 fused collide-stream step, all box cells)", "value": value,
         "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -174,7 +194,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16dev", "fp32pop"])
+    ap.add_argument("--storage", default="fp16dev", choices=["fp32", "fp16dev", "fp32pop"])
+    ap.add_argument("--no-other-storages", action="store_true",
+                    help="skip the short timing of the other storage modes")
     ap.add_argument("--check-every", type=int, default=100)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-lbm-steps", type=int, default=1000)
@@ -247,6 +269,30 @@ def main():
     launch_s = ms_per_step * 1e-3 / K
     peak, peak_kind = measured_peak_gbs()
     achieved = launch_bytes / launch_s / 1e9
+    traffic, traffic_src = measured_traffic(args.storage, n_cells)
+
+    # the other storage modes on the same structure, for context (not the headline)
+    others = {}
+    if not args.no_other_storages:
+        for st in ("fp32", "fp16dev", "fp32pop"):
+            if st == args.storage:
+                continue
+            so = Solver(ph.shape, storage=st, stream=int(stream.cuda_stream), check_every=K, **params)
+            so.set_structure(ph, react)
+            for _ in range(3):
+                so.solve_budget(K)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(5):
+                so.solve_budget(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            v = n_cells * K / (ms * 1e-3) / 1e6
+            others[st] = {"mlups": v, "hbm_frac": bytes_per_cell(st) * n_cells / (ms * 1e-3 / K) / 1e9 / peak}
+            so.close()
 
     # ---------------------------------------------------------- end to end
     # Through the public API with host buffers: pinned host structure ->
@@ -264,23 +310,29 @@ def main():
             R_tot, prof_R, prof_C = s.reaction_rate()
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
+        # device-to-host: 5 FP64 plane sums per x-plane for the readout, one
+        # 7-slot FP64 check per interval, the set-up's error words and counters
+        d2h = 40 * ph.shape[2] + 56 * (E // K) + 4 + 8 + 56
         e2e = {"value": n_cells * E * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(ph.nbytes + (react.nbytes if react is not None else 0)),
-               "d2h_bytes_per_step": int(8 + 2 * 8 * ph.shape[2]),
+               "d2h_bytes_per_step": int(d2h),
                "lbm_steps_per_e2e_step": E, "includes": "structure upload + GPU set-up + steps + readout"}
 
     line = {
-        "metric": "MLUPS (D3Q7 fused collide-stream, all box cells)",
+        "metric": "MLUPS (D3Q7 fused collide-stream step, all box cells)",
         "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "shape_zyx": list(ph.shape), "storage": args.storage,
                    "lbm_steps_per_bench_step": K, "active_fraction": info["n_active"] / n_cells,
-                   "l2": "inputs larger than L2 (population buffers 2 x %.0f MB)" % (7 * 4 * n_cells / 1e6),
+                   "l2": "inputs larger than L2 (state buffers 2 x %.0f MB)" % (
+                       (bytes_per_cell(args.storage) - 6) / 2 * n_cells / 1e6),
                    "parallelism": f"replicas x{world}", "setup_s": setup_s},
         "active_mlups": mlups * info["n_active"] / n_cells,
+        "other_storages": others,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": launch_bytes,
                      "kernel": "k_step_fp32" if args.storage == "fp32pop" else "k_march"},

@@ -468,6 +468,9 @@ static cudaError_t launch_one(const MarchMaps& maps, const MarchArgs& a, dim3 gr
     static bool attr_set = false;  // per template instance
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_march<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_march<S, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -491,9 +494,13 @@ int march_blocks_per_sm(int storage) {
     // the plain step variant sets the grid; the reduction variant runs once per check
     if (storage == CL_STORE_FP16DEV) {
         cudaFuncSetAttribute(k_march<StoreF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_march<StoreF16, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF16, false>, kThreads, smem);
     } else {
         cudaFuncSetAttribute(k_march<StoreF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_march<StoreF32, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF32, false>, kThreads, smem);
     }
     return nb > 0 ? nb : 1;
