@@ -232,6 +232,54 @@ const char* cl_status_str(cl_status s);
 /* Text of the last error raised on the calling thread ("" if none). */
 const char* cl_last_error_message(void);
 
+/* ---------------------------------------------------------------------
+ * Batches: many structures of uneven size advanced by one persistent launch.
+ * The paper solves one structure at a time on MPI ranks (Sec. 5.1, 5.3);
+ * a batch runs a set of such independent solves on one GPU.  Each member is
+ * an ordinary handle with its structure loaded; all members share storage
+ * mode (FP32 or FP16DEV, not FP32POP), check_every and step parity.  Batch
+ * calls are ordered on member 0's stream; members must not be stepped on
+ * their own while they belong to a batch that will step again.  The batch
+ * does not own its members: destroy the batch before them.
+ * --------------------------------------------------------------------- */
+typedef struct cl_batch* cl_batch_handle;
+
+/* Build the batch (work list, per-member TMA descriptors and arguments).
+   z_chunk: planes per work item (0: 32).  Errors: CL_ERR_ARG, CL_ERR_STATE
+   (member without structure or at another parity), CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n, int z_chunk);
+
+/* Free the batch's own buffers (members are untouched; NULL is ignored). */
+void cl_batch_destroy(cl_batch_handle b);
+
+/* Advance every member by exactly nsteps steps in one cooperative launch
+   (the same arithmetic as cl_lbm_step).  CL_ERR_TIMEOUT if the bounded grid
+   barrier gave up. */
+cl_status cl_batch_step(cl_batch_handle b, long long nsteps);
+
+/* Advance all members, check_every steps per launch (a captured CUDA graph
+   when the runtime captures cooperative launches), applying each member's
+   own stopping rule (as cl_lbm_solve) after every interval; converged
+   members leave the work list.  infos (nullable, n entries) receives each
+   member's outcome, n_converged (nullable) the count.  Returns
+   CL_ERR_NOT_CONVERGED if some member hit max_steps, CL_ERR_DIVERGED on a
+   non-finite member. */
+cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* infos, int* n_converged);
+
+/* Time steps_per_trial (even) steps for each z_chunk in {8, 16, 32, 64} and
+   L2 prefetch distance in {0, 2}, keep the fastest and report it (ms per
+   step in best_ms).  The trial steps are real steps of every member. */
+cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk, int* prefetch,
+                            double* best_ms);
+
+/* Set the work-item z length (>= 8) and prefetch distance directly (e.g.
+   from a cached autotuning result). */
+cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch);
+
+/* Resident blocks of the persistent launch, current work items, and whether
+   the solve runs from a captured graph (1) or plain launches (0). */
+cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* uses_graph);
+
 /* Cells of the transport phase 6-connected to the inlet plane x = 0 (y, z
    periodic), computed without allocating any device memory; for callers
    that cannot call cudaMalloc when they need it (a host application that

@@ -94,6 +94,13 @@ SIGNATURES = {
     "cl_last_error_message": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_char_p, []),
     "cl_active_mask_noalloc": (_S, [_P, _I, _I, _I, _I, _P, _P]),
+    "cl_batch_create": (_S, [ctypes.POINTER(_H), ctypes.POINTER(_H), _I, _I]),
+    "cl_batch_destroy": (None, [_H]),
+    "cl_batch_step": (_S, [_H, ctypes.c_longlong]),
+    "cl_batch_solve": (_S, [_H, ctypes.c_longlong, _P, ctypes.POINTER(_I)]),
+    "cl_batch_autotune": (_S, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
+    "cl_batch_configure": (_S, [_H, _I, _I]),
+    "cl_batch_info": (_S, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
 }
 
 _lock = threading.Lock()
@@ -327,3 +334,45 @@ def cl_lbm_get_step(h: int) -> int:
     s = ctypes.c_longlong()
     _check(load().cl_lbm_get_step(h, ctypes.byref(s)), "cl_lbm_get_step")
     return s.value
+
+
+# ------------------------------------------------------------------ batches
+def cl_batch_create(handles, z_chunk: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(handles))(*handles)
+    b = ctypes.c_void_p()
+    _check(load().cl_batch_create(ctypes.byref(b), arr, len(handles), int(z_chunk)), "cl_batch_create")
+    return b.value
+
+
+def cl_batch_destroy(b: int) -> None:
+    load().cl_batch_destroy(b)
+
+
+def cl_batch_step(b: int, nsteps: int) -> None:
+    _check(load().cl_batch_step(b, int(nsteps)), "cl_batch_step")
+
+
+def cl_batch_solve(b: int, n: int, max_steps: int):
+    infos = (cl_solve_info * n)()
+    nc = ctypes.c_int()
+    s = load().cl_batch_solve(b, int(max_steps), ctypes.cast(infos, ctypes.c_void_p), ctypes.byref(nc))
+    if s not in (CL_OK, CL_ERR_NOT_CONVERGED):
+        _check(s, "cl_batch_solve")
+    return s, [infos[i].as_dict() for i in range(n)], nc.value
+
+
+def cl_batch_autotune(b: int, steps_per_trial: int = 20):
+    zc, pf, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().cl_batch_autotune(b, int(steps_per_trial), ctypes.byref(zc), ctypes.byref(pf), ctypes.byref(ms)),
+           "cl_batch_autotune")
+    return zc.value, pf.value, ms.value
+
+
+def cl_batch_configure(b: int, z_chunk: int, prefetch: int) -> None:
+    _check(load().cl_batch_configure(b, int(z_chunk), int(prefetch)), "cl_batch_configure")
+
+
+def cl_batch_info(b: int):
+    g, n, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(load().cl_batch_info(b, ctypes.byref(g), ctypes.byref(n), ctypes.byref(u)), "cl_batch_info")
+    return dict(grid_blocks=g.value, n_items=n.value, uses_graph=bool(u.value))

@@ -7,43 +7,64 @@
 #include <chrono>
 #include <vector>
 
-#include "internal.cuh"
-#include "march.cuh"
+#include "handle.cuh"
 
 using namespace cl;
 
 namespace {
 
 thread_local char g_msg[512] = "";
+}  // namespace
 
+namespace cl {
 void set_msg(const char* where, cudaError_t e) {
     snprintf(g_msg, sizeof(g_msg), "%s: %s", where, cudaGetErrorString(e));
 }
 void set_msg_txt(const char* txt) { snprintf(g_msg, sizeof(g_msg), "%s", txt); }
-
 cl_status from_cuda(cudaError_t e) { return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA; }
+float reactive_factor(const cl_lbm* h) {
+    const double w = 0.125;
+    return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
+}
 
-#define CK(call)                    \
-    do {                            \
-        cudaError_t e_ = (call);    \
-        if (e_ != cudaSuccess) {    \
-            set_msg(#call, e_);     \
-            return from_cuda(e_);   \
-        }                           \
-    } while (0)
+MarchArgs make_margs(cl_lbm* h, int dst) {
+    MarchArgs a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
+    a.z_chunk = h->z_chunk;
+    a.prefetch = h->prefetch;
+    a.chi = h->st[dst].chi;
+    a.clo = h->st[dst].clo;
+    for (int i = 0; i < 6; ++i) a.d[i] = h->st[dst].d[i];
+    a.rfac = reactive_factor(h);
+    a.c_in = (float)h->p.c_in;
+    a.c_out = (float)h->p.c_out;
+    a.bc_in = h->p.bc_in;
+    a.bc_out = h->p.bc_out;
+    a.s_lo = h->s_lo;
+    a.inv_lo = 1.0f / h->s_lo;
+    a.s_d = h->s_d;
+    a.inv_d = 1.0f / h->s_d;
+    a.Csnap = h->Csnap_p;
+    a.partials = h->partials;
+    a.err = h->d_err;
+    return a;
+}
 
-#define CKS(stmt)                   \
-    do {                            \
-        cl_status s_ = (stmt);      \
-        if (s_ != CL_OK) return s_; \
-    } while (0)
+cl_status check_err_flag(cl_lbm* h) {
+    int herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    if (herr & 1) { set_msg_txt("phase code outside 0..3"); return CL_ERR_ARG; }
+    if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
+    if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
+    if (herr & 8) { set_msg_txt("a plane load of the step kernel did not arrive within its wait bound"); return CL_ERR_TIMEOUT; }
+    if (herr & 16) { set_msg_txt("dynamic shared memory of the step kernel is not 128-byte aligned"); return CL_ERR_CUDA; }
+    return CL_OK;
+}
+}  // namespace cl
 
-struct Graph {
-    cudaGraphExec_t exec = nullptr;
-    int parity = -1;
-    long long K = 0;
-    bool reduce = false;
-};
+namespace {
+
 
 // cuTensorMapEncodeTiled, fetched from the driver through the runtime
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -63,61 +84,9 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// One time level of the (C, delta) state, padded rows and two ghost rows per plane.
-struct MState {
-    float* chi = nullptr;
-    void* clo = nullptr;
-    void* d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-};
 
 }  // namespace
 
-struct cl_lbm {
-    cl_params p;
-    int nx, ny, nz;
-    long long N;
-    bool march = true;  // (C, delta) storage; false: 7 f32 populations
-    int px = 0;         // padded row pitch
-    long long NP = 0;   // padded, ghosted cell count
-    int el = 4;         // bytes per stored deviation
-    cudaStream_t s = nullptr;
-    cudaStream_t cap = nullptr;
-    std::vector<std::pair<void*, size_t>> allocs;
-
-    uint8_t *phase = nullptr, *react = nullptr, *active = nullptr, *touch = nullptr;
-    int* labels = nullptr;
-    int* d_err = nullptr;
-    double *D = nullptr, *dp = nullptr;
-    float* omega = nullptr;
-    uint16_t* mask = nullptr;
-    // population layout
-    float* pop[2] = {nullptr, nullptr};
-    float* Csnap = nullptr;
-    // (C, delta) layout
-    MState st[2];
-    uint16_t* mask_p = nullptr;
-    float* omega_p = nullptr;
-    float* Csnap_p = nullptr;
-    MarchMaps maps[2];
-    dim3 mgrid;
-    int z_chunk = 0;
-    int prefetch = kPrefetchDefault;
-    float s_lo = 1.f, s_d = 1.f;
-
-    int cur = 0;
-    float* fbuf = nullptr;
-    double* partials = nullptr;
-    int nblk_step = 0, nblk_stats = 0;
-    double* d_red = nullptr;    // [16]
-    double* d_plane = nullptr;  // [5 * nx]
-    double* h_red = nullptr;    // pinned [16 + 5 * nx]
-    bool have_react = false;
-    bool have_structure = false;
-    long long step = 0;
-    double D_b = 0, D_max = 0, dt = 0, k_lu = 0;
-    cl_structure_info info;
-    Graph graphs[4];
-};
 
 namespace {
 
@@ -144,10 +113,6 @@ cl_status dalloc_n(cl_lbm* h, T** out, long long n) {
 cudaMemcpyKind kind_in(int dev) { return dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int dev) { return dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
-float reactive_factor(const cl_lbm* h) {
-    const double w = 0.125;
-    return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
-}
 
 StepArgs make_args(cl_lbm* h) {
     StepArgs a;
@@ -167,28 +132,6 @@ StepArgs make_args(cl_lbm* h) {
     return a;
 }
 
-MarchArgs make_margs(cl_lbm* h, int dst) {
-    MarchArgs a;
-    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
-    a.z_chunk = h->z_chunk;
-    a.prefetch = h->prefetch;
-    a.chi = h->st[dst].chi;
-    a.clo = h->st[dst].clo;
-    for (int i = 0; i < 6; ++i) a.d[i] = h->st[dst].d[i];
-    a.rfac = reactive_factor(h);
-    a.c_in = (float)h->p.c_in;
-    a.c_out = (float)h->p.c_out;
-    a.bc_in = h->p.bc_in;
-    a.bc_out = h->p.bc_out;
-    a.s_lo = h->s_lo;
-    a.inv_lo = 1.0f / h->s_lo;
-    a.s_d = h->s_d;
-    a.inv_d = 1.0f / h->s_d;
-    a.Csnap = h->Csnap_p;
-    a.partials = h->partials;
-    a.err = h->d_err;
-    return a;
-}
 
 cl_status make_map(CUtensorMap* m, CUtensorMapDataType dt, int el, void* ptr, int px, int rows, int nz, int bx,
                    int by) {
@@ -321,17 +264,6 @@ cl_status need_structure(cl_lbm* h) {
     return CL_OK;
 }
 
-cl_status check_err_flag(cl_lbm* h) {
-    int herr = 0;
-    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
-    CK(cudaStreamSynchronize(h->s));
-    if (herr & 1) { set_msg_txt("phase code outside 0..3"); return CL_ERR_ARG; }
-    if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
-    if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
-    if (herr & 8) { set_msg_txt("a plane load of the step kernel did not arrive within its wait bound"); return CL_ERR_TIMEOUT; }
-    if (herr & 16) { set_msg_txt("dynamic shared memory of the step kernel is not 128-byte aligned"); return CL_ERR_CUDA; }
-    return CL_OK;
-}
 
 // stats + dt + omega, shared by set_structure and set_diffusivity
 cl_status derive_relaxation(cl_lbm* h, bool with_dp) {

@@ -1,0 +1,100 @@
+// The solver handle behind the opaque cl_handle, shared by the host files
+// of the library (not part of the public ABI).
+#pragma once
+
+#include <vector>
+
+#include "internal.cuh"
+#include "march.cuh"
+
+namespace cl {
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int parity = -1;
+    long long K = 0;
+    bool reduce = false;
+};
+
+// One time level of the (C, delta) state, padded rows and two ghost rows per plane.
+struct MState {
+    float* chi = nullptr;
+    void* clo = nullptr;
+    void* d[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+}  // namespace cl
+
+struct cl_lbm {
+    cl_params p;
+    int nx, ny, nz;
+    long long N;
+    bool march = true;  // (C, delta) storage; false: 7 f32 populations
+    int px = 0;         // padded row pitch
+    long long NP = 0;   // padded, ghosted cell count
+    int el = 4;         // bytes per stored deviation
+    cudaStream_t s = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+
+    uint8_t *phase = nullptr, *react = nullptr, *active = nullptr, *touch = nullptr;
+    int* labels = nullptr;
+    int* d_err = nullptr;
+    double *D = nullptr, *dp = nullptr;
+    float* omega = nullptr;
+    uint16_t* mask = nullptr;
+    // population layout
+    float* pop[2] = {nullptr, nullptr};
+    float* Csnap = nullptr;
+    // (C, delta) layout
+    cl::MState st[2];
+    uint16_t* mask_p = nullptr;
+    float* omega_p = nullptr;
+    float* Csnap_p = nullptr;
+    cl::MarchMaps maps[2];
+    dim3 mgrid;
+    int z_chunk = 0;
+    int prefetch = cl::kPrefetchDefault;
+    float s_lo = 1.f, s_d = 1.f;
+
+    int cur = 0;
+    float* fbuf = nullptr;
+    double* partials = nullptr;
+    int nblk_step = 0, nblk_stats = 0;
+    double* d_red = nullptr;    // [16]
+    double* d_plane = nullptr;  // [5 * nx]
+    double* h_red = nullptr;    // pinned [16 + 5 * nx]
+    bool have_react = false;
+    bool have_structure = false;
+    long long step = 0;
+    double D_b = 0, D_max = 0, dt = 0, k_lu = 0;
+    cl_structure_info info;
+    cl::Graph graphs[4];
+};
+
+namespace cl {
+
+// Host helpers defined in api.cu
+void set_msg(const char* where, cudaError_t e);
+void set_msg_txt(const char* txt);
+cl_status from_cuda(cudaError_t e);
+float reactive_factor(const cl_lbm* h);
+MarchArgs make_margs(cl_lbm* h, int dst);
+cl_status check_err_flag(cl_lbm* h);
+
+}  // namespace cl
+
+#define CK(call)                        \
+    do {                                \
+        cudaError_t e_ = (call);        \
+        if (e_ != cudaSuccess) {        \
+            cl::set_msg(#call, e_);     \
+            return cl::from_cuda(e_);   \
+        }                               \
+    } while (0)
+
+#define CKS(stmt)                       \
+    do {                                \
+        cl_status s_ = (stmt);          \
+        if (s_ != CL_OK) return s_;     \
+    } while (0)

@@ -90,6 +90,11 @@ __device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, i
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// descriptors that live in global memory are acquired before the TMA unit reads them
+__device__ __forceinline__ void tensormap_fence_acquire(const CUtensorMap* map) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(map))
+                 : "memory");
+}
 
 // ------------------------------------------------------- storage formats
 struct StoreF32 {
@@ -253,51 +258,36 @@ struct Pair<StoreF16> {
 // empty[s] when every consumer warp has released it.  A consumer keeps the
 // z-1 values it needs (its own cells one plane below) in registers, so a
 // slot is live only while its plane is the current or the next one.
+// One work item: the kBX x kBY column at (x0, y0), planes [zs, ze).  Planes
+// zs-1 .. ze stream through the ring; `seq` is the block's running plane
+// count before this item (it fixes each plane's slot and mbarrier phase, so
+// items can follow each other in one block).  Every plane is released after
+// use, including the last one.  Returns false if a bounded wait expired.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, 1) k_march(const __grid_constant__ MarchMaps maps,
-                                                                     const MarchArgs a) {
+__device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArgs& a, int x0, int y0, int zs,
+                                           int ze, unsigned char* slots, uint64_t* full, uint64_t* empty,
+                                           unsigned seq, bool fence_maps, double (&rv)[RED_N]) {
     using T = typename S::T;
     using L = SlotLayout<S>;
     using P = Pair<S>;
-    // Addressed directly (no integer round trip) so that every slot access
-    // compiles to a shared-memory load.
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
-    uint64_t* empty = full + kStages;
-    unsigned char* slots = smem_raw + 128;
-    if (smem_u32(smem_raw) & 127u) {  // TMA destinations need this alignment
-        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(a.err, 16);
-        return;
-    }
-
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * kBY;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
-    const int zs = blockIdx.z * a.z_chunk;
-    const int ze = min(nz, zs + a.z_chunk);
     const int nplanes = (ze - zs) + 2;  // zs-1 .. ze
     const long long pstride = (long long)px * (ny + 2);
-
-    double rv[RED_N];
-#pragma unroll
-    for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
-
-    if (tx == 0 && ty == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kBY);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
+    bool ok = true;
 
     if (ty == kBY) {
         // ------------------------------------------------------ producer
         if (tx == 0) {
+            if (fence_maps) {  // descriptors written to global memory before the launch
+                const CUtensorMap* mp = &maps->chi;
+                for (int i = 0; i < 14; ++i) tensormap_fence_acquire(mp + i);
+            }
             int k = 0;
-            bool ok = true;
             for (; k < nplanes && ok; ++k) {
-                const int s = k % kStages, u = k / kStages;
+                const unsigned g = seq + k;
+                const int s = g % kStages;
+                const unsigned u = g / kStages;
                 if (u > 0) ok = mbar_wait_bounded(&empty[s], (u - 1) & 1, a.err);
                 if (!ok) break;
                 unsigned char* sl = slots + s * L::bytes;
@@ -306,160 +296,305 @@ __global__ void __launch_bounds__(kThreads, 1) k_march(const __grid_constant__ M
                 uint64_t* bar = &full[s];
                 fence_proxy_async();
                 mbar_expect_tx(bar, L::tx);
-                tma_load_3d(sl + L::o_chi, &maps.chi, bar, x0, y0, z);
-                tma_load_3d(sl + L::o_clo, &maps.clo, bar, x0, y0, z);
-                tma_load_3d(sl + L::o_d3, &maps.d3, bar, x0, y0, z);
-                tma_load_3d(sl + L::o_d4, &maps.d4, bar, x0, y0, z);
-                tma_load_3d(sl + L::o_d1, &maps.d1, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_d2, &maps.d2, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_d5, &maps.d5, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_d6, &maps.d6, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_om, &maps.om, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_mk, &maps.mk, bar, x0, y0 + 1, z);
-                tma_load_3d(sl + L::o_chiL, &maps.chi_h, bar, x0 - L::HXF, y0 + 1, z);
-                tma_load_3d(sl + L::o_chiR, &maps.chi_h, bar, x0 + kBX, y0 + 1, z);
-                tma_load_3d(sl + L::o_cloL, &maps.clo_h, bar, x0 - L::HXL, y0 + 1, z);
-                tma_load_3d(sl + L::o_cloR, &maps.clo_h, bar, x0 + kBX, y0 + 1, z);
-                tma_load_3d(sl + L::o_d1L, &maps.d1_h, bar, x0 - L::HXL, y0 + 1, z);
-                tma_load_3d(sl + L::o_d2R, &maps.d2_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_chi, &maps->chi, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_clo, &maps->clo, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d3, &maps->d3, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d4, &maps->d4, bar, x0, y0, z);
+                tma_load_3d(sl + L::o_d1, &maps->d1, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d2, &maps->d2, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d5, &maps->d5, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_d6, &maps->d6, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_om, &maps->om, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_mk, &maps->mk, bar, x0, y0 + 1, z);
+                tma_load_3d(sl + L::o_chiL, &maps->chi_h, bar, x0 - L::HXF, y0 + 1, z);
+                tma_load_3d(sl + L::o_chiR, &maps->chi_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_cloL, &maps->clo_h, bar, x0 - L::HXL, y0 + 1, z);
+                tma_load_3d(sl + L::o_cloR, &maps->clo_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_d1L, &maps->d1_h, bar, x0 - L::HXL, y0 + 1, z);
+                tma_load_3d(sl + L::o_d2R, &maps->d2_h, bar, x0 + kBX, y0 + 1, z);
                 if (a.prefetch > 0 && k + a.prefetch < nplanes) {
                     int zp = zs - 1 + k + a.prefetch;
                     zp = zp >= nz ? zp - nz : zp;
-                    tma_prefetch_3d(&maps.chi, x0, y0, zp);
-                    tma_prefetch_3d(&maps.clo, x0, y0, zp);
-                    tma_prefetch_3d(&maps.d3, x0, y0, zp);
-                    tma_prefetch_3d(&maps.d4, x0, y0, zp);
-                    tma_prefetch_3d(&maps.d1, x0, y0 + 1, zp);
-                    tma_prefetch_3d(&maps.d2, x0, y0 + 1, zp);
-                    tma_prefetch_3d(&maps.d5, x0, y0 + 1, zp);
-                    tma_prefetch_3d(&maps.d6, x0, y0 + 1, zp);
-                    tma_prefetch_3d(&maps.om, x0, y0 + 1, zp);
-                    tma_prefetch_3d(&maps.mk, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->chi, x0, y0, zp);
+                    tma_prefetch_3d(&maps->clo, x0, y0, zp);
+                    tma_prefetch_3d(&maps->d3, x0, y0, zp);
+                    tma_prefetch_3d(&maps->d4, x0, y0, zp);
+                    tma_prefetch_3d(&maps->d1, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->d2, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->d5, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->d6, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->om, x0, y0 + 1, zp);
+                    tma_prefetch_3d(&maps->mk, x0, y0 + 1, zp);
                 }
             }
             if (!ok) {
                 // the loads still in flight land before shared memory is released
                 for (int j = k - 1; j >= 0 && j >= k - kStages; --j)
-                    mbar_wait_bounded(&full[j % kStages], (j / kStages) & 1, a.err);
+                    mbar_wait_bounded(&full[(seq + j) % kStages], ((seq + j) / kStages) & 1, a.err);
             }
         }
-    } else {
-        // ------------------------------------------------------ consumers
-        const int xa = x0 + 2 * tx;  // this lane's cells: xa, xa + 1
-        const int y = y0 + ty;
-        const bool row_ok = y < ny;
-        const int c_own = (ty + 1) * kBX + 2 * tx;  // element index, ghosted arrays
-        const int c_pl = ty * kBX + 2 * tx;         // element index, plain arrays
-        // values stay in storage units; cell_update applies the scales
-        const float inv_lo = 1.0f, inv_d = 1.0f, s_lo = 1.0f, s_d = 1.0f;
-        constexpr int EL = L::EL;
-        auto f1 = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
-        auto t1 = [&](const unsigned char* sl, int off, float inv) {
-            return S::ld(*reinterpret_cast<const T*>(sl + off), inv);
-        };
-        // x-halo neighbours: left of xa, right of xa + 1
-        const bool lane_l = tx == 0, lane_r = tx == 31;
-        const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (c_own - 1);
-        const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (c_own + 2);
-        const int xl_lo = lane_l ? L::o_cloL + EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + EL * (c_own - 1);
-        const int xr_lo = lane_r ? L::o_cloR + EL * (ty * L::HXL) : L::o_clo + EL * (c_own + 2);
-        const int xl_d1 = lane_l ? L::o_d1L + EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
-        const int xr_d2 = lane_r ? L::o_d2R + EL * (ty * L::HXL) : L::o_d2 + EL * (c_pl + 2);
-
-        bool ok = mbar_wait_bounded(&full[0], 0, a.err);  // plane zs-1
-        // own cells one plane below
-        float2 ph = *reinterpret_cast<const float2*>(slots + L::o_chi + 4 * c_own);
-        float2 pl = P::ld(slots + L::o_clo + EL * c_own, inv_lo);
-        float2 pd5 = P::ld(slots + L::o_d5 + EL * c_pl, inv_d);
-        __syncwarp();
-        if (tx == 0) mbar_arrive(&empty[0]);
-        ok &= mbar_wait_bounded(&full[1 % kStages], (1 / kStages) & 1, a.err);  // plane zs
-
-        for (int z = zs; z < ze && ok; ++z) {
-            const int k = z - zs + 1;
-            ok &= mbar_wait_bounded(&full[(k + 1) % kStages], ((k + 1) / kStages) & 1, a.err);
-            const unsigned char* sc = slots + (k % kStages) * L::bytes;
-            const unsigned char* sp = slots + ((k + 1) % kStages) * L::bytes;
-            const uint32_t mm = row_ok ? *reinterpret_cast<const uint32_t*>(sc + L::o_mk + 2 * c_pl) : 0u;
-            const uint32_t ma = mm & 0xffffu, mb = mm >> 16;
-            if ((ma | mb) & kActiveBit) {
-                // own pair
-                const float2 hx = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * c_own);
-                const float2 lx = P::ld(sc + L::o_clo + EL * c_own, inv_lo);
-                float2 dp[6];
-                dp[0] = P::ld(sc + L::o_d1 + EL * c_pl, inv_d);
-                dp[1] = P::ld(sc + L::o_d2 + EL * c_pl, inv_d);
-                dp[2] = P::ld(sc + L::o_d3 + EL * c_own, inv_d);
-                dp[3] = P::ld(sc + L::o_d4 + EL * c_own, inv_d);
-                dp[4] = P::ld(sc + L::o_d5 + EL * c_pl, inv_d);
-                dp[5] = P::ld(sc + L::o_d6 + EL * c_pl, inv_d);
-                const float2 om = *reinterpret_cast<const float2*>(sc + L::o_om + 4 * c_pl);
-                // y and z neighbours of both cells
-                const float2 hym = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own - kBX));
-                const float2 lym = P::ld(sc + L::o_clo + EL * (c_own - kBX), inv_lo);
-                const float2 dym = P::ld(sc + L::o_d3 + EL * (c_own - kBX), inv_d);
-                const float2 hyp = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own + kBX));
-                const float2 lyp = P::ld(sc + L::o_clo + EL * (c_own + kBX), inv_lo);
-                const float2 dyp = P::ld(sc + L::o_d4 + EL * (c_own + kBX), inv_d);
-                const float2 hzp = *reinterpret_cast<const float2*>(sp + L::o_chi + 4 * c_own);
-                const float2 lzp = P::ld(sp + L::o_clo + EL * c_own, inv_lo);
-                const float2 dzp = P::ld(sp + L::o_d6 + EL * c_pl, inv_d);
-                // outer x neighbours
-                const float hxl = f1(sc, xl_f), lxl = t1(sc, xl_lo, inv_lo), dxl = t1(sc, xl_d1, inv_d);
-                const float hxr = f1(sc, xr_f), lxr = t1(sc, xr_lo, inv_lo), dxr = t1(sc, xr_d2, inv_d);
-
-                const long long gi = xa + (long long)px * (y + 1) + pstride * z;
-                float2 cs = make_float2(0.f, 0.f), cso = cs;
-                if (REDUCE) cs = *reinterpret_cast<const float2*>(a.Csnap + gi);
-
-                float hA = 0.f, lA = 0.f, hB = 0.f, lB = 0.f, dA[6], dB[6];
-#pragma unroll
-                for (int i = 0; i < 6; ++i) { dA[i] = 0.f; dB[i] = 0.f; }
-                if (ma & kActiveBit) {
-                    const float dd[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
-                    const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
-                    const float nl[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
-                    const float nd[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
-                    cell_update<S, REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
-                }
-                if (mb & kActiveBit) {
-                    const float dd[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
-                    const float nh[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
-                    const float nl[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
-                    const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
-                    cell_update<S, REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
-                }
-                // inactive cells of the pair get zeros, which they already hold
-                *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
-                P::st(reinterpret_cast<T*>(a.clo) + gi, lA, lB, s_lo);
-#pragma unroll
-                for (int i = 0; i < 6; ++i) P::st(reinterpret_cast<T*>(a.d[i]) + gi, dA[i], dB[i], s_d);
-                if (y == ny - 1) {  // ghost row above row 0
-                    const long long gg = xa + pstride * z;
-                    *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
-                    P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
-                    P::st(reinterpret_cast<T*>(a.d[2]) + gg, dA[2], dB[2], s_d);
-                }
-                if (y == 0) {  // ghost row below row ny-1
-                    const long long gg = xa + (long long)px * (ny + 1) + pstride * z;
-                    *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
-                    P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
-                    P::st(reinterpret_cast<T*>(a.d[3]) + gg, dA[3], dB[3], s_d);
-                }
-                if (REDUCE) *reinterpret_cast<float2*>(a.Csnap + gi) = cso;
-                // this plane becomes the z-1 neighbour of the next one
-                ph = hx;
-                pl = lx;
-                pd5 = dp[4];
-            }
-            __syncwarp();
-            if (tx == 0) mbar_arrive(&empty[k % kStages]);
-        }
+        return ok;
     }
+    // ---------------------------------------------------------- consumers
+    const int xa = x0 + 2 * tx;  // this lane's cells: xa, xa + 1
+    const int y = y0 + ty;
+    const bool row_ok = y < ny;
+    const int c_own = (ty + 1) * kBX + 2 * tx;  // element index, ghosted arrays
+    const int c_pl = ty * kBX + 2 * tx;         // element index, plain arrays
+    // values stay in storage units; cell_update applies the scales
+    const float inv_lo = 1.0f, inv_d = 1.0f, s_lo = 1.0f, s_d = 1.0f;
+    constexpr int EL = L::EL;
+    auto f1 = [&](const unsigned char* sl, int off) { return *reinterpret_cast<const float*>(sl + off); };
+    auto t1 = [&](const unsigned char* sl, int off, float inv) {
+        return S::ld(*reinterpret_cast<const T*>(sl + off), inv);
+    };
+    auto slot = [&](int k) { return slots + ((seq + k) % kStages) * L::bytes; };
+    auto wait = [&](int k) { return mbar_wait_bounded(&full[(seq + k) % kStages], ((seq + k) / kStages) & 1, a.err); };
+    auto release = [&](int k) {
+        __syncwarp();
+        if (tx == 0) mbar_arrive(&empty[(seq + k) % kStages]);
+    };
+    // x-halo neighbours: left of xa, right of xa + 1
+    const bool lane_l = tx == 0, lane_r = tx == 31;
+    const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (c_own - 1);
+    const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (c_own + 2);
+    const int xl_lo = lane_l ? L::o_cloL + EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + EL * (c_own - 1);
+    const int xr_lo = lane_r ? L::o_cloR + EL * (ty * L::HXL) : L::o_clo + EL * (c_own + 2);
+    const int xl_d1 = lane_l ? L::o_d1L + EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
+    const int xr_d2 = lane_r ? L::o_d2R + EL * (ty * L::HXL) : L::o_d2 + EL * (c_pl + 2);
+
+    ok = wait(0);  // plane zs-1
+    // own cells one plane below
+    const unsigned char* s0 = slot(0);
+    float2 ph = *reinterpret_cast<const float2*>(s0 + L::o_chi + 4 * c_own);
+    float2 pl = P::ld(s0 + L::o_clo + EL * c_own, inv_lo);
+    float2 pd5 = P::ld(s0 + L::o_d5 + EL * c_pl, inv_d);
+    release(0);
+    ok &= wait(1);  // plane zs
+
+    int k = 1;
+    for (int z = zs; z < ze && ok; ++z, ++k) {
+        ok &= wait(k + 1);
+        const unsigned char* sc = slot(k);
+        const unsigned char* sp = slot(k + 1);
+        const uint32_t mm = row_ok ? *reinterpret_cast<const uint32_t*>(sc + L::o_mk + 2 * c_pl) : 0u;
+        const uint32_t ma = mm & 0xffffu, mb = mm >> 16;
+        if ((ma | mb) & kActiveBit) {
+            // own pair
+            const float2 hx = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * c_own);
+            const float2 lx = P::ld(sc + L::o_clo + EL * c_own, inv_lo);
+            float2 dp[6];
+            dp[0] = P::ld(sc + L::o_d1 + EL * c_pl, inv_d);
+            dp[1] = P::ld(sc + L::o_d2 + EL * c_pl, inv_d);
+            dp[2] = P::ld(sc + L::o_d3 + EL * c_own, inv_d);
+            dp[3] = P::ld(sc + L::o_d4 + EL * c_own, inv_d);
+            dp[4] = P::ld(sc + L::o_d5 + EL * c_pl, inv_d);
+            dp[5] = P::ld(sc + L::o_d6 + EL * c_pl, inv_d);
+            const float2 om = *reinterpret_cast<const float2*>(sc + L::o_om + 4 * c_pl);
+            // y and z neighbours of both cells
+            const float2 hym = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own - kBX));
+            const float2 lym = P::ld(sc + L::o_clo + EL * (c_own - kBX), inv_lo);
+            const float2 dym = P::ld(sc + L::o_d3 + EL * (c_own - kBX), inv_d);
+            const float2 hyp = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own + kBX));
+            const float2 lyp = P::ld(sc + L::o_clo + EL * (c_own + kBX), inv_lo);
+            const float2 dyp = P::ld(sc + L::o_d4 + EL * (c_own + kBX), inv_d);
+            const float2 hzp = *reinterpret_cast<const float2*>(sp + L::o_chi + 4 * c_own);
+            const float2 lzp = P::ld(sp + L::o_clo + EL * c_own, inv_lo);
+            const float2 dzp = P::ld(sp + L::o_d6 + EL * c_pl, inv_d);
+            // outer x neighbours
+            const float hxl = f1(sc, xl_f), lxl = t1(sc, xl_lo, inv_lo), dxl = t1(sc, xl_d1, inv_d);
+            const float hxr = f1(sc, xr_f), lxr = t1(sc, xr_lo, inv_lo), dxr = t1(sc, xr_d2, inv_d);
+
+            const long long gi = xa + (long long)px * (y + 1) + pstride * z;
+            float2 cs = make_float2(0.f, 0.f), cso = cs;
+            if (REDUCE) cs = *reinterpret_cast<const float2*>(a.Csnap + gi);
+
+            float hA = 0.f, lA = 0.f, hB = 0.f, lB = 0.f, dA[6], dB[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) { dA[i] = 0.f; dB[i] = 0.f; }
+            if (ma & kActiveBit) {
+                const float dd[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
+                const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
+                const float nl[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
+                const float nd[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
+                cell_update<S, REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
+            }
+            if (mb & kActiveBit) {
+                const float dd[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
+                const float nh[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
+                const float nl[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
+                const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
+                cell_update<S, REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+            }
+            // inactive cells of the pair get zeros, which they already hold
+            *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
+            P::st(reinterpret_cast<T*>(a.clo) + gi, lA, lB, s_lo);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) P::st(reinterpret_cast<T*>(a.d[i]) + gi, dA[i], dB[i], s_d);
+            if (y == ny - 1) {  // ghost row above row 0
+                const long long gg = xa + pstride * z;
+                *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                P::st(reinterpret_cast<T*>(a.d[2]) + gg, dA[2], dB[2], s_d);
+            }
+            if (y == 0) {  // ghost row below row ny-1
+                const long long gg = xa + (long long)px * (ny + 1) + pstride * z;
+                *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                P::st(reinterpret_cast<T*>(a.d[3]) + gg, dA[3], dB[3], s_d);
+            }
+            if (REDUCE) *reinterpret_cast<float2*>(a.Csnap + gi) = cso;
+            // this plane becomes the z-1 neighbour of the next one
+            ph = hx;
+            pl = lx;
+            pd5 = dp[4];
+        }
+        release(k);
+    }
+    if (ok) release(nplanes - 1);  // plane ze, read only as a z+1 neighbour
+    return ok;
+}
+
+__device__ __forceinline__ bool smem_ok(const unsigned char* smem, int* err) {
+    if (smem_u32(smem) & 127u) {  // TMA destinations need this alignment
+        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, 16);
+        return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty) {
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kBY);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// Warp roles: warps 0..kBY-1 each own one row of the tile (two cells per
+// lane) and compute; warp kBY is the producer and issues the TMA loads of
+// one plane per slot.  full[s] completes when a plane has landed in slot s,
+// empty[s] when every consumer warp has released it.  A consumer keeps the
+// z-1 values it needs (its own cells one plane below) in registers, so a
+// slot is live only while its plane is the current or the next one.
+template <class S, bool REDUCE>
+__global__ void __launch_bounds__(kThreads, 1) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
+    // Addressed directly (no integer round trip) so that every slot access
+    // compiles to a shared-memory load.
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kStages;
+    unsigned char* slots = smem_raw + 128;
+    if (!smem_ok(smem_raw, a.err)) return;
+    double rv[RED_N];
+#pragma unroll
+    for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+    init_ring(full, empty);
+    const int zs = blockIdx.z * a.z_chunk;
+    const int ze = min(a.nz, zs + a.z_chunk);
+    march_item<S, REDUCE>(&maps, a, blockIdx.x * kBX, blockIdx.y * kBY, zs, ze, slots, full, empty, 0u, false, rv);
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         block_sum_store<RED_N>(rv, a.partials + blk * RED_N);
     }
+}
+
+// ------------------------------------------------------- batched launch
+// Bounded grid-wide barrier of a cooperative launch: the counter is zeroed
+// before the launch and reaches (round + 1) * gridDim.x.  A block that gives
+// up (~2 s) raises bit 32 and the abort word so that no block waits forever.
+__device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, int* err) {
+    __syncthreads();
+    __shared__ int s_abort;
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        atomicAdd(counter, 1u);
+        const long long t0 = clock64();
+        int ab = 0;
+        for (;;) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
+            if (v >= target) break;
+            ab = *(volatile int*)abort_flag;
+            if (ab) break;
+            if (clock64() - t0 > (1LL << 32)) {
+                atomicOr(err, 32);
+                atomicExch(abort_flag, 1);
+                ab = 1;
+                break;
+            }
+        }
+        __threadfence();
+        s_abort = ab;
+    }
+    __syncthreads();
+    return s_abort == 0;
+}
+
+template <class S>
+__global__ void __launch_bounds__(kThreads, 1) k_march_batch(const BatchInst* __restrict__ insts,
+                                                            const WorkItem* __restrict__ items,
+                                                            const int* __restrict__ n_items_ptr, int nsteps,
+                                                            int parity0, int reduce_last, unsigned* counter,
+                                                            int* abort_flag, double* item_partials, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + kStages;
+    unsigned char* slots = smem_raw + 128;
+    if (!smem_ok(smem_raw, err)) { atomicExch(abort_flag, 1); return; }
+    init_ring(full, empty);
+    const int n_items = *n_items_ptr;
+    unsigned seq = 0;
+    for (int step = 0; step < nsteps; ++step) {
+        const int par = parity0 ^ (step & 1);
+        const bool red = reduce_last && step == nsteps - 1;
+        bool ok = true;
+        for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+            const WorkItem it = items[w];
+            const BatchInst* in = insts + it.inst;
+            // per-instance arguments staged once per item in shared memory
+            __shared__ MarchArgs s_args;
+            __syncthreads();
+            if (threadIdx.x == 0 && threadIdx.y == 0) s_args = in->args[par];
+            __syncthreads();
+            const MarchArgs& a = s_args;
+            double rv[RED_N];
+#pragma unroll
+            for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+            if (red) {
+                ok = march_item<S, true>(&in->maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq,
+                                         step < 2, rv);
+                block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
+            } else {
+                ok = march_item<S, false>(&in->maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq,
+                                          step < 2, rv);
+            }
+            seq += (unsigned)(it.ze - it.zs + 2);
+            ok = __syncthreads_and(ok);
+        }
+        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(abort_flag, 1);
+        if (!grid_sync(counter, (unsigned)(step + 1) * gridDim.x, abort_flag, err)) break;
+    }
+}
+
+// per-instance sums of the item partials (items of an instance are contiguous)
+__global__ void k_batch_finalize(const double* __restrict__ item_partials, const int* __restrict__ inst_first,
+                                 const int* __restrict__ inst_count, double* out) {
+    const int inst = blockIdx.x, slot = blockIdx.y;
+    const int first = inst_first[inst], cnt = inst_count[inst];
+    double acc = 0.0;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x) acc += item_partials[(long long)(first + j) * RED_N + slot];
+    __shared__ double sh[256];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[inst * RED_N + slot] = sh[0];
 }
 
 // ----------------------------------------------------------- host launch
@@ -486,6 +621,62 @@ cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const 
                       : launch_one<StoreF16, false>(maps, a, grid, smem, s);
     return reduce ? launch_one<StoreF32, true>(maps, a, grid, smem, s)
                   : launch_one<StoreF32, false>(maps, a, grid, smem, s);
+}
+
+template <class S>
+static cudaError_t launch_batch_t(const BatchLaunch& b, cudaStream_t s) {
+    const int smem = march_smem_bytes(b.storage);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_march_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_march_batch<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                     cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(b.grid, 1, 1);
+    cfg.blockDim = dim3(32, kBY + 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;  // blocks wait on one another at the step barrier
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_march_batch<S>, b.insts, b.items, b.n_items, b.nsteps, b.parity0,
+                              b.reduce_last, b.counter, b.abort_flag, b.item_partials, b.err);
+}
+
+cudaError_t launch_march_batch(const BatchLaunch& b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    return b.storage == CL_STORE_FP16DEV ? launch_batch_t<StoreF16>(b, s) : launch_batch_t<StoreF32>(b, s);
+}
+
+cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_first, const int* inst_count,
+                                  int n_inst, double* out, cudaStream_t s) {
+    k_batch_finalize<<<dim3(n_inst, RED_N), 256, 0, s>>>(item_partials, inst_first, inst_count, out);
+    return cudaGetLastError();
+}
+
+int march_batch_blocks_per_sm(int storage) {
+    const int smem = march_smem_bytes(storage);
+    int nb = 0;
+    if (storage == CL_STORE_FP16DEV) {
+        cudaFuncSetAttribute(k_march_batch<StoreF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_march_batch<StoreF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_batch<StoreF16>, kThreads, smem);
+    } else {
+        cudaFuncSetAttribute(k_march_batch<StoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaFuncSetAttribute(k_march_batch<StoreF32>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_batch<StoreF32>, kThreads, smem);
+    }
+    return nb;
 }
 
 int march_blocks_per_sm(int storage) {

@@ -36,6 +36,36 @@ struct MarchArgs {
     int* err;
 };
 
+// One structure of a batch: TMA descriptors and arguments for both source
+// parities (args[p] reads time level p and writes level p ^ 1).
+struct BatchInst {
+    MarchMaps maps[2];
+    MarchArgs args[2];
+};
+
+// A tile column of one instance over planes [zs, ze)
+struct WorkItem {
+    int inst, x0, y0, zs, ze;
+};
+
+struct BatchLaunch {
+    int storage;
+    int grid;  // co-resident blocks (cooperative launch)
+    const BatchInst* insts;
+    const WorkItem* items;
+    const int* n_items;  // device count, so the list can shrink between graph replays
+    int nsteps, parity0, reduce_last;
+    unsigned* counter;   // grid barrier counter (zeroed before each launch)
+    int* abort_flag;
+    double* item_partials;  // [item][RED_N] when reduce_last
+    int* err;
+};
+
+cudaError_t launch_march_batch(const BatchLaunch& b, cudaStream_t s);
+cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_first, const int* inst_count,
+                                  int n_inst, double* out, cudaStream_t s);
+int march_batch_blocks_per_sm(int storage);
+
 int march_slot_bytes(int storage);
 int march_smem_bytes(int storage);
 int march_blocks_per_sm(int storage);
