@@ -141,6 +141,11 @@ def with_reservoir(phase: np.ndarray) -> np.ndarray:
 EQ4_EPS045_IONOMER = 0.188743
 EQ4_EPS045_SOLID = 0.361257
 
+# Eq. 4 makes the ionomer share of the non-pore volume independent of the
+# porosity (beta_N = 0.3, theta_Pt = 0.4): eps_N / (1 - eps) = 0.343169
+# (tests check this literal against the oracle's Eq. 4).
+EQ4_IONOMER_SHARE = 0.343169
+
 WORKLOADS = {
     # plain method, small
     "pt_cl_48": dict(shape=(48, 48, 48), seed=0, kind="pt", pore=0.50, ionomer=0.20, c_d=0.01,
@@ -184,3 +189,31 @@ def make_workload(name: str, shape=None, seed=None, reactive: bool | None = None
         params["bc_out"] = 0
         params["k_ms"] = 0.0
     return ph, react, params
+
+
+def batch_workloads(n: int = 64, seed0: int = 100, edge_range=(32, 160), eps_range=(0.35, 0.65),
+                    dx_m: float = 2e-9):
+    """Many small structures of uneven size (the batched-launch workload).
+
+    Member i: a cube of edge uniform in edge_range, porosity uniform in
+    eps_range, Pt layer for even i and NPMC layer (5 % of the volume carved
+    as micropores) for odd i; Knudsen diffusivity at 353 K; D_eff set-up
+    (fixed concentrations 1 and 0 at the x faces, no reaction).
+    Returns a list of (phase, None, params)."""
+    out = []
+    for i in range(n):
+        seed = seed0 + i
+        u1 = hash4(seed, 0xBA7C, 1, 0) / 2.0**64
+        u2 = hash4(seed, 0xBA7C, 2, 0) / 2.0**64
+        L = edge_range[0] + int(u1 * (edge_range[1] - edge_range[0] + 1))
+        eps = eps_range[0] + u2 * (eps_range[1] - eps_range[0])
+        ion = (1.0 - eps) * EQ4_IONOMER_SHARE
+        if i % 2 == 0:
+            ph = pt_cl((L, L, L), seed, eps, ion)
+        else:
+            base = max(eps - 0.05, 0.05)
+            ph = npmc_cl((L, L, L), seed, base, (1.0 - base) * EQ4_IONOMER_SHARE, eps)
+        params = dict(dx_m=dx_m, knudsen=1, T_K=353.0, p_atm=1.0, M_kgmol=0.032, bc_in=0, bc_out=0,
+                      c_in=1.0, c_out=0.0, tau_ref=1.0, k_ms=0.0)
+        out.append((ph, None, params))
+    return out

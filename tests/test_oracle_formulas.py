@@ -83,3 +83,9 @@ def test_workload_literals_match_eq4():
     eN, eC, ePt = oracle.volume_fractions(0.45)
     assert inputs.EQ4_EPS045_IONOMER == pytest.approx(eN, abs=1e-6)
     assert inputs.EQ4_EPS045_SOLID == pytest.approx(eC + ePt, abs=1e-6)
+
+
+def test_ionomer_share_literal_matches_eq4():
+    for eps in (0.35, 0.5, 0.65):
+        eN, eC, ePt = oracle.volume_fractions(eps)
+        assert inputs.EQ4_IONOMER_SHARE == pytest.approx(eN / (1 - eps), abs=1e-6)
