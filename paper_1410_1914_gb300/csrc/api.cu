@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <chrono>
 #include <vector>
 
@@ -183,7 +184,7 @@ void choose_march_grid(cl_lbm* h) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int resident = nsm * march_blocks_per_sm(h->p.storage);
-    const int tiles = (h->px / kBX) * ((h->ny + kBY - 1) / kBY);
+    const int tiles = ((h->px + kBX - 1) / kBX) * ((h->ny + kBY - 1) / kBY);
     int best_gz = 1;
     double best = 1e30;
     const int gz_max = h->nz < 8 ? 1 : h->nz / 8;
@@ -197,7 +198,7 @@ void choose_march_grid(cl_lbm* h) {
         if (cost < best - 1e-9) { best = cost; best_gz = g; }
     }
     h->z_chunk = (h->nz + best_gz - 1) / best_gz;
-    h->mgrid = dim3(h->px / kBX, (h->ny + kBY - 1) / kBY, (h->nz + h->z_chunk - 1) / h->z_chunk);
+    h->mgrid = dim3((h->px + kBX - 1) / kBX, (h->ny + kBY - 1) / kBY, (h->nz + h->z_chunk - 1) / h->z_chunk);
 }
 
 void drop_graphs(cl_lbm* h) {
@@ -423,7 +424,10 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
 
     if (h->march) {
-        h->px = (h->nx + kBX - 1) / kBX * kBX;
+        // row pitch: a multiple of 8 cells (16-byte rows for TMA), at least one
+        // tile; the last tile may overhang it, TMA zero-fills that part without
+        // touching memory and no lane stores there
+        h->px = std::max((h->nx + 7) / 8 * 8, kBX);
         // L2 prefetch pays off for the FP32 state (memory-latency bound), not for FP16 (issue bound)
         h->prefetch = p->storage == CL_STORE_FP32 ? 2 : 0;
         if (const char* e = getenv("CL_LBM_PREFETCH")) h->prefetch = atoi(e);  // tuning override

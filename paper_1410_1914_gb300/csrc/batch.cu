@@ -27,6 +27,7 @@ struct cl_batch {
     cudaStream_t s = nullptr;
     cudaStream_t cap = nullptr;
     int grid = 0;
+    int grid_reduce = 0;
     int z_chunk = 32;
     int prefetch = 0;
     int parity = 0;
@@ -51,7 +52,7 @@ struct cl_batch {
 namespace {
 
 int items_of(const cl_lbm* h, int zc) {
-    return (h->px / kBX) * ((h->ny + kBY - 1) / kBY) * ((h->nz + zc - 1) / zc);
+    return ((h->px + kBX - 1) / kBX) * ((h->ny + kBY - 1) / kBY) * ((h->nz + zc - 1) / zc);
 }
 
 // Work list over the running structures, z ranges of z_chunk planes.
@@ -97,6 +98,7 @@ BatchLaunch launch_desc(cl_batch* b, int nsteps, bool reduce_last) {
     BatchLaunch L;
     L.storage = b->storage;
     L.grid = b->grid;
+    L.grid_reduce = b->grid_reduce;
     L.insts = b->d_insts;
     L.items = b->d_items;
     L.n_items = b->d_n_items;
@@ -191,9 +193,11 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int per_sm = march_batch_blocks_per_sm(b->storage);
-    if (per_sm < 1) { set_msg_txt("batched step kernel does not fit on an SM"); return fail(CL_ERR_CUDA); }
+    const int per_sm = march_batch_blocks_per_sm(b->storage, false);
+    const int per_sm_r = march_batch_blocks_per_sm(b->storage, true);
+    if (per_sm < 1 || per_sm_r < 1) { set_msg_txt("batched step kernel does not fit on an SM"); return fail(CL_ERR_CUDA); }
     b->grid = nsm * per_sm;
+    b->grid_reduce = nsm * per_sm_r;
     // the work list is largest at the smallest z chunk the autotuner tries
     for (int i = 0; i < n; ++i) b->max_items += items_of(b->m[i], std::min(8, b->z_chunk));
     e = cudaMallocAsync(&b->d_insts, sizeof(BatchInst) * n, b->s);

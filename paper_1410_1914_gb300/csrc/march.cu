@@ -534,8 +534,10 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, i
     return s_abort == 0;
 }
 
-template <class S>
-__global__ void __launch_bounds__(kThreads, 1) k_march_batch(const BatchInst* __restrict__ insts,
+// FP16 plain steps fit two resident blocks per SM; the others keep one
+template <class S, bool REDUCE>
+__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 2 : 1)
+    k_march_batch(const BatchInst* __restrict__ insts,
                                                             const WorkItem* __restrict__ items,
                                                             const int* __restrict__ n_items_ptr, int nsteps,
                                                             int parity0, int reduce_last, unsigned* counter,
@@ -550,7 +552,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_march_batch(const BatchInst* __
     unsigned seq = 0;
     for (int step = 0; step < nsteps; ++step) {
         const int par = parity0 ^ (step & 1);
-        const bool red = reduce_last && step == nsteps - 1;
+        const bool red = REDUCE && step == nsteps - 1;
         bool ok = true;
         for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
             const WorkItem it = items[w];
@@ -564,7 +566,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_march_batch(const BatchInst* __
             double rv[RED_N];
 #pragma unroll
             for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
-            if (red) {
+            if (REDUCE && red) {
                 ok = march_item<S, true>(&in->maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq,
                                          step < 2, rv);
                 block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
@@ -623,20 +625,20 @@ cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const 
                   : launch_one<StoreF32, false>(maps, a, grid, smem, s);
 }
 
-template <class S>
-static cudaError_t launch_batch_t(const BatchLaunch& b, cudaStream_t s) {
+template <class S, bool R>
+static cudaError_t launch_batch_t(const BatchLaunch& b, int grid, cudaStream_t s) {
     const int smem = march_smem_bytes(b.storage);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_march_batch<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_march_batch<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_march_batch<S>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(k_march_batch<S, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(b.grid, 1, 1);
+    cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(32, kBY + 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
@@ -645,15 +647,35 @@ static cudaError_t launch_batch_t(const BatchLaunch& b, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_march_batch<S>, b.insts, b.items, b.n_items, b.nsteps, b.parity0,
+    return cudaLaunchKernelEx(&cfg, k_march_batch<S, R>, b.insts, b.items, b.n_items, b.nsteps, b.parity0,
                               b.reduce_last, b.counter, b.abort_flag, b.item_partials, b.err);
 }
 
+template <class S>
+static cudaError_t launch_batch_s(const BatchLaunch& b, cudaStream_t s) {
+    cudaError_t e = cudaSuccess;
+    // plain steps (fewer registers, more resident blocks), then the reducing step
+    const int plain = b.reduce_last ? b.nsteps - 1 : b.nsteps;
+    BatchLaunch p = b;
+    if (plain > 0) {
+        p.nsteps = plain;
+        e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = launch_batch_t<S, false>(p, b.grid, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (b.reduce_last) {
+        p.nsteps = 1;
+        p.parity0 = b.parity0 ^ (plain & 1);
+        e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = launch_batch_t<S, true>(p, b.grid_reduce, s);
+    }
+    return e;
+}
+
 cudaError_t launch_march_batch(const BatchLaunch& b, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
-    if (e != cudaSuccess) return e;
-    return b.storage == CL_STORE_FP16DEV ? launch_batch_t<StoreF16>(b, s) : launch_batch_t<StoreF32>(b, s);
+    return b.storage == CL_STORE_FP16DEV ? launch_batch_s<StoreF16>(b, s) : launch_batch_s<StoreF32>(b, s);
 }
 
 cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_first, const int* inst_count,
@@ -662,21 +684,21 @@ cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_f
     return cudaGetLastError();
 }
 
-int march_batch_blocks_per_sm(int storage) {
-    const int smem = march_smem_bytes(storage);
+template <class S, bool R>
+static int batch_occupancy(int smem) {
     int nb = 0;
-    if (storage == CL_STORE_FP16DEV) {
-        cudaFuncSetAttribute(k_march_batch<StoreF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_march_batch<StoreF16>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_batch<StoreF16>, kThreads, smem);
-    } else {
-        cudaFuncSetAttribute(k_march_batch<StoreF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_march_batch<StoreF32>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_batch<StoreF32>, kThreads, smem);
-    }
+    cudaFuncSetAttribute(k_march_batch<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_march_batch<S, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march_batch<S, R>, kThreads, smem);
     return nb;
+}
+
+int march_batch_blocks_per_sm(int storage, bool reduce) {
+    const int smem = march_smem_bytes(storage);
+    if (storage == CL_STORE_FP16DEV)
+        return reduce ? batch_occupancy<StoreF16, true>(smem) : batch_occupancy<StoreF16, false>(smem);
+    return reduce ? batch_occupancy<StoreF32, true>(smem) : batch_occupancy<StoreF32, false>(smem);
 }
 
 int march_blocks_per_sm(int storage) {

@@ -20,7 +20,7 @@ struct MarchMaps {
 };
 
 struct MarchArgs {
-    int nx, ny, nz, px;  // px: padded row pitch (multiple of kBX)
+    int nx, ny, nz, px;  // px: padded row pitch (multiple of 8 cells, >= kBX)
     int z_chunk;         // planes per block
     int prefetch;        // L2 prefetch distance in planes (0: none)
     // destination time level (padded, two ghost rows per plane)
@@ -50,7 +50,8 @@ struct WorkItem {
 
 struct BatchLaunch {
     int storage;
-    int grid;  // co-resident blocks (cooperative launch)
+    int grid;         // co-resident blocks of the plain-step launch (cooperative)
+    int grid_reduce;  // co-resident blocks of the reducing-step launch
     const BatchInst* insts;
     const WorkItem* items;
     const int* n_items;  // device count, so the list can shrink between graph replays
@@ -64,7 +65,7 @@ struct BatchLaunch {
 cudaError_t launch_march_batch(const BatchLaunch& b, cudaStream_t s);
 cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_first, const int* inst_count,
                                   int n_inst, double* out, cudaStream_t s);
-int march_batch_blocks_per_sm(int storage);
+int march_batch_blocks_per_sm(int storage, bool reduce);
 
 int march_slot_bytes(int storage);
 int march_smem_bytes(int storage);
