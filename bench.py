@@ -264,6 +264,50 @@ def run_batch(args):
     return 0
 
 
+def run_converge(args):
+    """Time-to-converged D_eff (Eq. 19 readout within 1e-3, and staying there)
+    per storage mode, from the linear ramp, on a D_eff set-up of the Pt
+    recipe.  The reference is the FP32-state solve carried to an extrapolated
+    relative change below 1e-9."""
+    import torch
+    from paper_1410_1914_gb300 import Solver, inputs
+    from paper_1410_1914_gb300.convergence import deff_trace, time_to_tolerance
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    shape = args.shape or (48, 48, 48)
+    if shape == (48, 48, 48):
+        ph, react, params = inputs.make_workload("pt_cl_48")
+        label = "48^3 Pt layer, 2 nm, bulk D (plain-method small workload)"
+    else:
+        ph, react, params = inputs.make_workload("pt_cl_256", shape=shape, reactive=False)
+        label = f"{shape[2]}x{shape[1]}x{shape[0]} Pt layer, 2 nm, Knudsen D, D_eff set-up"
+    K = args.check_every
+    max_steps = args.max_steps
+
+    def solver(storage):
+        s = Solver(ph.shape, storage=storage, stream=int(stream.cuda_stream), check_every=K, **params)
+        s.set_structure(ph, react)
+        return s
+
+    ref_s = solver("fp32")
+    st, sec, val = deff_trace(ref_s, max_steps, K, stop_rel_change=1e-9)
+    ref = float(val[-1])
+    ref_s.close()
+    out = {}
+    for storage in ("fp32pop", "fp32", "fp16dev"):
+        s = solver(storage)
+        torch.cuda.synchronize()
+        st, sec, val = deff_trace(s, max_steps, K, stop_rel_change=1e-8)
+        n, t = time_to_tolerance(st, sec, val, ref, 1e-3)
+        out[storage] = {"steps_to_1e-3": n, "seconds_to_1e-3": t,
+                        "final_rel_err": abs(float(val[-1]) - ref) / abs(ref), "steps_run": int(st[-1])}
+        s.close()
+    line = {"metric": "time-to-converged D_eff (rel 1e-3)", "workload": label, "shape_zyx": list(ph.shape),
+            "reference_D_eff_over_Db": ref, "check_every": K, "by_storage": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -280,7 +324,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=1)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="override (nz ny nx)")
-    ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64"])
+    ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64", "converge"])
+    ap.add_argument("--max-steps", type=int, default=3_000_000)
     args = ap.parse_args()
     if args.shape:
         args.shape = tuple(args.shape)
@@ -290,6 +335,8 @@ def main():
         return run_reference(args)
     if args.workload == "batch64":
         return run_batch(args)
+    if args.workload == "converge":
+        return run_converge(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
