@@ -1,0 +1,157 @@
+"""Training data, training loop and evaluation of the learned warm start.
+
+Data: seeded QSGS cubes (Pt and NPMC layers, porosity 0.35-0.65, Knudsen
+diffusivity, D_eff set-up) solved to convergence by the batched LBM; the
+network input comes from each solver's set-up (``cl_lbm_features``) and the
+target is its converged field minus the linear ramp, times nx.
+
+Evaluation: on held-out cubes, the number of steps until D_eff stays within
+1e-3 of the converged value, from the linear ramp and from the network's
+prediction, with the same solver and stopping checks.  The LBM still
+computes the answer; the network only chooses where it starts.
+
+    python -m paper_1410_1914_gb300.warmstart_train --out weights.npz
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import inputs
+
+
+def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32", check_every: int = 200,
+                 tol_rel: float = 1e-6, max_steps: int = 2_000_000):
+    """Solve n seeded cubes in one batch; return (features, targets, masks, stats)."""
+    import torch
+
+    from . import warmstart as W
+    from .batch import Batch
+    from .solver import Solver
+    work = inputs.batch_workloads(n, seed0=seed0, edge_range=(size, size))
+    solvers = []
+    for ph, react, params in work:
+        s = Solver(ph.shape, storage=storage, check_every=check_every, tol_rel=tol_rel, tol_flux=1e-4, **params)
+        s.set_structure(ph, react)
+        solvers.append(s)
+    t0 = time.perf_counter()
+    b = Batch(solvers)
+    status, infos, nconv = b.solve(max_steps)
+    solve_s = time.perf_counter() - t0
+    feats = torch.empty(n, size, size, size, W.FEATURES, dtype=torch.bfloat16, device="cuda")
+    targets = torch.empty(n, size ** 3, dtype=torch.float32, device="cuda")
+    masks = torch.empty(n, size ** 3, dtype=torch.uint8, device="cuda")
+    for i, s in enumerate(solvers):
+        feats[i] = W.features(s)[0]
+        targets[i] = W.target(s)
+        masks[i] = W.active_mask(s)
+    b.close()
+    for s in solvers:
+        s.close()
+    stats = dict(n=n, size=size, status=status, converged=nconv, solve_seconds=solve_s,
+                 mean_steps=float(np.mean([x["steps"] for x in infos])))
+    return feats, targets, masks, stats
+
+
+def train(net, feats, targets, masks, steps: int, batch: int = 4, lr: float = 1e-3, seed: int = 0,
+          log_every: int = 100):
+    import torch
+    n, D = feats.shape[0], feats.shape[1]
+    rng = np.random.default_rng(seed)
+    losses = []
+    t0 = time.perf_counter()
+    for it in range(1, steps + 1):
+        idx = torch.from_numpy(rng.choice(n, size=batch, replace=False)).cuda()
+        x = feats.index_select(0, idx).contiguous()
+        # random y/z rolls and y<->z transposes keep the physics (periodic in y, z)
+        sy, sz = int(rng.integers(D)), int(rng.integers(D))
+        x = torch.roll(x, shifts=(sz, sy), dims=(1, 2))
+        t = torch.roll(targets.index_select(0, idx).view(batch, D, D, D), shifts=(sz, sy), dims=(1, 2))
+        m = torch.roll(masks.index_select(0, idx).view(batch, D, D, D), shifts=(sz, sy), dims=(1, 2))
+        if rng.random() < 0.5:
+            x, t, m = x.transpose(1, 2), t.transpose(1, 2), m.transpose(1, 2)
+        x, t, m = x.contiguous(), t.contiguous().view(-1), m.contiguous().view(-1)
+        lr_t = lr * 0.5 * (1 + np.cos(np.pi * it / steps))
+        net.forward(x, batch, D)
+        net.backward(t, m)
+        net.step(lr=float(lr_t))
+        if it % log_every == 0 or it == steps:
+            losses.append((it, net.loss_value(), time.perf_counter() - t0))
+    torch.cuda.synchronize()
+    return losses
+
+
+def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = "fp32", check_every: int = 200,
+             max_steps: int = 4_000_000, rel: float = 1e-3):
+    """Steps (and seconds) to D_eff within rel, from the ramp and from the warm start."""
+    import torch
+
+    from . import warmstart as W
+    from .convergence import deff_trace, time_to_tolerance
+    from .solver import Solver
+    work = inputs.batch_workloads(n, seed0=seed0, edge_range=(size, size))
+    rows = []
+    for ph, react, params in work:
+        ref_s = Solver(ph.shape, storage="fp32", check_every=check_every, **params)
+        ref_s.set_structure(ph, react)
+        st, sec, val = deff_trace(ref_s, max_steps, check_every, stop_rel_change=1e-9)
+        ref = float(val[-1])
+        ref_s.close()
+        row = {"reference_D_eff_over_Db": ref}
+        for mode in ("ramp", "warm"):
+            s = Solver(ph.shape, storage=storage, check_every=check_every, **params)
+            s.set_structure(ph, react)
+            t_inf = 0.0
+            if mode == "warm":
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                W.warm_start(net, s)
+                torch.cuda.synchronize()
+                t_inf = time.perf_counter() - t1
+            st, sec, val = deff_trace(s, max_steps, check_every, stop_rel_change=1e-8)
+            k, secs = time_to_tolerance(st, sec, val, ref, rel)
+            row[mode] = {"steps": k, "seconds": None if secs is None else secs + t_inf, "inference_s": t_inf,
+                         "final_rel_err": abs(float(val[-1]) - ref) / abs(ref)}
+            s.close()
+        if row["ramp"]["steps"] and row["warm"]["steps"]:
+            row["steps_saved_frac"] = 1.0 - row["warm"]["steps"] / row["ramp"]["steps"]
+        rows.append(row)
+    return rows
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n-train", type=int, default=256)
+    ap.add_argument("--size", type=int, default=48)
+    ap.add_argument("--steps", type=int, default=1500)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--eval-size", type=int, default=96)
+    ap.add_argument("--n-eval", type=int, default=3)
+    ap.add_argument("--out", default="warmstart_weights.npz")
+    ap.add_argument("--report", default=None)
+    args = ap.parse_args()
+    import torch
+
+    from .warmstart import UNet
+    torch.cuda.set_device(0)
+    feats, targets, masks, dstats = make_dataset(args.n_train, args.size)
+    print(json.dumps({"dataset": dstats}), flush=True)
+    net = UNet(seed=0)
+    losses = train(net, feats, targets, masks, args.steps, args.batch, args.lr)
+    print(json.dumps({"train": losses[-5:], "params": net.num_params()}), flush=True)
+    np.savez_compressed(args.out, **{k: v.astype(np.float16) for k, v in net.state_dict().items()})
+    rows = evaluate(net, args.eval_size, args.n_eval)
+    rep = {"dataset": dstats, "train_losses": losses, "params": net.num_params(), "eval": rows,
+           "config": vars(args)}
+    print(json.dumps({"eval": rows}), flush=True)
+    if args.report:
+        with open(args.report, "w") as fh:
+            json.dump(rep, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,148 @@
+"""Warm-start network kernels against the FP64 oracle (gpu).
+
+Convolution forward against oracle.unet.conv3d; weight and data gradients
+against central differences of the oracle (the convolution is linear, so the
+differences are exact up to rounding); the full network's forward and
+gradients against the oracle network and its finite differences.  BF16
+activations bound the agreement: 1e-2 relative per convolution, and a
+gradient cosine above 0.99 for the whole network.
+"""
+import numpy as np
+import pytest
+
+import oracle.unet as OU
+
+pytestmark = pytest.mark.gpu
+
+
+def _bf16(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(torch.bfloat16).float().numpy().astype(np.float64)
+
+
+def _dev(a, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda().contiguous()
+
+
+@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (48, 16), (96, 32), (192, 64), (64, 128)])
+def test_conv_forward(cuda_lib, ci, co):
+    import torch
+
+    from paper_1410_1914_gb300 import warmstart as W
+    rng = np.random.default_rng(ci * 1000 + co)
+    N, D, H, Wd = 2, 4, 6, 10
+    x = _bf16(rng.standard_normal((N, D, H, Wd, ci)))
+    w = _bf16(rng.standard_normal((27, co, ci)) / np.sqrt(27 * ci))
+    b = rng.standard_normal(co)
+    ref = OU.conv3d(x, w, b)
+    out = torch.empty(N, D, H, Wd, co, dtype=torch.bfloat16, device="cuda")
+    W._call("cl_nn_conv3d", W._p(_dev(x, torch.bfloat16)), W._p(_dev(w, torch.bfloat16)),
+            W._p(_dev(b, torch.float32)), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, 1, None)
+    torch.cuda.synchronize()
+    got = out.float().cpu().numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-2 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("ci,co", [(16, 16), (48, 16), (64, 128)])
+def test_conv_gradients_against_differences(cuda_lib, ci, co):
+    import torch
+
+    from paper_1410_1914_gb300 import warmstart as W
+    rng = np.random.default_rng(ci + co)
+    N, D, H, Wd = 1, 4, 4, 6
+    x = _bf16(rng.standard_normal((N, D, H, Wd, ci)))
+    w = _bf16(rng.standard_normal((27, co, ci)) / np.sqrt(27 * ci))
+    gy = _bf16(rng.standard_normal((N, D, H, Wd, co)))
+    zero_b = np.zeros(co)
+    f = lambda xx, ww: float(np.sum(OU.conv3d(xx, ww, zero_b) * gy))
+    # GPU weight gradient
+    M = N * D * H * Wd
+    ws = torch.empty(W._lib().cl_nn_wgrad_workspace(N, D, H, Wd, ci, co) // 4 + 1, dtype=torch.float32, device="cuda")
+    dw = torch.empty(27, co, ci, dtype=torch.float32, device="cuda")
+    dx_in = _dev(x, torch.bfloat16)
+    dgy = _dev(gy, torch.bfloat16)
+    W._call("cl_nn_conv3d_wgrad", W._p(dx_in), W._p(dgy), W._p(ws), W._p(dw), N, D, H, Wd, ci, co, ci, 0, co, 0, 1, None)
+    # GPU data gradient: the convolution with flipped, transposed weights
+    wd = torch.empty(27, ci, co, dtype=torch.bfloat16, device="cuda")
+    W._call("cl_nn_wt_dgrad", W._p(_dev(w, torch.bfloat16)), W._p(wd), co, ci, None)
+    gx = torch.empty(N, D, H, Wd, ci, dtype=torch.bfloat16, device="cuda")
+    W._call("cl_nn_conv3d", W._p(dgy), W._p(wd), None, W._p(gx), N, D, H, Wd, co, ci, co, 0, ci, 0, 0, 1, None)
+    torch.cuda.synchronize()
+    dw = dw.cpu().numpy()
+    gx = gx.float().cpu().numpy()
+    h = 0.5
+    for _ in range(12):
+        t, o, i = rng.integers(27), rng.integers(co), rng.integers(ci)
+        wp, wm = w.copy(), w.copy()
+        wp[t, o, i] += h
+        wm[t, o, i] -= h
+        fd = (f(x, wp) - f(x, wm)) / (2 * h)
+        assert dw[t, o, i] == pytest.approx(fd, rel=1e-2, abs=1e-2 * (1 + abs(fd)))
+    for _ in range(12):
+        idx = tuple(rng.integers(s) for s in x.shape)
+        xp, xm = x.copy(), x.copy()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (f(xp, w) - f(xm, w)) / (2 * h)
+        assert gx[idx] == pytest.approx(fd, rel=2e-2, abs=2e-2 * (1 + abs(fd)))
+
+
+def _oracle_params(net):
+    P = {}
+    for name, ci, co in OU.CONV_LAYERS:
+        w, b = net.params[name]
+        P[name] = (_bf16(w.cpu().numpy()), b.cpu().numpy().astype(np.float64))
+    hw, hb = net.params["head"]
+    P["head"] = (hw.cpu().numpy().astype(np.float64), float(hb.cpu().numpy()[0]))
+    return P
+
+
+def test_network_forward_and_gradients(cuda_lib):
+    import torch
+
+    from paper_1410_1914_gb300 import warmstart as W
+    rng = np.random.default_rng(5)
+    net = W.UNet(seed=3)
+    # non-trivial biases so that ReLUs are mixed
+    for name, _, co in W.CONV_LAYERS:
+        net.params[name][1].copy_(torch.from_numpy(rng.standard_normal(co).astype(np.float32) * 0.1).cuda())
+    net.params["head"][0].copy_(torch.from_numpy(rng.standard_normal(16).astype(np.float32) * 0.3).cuda())
+    N, D = 1, 8
+    x = _bf16(rng.standard_normal((N, D, D, D, 16)))
+    target = rng.standard_normal(N * D ** 3)
+    mask = (rng.random(N * D ** 3) < 0.7).astype(np.uint8)
+    xd = _dev(x, torch.bfloat16)
+    out = net.forward(xd, N, D)
+    P = _oracle_params(net)
+    ref = OU.forward(P, x).reshape(-1)
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.corrcoef(got, ref)[0, 1] > 0.999
+    np.testing.assert_allclose(got, ref, rtol=0, atol=0.05 * np.abs(ref).max())
+    tt = _dev(target, torch.float32)
+    mm = _dev(mask, torch.uint8)
+    net.backward(tt, mm)
+    torch.cuda.synchronize()
+    assert net.loss_value() == pytest.approx(OU.masked_mse(ref.reshape(-1), target, mask), rel=2e-2)
+    # finite differences of the oracle loss for sampled parameters of every layer
+    ga, gf = [], []
+    h = 1e-3
+    for name in [n for n, _, _ in OU.CONV_LAYERS] + ["head"]:
+        gw = net.grads[name][0].cpu().numpy()
+        for _ in range(3):
+            idx = tuple(rng.integers(s) for s in gw.shape)
+            Pp = dict(P)
+            Pm = dict(P)
+            wp, wm = P[name][0].copy(), P[name][0].copy()
+            wp[idx] += h
+            wm[idx] -= h
+            Pp[name] = (wp, P[name][1])
+            Pm[name] = (wm, P[name][1])
+            lp = OU.masked_mse(OU.forward(Pp, x).reshape(-1), target, mask)
+            lm = OU.masked_mse(OU.forward(Pm, x).reshape(-1), target, mask)
+            gf.append((lp - lm) / (2 * h))
+            ga.append(float(gw[idx]))
+    ga, gf = np.array(ga), np.array(gf)
+    cos = float(np.dot(ga, gf) / (np.linalg.norm(ga) * np.linalg.norm(gf)))
+    assert cos > 0.99, (cos, ga, gf)
+    assert np.linalg.norm(ga) == pytest.approx(np.linalg.norm(gf), rel=0.05)

@@ -151,3 +151,35 @@ def test_active_mask_periodic_wrap():
     assert a[1, 4, 5] == 1 and a[1, 0, 0] == 1 and a.sum() == 7
     ph[1, 4, 2] = 1        # cut the seam crossing
     assert oracle.active_mask(ph)[1, 4, 5] == 0
+
+
+# ------------------------------------------------- warm-start network oracle
+def test_network_oracle_conv_matches_scipy_correlate():
+    """oracle.unet.conv3d: x zero padded, y and z periodic, equals a sum of
+    scipy.ndimage.correlate calls on numpy-padded inputs (wrap in z and y,
+    zeros in x)."""
+    import scipy.ndimage as ndi
+
+    import oracle.unet as OU
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((1, 5, 6, 7, 3))
+    w = rng.standard_normal((27, 2, 3))
+    b = rng.standard_normal(2)
+    got = OU.conv3d(x, w, b)
+    for o in range(2):
+        ref = np.full(x.shape[1:4], b[o])
+        for i in range(3):
+            k = w[:, o, i].reshape(3, 3, 3)  # taps ordered (kz, ky, kx)
+            xp = np.pad(x[0, ..., i], ((1, 1), (1, 1), (0, 0)), mode="wrap")
+            xp = np.pad(xp, ((0, 0), (0, 0), (1, 1)), mode="constant")
+            ref += ndi.correlate(xp, k, mode="constant", cval=0.0)[1:-1, 1:-1, 1:-1]
+        np.testing.assert_allclose(got[0, ..., o], ref, atol=1e-12)
+
+
+def test_network_oracle_pool_up_are_adjoint_scaled():
+    """<pool(a), b> = <a, up(b)> / 8 (average pooling vs nearest upsampling)."""
+    import oracle.unet as OU
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal((1, 4, 6, 8, 3))
+    bb = rng.standard_normal((1, 2, 3, 4, 3))
+    assert np.sum(OU.pool(a) * bb) == pytest.approx(np.sum(a * OU.up(bb)) / 8, rel=1e-12)
