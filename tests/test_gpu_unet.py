@@ -37,8 +37,9 @@ def test_conv_forward(cuda_lib, ci, co):
     b = rng.standard_normal(co)
     ref = OU.conv3d(x, w, b)
     out = torch.empty(N, D, H, Wd, co, dtype=torch.bfloat16, device="cuda")
-    W._call("cl_nn_conv3d", W._p(_dev(x, torch.bfloat16)), W._p(_dev(w, torch.bfloat16)),
-            W._p(_dev(b, torch.float32)), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, 1, None)
+    # keep the device copies alive until the kernel has run
+    xd, wd, bd = _dev(x, torch.bfloat16), _dev(w, torch.bfloat16), _dev(b, torch.float32)
+    W._call("cl_nn_conv3d", W._p(xd), W._p(wd), W._p(bd), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, 1, None)
     torch.cuda.synchronize()
     got = out.float().cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-2 * np.abs(ref).max())
@@ -65,7 +66,8 @@ def test_conv_gradients_against_differences(cuda_lib, ci, co):
     W._call("cl_nn_conv3d_wgrad", W._p(dx_in), W._p(dgy), W._p(ws), W._p(dw), N, D, H, Wd, ci, co, ci, 0, co, 0, 1, None)
     # GPU data gradient: the convolution with flipped, transposed weights
     wd = torch.empty(27, ci, co, dtype=torch.bfloat16, device="cuda")
-    W._call("cl_nn_wt_dgrad", W._p(_dev(w, torch.bfloat16)), W._p(wd), co, ci, None)
+    w_dev = _dev(w, torch.bfloat16)
+    W._call("cl_nn_wt_dgrad", W._p(w_dev), W._p(wd), co, ci, None)
     gx = torch.empty(N, D, H, Wd, ci, dtype=torch.bfloat16, device="cuda")
     W._call("cl_nn_conv3d", W._p(dgy), W._p(wd), None, W._p(gx), N, D, H, Wd, co, ci, co, 0, ci, 0, 0, 1, None)
     torch.cuda.synchronize()
