@@ -7,7 +7,8 @@ convolutions with FP32 accumulation); this module only sequences them and
 owns the device buffers (torch tensors, used as memory).
 
 Input (16 channels per voxel, from ``cl_lbm_features``): active, solid,
-ionomer, micropore, scaled log relative diffusivity, x position in [0, 1].
+ionomer, micropore, scaled log relative diffusivity, the linear ramp
+between the two face concentrations.
 Output: the correction to the linear ramp, in units of (C_in - C_out)/nx, so
 that the same local structure gives the same target at any box length; the
 warm start is ramp + output / nx on active cells.

@@ -129,7 +129,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--eval-size", type=int, default=96)
+    ap.add_argument("--eval-size", type=int, nargs="+", default=[96])
     ap.add_argument("--n-eval", type=int, default=3)
     ap.add_argument("--out", default="warmstart_weights.npz")
     ap.add_argument("--report", default=None)
@@ -144,10 +144,15 @@ def main():
     losses = train(net, feats, targets, masks, args.steps, args.batch, args.lr)
     print(json.dumps({"train": losses[-5:], "params": net.num_params()}), flush=True)
     np.savez_compressed(args.out, **{k: v.astype(np.float16) for k, v in net.state_dict().items()})
-    rows = evaluate(net, args.eval_size, args.n_eval)
+    rows = []
+    for size in args.eval_size:
+        r = evaluate(net, size, args.n_eval)
+        for x in r:
+            x["size"] = size
+        print(json.dumps({"eval": r}), flush=True)
+        rows += r
     rep = {"dataset": dstats, "train_losses": losses, "params": net.num_params(), "eval": rows,
            "config": vars(args)}
-    print(json.dumps({"eval": rows}), flush=True)
     if args.report:
         with open(args.report, "w") as fh:
             json.dump(rep, fh, indent=1)
