@@ -37,19 +37,43 @@ def test_header_declares_the_entry_points():
         assert required in names
 
 
+def declared_arity():
+    """name -> number of parameters, from the prototypes in include/*.h."""
+    out = {}
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w\s\*]*?\b(cl_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.M):
+            if m.group(0).lstrip().startswith("typedef"):
+                continue
+            args = m.group(2).strip()
+            out[m.group(1)] = 0 if args in ("", "void") else args.count(",") + 1
+    return out
+
+
+def _bindings():
+    from paper_1410_1914_gb300 import _lib, warmstart
+    sigs = {n: len(a) for n, (_, a) in _lib.SIGNATURES.items()}
+    sigs.update({n: len(a) for n, (_, a) in warmstart._SIGS.items()})
+    return sigs
+
+
 def test_every_declared_symbol_is_exported(lib):
-    from paper_1410_1914_gb300 import _lib
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
-    # the binding mirrors every declared function
-    assert set(declared_functions()) <= set(_lib.SIGNATURES), set(declared_functions()) - set(_lib.SIGNATURES)
+    # the bindings mirror every declared function, with the same arity
+    sigs = _bindings()
+    assert set(declared_functions()) <= set(sigs), set(declared_functions()) - set(sigs)
+    arity = declared_arity()
+    assert set(arity) == set(declared_functions())
+    bad = {n: (k, sigs[n]) for n, k in arity.items() if sigs[n] != k}
+    assert not bad, bad
 
 
 def test_struct_layouts_match_c(tmp_path):
     from paper_1410_1914_gb300 import _lib
     structs = {"cl_params": _lib.cl_params, "cl_structure_info": _lib.cl_structure_info,
                "cl_solve_info": _lib.cl_solve_info}
-    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cl_lbm.h"', "int main(void){"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cl_lbm.h"', '#include "cl_nn.h"', "int main(void){"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')
         for f, _ in cls._fields_:
