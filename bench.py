@@ -32,7 +32,17 @@ import hashlib
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
-KERNEL_SRC = os.path.join(ROOT, "paper_1410_1914_gb300", "csrc", "march.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1410_1914_gb300", "csrc", f)
+               for f in ("march.cu", "march.cuh", "device_util.cuh")]
+
+
+def kernel_src_sha256() -> str:
+    """sha256 over the step kernel's sources (the key of profiles/traffic.json)."""
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 sys.path.insert(0, ROOT)
 
@@ -116,8 +126,7 @@ def measured_traffic(storage: str, n_cells: int):
     try:
         with open(TRAFFIC_JSON) as fh:
             rec = json.load(fh)[storage]
-        with open(KERNEL_SRC, "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        sha = kernel_src_sha256()
     except (OSError, KeyError, ValueError):
         return None, "no capture"
     if rec.get("src_sha256") != sha:
