@@ -127,7 +127,14 @@ cl_status cl_nn_to_bf16(const float* a, void* b, long long n, void* stream);
    channels 0 active (inlet-connected transport cell), 1 solid, 2 ionomer,
    3 micropore, 4 max(0, 1 + ln(D/D_max)/6) on active cells with
    D/D_max = (1/omega - 1/2)/(tau_ref - 1/2) (Eq. 24), 5 the linear ramp
-   c_in + (c_out - c_in)(x + 1/2)/nx, 6..15 zero.  Synchronises the stream.
+   c_in + (c_out - c_in)(x + 1/2)/nx, 6 the series-resistor profile s(x):
+   the inlet half cell, the links between planes x and x+1 and the outlet
+   half cell in series, each with the mean over its ny*nz cross-section of
+   the steady D3Q7 face conductance (2 D/D_max for a half cell, the harmonic
+   2 D_a D_b/(D_a + D_b) for a link between two active cells, 0 otherwise),
+   s(x) = c_in - (c_in - c_out) (R_inlet + sum_{x'<x} R_link(x')) / R_total;
+   7 (s(x) - ramp(x)) nx / (4 (c_in - c_out)), 8..15 zero.
+   Uses the handle's readout scratch; synchronises the stream.
    Errors: CL_ERR_STATE without a structure, CL_ERR_ARG for NULL. */
 cl_status cl_lbm_features(cl_handle h, void* feat);
 

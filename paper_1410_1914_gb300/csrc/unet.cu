@@ -431,13 +431,81 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __rest
 }
 
 // ----------------------------------------------------- warm-start I/O
+// D / D_max of an active cell from its relaxation rate (Eq. 24 inverted):
+// (1/omega - 1/2) / (tau_ref - 1/2).
+__device__ __forceinline__ float rel_diffusivity(float omega, float tau_ref) {
+    return (1.f / omega - 0.5f) / (tau_ref - 0.5f);
+}
+
+// Cross-section conductances along x, per unit area, in units of D_max:
+//   G[2x]     = mean over the ny*nz cells of plane x of D/D_max (0 on
+//               inactive cells); the half-cell faces at the two x ends
+//               conduct 2 G[0] and 2 G[2(nx-1)];
+//   G[2x + 1] = mean over the ny*nz links between planes x and x+1 of the
+//               harmonic link conductance 2 D_a D_b / (D_a + D_b) (0 unless
+//               both cells are active): the same face conductance as the
+//               steady D3Q7 flux between two cells.
+// One block per plane, fixed reduction order.
+__global__ void k_plane_conductance(const uint16_t* __restrict__ mask, const float* __restrict__ omega, int nx,
+                                    long long nyz, float tau_ref, double* __restrict__ G) {
+    const int x = blockIdx.x;
+    double sp = 0.0, sl = 0.0;
+    for (long long r = threadIdx.x; r < nyz; r += blockDim.x) {
+        const long long c = x + (long long)nx * r;
+        if (!(mask[c] & kActiveBit)) continue;
+        const double a = (double)rel_diffusivity(omega[c], tau_ref);
+        sp += a;
+        if (x + 1 < nx && (mask[c + 1] & kActiveBit)) {
+            const double b = (double)rel_diffusivity(omega[c + 1], tau_ref);
+            sl += 2.0 * a * b / (a + b);
+        }
+    }
+    __shared__ double sh[2][256];
+    sh[0][threadIdx.x] = sp;
+    sh[1][threadIdx.x] = sl;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
+            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        G[2 * x] = sh[0][0] / (double)nyz;
+        G[2 * x + 1] = sh[1][0] / (double)nyz;
+    }
+}
+
+// Series-resistor profile between the two Dirichlet faces: the inlet half
+// cell (resistance 1/(2 G[0])), the links between planes (1/G[2x+1]) and the
+// outlet half cell (1/(2 G[2(nx-1)])) in series; the concentration at the
+// centre of plane x is
+//   s(x) = c_in - (c_in - c_out) (R_inlet + sum_{x' < x} R_link(x')) / R_total,
+// the linear ramp when every plane conducts alike.  One thread.
+__global__ void k_series_profile(const double* __restrict__ G, int nx, double c_in, double c_out,
+                                 double* __restrict__ s) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double r_in = 1.0 / fmax(2.0 * G[0], 1e-12);
+    double tot = r_in + 1.0 / fmax(2.0 * G[2 * (nx - 1)], 1e-12);
+    for (int x = 0; x + 1 < nx; ++x) tot += 1.0 / fmax(G[2 * x + 1], 1e-12);
+    double acc = r_in;
+    for (int x = 0; x < nx; ++x) {
+        s[x] = c_in - (c_in - c_out) * acc / tot;
+        if (x + 1 < nx) acc += 1.0 / fmax(G[2 * x + 1], 1e-12);
+    }
+}
+
 // Network input features from a solver's set-up, 16 channels per voxel:
-// 0 active, 1 solid, 2 ionomer, 3 micropore, 4 log(omega-derived D / D_max)
-// scaled to [0, 1] (0 inactive), 5 the linear ramp, 6..15 zero.  D / D_max =
-// (1/omega - 1/2) / (tau_ref - 1/2) on active cells.
+// 0 active, 1 solid, 2 ionomer, 3 micropore, 4 log(D / D_max) mapped to
+// max(0, 1 + ln(D/D_max)/6) on active cells (0 elsewhere), 5 the linear ramp,
+// 6 the series-resistor profile s(x), 7 (s(x) - ramp(x)) nx / (4 (c_in -
+// c_out)), 8..15 zero.  Channels 6 and 7 carry what a field at one place
+// cannot see locally: how the resistance of every plane in x shifts the
+// mean profile.
 __global__ void k_features(const uint8_t* __restrict__ phase, const uint16_t* __restrict__ mask,
-                           const float* __restrict__ omega, int nx, long long N, float tau_ref, float c_in, float c_out,
-                           __nv_bfloat16* __restrict__ feat) {
+                           const float* __restrict__ omega, const double* __restrict__ series, int nx, long long N,
+                           float tau_ref, float c_in, float c_out, __nv_bfloat16* __restrict__ feat) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const bool act = (mask[c] & kActiveBit) != 0;
         const uint8_t ph = phase[c];
@@ -448,12 +516,13 @@ __global__ void k_features(const uint8_t* __restrict__ phase, const uint16_t* __
         f[1] = ph == 1 ? 1.f : 0.f;
         f[2] = ph == 2 ? 1.f : 0.f;
         f[3] = ph == 3 ? 1.f : 0.f;
-        if (act) {
-            const float rel = (1.f / omega[c] - 0.5f) / (tau_ref - 0.5f);
-            f[4] = fmaxf(0.f, 1.f + logf(fmaxf(rel, 1e-6f)) / 6.f);
-        }
+        if (act) f[4] = fmaxf(0.f, 1.f + logf(fmaxf(rel_diffusivity(omega[c], tau_ref), 1e-6f)) / 6.f);
         const int x = (int)(c % nx);
-        f[5] = c_in + (c_out - c_in) * (x + 0.5f) / nx;
+        const float ramp = c_in + (c_out - c_in) * (x + 0.5f) / nx;
+        f[5] = ramp;
+        const float s = (float)series[x];
+        f[6] = s;
+        f[7] = c_in != c_out ? (s - ramp) * (float)nx / (4.f * (c_in - c_out)) : 0.f;
 #pragma unroll
         for (int k = 0; k < 16; k += 2)
             *reinterpret_cast<__nv_bfloat162*>(feat + c * 16 + k) = __floats2bfloat162_rn(f[k], f[k + 1]);
@@ -614,8 +683,13 @@ extern "C" {
 cl_status cl_lbm_features(cl_handle h, void* feat) {
     CKS(h && h->have_structure ? CL_OK : CL_ERR_STATE);
     if (!feat) return CL_ERR_ARG;
-    k_features<<<kEw, 256, 0, h->s>>>(h->phase, h->mask, h->omega, h->nx, h->N, (float)h->p.tau_ref, (float)h->p.c_in,
-                                      (float)h->p.c_out, (__nv_bfloat16*)feat);
+    // cross-section conductances and the series profile in the readout scratch (5 nx doubles)
+    double* G = h->d_plane;
+    double* series = h->d_plane + 2 * h->nx;
+    k_plane_conductance<<<h->nx, 256, 0, h->s>>>(h->mask, h->omega, h->nx, h->N / h->nx, (float)h->p.tau_ref, G);
+    k_series_profile<<<1, 32, 0, h->s>>>(G, h->nx, h->p.c_in, h->p.c_out, series);
+    k_features<<<kEw, 256, 0, h->s>>>(h->phase, h->mask, h->omega, series, h->nx, h->N, (float)h->p.tau_ref,
+                                      (float)h->p.c_in, (float)h->p.c_out, (__nv_bfloat16*)feat);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(h->s));
     return CL_OK;

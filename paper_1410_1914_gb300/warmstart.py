@@ -8,7 +8,9 @@ owns the device buffers (torch tensors, used as memory).
 
 Input (16 channels per voxel, from ``cl_lbm_features``): active, solid,
 ionomer, micropore, scaled log relative diffusivity, the linear ramp
-between the two face concentrations.
+between the two face concentrations, the series-resistor profile of the
+planes along x and its deviation from the ramp (the part of the mean
+profile that no bounded receptive field sees).
 Output: the correction to the linear ramp, in units of (C_in - C_out)/nx, so
 that the same local structure gives the same target at any box length; the
 warm start is ramp + output / nx on active cells.
@@ -104,11 +106,23 @@ class UNet:
         self.shape = None
 
     # ------------------------------------------------------------ buffers
+    _BUF_KEYS = ("a", "g", "out", "gy", "loss", "loss_ws", "wsp", "wd")
+
     def _alloc(self, N, D):
+        """Activation, gradient and workspace buffers for batch N of D^3 cubes,
+        kept per shape so that alternating shapes does not reallocate."""
         torch = self.torch
         if self.shape == (N, D):
             return
+        if not hasattr(self, "_bufs"):
+            self._bufs = {}
+        if self.shape is not None:
+            self._bufs[self.shape] = {k: getattr(self, k) for k in self._BUF_KEYS}
         self.shape = (N, D)
+        if (N, D) in self._bufs:
+            for k, v in self._bufs[(N, D)].items():
+                setattr(self, k, v)
+            return
         bf = dict(dtype=torch.bfloat16, device=self.dev)
         sizes = {1: D, 2: D // 2, 3: D // 4, 4: D // 8}
         chans = {"e1a": (1, 16), "cat1": (1, 48), "d1a": (1, 16), "d1": (1, 16),

@@ -24,8 +24,9 @@ from . import inputs
 
 
 def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32", check_every: int = 200,
-                 tol_rel: float = 1e-6, max_steps: int = 2_000_000):
-    """Solve n seeded cubes in one batch; return (features, targets, masks, stats)."""
+                 tol_rel: float = 1e-6, max_steps: int = 4_000_000):
+    """Solve n seeded cubes of edge `size` in one batch; return (features,
+    targets, masks, stats)."""
     import torch
 
     from . import warmstart as W
@@ -51,42 +52,56 @@ def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32
     b.close()
     for s in solvers:
         s.close()
-    stats = dict(n=n, size=size, status=status, converged=nconv, solve_seconds=solve_s,
-                 mean_steps=float(np.mean([x["steps"] for x in infos])))
+    stats = dict(n=n, size=size, seed0=seed0, tol_rel=tol_rel, status=status, converged=nconv,
+                 solve_seconds=solve_s, mean_steps=float(np.mean([x["steps"] for x in infos])))
     return feats, targets, masks, stats
 
 
-def train(net, feats, targets, masks, steps: int, batch: int = 4, lr: float = 1e-3, seed: int = 0,
-          log_every: int = 100):
+def _augment(rng, x, t, m, D):
+    """Random y/z rolls and a y<->z transpose: the structures are periodic in
+    y and z and statistically isotropic there, so the target moves with them."""
     import torch
-    n, D = feats.shape[0], feats.shape[1]
+    B = x.shape[0]
+    sy, sz = int(rng.integers(D)), int(rng.integers(D))
+    x = torch.roll(x, shifts=(sz, sy), dims=(1, 2))
+    t = torch.roll(t.view(B, D, D, D), shifts=(sz, sy), dims=(1, 2))
+    m = torch.roll(m.view(B, D, D, D), shifts=(sz, sy), dims=(1, 2))
+    if rng.random() < 0.5:
+        x, t, m = x.transpose(1, 2), t.transpose(1, 2), m.transpose(1, 2)
+    return x.contiguous(), t.contiguous().view(-1), m.contiguous().view(-1)
+
+
+def train(net, groups, steps: int, lr: float = 1e-3, seed: int = 0, log_every: int = 100):
+    """groups: list of (feats, targets, masks, batch, weight); each step draws
+    one group with probability proportional to its weight, then a batch of
+    distinct cubes from it.  Cosine learning-rate decay."""
+    import torch
     rng = np.random.default_rng(seed)
+    w = np.array([g[4] for g in groups], dtype=np.float64)
+    w /= w.sum()
     losses = []
     t0 = time.perf_counter()
     for it in range(1, steps + 1):
-        idx = torch.from_numpy(rng.choice(n, size=batch, replace=False)).cuda()
-        x = feats.index_select(0, idx).contiguous()
-        # random y/z rolls and y<->z transposes keep the physics (periodic in y, z)
-        sy, sz = int(rng.integers(D)), int(rng.integers(D))
-        x = torch.roll(x, shifts=(sz, sy), dims=(1, 2))
-        t = torch.roll(targets.index_select(0, idx).view(batch, D, D, D), shifts=(sz, sy), dims=(1, 2))
-        m = torch.roll(masks.index_select(0, idx).view(batch, D, D, D), shifts=(sz, sy), dims=(1, 2))
-        if rng.random() < 0.5:
-            x, t, m = x.transpose(1, 2), t.transpose(1, 2), m.transpose(1, 2)
-        x, t, m = x.contiguous(), t.contiguous().view(-1), m.contiguous().view(-1)
+        feats, targets, masks, batch, _ = groups[int(rng.choice(len(groups), p=w))]
+        n, D = feats.shape[0], feats.shape[1]
+        idx = torch.from_numpy(rng.choice(n, size=min(batch, n), replace=False)).cuda()
+        x, t, m = _augment(rng, feats.index_select(0, idx), targets.index_select(0, idx),
+                           masks.index_select(0, idx), D)
         lr_t = lr * 0.5 * (1 + np.cos(np.pi * it / steps))
-        net.forward(x, batch, D)
+        net.forward(x, x.shape[0], D)
         net.backward(t, m)
         net.step(lr=float(lr_t))
         if it % log_every == 0 or it == steps:
-            losses.append((it, net.loss_value(), time.perf_counter() - t0))
+            losses.append((it, D, net.loss_value(), time.perf_counter() - t0))
     torch.cuda.synchronize()
     return losses
 
 
 def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = "fp32", check_every: int = 200,
-             max_steps: int = 4_000_000, rel: float = 1e-3):
-    """Steps (and seconds) to D_eff within rel, from the ramp and from the warm start."""
+             max_steps: int = 6_000_000, rel: float = 1e-3):
+    """Steps (and seconds) to D_eff within rel, from the ramp and from the
+    warm start.  The ramp run is carried on to an extrapolated relative
+    change below 1e-9 and its last D_eff is the converged reference."""
     import torch
 
     from . import warmstart as W
@@ -95,12 +110,7 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
     work = inputs.batch_workloads(n, seed0=seed0, edge_range=(size, size))
     rows = []
     for ph, react, params in work:
-        ref_s = Solver(ph.shape, storage="fp32", check_every=check_every, **params)
-        ref_s.set_structure(ph, react)
-        st, sec, val = deff_trace(ref_s, max_steps, check_every, stop_rel_change=1e-9)
-        ref = float(val[-1])
-        ref_s.close()
-        row = {"reference_D_eff_over_Db": ref}
+        row = {}
         for mode in ("ramp", "warm"):
             s = Solver(ph.shape, storage=storage, check_every=check_every, **params)
             s.set_structure(ph, react)
@@ -111,11 +121,14 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
                 W.warm_start(net, s)
                 torch.cuda.synchronize()
                 t_inf = time.perf_counter() - t1
-            st, sec, val = deff_trace(s, max_steps, check_every, stop_rel_change=1e-8)
+            st, sec, val = deff_trace(s, max_steps, check_every, stop_rel_change=1e-9 if mode == "ramp" else 1e-8)
+            s.close()
+            if mode == "ramp":
+                ref = float(val[-1])
+                row["reference_D_eff_over_Db"] = ref
             k, secs = time_to_tolerance(st, sec, val, ref, rel)
             row[mode] = {"steps": k, "seconds": None if secs is None else secs + t_inf, "inference_s": t_inf,
                          "final_rel_err": abs(float(val[-1]) - ref) / abs(ref)}
-            s.close()
         if row["ramp"]["steps"] and row["warm"]["steps"]:
             row["steps_saved_frac"] = 1.0 - row["warm"]["steps"] / row["ramp"]["steps"]
         rows.append(row)
@@ -124,10 +137,9 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n-train", type=int, default=256)
-    ap.add_argument("--size", type=int, default=48)
-    ap.add_argument("--steps", type=int, default=1500)
-    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--data", nargs="+", default=["48:256:4", "96:48:1"],
+                    help="training groups edge:count:batch (cubes of that edge, solved, batch per step)")
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-size", type=int, nargs="+", default=[96])
     ap.add_argument("--n-eval", type=int, default=3)
@@ -138,11 +150,17 @@ def main():
 
     from .warmstart import UNet
     torch.cuda.set_device(0)
-    feats, targets, masks, dstats = make_dataset(args.n_train, args.size)
-    print(json.dumps({"dataset": dstats}), flush=True)
+    groups, dstats = [], []
+    for k, spec in enumerate(args.data):
+        size, count, batch = (int(v) for v in spec.split(":"))
+        f, t, m, st = make_dataset(count, size, seed0=1000 + 10000 * k, tol_rel=1e-6 if size <= 64 else 1e-5)
+        print(json.dumps({"dataset": st}), flush=True)
+        dstats.append(st)
+        # equal voxels per draw: weight a group by its cubes' share of the data volume
+        groups.append((f, t, m, batch, count * size ** 3))
     net = UNet(seed=0)
-    losses = train(net, feats, targets, masks, args.steps, args.batch, args.lr)
-    print(json.dumps({"train": losses[-5:], "params": net.num_params()}), flush=True)
+    losses = train(net, groups, args.steps, args.lr)
+    print(json.dumps({"train": losses[-6:], "params": net.num_params()}), flush=True)
     np.savez_compressed(args.out, **{k: v.astype(np.float16) for k, v in net.state_dict().items()})
     rows = []
     for size in args.eval_size:

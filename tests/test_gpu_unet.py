@@ -148,3 +148,54 @@ def test_network_forward_and_gradients(cuda_lib):
     cos = float(np.dot(ga, gf) / (np.linalg.norm(ga) * np.linalg.norm(gf)))
     assert cos > 0.99, (cos, ga, gf)
     assert np.linalg.norm(ga) == pytest.approx(np.linalg.norm(gf), rel=0.05)
+
+
+def test_features_target_and_warm_field(cuda_lib):
+    """Solver glue: the 16 input channels against the oracle's set-up
+    (active set, D/D_max of Eq. 7-9, the series-resistor profile written out
+    here in numpy), the training target against the solver's own field, and
+    the warm-started field against ramp + prediction."""
+    import torch
+
+    import oracle
+    from paper_1410_1914_gb300 import Solver, inputs
+    from paper_1410_1914_gb300 import warmstart as W
+    ph, _, params = inputs.batch_workloads(2, seed0=7, edge_range=(24, 24))[1]
+    nz, ny, nx = ph.shape
+    o = oracle.OracleLBM(ph, **params)
+    act = o.active().astype(bool)
+    rel = np.where(act, o.D() / o.D_max, 0.0)
+    x = np.arange(nx)
+    ramp = 1.0 - (x + 0.5) / nx
+    # series resistors: inlet half cell, harmonic links between planes, outlet half cell
+    a, b = rel[:, :, :-1], rel[:, :, 1:]
+    both = act[:, :, :-1] & act[:, :, 1:]
+    g_link = np.where(both, 2 * a * b / np.where(both, a + b, 1.0), 0.0).sum(axis=(0, 1)) / (ny * nz)
+    R = np.concatenate([[1 / (2 * rel[:, :, 0].sum() / (ny * nz))], 1 / g_link,
+                        [1 / (2 * rel[:, :, -1].sum() / (ny * nz))]])
+    series = 1.0 - np.cumsum(R)[:-1] / R.sum()
+    exp = np.zeros(ph.shape + (16,))
+    exp[..., 0] = act
+    exp[..., 1] = ph == 1
+    exp[..., 2] = ph == 2
+    exp[..., 3] = ph == 3
+    exp[..., 4] = np.where(act, np.maximum(0.0, 1.0 + np.log(np.maximum(rel, 1e-6)) / 6.0), 0.0)
+    exp[..., 5] = ramp
+    exp[..., 6] = series
+    exp[..., 7] = (series - ramp) * nx / 4.0
+    with Solver(ph.shape, storage="fp32", **params) as s:
+        s.set_structure(ph)
+        f = W.features(s)[0].float().cpu().numpy()
+        np.testing.assert_allclose(f, exp, rtol=2 ** -7, atol=1e-5)
+        # target: (C - ramp) * nx / (c_in - c_out) on active cells
+        s.step(300)
+        C = s.field()
+        t = W.target(s).cpu().numpy().reshape(ph.shape)
+        np.testing.assert_allclose(t, np.where(act, (C - ramp) * nx, 0.0), rtol=1e-6, atol=1e-5)
+        # warm field: ramp + prediction on active cells, 0 elsewhere
+        pred = np.random.default_rng(0).standard_normal(ph.size).astype(np.float32) * 0.01
+        pd = torch.from_numpy(pred).cuda()
+        W._call("cl_lbm_init_warm", __import__("ctypes").c_void_p(s.h), W._p(pd))
+        torch.cuda.synchronize()
+        C0 = s.field()
+        np.testing.assert_allclose(C0, np.where(act, ramp + pred.reshape(ph.shape), 0.0), rtol=0, atol=1e-7)
