@@ -424,10 +424,13 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
 
     if (h->march) {
-        // row pitch: a multiple of 8 cells (16-byte rows for TMA), at least one
-        // tile; the last tile may overhang it, TMA zero-fills that part without
-        // touching memory and no lane stores there
-        h->px = std::max((h->nx + 7) / 8 * 8, kBX);
+        // row pitch: a multiple of 16 cells, so that every row starts on a
+        // 32-byte sector of the f16 arrays and the lanes that store a sector
+        // never reach past the row; at least one tile.  The last tile may
+        // overhang the pitch: TMA zero-fills that part without touching
+        // memory, and no lane stores there (a sector with an active cell
+        // lies inside the pitch)
+        h->px = std::max((h->nx + 15) / 16 * 16, kBX);
         // L2 prefetch pays off for the FP32 state (memory-latency bound), not for FP16 (issue bound)
         h->prefetch = p->storage == CL_STORE_FP32 ? 2 : 0;
         if (const char* e = getenv("CL_LBM_PREFETCH")) h->prefetch = atoi(e);  // tuning override

@@ -363,23 +363,40 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
     const int xl_d1 = lane_l ? L::o_d1L + EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
     const int xr_d2 = lane_r ? L::o_d2R + EL * (ty * L::HXL) : L::o_d2 + EL * (c_pl + 2);
 
-    ok = wait(0);  // plane zs-1
+    // every lane of a warp leaves the plane loop together (warp votes below)
+    ok = __all_sync(0xffffffffu, wait(0));  // plane zs-1
     // own cells one plane below
     const unsigned char* s0 = slot(0);
     float2 ph = *reinterpret_cast<const float2*>(s0 + L::o_chi + 4 * c_own);
     float2 pl = P::ld(s0 + L::o_clo + EL * c_own, inv_lo);
     float2 pd5 = P::ld(s0 + L::o_d5 + EL * c_pl, inv_d);
     release(0);
-    ok &= wait(1);  // plane zs
+    ok = __all_sync(0xffffffffu, ok && wait(1));  // plane zs
 
     int k = 1;
     for (int z = zs; z < ze && ok; ++z, ++k) {
-        ok &= wait(k + 1);
+        ok = __all_sync(0xffffffffu, ok && wait(k + 1));
         const unsigned char* sc = slot(k);
         const unsigned char* sp = slot(k + 1);
         const uint32_t mm = row_ok ? *reinterpret_cast<const uint32_t*>(sc + L::o_mk + 2 * c_pl) : 0u;
         const uint32_t ma = mm & 0xffffu, mb = mm >> 16;
-        if ((ma | mb) & kActiveBit) {
+        // Stores go by whole 32-byte sectors: a lane writes (zeros for an
+        // inactive pair, which those cells already hold) whenever any pair
+        // in its sector is active, so that no sector is written in part --
+        // a partial sector costs a DRAM read to fill it -- and sectors of
+        // inactive cells only are not written at all.  Rows start on
+        // 16-cell boundaries (px is a multiple of 16), so 4 lanes cover an
+        // f32 sector and 8 lanes an f16 sector.
+        const bool pact = ((ma | mb) & kActiveBit) != 0;
+        const unsigned vote = __ballot_sync(0xffffffffu, pact);
+        const bool st_f32 = ((vote >> (tx & ~3)) & 0xFu) != 0;
+        const bool st_el = EL == 4 ? st_f32 : ((vote >> (tx & ~7)) & 0xFFu) != 0;
+        float hA = 0.f, lA = 0.f, hB = 0.f, lB = 0.f, dA[6], dB[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) { dA[i] = 0.f; dB[i] = 0.f; }
+        float2 cso = make_float2(0.f, 0.f);
+        const long long gi = xa + (long long)px * (y + 1) + pstride * z;
+        if (pact) {
             // own pair
             const float2 hx = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * c_own);
             const float2 lx = P::ld(sc + L::o_clo + EL * c_own, inv_lo);
@@ -405,13 +422,9 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
             const float hxl = f1(sc, xl_f), lxl = t1(sc, xl_lo, inv_lo), dxl = t1(sc, xl_d1, inv_d);
             const float hxr = f1(sc, xr_f), lxr = t1(sc, xr_lo, inv_lo), dxr = t1(sc, xr_d2, inv_d);
 
-            const long long gi = xa + (long long)px * (y + 1) + pstride * z;
-            float2 cs = make_float2(0.f, 0.f), cso = cs;
+            float2 cs = make_float2(0.f, 0.f);
             if (REDUCE) cs = *reinterpret_cast<const float2*>(a.Csnap + gi);
 
-            float hA = 0.f, lA = 0.f, hB = 0.f, lB = 0.f, dA[6], dB[6];
-#pragma unroll
-            for (int i = 0; i < 6; ++i) { dA[i] = 0.f; dB[i] = 0.f; }
             if (ma & kActiveBit) {
                 const float dd[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
                 const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
@@ -426,28 +439,35 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
                 const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
                 cell_update<S, REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
             }
-            // inactive cells of the pair get zeros, which they already hold
-            *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
-            P::st(reinterpret_cast<T*>(a.clo) + gi, lA, lB, s_lo);
-#pragma unroll
-            for (int i = 0; i < 6; ++i) P::st(reinterpret_cast<T*>(a.d[i]) + gi, dA[i], dB[i], s_d);
-            if (y == ny - 1) {  // ghost row above row 0
-                const long long gg = xa + pstride * z;
-                *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
-                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
-                P::st(reinterpret_cast<T*>(a.d[2]) + gg, dA[2], dB[2], s_d);
-            }
-            if (y == 0) {  // ghost row below row ny-1
-                const long long gg = xa + (long long)px * (ny + 1) + pstride * z;
-                *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
-                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
-                P::st(reinterpret_cast<T*>(a.d[3]) + gg, dA[3], dB[3], s_d);
-            }
-            if (REDUCE) *reinterpret_cast<float2*>(a.Csnap + gi) = cso;
             // this plane becomes the z-1 neighbour of the next one
             ph = hx;
             pl = lx;
             pd5 = dp[4];
+        }
+        if (st_f32) {
+            *reinterpret_cast<float2*>(a.chi + gi) = make_float2(hA, hB);
+            if (REDUCE) *reinterpret_cast<float2*>(a.Csnap + gi) = cso;
+        }
+        if (st_el) {
+            P::st(reinterpret_cast<T*>(a.clo) + gi, lA, lB, s_lo);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) P::st(reinterpret_cast<T*>(a.d[i]) + gi, dA[i], dB[i], s_d);
+        }
+        if (y == ny - 1) {  // ghost row above row 0
+            const long long gg = xa + pstride * z;
+            if (st_f32) *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+            if (st_el) {
+                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                P::st(reinterpret_cast<T*>(a.d[2]) + gg, dA[2], dB[2], s_d);
+            }
+        }
+        if (y == 0) {  // ghost row below row ny-1
+            const long long gg = xa + (long long)px * (ny + 1) + pstride * z;
+            if (st_f32) *reinterpret_cast<float2*>(a.chi + gg) = make_float2(hA, hB);
+            if (st_el) {
+                P::st(reinterpret_cast<T*>(a.clo) + gg, lA, lB, s_lo);
+                P::st(reinterpret_cast<T*>(a.d[3]) + gg, dA[3], dB[3], s_d);
+            }
         }
         release(k);
     }

@@ -20,7 +20,7 @@ struct MarchMaps {
 };
 
 struct MarchArgs {
-    int nx, ny, nz, px;  // px: padded row pitch (multiple of 8 cells, >= kBX)
+    int nx, ny, nz, px;  // px: padded row pitch (multiple of 16 cells, >= kBX)
     int z_chunk;         // planes per block
     int prefetch;        // L2 prefetch distance in planes (0: none)
     // destination time level (padded, two ghost rows per plane)
