@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import ctypes
 import math
+import os
 
 import numpy as np
 
@@ -278,6 +279,19 @@ class UNet:
 
     def num_params(self) -> int:
         return sum(p.numel() for n in self.params for p in self.params[n])
+
+
+# ---------------------------------------------------------------- weights
+WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "warmstart_unet.npz")
+
+
+def load_pretrained(path: str = WEIGHTS) -> "UNet":
+    """The network with the weights trained by ``warmstart_train`` (float16
+    on disk, FP32 masters and BF16 copies on the GPU)."""
+    net = UNet(seed=0)
+    with np.load(path) as z:
+        net.load_state_dict({k: z[k] for k in z.files})
+    return net
 
 
 # ---------------------------------------------------------------- solver glue
