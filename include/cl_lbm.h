@@ -172,9 +172,12 @@ cl_status cl_lbm_step(cl_handle h, long long nsteps);
 
 /* Advance until the stopping rule fires or p->max_steps more steps are
    taken: every check_every steps the fused reduction gives J_in, J_out, R
-   and sum|dC|; converged when the flux balance is below tol_flux and the
-   geometric-series extrapolation of the tracked readout's remaining change
-   (D_eff for a Dirichlet outlet, R otherwise) is below tol_rel of it.
+   and sum|dC|; converged when, at two checks in a row, the flux balance is
+   below tol_flux and the estimated remaining change of the tracked readout
+   (D_eff for a Dirichlet outlet, R otherwise) is below tol_rel of it.  The
+   estimate is the geometric-series tail of the last two increments when
+   they shrink with one sign, and the larger increment when the sign flips
+   (a turning point, as after a warm start that overshoots).
    Returns CL_ERR_NOT_CONVERGED at the budget, CL_ERR_DIVERGED on NaN/Inf.
    info may be NULL. */
 cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info);

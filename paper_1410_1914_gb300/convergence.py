@@ -15,18 +15,57 @@ import time
 import numpy as np
 
 
+def remaining_change(dq: float, dq_prev: float) -> float:
+    """Remaining change of a readout from its last two increments: the
+    geometric tail |dq| rho/(1 - rho) when they shrink with the same sign,
+    unbounded when they do not shrink, and the larger increment when the
+    sign flips (a turning point must not pass for convergence).  The same
+    rule as the library's stopping test."""
+    if dq == 0.0 and dq_prev == 0.0:
+        return 0.0
+    rho = dq / dq_prev if dq_prev != 0.0 else (np.inf if dq > 0 else -np.inf)
+    if rho >= 1.0:
+        return np.inf
+    if rho > 0.0:
+        return abs(dq) * rho / (1.0 - rho)
+    return max(abs(dq), abs(dq_prev))
+
+
+class StopRule:
+    """Feed the tracked readout once per check; `update` returns True when
+    the estimated remaining relative change has been below `tol` at two
+    checks in a row (a single quiet check at a turning point does not stop).
+    The library's stopping test applies the same rule."""
+
+    def __init__(self, tol: float):
+        self.tol = tol
+        self.q = self.dq = None
+        self.quiet = 0
+
+    def update(self, q: float) -> bool:
+        if self.q is not None:
+            dq = q - self.q
+            if self.dq is not None:
+                est = remaining_change(dq, self.dq)
+                self.quiet = self.quiet + 1 if (q != 0 and est / abs(q) < self.tol) else 0
+            self.dq = dq
+        self.q = q
+        return self.quiet >= 2
+
+
 def deff_trace(solver, max_steps: int, check_every: int, stop_rel_change: float = 1e-7):
     """Run from the current state; return (steps, seconds, D_eff/D_b) per check.
 
     Stops after max_steps or once the extrapolated relative change of the
-    outlet flux falls below stop_rel_change (the solver's own stopping rule
-    with tol_rel = stop_rel_change)."""
+    outlet flux has been below stop_rel_change at two checks in a row (the
+    solver's own stopping rule with tol_rel = stop_rel_change, without its
+    flux-balance test)."""
     info = solver.info()
     nz, ny, nx = solver.shape
     p = solver.params
     scale = nx / ((p.c_in - p.c_out) * ny * nz) * p.dx_m * p.dx_m / info["dt_s"] / info["D_b"]
     steps, secs, vals = [], [], []
-    q_prev = dq_prev = None
+    rule = StopRule(stop_rel_change)
     t0 = time.perf_counter()
     n = 0
     while n + check_every <= max_steps:
@@ -36,16 +75,8 @@ def deff_trace(solver, max_steps: int, check_every: int, stop_rel_change: float 
         steps.append(n)
         secs.append(time.perf_counter() - t0)
         vals.append(q * scale)
-        if q_prev is not None and dq_prev is not None and dq_prev != 0:
-            dq = q - q_prev
-            rho = dq / dq_prev
-            est = abs(dq) * rho / (1 - rho) if 0 < rho < 1 else (abs(dq) if rho <= 0 else np.inf)
-            if abs(q) > 0 and est / abs(q) < stop_rel_change:
-                break
-            dq_prev = dq
-        elif q_prev is not None:
-            dq_prev = q - q_prev
-        q_prev = q
+        if rule.update(q):
+            break
     return np.array(steps), np.array(secs), np.array(vals)
 
 

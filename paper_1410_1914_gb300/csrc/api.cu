@@ -595,7 +595,7 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
     CKS(get_graph(h, K, true, &g));
     const bool track_deff = h->p.bc_in == CL_BC_DIRICHLET && h->p.bc_out == CL_BC_DIRICHLET && h->p.c_in != h->p.c_out;
     double q_prev = NAN, dq_prev = NAN;
-    int nchecks = 0;
+    int nchecks = 0, quiet = 0;
     cl_solve_info inf;
     memset(&inf, 0, sizeof(inf));
     inf.rel_change = INFINITY;
@@ -618,18 +618,14 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
         inf.flux_balance = fabs(inf.J_in - inf.J_out - inf.R) / fmax(fabs(inf.J_in), 1e-300);
         const double q = track_deff ? inf.J_out : inf.R;
         const double dq = q - q_prev;
-        double est = INFINITY;
-        if (nchecks >= 2) {
-            const double rho = dq / dq_prev;
-            if (rho >= 1.0) est = INFINITY;
-            else if (rho > 0.0) est = fabs(dq) * rho / (1.0 - rho);
-            else est = fabs(dq);
-        }
+        const double est = nchecks >= 2 ? remaining_change(dq, dq_prev) : INFINITY;
         inf.rel_change = q != 0 ? est / fabs(q) : INFINITY;
         q_prev = q;
         dq_prev = dq;
         ++nchecks;
-        if (nchecks >= 3 && inf.flux_balance < h->p.tol_flux && inf.rel_change < h->p.tol_rel) {
+        // both tests must pass at two checks in a row (one quiet check at a turning point is not enough)
+        quiet = (inf.flux_balance < h->p.tol_flux && inf.rel_change < h->p.tol_rel) ? quiet + 1 : 0;
+        if (quiet >= 2) {
             result = CL_OK;
             inf.converged = 1;
             break;

@@ -260,7 +260,7 @@ cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* 
     const int n = b->n;
     std::vector<cl_solve_info> inf(n);
     std::vector<double> q_prev(n, NAN), dq_prev(n, NAN);
-    std::vector<int> nchecks(n, 0);
+    std::vector<int> nchecks(n, 0), quiet(n, 0);
     for (auto& x : inf) { memset(&x, 0, sizeof(x)); x.rel_change = INFINITY; }
     std::fill(b->active.begin(), b->active.end(), 1);
     CKS(upload_items(b));
@@ -292,18 +292,13 @@ cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* 
                                         h->p.c_in != h->p.c_out;
                 const double q = track_deff ? x.J_out : x.R;
                 const double dq = q - q_prev[i];
-                double est = INFINITY;
-                if (nchecks[i] >= 2) {
-                    const double rho = dq / dq_prev[i];
-                    if (rho >= 1.0) est = INFINITY;
-                    else if (rho > 0.0) est = fabs(dq) * rho / (1.0 - rho);
-                    else est = fabs(dq);
-                }
+                const double est = nchecks[i] >= 2 ? remaining_change(dq, dq_prev[i]) : INFINITY;
                 x.rel_change = q != 0 ? est / fabs(q) : INFINITY;
                 q_prev[i] = q;
                 dq_prev[i] = dq;
                 ++nchecks[i];
-                if (nchecks[i] >= 3 && x.flux_balance < h->p.tol_flux && x.rel_change < h->p.tol_rel) {
+                quiet[i] = (x.flux_balance < h->p.tol_flux && x.rel_change < h->p.tol_rel) ? quiet[i] + 1 : 0;
+                if (quiet[i] >= 2) {
                     x.converged = 1;
                     stop = true;
                 }

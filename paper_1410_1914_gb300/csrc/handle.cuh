@@ -2,6 +2,7 @@
 // of the library (not part of the public ABI).
 #pragma once
 
+#include <math.h>
 #include <vector>
 
 #include "internal.cuh"
@@ -24,6 +25,22 @@ struct MState {
 };
 
 }  // namespace cl
+
+// Remaining change of the tracked readout after the last check, from the
+// last two increments dq (latest) and dq_prev: the geometric tail
+// |dq| rho / (1 - rho) when they shrink with the same sign (0 < rho < 1), no
+// bound when they do not shrink (rho >= 1), and, when the sign flips (a
+// turning point or an oscillation, where the geometric model does not
+// hold), the larger of the two increments -- so that a turning point, where
+// one increment is near zero, cannot pass for convergence.  Two zero
+// increments (a state that no longer changes) give zero.
+inline double remaining_change(double dq, double dq_prev) {
+    if (dq == 0.0 && dq_prev == 0.0) return 0.0;
+    const double rho = dq / dq_prev;
+    if (rho >= 1.0) return INFINITY;
+    if (rho > 0.0) return fabs(dq) * rho / (1.0 - rho);
+    return fmax(fabs(dq), fabs(dq_prev));
+}
 
 struct cl_lbm {
     cl_params p;
