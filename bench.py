@@ -326,7 +326,8 @@ def run_converge(args):
             W.warm_start(net, s)
             torch.cuda.synchronize()
             inf_s = time.perf_counter() - t1
-        st, sec, val = deff_trace(s, max_steps, K, stop_rel_change=1e-8)
+        # the trace only has to outlast the 1e-3 band; FP16 readouts carry ~1e-5 noise
+        st, sec, val = deff_trace(s, max_steps, K, stop_rel_change=1e-7)
         n, t = time_to_tolerance(st, sec, val, ref, 1e-3)
         out[storage + ("+warm" if warm else "")] = {
             "steps_to_1e-3": n, "iteration_s": t, "setup_s": setup_s, "inference_s": inf_s,
@@ -334,11 +335,13 @@ def run_converge(args):
             "final_rel_err": abs(float(val[-1]) - ref) / abs(ref), "steps_run": int(st[-1])}
         s.close()
     plain = out["fp32pop"]["seconds_to_1e-3"]
+    state32 = out["fp32"]["seconds_to_1e-3"]
     best = out.get("fp16dev+warm", out["fp16dev"])["seconds_to_1e-3"]
     line = {"metric": "time-to-converged D_eff (rel 1e-3)", "unit": "s", "higher_is_better": False,
             "workload": label, "shape_zyx": list(ph.shape), "reference_D_eff_over_Db": ref, "check_every": K,
             "by_arm": out,
             "fp16_warm_vs_plain_fp32": (None if plain is None or best is None else plain / best),
+            "fp16_warm_vs_fp32_state_ramp": (None if state32 is None or best is None else state32 / best),
             "plain_fp32_note": "fp32pop = plain FP32 populations from the linear ramp" + (
                 "; it never came within 1e-3" if plain is None else "")}
     print(json.dumps(line), flush=True)
