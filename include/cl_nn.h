@@ -11,7 +11,9 @@
  * Building blocks for training and inference, every one a kernel of this
  * library (no cuDNN, no cuBLAS):
  *   - 3x3x3 convolutions as implicit GEMMs on the tensor cores (BF16
- *     operands, FP32 accumulation), forward, data gradient (the same
+ *     operands, FP32 accumulation; tcgen05 with the accumulator in tensor
+ *     memory when both channel counts are multiples of 16), forward, data
+ *     gradient (the same
  *     convolution with the kernel flipped and its channel axes swapped) and
  *     weight gradient (reduced over voxels in fixed-size slices, summed in a
  *     fixed order: deterministic);
@@ -117,6 +119,12 @@ cl_status cl_nn_head_bwd(const void* x, const float* w, const float* y, const fl
    receives the BF16 copy the convolutions read. */
 cl_status cl_nn_adam(float* p, const float* g, float* m, float* v, void* p_bf16, long long n, float lr, float b1, float b2,
                      float eps, int step, void* stream);
+
+/* Error state of the network kernels since the last call: synchronises
+   the stream, returns CL_ERR_TIMEOUT (and clears it) if a bounded wait of a
+   tensor-core convolution expired (its output is then incomplete), else
+   CL_OK; CL_ERR_CUDA if the state cannot be read. */
+cl_status cl_nn_check(void* stream);
 
 /* b = BF16(a), round to nearest even, n elements. */
 cl_status cl_nn_to_bf16(const float* a, void* b, long long n, void* stream);

@@ -1,0 +1,337 @@
+// 3x3x3 convolution of the warm-start network on the 5th-generation tensor
+// cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory).
+//
+// Implicit GEMM: out[v][n] = sum over taps t and input channels c of
+// in[shift(v, t)][c] * w[t][n][c].  One CTA computes 128 consecutive output
+// voxels (M = 128) for all output channels (N = co, 16..256); the reduction
+// runs over 27 taps x ci in k-steps of CK channels of one tap.
+//
+// Roles (160 threads):
+//   warps 0-3  producers: thread r gathers the CK input channels of voxel
+//              v0 + r shifted by the tap (x zero padded, y and z periodic or
+//              zero padded) and the tap's weight rows into a shared-memory
+//              stage with cp.async (zero fill outside the box), then arrives
+//              on the stage's `full` barrier once its copies have landed and
+//              have been made visible to the tensor core (async proxy);
+//              afterwards they run the epilogue: tcgen05.ld of their 32 TMEM
+//              lanes (warp w owns lanes 32w..32w+31), bias, ReLU, BF16 store;
+//   warp 4     allocates and frees the tensor memory; its lane 0 issues the
+//              MMAs of each stage and commits them to the stage's `empty`
+//              barrier (the stage can be refilled when they completed) and,
+//              after the last stage, to `done`.
+//
+// Shared-memory operand layout: K-major, no swizzle.  A tile of R rows x CK
+// columns is stored as 8x8 core matrices (8 rows of 16 bytes, contiguous):
+// element (r, k) at (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
+// with SBO = CK / 8 * 128, so the leading-dimension offset (next core matrix
+// along K) is 128 bytes and one K = 16 instruction covers 256 bytes.
+//
+// Every wait is bounded; on expiry the CTA records an error bit, stops
+// issuing work, waits (bounded) for the MMAs it issued, frees its tensor
+// memory and returns.
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "internal.cuh"
+#include "nn.cuh"
+
+namespace cl {
+
+namespace {
+
+constexpr int kTcM = 128;       // output voxels per CTA (TMEM lanes)
+constexpr int kTcStages = 4;    // shared-memory stages
+constexpr int kTcThreads = 160; // 4 producer/epilogue warps + 1 MMA warp
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool bar_try_wait(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait (~1 s of SM clock); false on expiry
+__device__ __forceinline__ bool bar_wait(uint64_t* b, uint32_t parity) {
+    if (bar_try_wait(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!bar_try_wait(b, parity))
+        if (clock64() - t0 > (1LL << 31)) return false;
+    return true;
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// generic-proxy writes to shared memory become visible to the tensor core
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// shared-memory matrix descriptor: K-major, no swizzle
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of this architecture
+    return d;                // base offset 0, swizzle none
+}
+
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcShape {
+    int CK;        // channels per k-step (16..64, divides ci)
+    int N;         // output channels (co)
+    int ncols;     // TMEM columns (power of two >= max(32, N))
+    int a_bytes;   // 128 x CK x 2
+    int b_bytes;   // N x CK x 2
+    int stage;     // a_bytes + b_bytes
+    int smem;      // dynamic shared memory
+};
+
+}  // namespace
+
+__host__ __device__ inline TcShape tc_shape(int ci, int co) {
+    TcShape s;
+    s.CK = ci <= 64 ? ci : (ci % 64 == 0 ? 64 : (ci % 48 == 0 ? 48 : (ci % 32 == 0 ? 32 : 16)));
+    s.N = co;
+    int c = 32;
+    while (c < co) c <<= 1;
+    s.ncols = c;
+    s.a_bytes = kTcM * s.CK * 2;
+    s.b_bytes = co * s.CK * 2;
+    s.stage = s.a_bytes + s.b_bytes;
+    s.smem = 1024 + kTcStages * s.stage;
+    return s;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* __restrict__ in,
+                                                          const __nv_bfloat16* __restrict__ w,
+                                                          const float* __restrict__ bias,
+                                                          __nv_bfloat16* __restrict__ out, ConvGeom g, int relu,
+                                                          int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const TcShape sh = tc_shape(g.ci, g.co);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* done = empty + kTcStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    unsigned char* stages = smem + 1024;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const long long v0 = (long long)blockIdx.x * kTcM;
+    const int CK = sh.CK, kgroups = CK / 8;
+    const int ksteps = 27 * (g.ci / CK);
+    const uint32_t sbo_a = (uint32_t)kgroups * 128u, sbo_b = sbo_a;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            bar_init(&full[s], 128);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(sh.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------ producers
+        const int r = tid;  // output row of this thread
+        const long long v = v0 + r;
+        const bool row_ok = v < M;
+        int x = 0, y = 0, z = 0;
+        long long nb = 0;
+        if (row_ok) {
+            x = (int)(v % g.W);
+            long long q = v / g.W;
+            y = (int)(q % g.H);
+            q /= g.H;
+            z = (int)(q % g.D);
+            nb = q / g.D;
+        }
+        const uint32_t a_row = (uint32_t)(r >> 3) * sbo_a + (uint32_t)(r & 7) * 16u;
+        bool ok = true;
+        int issued = 0;  // stages whose copies were issued
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kTcStages;
+            if (ks >= kTcStages) {
+                if (!bar_wait(&empty[s], ((ks / kTcStages) - 1) & 1)) { ok = false; }
+            }
+            if (!ok || *(volatile int*)abort_flag) { ok = false; break; }
+            const int t = ks / (g.ci / CK);
+            const int c0 = (ks % (g.ci / CK)) * CK;
+            unsigned char* st = stages + s * sh.stage;
+            // A: the tap-shifted input row of this voxel
+            const int qx = x + t % 3 - 1;
+            int qy = y + (t / 3) % 3 - 1, qz = z + t / 9 - 1;
+            bool valid = row_ok && qx >= 0 && qx < g.W;
+            if (g.periodic_yz) {
+                qy = qy < 0 ? qy + g.H : (qy >= g.H ? qy - g.H : qy);
+                qz = qz < 0 ? qz + g.D : (qz >= g.D ? qz - g.D : qz);
+            } else {
+                valid = valid && qy >= 0 && qy < g.H && qz >= 0 && qz < g.D;
+            }
+            const long long sv = valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nb)) : 0;
+            const __nv_bfloat16* src = in + sv * g.in_stride + g.in_off + c0;
+            const uint32_t a_base = smem_addr(st) + a_row;
+            for (int h = 0; h < kgroups; ++h) cp_async16(a_base + (uint32_t)h * 128u, src + 8 * h, valid);
+            // B: weight rows of this tap and channel chunk, shared by the 128 threads
+            const uint32_t b_base = smem_addr(st + sh.a_bytes);
+            const __nv_bfloat16* wt = w + (long long)t * g.co * g.ci + c0;
+            for (int e = r; e < g.co * kgroups; e += 128) {
+                const int n = e / kgroups, h = e % kgroups;
+                cp_async16(b_base + (uint32_t)(n >> 3) * sbo_b + (uint32_t)h * 128u + (uint32_t)(n & 7) * 16u,
+                           wt + (long long)n * g.ci + 8 * h, true);
+            }
+            cp_async_commit();
+            ++issued;
+            // stage ks - 2 has landed: publish it to the tensor core
+            if (ks >= 2) {
+                cp_async_wait<2>();
+                fence_async_shared();
+                bar_arrive(&full[(ks - 2) % kTcStages]);
+            }
+        }
+        // publish the stages still in flight (also after an abort, so that
+        // no copy is outstanding when the CTA leaves)
+        cp_async_wait<0>();
+        fence_async_shared();
+        for (int ks = (issued >= 2 ? issued - 2 : 0); ks < issued; ++ks) bar_arrive(&full[ks % kTcStages]);
+        if (!ok) {
+            atomicOr(err, 64);
+            *(volatile int*)abort_flag = 1;
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16(kTcM, g.co);
+        int ks = 0;
+        for (; ks < ksteps; ++ks) {
+            const int s = ks % kTcStages;
+            if (!bar_wait(&full[s], (ks / kTcStages) & 1) || *(volatile int*)abort_flag) {
+                atomicOr(err, 64);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(stages + s * sh.stage), b0 = a0 + (uint32_t)sh.a_bytes;
+            for (int kk = 0; kk < CK / 16; ++kk) {
+                const uint64_t ad = sdesc(a0 + (uint32_t)kk * 256u, 128u, sbo_a);
+                const uint64_t bd = sdesc(b0 + (uint32_t)kk * 256u, 128u, sbo_b);
+                mma_bf16_ss(tmem, ad, bd, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        }
+        mma_commit(done);  // every MMA issued so far has completed
+    }
+
+    // ---------------------------------------------------------- epilogue
+    if (warp < 4) {
+        const bool ok = bar_wait(done, 0);
+        tc_fence_after();
+        if (!ok) atomicOr(err, 64);
+        const long long v = v0 + tid;
+        const bool store = ok && !*(volatile int*)abort_flag && v < M;
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < g.co; c += 16) {
+            uint32_t acc[16];
+            tmem_ld16(lane_base + (uint32_t)c, acc);  // warp-wide: every lane takes part
+            if (store) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float a = __uint_as_float(acc[2 * j]) + (bias ? bias[c + 2 * j] : 0.f);
+                    float b = __uint_as_float(acc[2 * j + 1]) + (bias ? bias[c + 2 * j + 1] : 0.f);
+                    if (relu) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
+                    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                    pk[j] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(out + v * g.out_stride + g.out_off + c);
+                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.ncols) : "memory");
+    }
+}
+
+bool conv3d_tc_supported(const ConvGeom& g) {
+    return g.ci % 16 == 0 && g.co % 16 == 0 && g.co >= 16 && g.co <= 256 && g.in_stride % 8 == 0 &&
+           g.in_off % 8 == 0 && g.out_stride % 8 == 0 && g.out_off % 8 == 0 && tc_shape(g.ci, g.co).smem <= 227 * 1024;
+}
+
+cudaError_t launch_conv3d_tc(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, __nv_bfloat16* out,
+                             const ConvGeom& g, int relu, int* err, cudaStream_t s) {
+    const TcShape sh = tc_shape(g.ci, g.co);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+    if (e != cudaSuccess) return e;
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const unsigned grid = (unsigned)((M + kTcM - 1) / kTcM);
+    k_conv3d_tc<<<grid, kTcThreads, sh.smem, s>>>(in, w, bias, out, g, relu, err);
+    return cudaGetLastError();
+}
+
+}  // namespace cl

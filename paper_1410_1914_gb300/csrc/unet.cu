@@ -3,9 +3,11 @@
 // to a correction of the linear initial field.  Layout NDHWC, activations
 // BF16, accumulation FP32, weights kept as FP32 masters with BF16 copies.
 //
-// 3x3x3 convolutions are implicit GEMMs on the tensor cores
-// (mma.sync m16n8k16, BF16 in, FP32 accumulate): rows are output voxels,
-// columns output channels, the reduction runs over 27 taps x input channels.
+// 3x3x3 convolutions are implicit GEMMs on the tensor cores: rows are
+// output voxels, columns output channels, the reduction runs over 27 taps x
+// input channels.  Channel counts that are multiples of 16 run on tcgen05
+// with the accumulator in tensor memory (conv_tc.cu); others on the
+// warp-level mma.sync m16n8k16 kernel below (BF16 in, FP32 accumulate).
 // x is zero padded, y and z wrap (the catalyst-layer structures are periodic
 // in y and z).  The data gradient is the same convolution applied to the
 // output gradient with the kernel flipped and its channel axes swapped; the
@@ -14,17 +16,12 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "internal.cuh"
+#include "nn.cuh"
 
 namespace cl {
-
-struct ConvGeom {
-    int N, D, H, W;   // voxels per batch item
-    int ci, co;       // channels
-    int in_stride, in_off;    // input channel stride / offset (concat buffers)
-    int out_stride, out_off;  // output channel stride / offset
-    int periodic_yz;
-};
 
 __device__ __forceinline__ uint32_t ld_bf16x2(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
 
@@ -109,9 +106,33 @@ __global__ void __launch_bounds__(128) k_conv3d(const __nv_bfloat16* __restrict_
     }
 }
 
+// error bits of the network kernels (bit 64: a bounded wait of the tcgen05
+// convolution expired), read and cleared by cl_nn_check
+__device__ int g_nn_err;
+
+static int* nn_err_ptr() {
+    static std::mutex mu;
+    static int* addr[64] = {nullptr};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_nn_err) != cudaSuccess) return nullptr;
+        addr[dev] = static_cast<int*>(p);
+    }
+    return addr[dev];
+}
+
 cudaError_t launch_conv3d(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, __nv_bfloat16* out,
                           const ConvGeom& g, int relu, cudaStream_t s) {
     if (g.ci % 16 || g.co % 8) return cudaErrorInvalidValue;
+    if (conv3d_tc_supported(g)) {
+        int* err = nn_err_ptr();
+        if (!err) return cudaErrorInvalidValue;
+        return launch_conv3d_tc(in, w, bias, out, g, relu, err, s);
+    }
+    // output channel counts that are not a multiple of 16: warp-level MMA
     const long long M = (long long)g.N * g.D * g.H * g.W;
     const unsigned gx = (unsigned)((M + 63) / 64);
     if (g.co % 64 == 0) k_conv3d<8><<<dim3(gx, g.co / 64), 128, 0, s>>>(in, w, bias, out, g, relu);
@@ -666,6 +687,22 @@ cl_status cl_nn_adam(float* p, const float* g, float* m, float* v, void* p_bf16,
     const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
     k_adam<<<kEw, 256, 0, (cudaStream_t)stream>>>(p, g, m, v, (__nv_bfloat16*)p_bf16, n, lr, b1, b2, eps, c1, c2);
     return st_of(cudaGetLastError());
+}
+
+cl_status cl_nn_check(void* stream) {
+    int* err = nn_err_ptr();
+    if (!err) return CL_ERR_CUDA;
+    int h = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return CL_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+    if (h) {
+        const int zero = 0;
+        if (cudaMemcpyAsync(err, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) return CL_ERR_CUDA;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return CL_ERR_CUDA;
+        return CL_ERR_TIMEOUT;
+    }
+    return CL_OK;
 }
 
 cl_status cl_nn_to_bf16(const float* a, void* b, long long n, void* stream) {

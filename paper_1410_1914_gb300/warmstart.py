@@ -58,6 +58,7 @@ _SIGS = {
     "cl_nn_head_bwd": (_S, [_P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _LL, _I, _P]),
     "cl_nn_adam": (_S, [_P, _P, _P, _P, _P, _LL, _F, _F, _F, _F, _I, _P]),
     "cl_nn_to_bf16": (_S, [_P, _P, _LL, _P]),
+    "cl_nn_check": (_S, [_P]),
     "cl_lbm_features": (_S, [_P, _P]),
     "cl_lbm_target": (_S, [_P, _P]),
     "cl_lbm_init_warm": (_S, [_P, _P]),
@@ -262,6 +263,11 @@ class UNet:
                 _call("cl_nn_adam", _p(p), _p(self.grads[n][k]), _p(m), _p(v), _p(pb), p.numel(), lr, b1, b2, eps,
                       self.t, s)
 
+    def check(self):
+        """Raise if a bounded wait of a tensor-core convolution expired since
+        the last check (synchronises the current stream)."""
+        _call("cl_nn_check", self._stream())
+
     def loss_value(self) -> float:
         return float(self.loss[0].item())
 
@@ -325,5 +331,6 @@ def warm_start(net: UNet, solver):
     assert nz == ny == nx and nx % 8 == 0, "the network runs on cubes whose edge is a multiple of 8"
     f = features(solver)
     pred = net.forward(f, 1, nx)
+    net.check()
     pred = pred.mul(float(solver.params.c_in - solver.params.c_out) / nx)
     _call("cl_lbm_init_warm", ctypes.c_void_p(solver.h), _p(pred))

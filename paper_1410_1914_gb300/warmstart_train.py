@@ -92,6 +92,7 @@ def train(net, groups, steps: int, lr: float = 1e-3, seed: int = 0, log_every: i
         net.backward(t, m)
         net.step(lr=float(lr_t))
         if it % log_every == 0 or it == steps:
+            net.check()
             losses.append((it, D, net.loss_value(), time.perf_counter() - t0))
     torch.cuda.synchronize()
     return losses

@@ -25,7 +25,7 @@ def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda().contiguous()
 
 
-@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (48, 16), (96, 32), (192, 64), (64, 128)])
+@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (48, 16), (96, 32), (192, 64), (64, 128), (64, 192), (16, 8)])
 def test_conv_forward(cuda_lib, ci, co):
     import torch
 
@@ -40,7 +40,7 @@ def test_conv_forward(cuda_lib, ci, co):
     # keep the device copies alive until the kernel has run
     xd, wd, bd = _dev(x, torch.bfloat16), _dev(w, torch.bfloat16), _dev(b, torch.float32)
     W._call("cl_nn_conv3d", W._p(xd), W._p(wd), W._p(bd), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, 1, None)
-    torch.cuda.synchronize()
+    W._call("cl_nn_check", None)
     got = out.float().cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-2 * np.abs(ref).max())
 
