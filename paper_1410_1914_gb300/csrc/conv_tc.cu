@@ -318,6 +318,247 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
     }
 }
 
+// ------------------------------------------------------------ weight grad
+// dW[t][co][ci] = sum_v dO[v][co] * I[shift(v, t)][ci] as, per tap, a GEMM
+// D[m = co][n = ci] over K = voxels.  Both operands come straight from the
+// NDHWC activations, which hold 8 consecutive channels of one voxel in 16
+// bytes: that is the MN-major layout (M, resp. N, contiguous), so A = dO
+// and B = the tap-shifted input are staged with 16-byte copies as for the
+// forward pass.  A CTA owns a slice of voxels and a group of TG taps, one
+// FP32 accumulator of 128 lanes x ci columns per tap in tensor memory
+// (TG * ci <= 256 columns, so two CTAs share an SM), and writes one partial
+// dW per slice; a second kernel sums the slices in a fixed order.
+// Lanes co..127 of the accumulators (M is padded to 128) are never read.
+//
+// MN-major core matrix: 8 voxels (K) x 8 channels (16 bytes); element
+// (m, k) of a stage at (m / 8) * MNS + (k / 8) * 128 + (k % 8) * 16 +
+// (m % 8) * 2, MNS = KT / 8 * 128: core matrices adjacent along K are 128
+// bytes apart, along M (or N) MNS bytes apart.
+constexpr int kWgKT = 32;  // voxels per stage
+
+__host__ __device__ inline int wg_taps_per_group(int ci) {
+    int tg = 256 / ci;
+    return tg > 27 ? 27 : (tg < 1 ? 1 : tg);
+}
+
+__host__ __device__ inline int wg_ncols(int tg, int ci) {
+    int c = 32;
+    while (c < tg * ci) c <<= 1;
+    return c;
+}
+
+__host__ __device__ inline int wg_stage_bytes(int tg, int ci) { return kTcM * kWgKT * 2 + tg * ci * kWgKT * 2; }
+
+long long wgrad_tc_slice(const ConvGeom& g) {
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const int groups = (27 + wg_taps_per_group(g.ci) - 1) / wg_taps_per_group(g.ci);
+    long long ns = 304 / groups;  // about two CTAs per SM in all
+    if (ns < 1) ns = 1;
+    long long slice = (M + ns - 1) / ns;
+    slice = (slice + kWgKT - 1) / kWgKT * kWgKT;
+    return slice < kWgKT ? kWgKT : slice;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_conv3d_wgrad_tc(const __nv_bfloat16* __restrict__ in,
+                                                                const __nv_bfloat16* __restrict__ dout,
+                                                                float* __restrict__ partial, ConvGeom g,
+                                                                long long slice, uint32_t lbo_mn, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int TG = wg_taps_per_group(g.ci);
+    const int ncols = wg_ncols(TG, g.ci);
+    const int stage_bytes = wg_stage_bytes(TG, g.ci);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kTcStages;
+    uint64_t* done = empty + kTcStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    unsigned char* stages = smem + 1024;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const long long vs = (long long)blockIdx.x * slice;
+    const long long ve = vs + slice < M ? vs + slice : M;
+    const int t0 = blockIdx.y * TG;
+    const int ntap = 27 - t0 < TG ? 27 - t0 : TG;
+    const int ksteps = vs < ve ? (int)((ve - vs + kWgKT - 1) / kWgKT) : 0;
+    const uint32_t mns = (uint32_t)(kWgKT / 8) * 128u;  // stride between core matrices along M / N
+    const int a_bytes = kTcM * kWgKT * 2;
+    const int b_tap_bytes = g.ci * kWgKT * 2;
+
+    if (tid == 0) {
+        for (int s = 0; s < kTcStages; ++s) {
+            bar_init(&full[s], 128);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------ producers
+        // thread: voxel k = tid % 32 of the stage, chunk lanes tid / 32
+        const int k = tid & 31, part = tid >> 5;
+        bool ok = true;
+        int issued = 0;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kTcStages;
+            if (ks >= kTcStages && !bar_wait(&empty[s], ((ks / kTcStages) - 1) & 1)) ok = false;
+            if (!ok || *(volatile int*)abort_flag) { ok = false; break; }
+            const long long v = vs + (long long)ks * kWgKT + k;
+            const bool vok = v < ve;
+            int x = 0, y = 0, z = 0;
+            long long nb = 0;
+            if (vok) {
+                x = (int)(v % g.W);
+                long long q = v / g.W;
+                y = (int)(q % g.H);
+                q /= g.H;
+                z = (int)(q % g.D);
+                nb = q / g.D;
+            }
+            unsigned char* st = stages + s * stage_bytes;
+            const uint32_t kofs = (uint32_t)(k >> 3) * 128u + (uint32_t)(k & 7) * 16u;
+            // A: dO[v][0..co), 8 channels per chunk
+            const uint32_t a_base = smem_addr(st) + kofs;
+            const __nv_bfloat16* srcA = dout + (vok ? v : 0) * g.out_stride + g.out_off;
+            for (int mc = part; mc < g.co / 8; mc += 4) cp_async16(a_base + (uint32_t)mc * mns, srcA + 8 * mc, vok);
+            // B: for each tap of the group, I[shift(v, t)][0..ci)
+            for (int j = 0; j < ntap; ++j) {
+                const int t = t0 + j;
+                const int qx = x + t % 3 - 1;
+                int qy = y + (t / 3) % 3 - 1, qz = z + t / 9 - 1;
+                bool valid = vok && qx >= 0 && qx < g.W;
+                if (g.periodic_yz) {
+                    qy = qy < 0 ? qy + g.H : (qy >= g.H ? qy - g.H : qy);
+                    qz = qz < 0 ? qz + g.D : (qz >= g.D ? qz - g.D : qz);
+                } else {
+                    valid = valid && qy >= 0 && qy < g.H && qz >= 0 && qz < g.D;
+                }
+                const long long sv =
+                    valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nb)) : 0;
+                const __nv_bfloat16* srcB = in + sv * g.in_stride + g.in_off;
+                const uint32_t b_base = smem_addr(st + a_bytes + j * b_tap_bytes) + kofs;
+                for (int nc = part; nc < g.ci / 8; nc += 4) cp_async16(b_base + (uint32_t)nc * mns, srcB + 8 * nc, valid);
+            }
+            cp_async_commit();
+            ++issued;
+            if (ks >= 2) {
+                cp_async_wait<2>();
+                fence_async_shared();
+                bar_arrive(&full[(ks - 2) % kTcStages]);
+            }
+        }
+        cp_async_wait<0>();
+        fence_async_shared();
+        for (int ks = (issued >= 2 ? issued - 2 : 0); ks < issued; ++ks) bar_arrive(&full[ks % kTcStages]);
+        if (!ok) {
+            atomicOr(err, 64);
+            *(volatile int*)abort_flag = 1;
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        // A and B MN-major (transpose bits 15 and 16)
+        const uint32_t idesc = idesc_bf16(kTcM, g.ci) | (1u << 15) | (1u << 16);
+        const uint32_t k_step = 128u;  // stride between core matrices along K
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kTcStages;
+            if (!bar_wait(&full[s], (ks / kTcStages) & 1) || *(volatile int*)abort_flag) {
+                atomicOr(err, 64);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t a0 = smem_addr(stages + s * stage_bytes);
+            for (int kk = 0; kk < kWgKT / 16; ++kk) {
+                const uint32_t koff = (uint32_t)kk * 2u * k_step;
+                // lbo_mn: which descriptor field carries the M/N stride
+                const uint64_t ad = lbo_mn ? sdesc(a0 + koff, mns, k_step) : sdesc(a0 + koff, k_step, mns);
+                for (int j = 0; j < ntap; ++j) {
+                    const uint32_t b0 = a0 + (uint32_t)a_bytes + (uint32_t)(j * b_tap_bytes) + koff;
+                    const uint64_t bd = lbo_mn ? sdesc(b0, mns, k_step) : sdesc(b0, k_step, mns);
+                    mma_bf16_ss(tmem + (uint32_t)(j * g.ci), ad, bd, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);
+    }
+
+    // ---------------------------------------------------------- epilogue
+    if (warp < 4) {
+        const bool ok = bar_wait(done, 0);
+        tc_fence_after();
+        if (!ok) atomicOr(err, 64);
+        const int m = tid;  // output channel co of this lane
+        const bool store = ok && !*(volatile int*)abort_flag && m < g.co;
+        if (warp * 32 < g.co) {  // warps whose lanes are all padding skip the reads
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int j = 0; j < ntap; ++j) {
+                float* dst = partial + (((long long)blockIdx.x * 27 + t0 + j) * g.co + m) * g.ci;
+                for (int c = 0; c < g.ci; c += 16) {
+                    uint32_t acc[16];
+                    tmem_ld16(lane_base + (uint32_t)(j * g.ci + c), acc);
+                    if (store) {
+                        // an empty slice (no k-step) contributes zeros
+                        float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            d4[q] = ksteps > 0 ? make_float4(__uint_as_float(acc[4 * q]), __uint_as_float(acc[4 * q + 1]),
+                                                             __uint_as_float(acc[4 * q + 2]),
+                                                             __uint_as_float(acc[4 * q + 3]))
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(ncols) : "memory");
+    }
+}
+
+bool conv3d_wgrad_tc_supported(const ConvGeom& g) {
+    const int tg = wg_taps_per_group(g.ci);
+    return g.ci % 16 == 0 && g.co % 16 == 0 && g.co <= 128 && g.ci <= 256 && g.in_stride % 8 == 0 &&
+           g.in_off % 8 == 0 && g.out_stride % 8 == 0 && g.out_off % 8 == 0 &&
+           1024 + kTcStages * wg_stage_bytes(tg, g.ci) <= 227 * 1024;
+}
+
+long long wgrad_tc_workspace_floats(const ConvGeom& g) {
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const long long slice = wgrad_tc_slice(g);
+    return ((M + slice - 1) / slice) * 27LL * g.co * g.ci;
+}
+
+cudaError_t launch_conv3d_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial,
+                                   const ConvGeom& g, int lbo_mn, int* err, int* nslices, cudaStream_t s) {
+    const int tg = wg_taps_per_group(g.ci);
+    const int smem = 1024 + kTcStages * wg_stage_bytes(tg, g.ci);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const long long M = (long long)g.N * g.D * g.H * g.W;
+    const long long slice = wgrad_tc_slice(g);
+    const int ns = (int)((M + slice - 1) / slice);
+    *nslices = ns;
+    k_conv3d_wgrad_tc<<<dim3(ns, (27 + tg - 1) / tg), kTcThreads, smem, s>>>(in, dout, partial, g, slice,
+                                                                          (uint32_t)lbo_mn, err);
+    return cudaGetLastError();
+}
+
 bool conv3d_tc_supported(const ConvGeom& g) {
     return g.ci % 16 == 0 && g.co % 16 == 0 && g.co >= 16 && g.co <= 256 && g.in_stride % 8 == 0 &&
            g.in_off % 8 == 0 && g.out_stride % 8 == 0 && g.out_off % 8 == 0 && tc_shape(g.ci, g.co).smem <= 227 * 1024;

@@ -20,4 +20,13 @@ bool conv3d_tc_supported(const ConvGeom& g);
 cudaError_t launch_conv3d_tc(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, __nv_bfloat16* out,
                              const ConvGeom& g, int relu, int* err, cudaStream_t s);
 
+// tcgen05 weight gradient: per-slice partials [slice][27][co][ci] in
+// `partial` (wgrad_tc_workspace_floats of them); *nslices receives their
+// count.  lbo_mn selects which descriptor offset field carries the stride
+// between core matrices along M / N for the MN-major operands.
+bool conv3d_wgrad_tc_supported(const ConvGeom& g);
+long long wgrad_tc_workspace_floats(const ConvGeom& g);
+cudaError_t launch_conv3d_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial,
+                                   const ConvGeom& g, int lbo_mn, int* err, int* nslices, cudaStream_t s);
+
 }  // namespace cl

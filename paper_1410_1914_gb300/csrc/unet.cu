@@ -216,9 +216,24 @@ long long wgrad_slice(const ConvGeom& g) {
     return slice;
 }
 
+// which descriptor field carries the M/N core-matrix stride of the MN-major
+// operands of the tcgen05 weight gradient
+constexpr int kWgradLboMN = 0;
+
 cudaError_t launch_conv3d_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial, float* dw,
                                 const ConvGeom& g, cudaStream_t s) {
     if (g.ci % 16 || g.co % 16) return cudaErrorInvalidValue;
+    if (conv3d_wgrad_tc_supported(g)) {
+        int* err = nn_err_ptr();
+        if (!err) return cudaErrorInvalidValue;
+        int ns = 0;
+        cudaError_t e = launch_conv3d_wgrad_tc(in, dout, partial, g, kWgradLboMN, err, &ns, s);
+        if (e != cudaSuccess) return e;
+        const long long n = 27LL * g.co * g.ci;
+        k_sum_slices<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(partial, ns, n, dw);
+        return cudaGetLastError();
+    }
+    // more than 128 output channels: warp-level MMA
     const long long M = (long long)g.N * g.D * g.H * g.W;
     const long long slice = wgrad_slice(g);
     const int ns = (int)((M + slice - 1) / slice);
@@ -605,7 +620,9 @@ long long cl_nn_wgrad_workspace(int N, int D, int H, int W, int ci, int co) {
     const ConvGeom g = geom(N, D, H, W, ci, co, ci, 0, co, 0, 1);
     const long long M = (long long)N * D * H * W;
     const long long slice = wgrad_slice(g);
-    return ((M + slice - 1) / slice) * 27LL * co * ci * (long long)sizeof(float);
+    const long long legacy = ((M + slice - 1) / slice) * 27LL * co * ci;
+    const long long tc = wgrad_tc_workspace_floats(g);
+    return (legacy > tc ? legacy : tc) * (long long)sizeof(float);
 }
 
 cl_status cl_nn_conv3d_wgrad(const void* in, const void* dout, float* workspace, float* dw, int N, int D, int H, int W,

@@ -90,6 +90,34 @@ def test_conv_gradients_against_differences(cuda_lib, ci, co):
         assert gx[idx] == pytest.approx(fd, rel=2e-2, abs=2e-2 * (1 + abs(fd)))
 
 
+@pytest.mark.parametrize("ci,co,shape", [(16, 16, (1, 3, 5, 7)), (48, 16, (2, 4, 4, 6)), (96, 32, (1, 4, 6, 6)),
+                                          (192, 64, (1, 3, 4, 8)), (64, 128, (1, 5, 3, 9)), (16, 128, (2, 2, 2, 2))])
+def test_wgrad_full_tensor(cuda_lib, ci, co, shape):
+    """Every entry of dW[t][o][i] = sum_v gy[v][o] x_t[v][i], where x_t (the
+    input shifted by tap t, with the padding rules) comes from the oracle's
+    convolution with an identity kernel at that tap.  Products of BF16
+    values are exact in FP32, so only the summation order differs."""
+    import torch
+
+    from paper_1410_1914_gb300 import warmstart as W
+    rng = np.random.default_rng(7 * ci + co)
+    N, D, H, Wd = shape
+    x = _bf16(rng.standard_normal((N, D, H, Wd, ci)))
+    gy = _bf16(rng.standard_normal((N, D, H, Wd, co)))
+    exp = np.zeros((27, co, ci))
+    for tap in range(27):
+        wid = np.zeros((27, ci, ci))
+        wid[tap] = np.eye(ci)
+        xt = OU.conv3d(x, wid, np.zeros(ci)).reshape(-1, ci)
+        exp[tap] = gy.reshape(-1, co).T @ xt
+    ws = torch.empty(W._lib().cl_nn_wgrad_workspace(N, D, H, Wd, ci, co) // 4 + 1, dtype=torch.float32, device="cuda")
+    dw = torch.empty(27, co, ci, dtype=torch.float32, device="cuda")
+    xd, gd = _dev(x, torch.bfloat16), _dev(gy, torch.bfloat16)
+    W._call("cl_nn_conv3d_wgrad", W._p(xd), W._p(gd), W._p(ws), W._p(dw), N, D, H, Wd, ci, co, ci, 0, co, 0, 1, None)
+    W._call("cl_nn_check", None)
+    np.testing.assert_allclose(dw.cpu().numpy(), exp, rtol=0, atol=1e-5 * np.abs(exp).max() + 1e-6)
+
+
 def _oracle_params(net):
     P = {}
     for name, ci, co in OU.CONV_LAYERS:
