@@ -348,6 +348,117 @@ def run_converge(args):
     return 0
 
 
+def run_unet(args):
+    """One training step of the warm-start network (forward, masked-MSE
+    backward through every layer, Adam) on a batch of 4 cubes of 48^3 with
+    synthetic features and targets, and the per-layer convolution kernels
+    (forward, data gradient, weight gradient) timed alone.  Roofline: the
+    convolutions' FLOPs against the measured dense BF16 tensor peak."""
+    import ctypes
+
+    import torch
+    from paper_1410_1914_gb300 import warmstart as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    N, D = 4, 48
+    g = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.rand(N, D, D, D, W.FEATURES, device="cuda", generator=g).to(torch.bfloat16)
+    tgt = torch.randn(N * D ** 3, device="cuda", generator=g)
+    mask = (torch.rand(N * D ** 3, device="cuda", generator=g) < 0.5).to(torch.uint8)
+    net = W.UNet(seed=0)
+    levels = {"e1": 1, "d1": 1, "e2": 2, "d2": 2, "e3": 3, "d3": 3, "bt": 4}
+    step_flop = 0.0
+    for name, ci, co in W.CONV_LAYERS:
+        d = D >> (levels[name[:2]] - 1)
+        passes = 2 if name == "e1a" else 3  # the first layer needs no data gradient
+        step_flop += passes * 2.0 * 27 * ci * co * N * d ** 3
+
+    def train_step():
+        net.forward(x, N, D)
+        net.backward(tgt, mask)
+        net.step(lr=1e-4)
+
+    for _ in range(args.warmup):
+        train_step()
+    net.check()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            train_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    net.check()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-layer kernels alone
+    layers = []
+    conv_ms = 0.0
+    for name, ci, co in W.CONV_LAYERS:
+        d = D >> (levels[name[:2]] - 1)
+        M = N * d ** 3
+        xi = torch.randn(M * ci, device="cuda", generator=g).to(torch.bfloat16)
+        wi = (torch.randn(27 * co * ci, device="cuda", generator=g) * 0.05).to(torch.bfloat16)
+        yo = torch.empty(M * co, device="cuda", dtype=torch.bfloat16)
+        gy = torch.randn(M * co, device="cuda", generator=g).to(torch.bfloat16)
+        gx = torch.empty(M * ci, device="cuda", dtype=torch.bfloat16)
+        wd = torch.empty_like(wi)
+        W._call("cl_nn_wt_dgrad", W._p(wi), W._p(wd), co, ci, sp)
+        dw = torch.empty(27 * co * ci, device="cuda")
+        ws = torch.empty(W._lib().cl_nn_wgrad_workspace(N, d, d, d, ci, co) // 4 + 1, device="cuda")
+        runs = {
+            "fwd": lambda: W._call("cl_nn_conv3d", W._p(xi), W._p(wi), None, W._p(yo), N, d, d, d, ci, co, ci, 0, co, 0,
+                                   1, 1, sp),
+            "dgrad": lambda: W._call("cl_nn_conv3d", W._p(gy), W._p(wd), None, W._p(gx), N, d, d, d, co, ci, co, 0, ci,
+                                     0, 0, 1, sp),
+            "wgrad": lambda: W._call("cl_nn_conv3d_wgrad", W._p(xi), W._p(gy), W._p(ws), W._p(dw), N, d, d, d, ci, co,
+                                     ci, 0, co, 0, 1, sp),
+        }
+        row = {"layer": name, "edge": d, "ci": ci, "co": co}
+        flop = 2.0 * 27 * ci * co * M
+        for k, f in runs.items():
+            if k == "dgrad" and name == "e1a":
+                continue
+            for _ in range(3):
+                f()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(10):
+                f()
+            b.record(stream)
+            torch.cuda.synchronize()
+            kms = a.elapsed_time(b) / 10
+            conv_ms += kms
+            row[k + "_ms"] = round(kms, 4)
+            row[k + "_tflops"] = round(flop / (kms * 1e-3) / 1e12, 1)
+        layers.append(row)
+    net.check()
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, peak_kind = float(json.load(fh)["bf16_tflops"]), "measured bf16_tflops (burst)"
+    except (OSError, KeyError, ValueError):
+        peak, peak_kind = 1900.0, "fallback"
+    achieved = step_flop / (conv_ms * 1e-3) / 1e12
+    line = {
+        "metric": "warm-start network training step (4 x 48^3, forward + backward + Adam)",
+        "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": "U-Net 16/32/64/128 channels, 1,466,065 parameters, batch 4 x 48^3 x 16 features",
+                   "conv_flop_per_step": step_flop},
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "convolution kernels (sum of per-layer times alone)"},
+        "conv_ms_per_step_alone": conv_ms,
+        "layers": layers,
+        "clocks": clocks.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,7 +475,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=1)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="override (nz ny nx)")
-    ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64", "converge"])
+    ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64", "converge", "unet_train"])
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--no-warm", action="store_true", help="converge workload: skip the learned warm-start arms")
     args = ap.parse_args()
@@ -378,6 +489,8 @@ def main():
         return run_batch(args)
     if args.workload == "converge":
         return run_converge(args)
+    if args.workload == "unet_train":
+        return run_unet(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
