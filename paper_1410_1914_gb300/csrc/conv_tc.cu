@@ -40,7 +40,9 @@ namespace cl {
 namespace {
 
 constexpr int kTcM = 128;       // output voxels per CTA (TMEM lanes)
-constexpr int kTcStages = 4;    // shared-memory stages
+constexpr int kTcStages = 4;    // shared-memory stages of the weight gradient
+constexpr int kFwStages = 6;    // shared-memory stages of the forward kernel
+constexpr int kLag = kFwStages - 2;  // its stages whose copies are in flight per thread
 constexpr int kTcThreads = 160; // 4 producer/epilogue warps + 1 MMA warp
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -74,8 +76,15 @@ __device__ __forceinline__ void bar_arrive(uint64_t* b) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared; zero fill when !valid.  The
+// .ca form keeps the line in L1: the taps of neighbouring voxels read the
+// same activation rows again within the CTA.
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async16_ca(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -140,7 +149,14 @@ struct TcShape {
 
 __host__ __device__ inline TcShape tc_shape(int ci, int co) {
     TcShape s;
-    s.CK = ci <= 64 ? ci : (ci % 64 == 0 ? 64 : (ci % 48 == 0 ? 48 : (ci % 32 == 0 ? 32 : 16)));
+    // widest channel chunk that divides ci and keeps the stages within ~200 KB
+    const int cands[4] = {64, 48, 32, 16};
+    s.CK = 16;
+    for (int i = 0; i < 4; ++i) {
+        const int ck = cands[i];
+        if (ck > ci || ci % ck) continue;
+        if (1024 + kFwStages * (kTcM + co) * ck * 2 <= 200 * 1024) { s.CK = ck; break; }
+    }
     s.N = co;
     int c = 32;
     while (c < co) c <<= 1;
@@ -148,7 +164,7 @@ __host__ __device__ inline TcShape tc_shape(int ci, int co) {
     s.a_bytes = kTcM * s.CK * 2;
     s.b_bytes = co * s.CK * 2;
     s.stage = s.a_bytes + s.b_bytes;
-    s.smem = 1024 + kTcStages * s.stage;
+    s.smem = 1024 + kFwStages * s.stage;
     return s;
 }
 
@@ -160,8 +176,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
     extern __shared__ __align__(1024) unsigned char smem[];
     const TcShape sh = tc_shape(g.ci, g.co);
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-    uint64_t* empty = full + kTcStages;
-    uint64_t* done = empty + kTcStages;
+    uint64_t* empty = full + kFwStages;
+    uint64_t* done = empty + kFwStages;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
     unsigned char* stages = smem + 1024;
@@ -174,7 +190,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
     const uint32_t sbo_a = (uint32_t)kgroups * 128u, sbo_b = sbo_a;
 
     if (tid == 0) {
-        for (int s = 0; s < kTcStages; ++s) {
+        for (int s = 0; s < kFwStages; ++s) {
             bar_init(&full[s], 128);
             bar_init(&empty[s], 1);
         }
@@ -212,9 +228,9 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
         bool ok = true;
         int issued = 0;  // stages whose copies were issued
         for (int ks = 0; ks < ksteps; ++ks) {
-            const int s = ks % kTcStages;
-            if (ks >= kTcStages) {
-                if (!bar_wait(&empty[s], ((ks / kTcStages) - 1) & 1)) { ok = false; }
+            const int s = ks % kFwStages;
+            if (ks >= kFwStages) {
+                if (!bar_wait(&empty[s], ((ks / kFwStages) - 1) & 1)) { ok = false; }
             }
             if (!ok || *(volatile int*)abort_flag) { ok = false; break; }
             const int t = ks / (g.ci / CK);
@@ -233,7 +249,7 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
             const long long sv = valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nb)) : 0;
             const __nv_bfloat16* src = in + sv * g.in_stride + g.in_off + c0;
             const uint32_t a_base = smem_addr(st) + a_row;
-            for (int h = 0; h < kgroups; ++h) cp_async16(a_base + (uint32_t)h * 128u, src + 8 * h, valid);
+            for (int h = 0; h < kgroups; ++h) cp_async16_ca(a_base + (uint32_t)h * 128u, src + 8 * h, valid);
             // B: weight rows of this tap and channel chunk, shared by the 128 threads
             const uint32_t b_base = smem_addr(st + sh.a_bytes);
             const __nv_bfloat16* wt = w + (long long)t * g.co * g.ci + c0;
@@ -244,18 +260,18 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
             }
             cp_async_commit();
             ++issued;
-            // stage ks - 2 has landed: publish it to the tensor core
-            if (ks >= 2) {
-                cp_async_wait<2>();
+            // stage ks - kLag has landed: publish it to the tensor core
+            if (ks >= kLag) {
+                cp_async_wait<kLag>();
                 fence_async_shared();
-                bar_arrive(&full[(ks - 2) % kTcStages]);
+                bar_arrive(&full[(ks - kLag) % kFwStages]);
             }
         }
         // publish the stages still in flight (also after an abort, so that
         // no copy is outstanding when the CTA leaves)
         cp_async_wait<0>();
         fence_async_shared();
-        for (int ks = (issued >= 2 ? issued - 2 : 0); ks < issued; ++ks) bar_arrive(&full[ks % kTcStages]);
+        for (int ks = (issued >= kLag ? issued - kLag : 0); ks < issued; ++ks) bar_arrive(&full[ks % kFwStages]);
         if (!ok) {
             atomicOr(err, 64);
             *(volatile int*)abort_flag = 1;
@@ -265,8 +281,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_tc(const __nv_bfloat16* _
         const uint32_t idesc = idesc_bf16(kTcM, g.co);
         int ks = 0;
         for (; ks < ksteps; ++ks) {
-            const int s = ks % kTcStages;
-            if (!bar_wait(&full[s], (ks / kTcStages) & 1) || *(volatile int*)abort_flag) {
+            const int s = ks % kFwStages;
+            if (!bar_wait(&full[s], (ks / kFwStages) & 1) || *(volatile int*)abort_flag) {
                 atomicOr(err, 64);
                 *(volatile int*)abort_flag = 1;
                 break;
@@ -449,7 +465,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_wgrad_tc(const __nv_bfloa
                     valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nb)) : 0;
                 const __nv_bfloat16* srcB = in + sv * g.in_stride + g.in_off;
                 const uint32_t b_base = smem_addr(st + a_bytes + j * b_tap_bytes) + kofs;
-                for (int nc = part; nc < g.ci / 8; nc += 4) cp_async16(b_base + (uint32_t)nc * mns, srcB + 8 * nc, valid);
+                for (int nc = part; nc < g.ci / 8; nc += 4)
+                    cp_async16_ca(b_base + (uint32_t)nc * mns, srcB + 8 * nc, valid);
             }
             cp_async_commit();
             ++issued;

@@ -185,14 +185,15 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
     const float rf = a.rfac;
     const float lx = lxs * inv_lo;
     const float Cx = hx + lx;
+    // catalytic face: r dopp - (1 - r) w C (the half-way first-order sink)
+    const float q_cat = (1.0f - rf) * ws * Cx;
     float av[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const int fb = i ^ 1;
         const float dopp = dds[fb];
         const float a_open = ws * ((nh[i] - hx) + (nls[i] - lxs) * inv_lo) + nds[i];
-        const float r = (m & (1u << (kReactShift + fb))) ? rf : 1.0f;
-        float a_closed = r * dopp - (1.0f - r) * ws * Cx;
+        float a_closed = (m & (1u << (kReactShift + fb))) ? fmaf(rf, dopp, -q_cat) : dopp;
         if (i == 0 && x == 0)
             a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_in - hx) - lx) - dopp : dopp;
         if (i == 1 && x == a.nx - 1)
