@@ -426,19 +426,36 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
             float2 cs = make_float2(0.f, 0.f);
             if (REDUCE) cs = *reinterpret_cast<const float2*>(a.Csnap + gi);
 
-            if (ma & kActiveBit) {
-                const float dd[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
-                const float nh[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
-                const float nl[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
-                const float nd[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
-                cell_update<S, REDUCE>(a, ma, om.x, hx.x, lx.x, dd, nh, nl, nd, xa, hA, lA, dA, rv, cs.x, cso.x);
-            }
-            if (mb & kActiveBit) {
-                const float dd[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
-                const float nh[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
-                const float nl[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
-                const float nd[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
-                cell_update<S, REDUCE>(a, mb, om.y, hx.y, lx.y, dd, nh, nl, nd, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+            const bool act_a = (ma & kActiveBit) != 0, act_b = (mb & kActiveBit) != 0;
+            const float dda[6] = {dp[0].x, dp[1].x, dp[2].x, dp[3].x, dp[4].x, dp[5].x};
+            const float nha[6] = {hxl, hx.y, hym.x, hyp.x, ph.x, hzp.x};
+            const float nla[6] = {lxl, lx.y, lym.x, lyp.x, pl.x, lzp.x};
+            const float nda[6] = {dxl, dp[1].y, dym.x, dyp.x, pd5.x, dzp.x};
+            const float ddb[6] = {dp[0].y, dp[1].y, dp[2].y, dp[3].y, dp[4].y, dp[5].y};
+            const float nhb[6] = {hx.x, hxr, hym.y, hyp.y, ph.y, hzp.y};
+            const float nlb[6] = {lx.x, lxr, lym.y, lyp.y, pl.y, lzp.y};
+            const float ndb[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
+            if (REDUCE) {
+                // the reductions must see active cells only
+                if (act_a) cell_update<S, true>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, cs.x, cso.x);
+                if (act_b)
+                    cell_update<S, true>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+            } else {
+                // both cells of the pair without a branch; an inactive cell's
+                // result (finite: its neighbours and omega slots hold zeros or
+                // state values) is replaced by the zeros it keeps
+                cell_update<S, false>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, cs.x, cso.x);
+                cell_update<S, false>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+                if (!act_a) {
+                    hA = 0.f; lA = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) dA[i] = 0.f;
+                }
+                if (!act_b) {
+                    hB = 0.f; lB = 0.f;
+#pragma unroll
+                    for (int i = 0; i < 6; ++i) dB[i] = 0.f;
+                }
             }
             // this plane becomes the z-1 neighbour of the next one
             ph = hx;
