@@ -519,7 +519,8 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty) {
 // z-1 values it needs (its own cells one plane below) in registers, so a
 // slot is live only while its plane is the current or the next one.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, 1) k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
+__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 3 : 1)
+    k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
     // Addressed directly (no integer round trip) so that every slot access
     // compiles to a shared-memory load.
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -572,9 +573,10 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, i
     return s_abort == 0;
 }
 
-// FP16 plain steps fit two resident blocks per SM; the others keep one
+// FP16 plain steps fit three resident blocks per SM; the others keep the
+// registers they need
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 2 : 1)
+__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 3 : 1)
     k_march_batch(const BatchInst* __restrict__ insts,
                                                             const WorkItem* __restrict__ items,
                                                             const int* __restrict__ n_items_ptr, int nsteps,
