@@ -505,7 +505,8 @@ def main():
     from paper_1410_1914_gb300 import Solver, inputs
     from paper_1410_1914_gb300 import _lib as L
 
-    ph, react, params = inputs.make_workload(WORKLOAD, shape=args.shape, seed=1 + rank)
+    from paper_1410_1914_gb300.replicas import aggregate_rate, max_over_ranks, rank_seed
+    ph, react, params = inputs.make_workload(WORKLOAD, shape=args.shape, seed=rank_seed(1, rank))
     n_cells = ph.size
     K = args.check_every
     stream = torch.cuda.current_stream()
@@ -535,13 +536,8 @@ def main():
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_updates = n_cells * K * args.steps * world
-    mlups = total_updates / (elapsed_ms * 1e-3) / 1e6
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+    mlups = aggregate_rate(n_cells * K * args.steps, world, elapsed_ms * 1e-3) / 1e6
     ms_per_step = elapsed_ms / args.steps
 
     # roofline of the fused step kernel (average launch = interval time / K)
@@ -589,11 +585,11 @@ def main():
             s.solve_budget(E)
             R_tot, prof_R, prof_C = s.reaction_rate()
         torch.cuda.synchronize()
-        el = time.perf_counter() - t0
+        el = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         # device-to-host: 5 FP64 plane sums per x-plane for the readout, one
         # 7-slot FP64 check per interval, the set-up's error words and counters
         d2h = 40 * ph.shape[2] + 56 * (E // K) + 4 + 8 + 56
-        e2e = {"value": n_cells * E * args.e2e_steps * world / el / 1e6, "unit": "MLUPS",
+        e2e = {"value": aggregate_rate(n_cells * E * args.e2e_steps, world, el) / 1e6, "unit": "MLUPS",
                "h2d_bytes_per_step": int(ph.nbytes + (react.nbytes if react is not None else 0)),
                "d2h_bytes_per_step": int(d2h),
                "lbm_steps_per_e2e_step": E, "includes": "structure upload + GPU set-up + steps + readout"}
