@@ -24,9 +24,11 @@ from . import inputs
 
 
 def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32", check_every: int = 200,
-                 tol_rel: float = 1e-6, max_steps: int = 4_000_000):
+                 tol_rel: float = 1e-6, max_steps: int = 4_000_000, net=None):
     """Solve n seeded cubes of edge `size` in one batch; return (features,
-    targets, masks, stats)."""
+    targets, masks, stats).  With `net`, every solve starts from that
+    network's warm start (the converged fields, hence the targets, are the
+    same; only the number of steps changes)."""
     import torch
 
     from . import warmstart as W
@@ -34,11 +36,13 @@ def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32
     from .solver import Solver
     work = inputs.batch_workloads(n, seed0=seed0, edge_range=(size, size))
     solvers = []
+    t0 = time.perf_counter()
     for ph, react, params in work:
         s = Solver(ph.shape, storage=storage, check_every=check_every, tol_rel=tol_rel, tol_flux=1e-4, **params)
         s.set_structure(ph, react)
+        if net is not None:
+            W.warm_start(net, s)
         solvers.append(s)
-    t0 = time.perf_counter()
     b = Batch(solvers)
     status, infos, nconv = b.solve(max_steps)
     solve_s = time.perf_counter() - t0
@@ -52,7 +56,8 @@ def make_dataset(n: int, size: int = 48, seed0: int = 1000, storage: str = "fp32
     b.close()
     for s in solvers:
         s.close()
-    stats = dict(n=n, size=size, seed0=seed0, tol_rel=tol_rel, status=status, converged=nconv,
+    stats = dict(n=n, size=size, seed0=seed0, tol_rel=tol_rel, storage=storage, warm=net is not None,
+                 status=status, converged=nconv,
                  solve_seconds=solve_s, mean_steps=float(np.mean([x["steps"] for x in infos])))
     return feats, targets, masks, stats
 
@@ -141,6 +146,10 @@ def main():
     ap.add_argument("--data", nargs="+", default=["48:256:4", "96:48:1"],
                     help="training groups edge:count:batch (cubes of that edge, solved, batch per step)")
     ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--data-storage", default="fp32", choices=["fp32", "fp16dev"],
+                    help="storage mode of the solves that make the training targets")
+    ap.add_argument("--data-warm", default=None,
+                    help="weights whose warm start speeds up the training solves (targets unchanged)")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--eval-size", type=int, nargs="+", default=[96])
     ap.add_argument("--n-eval", type=int, default=3)
@@ -152,9 +161,14 @@ def main():
     from .warmstart import UNet
     torch.cuda.set_device(0)
     groups, dstats = [], []
+    data_net = None
+    if args.data_warm:
+        from .warmstart import load_pretrained
+        data_net = load_pretrained(args.data_warm)
     for k, spec in enumerate(args.data):
         size, count, batch = (int(v) for v in spec.split(":"))
-        f, t, m, st = make_dataset(count, size, seed0=1000 + 10000 * k, tol_rel=1e-6 if size <= 64 else 1e-5)
+        f, t, m, st = make_dataset(count, size, seed0=1000 + 10000 * k, storage=args.data_storage,
+                                   tol_rel=1e-6 if size <= 64 else 1e-5, net=data_net)
         print(json.dumps({"dataset": st}), flush=True)
         dstats.append(st)
         # equal voxels per draw: weight a group by its cubes' share of the data volume
