@@ -10,8 +10,12 @@
     boxes against scipy's sparse direct solver;
   * invariants: mass conservation in a closed box, the exact per-step balance
     sum C(t+1) - sum C(t) = J_in - J_out - R, mirror symmetries, tau_ref
-    invariance of 1D steady states.
+    invariance of 1D steady states;
+  * the validation geometry of Sec. 5.1 (a solid sphere filling a cube) in a
+    band around its printed D_eff.
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -237,3 +241,33 @@ def test_no_path_is_an_error():
     ph = np.ones((3, 3, 5), np.uint8)
     with pytest.raises(ValueError):
         oracle.OracleLBM(ph, dx_m=DX, D_bulk=DB)
+
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+# ------------------------------------------------------- sphere in a cube
+def _sphere_phase(n):
+    c = (np.arange(n) + 0.5) - n / 2
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    return ((x * x + y * y + z * z) < (n / 2) ** 2).astype(np.uint8)  # 1 = solid
+
+
+def test_sphere_in_cube_matches_the_printed_validation_band():
+    """Sec. 5.1 validates the solver on a cube holding a solid sphere whose
+    diameter is the cube side and prints D_eff/D = 0.3317.  Voxel rule and
+    lattice differ here (cell centres inside the sphere are solid; D3Q7), so
+    the printed value is a band: the oracle at 32^3 must land within 4 %.
+    The resolution error of this geometry is itself a few per cent at 32^3
+    (0.321 at 32^3, 0.332 at 48^3, 0.338 at 96^3 by the finite-volume
+    equivalent of the scheme)."""
+    import json
+    with open(os.path.join(HERE, "golden", "paper_values.json")) as fh:
+        ref = json.load(fh)["sphere_in_cube_deff"]["value"]
+    ph = _sphere_phase(32)
+    o = oracle.OracleLBM(ph, D_bulk=1e-5, knudsen=0, tau_ref=1.0)
+    o.solve(tol=1e-9, check_every=200, max_steps=400_000)
+    d_eff, d_rel, _ = o.effective_diffusivity()
+    assert d_rel == pytest.approx(ref, rel=0.04)
+    # the porosity of the voxelised sphere is close to 1 - pi/6
+    assert 1 - ph.mean() == pytest.approx(1 - np.pi / 6, abs=0.01)
