@@ -55,6 +55,7 @@ class _Params(ctypes.Structure):
         ("D_ionomer", ctypes.c_double), ("k_ms", ctypes.c_double),
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
+        ("carrier", ctypes.c_int),
     ]
 
 
@@ -162,18 +163,21 @@ def pore_diameter(phase: np.ndarray, dx_m: float) -> np.ndarray:
     return out
 
 
-def active_mask(phase: np.ndarray, ionomer_transport: bool = False) -> np.ndarray:
-    """Transport cells 6-connected to the inlet plane x = 0 (y, z periodic)."""
+def active_mask(phase: np.ndarray, ionomer_transport: bool = False, protons: bool = False) -> np.ndarray:
+    """Transport cells 6-connected to the inlet plane x = 0 (y, z periodic).
+    Transport phases: pore and micropore (+ ionomer if ionomer_transport);
+    ionomer alone if protons (Eq. 16)."""
     phase = np.ascontiguousarray(phase, dtype=np.uint8)
     nz, ny, nx = phase.shape
     out = np.zeros(phase.shape, dtype=np.uint8)
-    lib().orc_active_mask(_ptr(phase), nx, ny, nz, int(bool(ionomer_transport)), _ptr(out))
+    mode = 2 if protons else int(bool(ionomer_transport))
+    lib().orc_active_mask(_ptr(phase), nx, ny, nz, mode, _ptr(out))
     return out
 
 
 # ---------------------------------------------------------------- solver
 DEFAULTS = dict(dx_m=2e-9, T_K=353.0, p_atm=1.0, M_kgmol=0.032, D_bulk=0.0, D_ionomer=0.0,
-                k_ms=0.0, knudsen=0, bc_in=0, bc_out=0, c_in=1.0, c_out=0.0, tau_ref=1.0)
+                k_ms=0.0, knudsen=0, bc_in=0, bc_out=0, c_in=1.0, c_out=0.0, tau_ref=1.0, carrier=0)
 
 
 class OracleLBM:
@@ -194,7 +198,9 @@ class OracleLBM:
         self.params = p
         cp = _Params(nx, ny, nz, p["dx_m"], p["T_K"], p["p_atm"], p["M_kgmol"], p["D_bulk"],
                      p["D_ionomer"], p["k_ms"], int(p["knudsen"]), int(p["bc_in"]), int(p["bc_out"]),
-                     p["c_in"], p["c_out"], p["tau_ref"])
+                     p["c_in"], p["c_out"], p["tau_ref"], int(p["carrier"]))
+        if int(p["carrier"]) == 1 and not (p["D_ionomer"] > 0 and p["k_ms"] == 0):
+            raise ValueError("protons (carrier 1) need D_ionomer > 0 (the conductivity) and k_ms = 0")
         self._react = None if react is None else np.ascontiguousarray(react, dtype=np.uint8)
         self._Dov = None if D is None else np.ascontiguousarray(D, dtype=np.float64)
         h = lib().orc_lbm_new(ctypes.byref(cp), _ptr(self.phase),

@@ -25,6 +25,10 @@
  *   Eq. 17b + 18a   first-order kinetics with uniform ionomer potential,
  *                   placed as a surface (Robin) condition on catalyst faces
  *   Eq. 19          effective diffusivity from the outlet flux
+ *   Eq. 16, Sec. 5.2  proton conduction (carrier 1): the same scheme on the
+ *                   ionomer phase alone with a uniform conductivity, no
+ *                   source; the Eq. 19 readout then is the effective
+ *                   conductivity, normalised by the ionomer's own
  *
  * Lattice directions: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z.
  * Phase codes: 0 pore, 1 solid (carbon / Pt / catalyst), 2 ionomer,
@@ -62,6 +66,8 @@ typedef struct {
     int bc_in, bc_out;  /* 0 Dirichlet, 1 zero flux */
     double c_in, c_out; /* boundary concentrations */
     double tau_ref;     /* relaxation time of the most diffusive active cell */
+    int carrier;        /* 0: O2 in the pore space (Eq. 6); 1: protons in the ionomer
+                           (Eq. 16 with S_e = 0 and uniform conductivity D_ionomer) */
 } orc_params;
 
 static long idx3(int x, int y, int z, int nx, int ny) { return x + (long)nx * (y + (long)ny * z); }
@@ -181,13 +187,19 @@ void orc_pore_diameter(const int32_t* counts, long N, double dx_m, double* d_p)
  * connected-phase labelling of Sec. 2.1.3.  Plain breadth-first search.
  * Returns the number of active cells.
  * ---------------------------------------------------------------------- */
-static int is_transport(uint8_t p, int ionomer_transport)
+/* Phases that carry the transported quantity.  mode 0: pore and micropore
+ * (O2, Eq. 6); 1: pore, micropore and ionomer (O2 dissolved in ionomer with
+ * its own D, Eq. 15); 2: ionomer only (protons, Eq. 16). */
+static int is_transport(uint8_t p, int mode)
 {
-    return p == 0 || p == 3 || (p == 2 && ionomer_transport);
+    if (mode == 2) return p == 2;
+    return p == 0 || p == 3 || (p == 2 && mode == 1);
 }
 
-long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
-                     uint8_t* active)
+/* Transport cells 6-connected to the inlet plane x = 0 (y, z periodic),
+ * by breadth-first search; `mode` selects the transport phases as in
+ * is_transport.  Returns the number of active cells. */
+long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int mode, uint8_t* active)
 {
     long N = (long)nx * ny * nz;
     long* queue = (long*)malloc(sizeof(long) * (N > 0 ? N : 1));
@@ -196,7 +208,7 @@ long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int ionomer_t
     for (int z = 0; z < nz; ++z)
         for (int y = 0; y < ny; ++y) {
             long c = idx3(0, y, z, nx, ny);
-            if (is_transport(phase[c], ionomer_transport)) { active[c] = 1; queue[tail++] = c; }
+            if (is_transport(phase[c], mode)) { active[c] = 1; queue[tail++] = c; }
         }
     while (head < tail) {
         long c = queue[head++];
@@ -205,7 +217,7 @@ long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int ionomer_t
             int qx = x + CX[i];
             if (qx < 0 || qx >= nx) continue;
             long n = idx3(qx, wrap(y + CY[i], ny), wrap(z + CZ[i], nz), nx, ny);
-            if (!active[n] && is_transport(phase[n], ionomer_transport)) {
+            if (!active[n] && is_transport(phase[n], mode)) {
                 active[n] = 1;
                 queue[tail++] = n;
             }
@@ -288,7 +300,8 @@ orc_lbm* orc_lbm_new(const orc_params* p, const uint8_t* phase, const uint8_t* r
     s->g = (double*)calloc((size_t)N * Q, sizeof(double));
     s->gn = (double*)calloc((size_t)N * Q, sizeof(double));
 
-    long n_active = orc_active_mask(phase, p->nx, p->ny, p->nz, p->D_ionomer > 0, s->active);
+    long n_active = orc_active_mask(phase, p->nx, p->ny, p->nz, p->carrier == 1 ? 2 : (p->D_ionomer > 0),
+                                    s->active);
     if (n_active == 0) { /* nothing percolates */
         free(s->phase); free(s->active); free(s->react); free(s->D); free(s->tau);
         free(s->g); free(s->gn); free(s);
@@ -470,7 +483,9 @@ void orc_lbm_effective_diffusivity(const orc_lbm* s, double out[3])
     double dlu = jd * s->p.nx / (s->p.c_in - s->p.c_out);
     out[2] = dlu;
     out[0] = dlu * s->p.dx_m * s->p.dx_m / s->dt;
-    out[1] = out[0] / s->D_b;
+    /* normalised by the bulk D of O2, or by the ionomer's own conductivity
+     * for protons (the effective conductivity of Sec. 5.2) */
+    out[1] = out[0] / (s->p.carrier == 1 ? s->p.D_ionomer : s->D_b);
 }
 
 /*

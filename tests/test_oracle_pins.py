@@ -271,3 +271,65 @@ def test_sphere_in_cube_matches_the_printed_validation_band():
     assert d_rel == pytest.approx(ref, rel=0.04)
     # the porosity of the voxelised sphere is close to 1 - pi/6
     assert 1 - ph.mean() == pytest.approx(1 - np.pi / 6, abs=0.01)
+
+
+# ------------------------------------------------ proton conduction (Eq. 16)
+SIGMA = 3.0  # ionomer conductivity in any unit (the normalised results do not depend on it)
+
+
+def test_protons_see_the_ionomer_and_o2_the_pores():
+    """Parallel channels along x: ionomer fills 5 of 20 cross-section cells,
+    pore 8, solid the rest.  Protons (Eq. 16, uniform conductivity, no
+    source) give sigma_eff / sigma = 5/20 exactly; O2 in the same box gives
+    D_eff / D_b = 8/20.  The carrier alone decides which phase conducts."""
+    ph = np.ones((4, 5, 12), np.uint8)  # (nz, ny, nx)
+    ph[0, 0:5, :] = 2                   # 5 ionomer lines
+    ph[2, 0:5, :] = 0                   # 5 pore lines
+    ph[3, 1:4, :] = 0                   # 3 more pore lines
+    op = oracle.OracleLBM(ph, dx_m=DX, D_bulk=DB, D_ionomer=SIGMA, carrier=1, tau_ref=0.8)
+    _solve(op)
+    assert op.effective_diffusivity()[1] == pytest.approx(5 / 20, rel=1e-11)
+    assert op.active().sum() == 5 * 12
+    oo = oracle.OracleLBM(ph, dx_m=DX, D_bulk=DB, tau_ref=0.8)
+    _solve(oo)
+    assert oo.effective_diffusivity()[1] == pytest.approx(8 / 20, rel=1e-11)
+
+
+def test_protons_ignore_ionomer_pockets_and_pore_links():
+    """An ionomer pocket joined to the inlet only through pore cells is not
+    on the proton path (the active set is ionomer 6-connected to x = 0)."""
+    ph = np.ones((3, 3, 8), np.uint8)
+    ph[1, 1, :] = 2          # one ionomer line through the box
+    ph[0, 0, 0:3] = 0        # pore from the inlet ...
+    ph[0, 0, 3:6] = 2        # ... to an ionomer pocket
+    act = oracle.active_mask(ph, protons=True)
+    assert act[1, 1].all() and not act[0, 0].any()
+    o = oracle.OracleLBM(ph, dx_m=DX, D_bulk=DB, D_ionomer=SIGMA, carrier=1)
+    _solve(o)
+    assert o.effective_diffusivity()[1] == pytest.approx(1 / 9, rel=1e-11)
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_protons_tau1_equal_finite_volume(seed):
+    """Random ionomer network: the proton steady state at tau = 1 equals
+    the finite-volume solution on the ionomer cells connected to x = 0."""
+    rng = np.random.default_rng(seed)
+    shape = (5, 6, 9)
+    ph = rng.choice([0, 1, 2, 3], size=shape, p=[0.3, 0.2, 0.45, 0.05]).astype(np.uint8)
+    ph[:, :, 0] = 2  # an ionomer inlet plane
+    o = oracle.OracleLBM(ph, dx_m=DX, D_bulk=DB, D_ionomer=SIGMA, carrier=1, tau_ref=1.0, c_in=1.0, c_out=0.0)
+    _solve(o, tol=1e-15, check=500)
+    act = o.active() > 0
+    assert act.sum() == oracle.active_mask(ph, protons=True).sum()
+    assert not act[ph != 2].any()
+    D_lu = np.where(act, 0.25 * (o.tau() - 0.5), 0.0)
+    Cf = _fv_solution(act, D_lu, np.zeros(shape, np.uint8), 0.0, 0, 0, 1.0, 0.0)
+    np.testing.assert_allclose(o.concentration()[act], Cf[act], rtol=0, atol=1e-11)
+
+
+def test_protons_need_a_conductivity_and_no_sink():
+    ph = np.full((2, 2, 4), 2, np.uint8)
+    with pytest.raises(ValueError):
+        oracle.OracleLBM(ph, carrier=1)                 # D_ionomer = 0
+    with pytest.raises(ValueError):
+        oracle.OracleLBM(ph, carrier=1, D_ionomer=1.0, k_ms=1.0)
