@@ -70,6 +70,13 @@ typedef enum {
     CL_STORE_FP32POP = 2
 } cl_storage;
 
+/* What the solve transports.  O2: the pore space (pore 0 and micropore 3,
+   plus ionomer 2 when D_ionomer > 0), Eq. 6 / Eq. 15.  PROTON: the ionomer
+   phase alone with the uniform conductivity D_ionomer and no source --
+   Eq. 16 with S_e = 0, whose Eq. 19-type readout is the effective proton
+   conductivity of Sec. 5.2 (potential boundary values in c_in / c_out). */
+typedef enum { CL_CARRIER_O2 = 0, CL_CARRIER_PROTON = 1 } cl_carrier;
+
 typedef enum {
     CL_REACT_GIVEN = 0,   /* reactive faces from the mask given to set_structure (NULL: none) */
     CL_REACT_ALL_PORE_SOLID = 1 /* every face between a pore (0) and a solid (1) cell */
@@ -95,6 +102,7 @@ typedef struct {
     double tau_ref;        /* relaxation time of the most diffusive active cell (> 0.5) */
     int storage;           /* cl_storage */
     int react_rule;        /* cl_react_rule */
+    int carrier;           /* cl_carrier; PROTON needs D_ionomer > 0 and k_ms = 0 */
     int check_every;       /* steps between convergence checks in cl_lbm_solve (even, >= 2) */
     double tol_flux;       /* |J_in - J_out - R| / |J_in| below this ... */
     double tol_rel;        /* ... and the extrapolated relative error of the tracked readout
@@ -197,7 +205,9 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
    Per step: sum C(t+1) - sum C(t) = J_in - J_out - R. */
 cl_status cl_lbm_fluxes(cl_handle h, double out[5]);
 
-/* Eq. 19 from the outlet flux: D_eff [m^2/s] and D_eff / D_b.  Needs
+/* Eq. 19 from the outlet flux: D_eff [m^2/s] and D_eff / D_b.  For the
+   PROTON carrier the same readout is the effective conductivity (in the
+   unit of D_ionomer) and the ratio is taken to D_ionomer (Sec. 5.2).  Needs
    Dirichlet at both ends and c_in != c_out (else CL_ERR_STATE).
    Either pointer may be NULL. */
 cl_status cl_lbm_effective_diffusivity(cl_handle h, double* d_eff_m2s, double* d_eff_over_db);

@@ -24,6 +24,7 @@ CL_ERR_DIVERGED, CL_ERR_NOT_CONVERGED, CL_ERR_NO_PATH, CL_ERR_TIMEOUT = 5, 6, 7,
 CL_BC_DIRICHLET, CL_BC_ZERO_FLUX = 0, 1
 CL_STORE_FP32, CL_STORE_FP16DEV, CL_STORE_FP32POP = 0, 1, 2
 CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID = 0, 1
+CL_CARRIER_O2, CL_CARRIER_PROTON = 0, 1
 
 cl_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 cl_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -37,7 +38,8 @@ class cl_params(ctypes.Structure):
         ("k_ms", ctypes.c_double),
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
-        ("storage", ctypes.c_int), ("react_rule", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("storage", ctypes.c_int), ("react_rule", ctypes.c_int), ("carrier", ctypes.c_int),
+        ("check_every", ctypes.c_int),
         ("tol_flux", ctypes.c_double), ("tol_rel", ctypes.c_double),
         ("max_steps", ctypes.c_longlong),
         ("cuda_stream", ctypes.c_void_p),

@@ -23,6 +23,12 @@ void set_msg(const char* where, cudaError_t e) {
 }
 void set_msg_txt(const char* txt) { snprintf(g_msg, sizeof(g_msg), "%s", txt); }
 cl_status from_cuda(cudaError_t e) { return e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA; }
+
+// bit k set: phase code k carries the transported quantity
+int transport_phases(const cl_params& p) {
+    if (p.carrier == CL_CARRIER_PROTON) return 1 << 2;           // ionomer (Eq. 16)
+    return (1 << 0) | (1 << 3) | (p.D_ionomer > 0 ? 1 << 2 : 0);  // pore, micropore (+ ionomer, Eq. 15)
+}
 float reactive_factor(const cl_lbm* h) {
     const double w = 0.125;
     return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
@@ -269,7 +275,7 @@ cl_status need_structure(cl_lbm* h) {
 // stats + dt + omega, shared by set_structure and set_diffusivity
 cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
     double* stat_out = h->d_red + 8;  // 7 slots
-    CK(launch_stats(h->phase, h->mask, h->D, with_dp ? h->dp : nullptr, h->N, h->nx, h->p.D_ionomer > 0,
+    CK(launch_stats(h->phase, h->mask, h->D, with_dp ? h->dp : nullptr, h->N, h->nx, transport_phases(h->p),
                     h->partials, h->nblk_stats, stat_out, h->s));
     double st[7];
     CK(cudaMemcpyAsync(st, stat_out, sizeof(st), cudaMemcpyDeviceToHost, h->s));
@@ -407,6 +413,11 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if ((p->bc_in != 0 && p->bc_in != 1) || (p->bc_out != 0 && p->bc_out != 1)) { set_msg_txt("bad boundary type"); return CL_ERR_ARG; }
     if (p->storage != CL_STORE_FP32 && p->storage != CL_STORE_FP16DEV && p->storage != CL_STORE_FP32POP) { set_msg_txt("bad storage mode"); return CL_ERR_ARG; }
     if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
+    if (p->carrier != CL_CARRIER_O2 && p->carrier != CL_CARRIER_PROTON) { set_msg_txt("bad carrier"); return CL_ERR_ARG; }
+    if (p->carrier == CL_CARRIER_PROTON && !(p->D_ionomer > 0 && p->k_ms == 0)) {
+        set_msg_txt("the proton carrier needs D_ionomer > 0 (its conductivity) and k_ms = 0");
+        return CL_ERR_ARG;
+    }
     if (p->check_every < 2 || (p->check_every & 1)) { set_msg_txt("check_every must be even and >= 2"); return CL_ERR_ARG; }
     if ((p->alloc == nullptr) != (p->free == nullptr)) { set_msg_txt("alloc and free must both be set or both NULL"); return CL_ERR_ARG; }
     if (!(fabs(p->c_in) < 1e30) || !(fabs(p->c_out) < 1e30)) { set_msg_txt("boundary concentrations must be finite"); return CL_ERR_ARG; }
@@ -514,8 +525,8 @@ cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t*
     CK(launch_validate(h->phase, h->N, h->d_err, h->s));
     CKS(check_err_flag(h));
     h->have_structure = false;
-    const int ion = h->p.D_ionomer > 0;
-    CK(launch_percolation(h->phase, h->nx, h->ny, h->nz, ion, h->labels, h->touch, h->active, h->d_err, h->s));
+    CK(launch_percolation(h->phase, h->nx, h->ny, h->nz, transport_phases(h->p), h->labels, h->touch, h->active,
+                          h->d_err, h->s));
     CKS(check_err_flag(h));
     // Eq. 7 unless the bulk value is given
     h->D_b = h->p.D_bulk > 0 ? h->p.D_bulk : 0.22e-4 * pow(h->p.T_K / 293.2, 1.5) / h->p.p_atm;
@@ -666,7 +677,8 @@ cl_status cl_lbm_effective_diffusivity(cl_handle h, double* d_eff_m2s, double* d
     const double dlu = jd * h->nx / (h->p.c_in - h->p.c_out);
     const double d = dlu * h->p.dx_m * h->p.dx_m / h->dt;
     if (d_eff_m2s) *d_eff_m2s = d;
-    if (d_eff_over_db) *d_eff_over_db = d / h->D_b;
+    // protons: the effective conductivity over the ionomer's own (Sec. 5.2)
+    if (d_eff_over_db) *d_eff_over_db = d / (h->p.carrier == CL_CARRIER_PROTON ? h->p.D_ionomer : h->D_b);
     return CL_OK;
 }
 

@@ -37,7 +37,7 @@ struct StepArgs {
 
 // ---- setup (kernels.cu) ----
 cudaError_t launch_validate(const uint8_t* phase, long long N, int* d_err, cudaStream_t s);
-cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
+cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int transport_phase_mask,
                                int* labels, uint8_t* touch, uint8_t* active, int* d_err,
                                cudaStream_t s);
 cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int nx, int ny, int nz,
@@ -55,7 +55,7 @@ cudaError_t launch_masks(const uint8_t* phase, const uint8_t* active, const uint
 // stats: out[0] n_transport, [1] n_active, [2] wall links, [3] react links,
 //        [4] sum d_p over pore cells, [5] pore cells, [6] D_max (max)
 cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const double* D,
-                         const double* dp, long long N, int nx, int ionomer_transport,
+                         const double* dp, long long N, int nx, int transport_phase_mask,
                          double* partials, int nblocks, double* out, cudaStream_t s);
 
 // ---- FP32 solver (kernels.cu) ----

@@ -9,9 +9,8 @@ namespace cl {
 
 // --------------------------------------------------------------- helpers
 __device__ __forceinline__ bool is_pore(uint8_t p) { return p == 0 || p == 3; }
-__device__ __forceinline__ bool is_transport(uint8_t p, int ion) {
-    return p == 0 || p == 3 || (p == 2 && ion);
-}
+// `tmask` bit k set: phase code k carries the transported quantity
+__device__ __forceinline__ bool is_transport(uint8_t p, int tmask) { return p < 4 && ((tmask >> p) & 1); }
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // ------------------------------------------------------------ validation
@@ -58,27 +57,27 @@ __device__ void uf_union(int* L, int a, int b, int* err) {
     atomicOr(err, 2);
 }
 
-__global__ void k_uf_init(const uint8_t* __restrict__ phase, long long N, int ion, int* L,
+__global__ void k_uf_init(const uint8_t* __restrict__ phase, long long N, int tmask, int* L,
                           uint8_t* touch) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
-        L[c] = is_transport(phase[c], ion) ? (int)c : -1;
+        L[c] = is_transport(phase[c], tmask) ? (int)c : -1;
         touch[c] = 0;
     }
 }
 
-__global__ void k_uf_merge(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ion, int* L,
+__global__ void k_uf_merge(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int tmask, int* L,
                            int* err) {
     const long long N = (long long)nx * ny * nz;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
-        if (!is_transport(phase[c], ion)) continue;
+        if (!is_transport(phase[c], tmask)) continue;
         const int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
-        if (x > 0 && is_transport(phase[c - 1], ion)) uf_union(L, (int)c, (int)(c - 1), err);
+        if (x > 0 && is_transport(phase[c - 1], tmask)) uf_union(L, (int)c, (int)(c - 1), err);
         long long n = x + (long long)nx * (wrapi(y - 1, ny) + (long long)ny * z);
-        if (n != c && is_transport(phase[n], ion)) uf_union(L, (int)c, (int)n, err);
+        if (n != c && is_transport(phase[n], tmask)) uf_union(L, (int)c, (int)n, err);
         n = x + (long long)nx * (y + (long long)ny * wrapi(z - 1, nz));
-        if (n != c && is_transport(phase[n], ion)) uf_union(L, (int)c, (int)n, err);
+        if (n != c && is_transport(phase[n], tmask)) uf_union(L, (int)c, (int)n, err);
     }
 }
 
@@ -101,12 +100,12 @@ __global__ void k_uf_active(long long N, const int* __restrict__ L, const uint8_
         active[c] = (L[c] >= 0 && touch[L[c]]) ? 1 : 0;
 }
 
-cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int ion, int* labels,
+cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int tmask, int* labels,
                                uint8_t* touch, uint8_t* active, int* d_err, cudaStream_t s) {
     const long long N = (long long)nx * ny * nz;
     const int g = 152 * 8, b = 256;
-    k_uf_init<<<g, b, 0, s>>>(phase, N, ion, labels, touch);
-    k_uf_merge<<<g, b, 0, s>>>(phase, nx, ny, nz, ion, labels, d_err);
+    k_uf_init<<<g, b, 0, s>>>(phase, N, tmask, labels, touch);
+    k_uf_merge<<<g, b, 0, s>>>(phase, nx, ny, nz, tmask, labels, d_err);
     k_uf_flatten<<<g, b, 0, s>>>(N, labels, d_err);
     k_uf_touch<<<g, b, 0, s>>>(nx, N, labels, touch);
     k_uf_active<<<g, b, 0, s>>>(N, labels, touch, active);
@@ -290,14 +289,14 @@ cudaError_t launch_masks(const uint8_t* phase, const uint8_t* active, const uint
 constexpr int kStatN = 7;
 __global__ void k_stats(const uint8_t* __restrict__ phase, const uint16_t* __restrict__ mask,
                         const double* __restrict__ D, const double* __restrict__ dp, long long N, int nx,
-                        int ion, double* partials) {
+                        int tmask, double* partials) {
     double v[kStatN] = {0, 0, 0, 0, 0, 0, 0};
     double dmax = 0.0;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         const uint8_t ph = phase[c];
         const uint16_t m = mask[c];
-        v[0] += is_transport(ph, ion) ? 1.0 : 0.0;
+        v[0] += is_transport(ph, tmask) ? 1.0 : 0.0;
         if (m & kActiveBit) {
             v[1] += 1.0;
             const int x = (int)(c % nx);
@@ -349,9 +348,9 @@ __global__ void k_finalize(const double* __restrict__ partials, int nblocks, int
 }
 
 cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const double* D, const double* dp,
-                            long long N, int nx, int ion, double* partials, int nblocks, double* out,
+                            long long N, int nx, int tmask, double* partials, int nblocks, double* out,
                             cudaStream_t s) {
-    k_stats<<<nblocks, 256, 0, s>>>(phase, mask, D, dp, N, nx, ion, partials);
+    k_stats<<<nblocks, 256, 0, s>>>(phase, mask, D, dp, N, nx, tmask, partials);
     k_finalize<<<kStatN, 1024, 0, s>>>(partials, nblocks, kStatN, 1u << 6, out);
     return cudaGetLastError();
 }

@@ -65,7 +65,8 @@ extern "C" cl_status cl_active_mask_noalloc(const uint8_t* phase, int nx, int ny
     cudaStream_t s = (cudaStream_t)cuda_stream;
     if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return CL_ERR_CUDA;
     if (cl::launch_validate(phase, N, err, s) != cudaSuccess) return CL_ERR_CUDA;
-    if (cl::launch_percolation(phase, nx, ny, nz, ionomer_transport ? 1 : 0, labels, flags, active, err, s) !=
+    // transport phases as bits of the phase code: pore and micropore (0x9), plus ionomer (0xD)
+    if (cl::launch_percolation(phase, nx, ny, nz, ionomer_transport ? 0xD : 0x9, labels, flags, active, err, s) !=
         cudaSuccess)
         return CL_ERR_CUDA;
     int herr = 0;

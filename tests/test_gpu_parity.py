@@ -185,10 +185,10 @@ def test_converged_deff_small_workload(cuda_lib, storage, rel):
 
 def _fv_deff_uniform(solid):
     """D_eff / D of the cell-centred finite-volume solution (uniform D on the
-    pore cells, half-cell Dirichlet faces 1 | 0 in x, periodic y and z),
-    assembled with numpy and solved by conjugate gradients.  With tau = 1
-    this is the steady state of the D3Q7 scheme (pinned on the oracle in
-    test_oracle_pins.py)."""
+    conducting cells ~solid, half-cell Dirichlet faces 1 | 0 in x, periodic
+    y and z), assembled with numpy and solved by conjugate gradients.  With
+    tau = 1 this is the steady state of the D3Q7 scheme (pinned on the
+    oracle in test_oracle_pins.py)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spl
     nz, ny, nx = solid.shape
@@ -245,3 +245,60 @@ def test_sphere_in_cube_96(cuda_lib):
     with open(os.path.join(HERE, "golden", "paper_values.json")) as fh:
         ref = json.load(fh)["sphere_in_cube_deff"]["value"]
     assert d_rel == pytest.approx(ref, rel=0.04)
+
+
+# ------------------------------------------------ proton conduction (Eq. 16)
+SIGMA = 2.5  # ionomer conductivity (any unit; results are normalised by it)
+
+
+def _proton_case(shape=(16, 20, 70), seed=31):
+    ph = inputs.pt_cl(shape, seed, 0.45, 0.1887)
+    params = dict(dx_m=2e-9, D_bulk=2.9e-5, knudsen=1, D_ionomer=SIGMA, carrier=1, tau_ref=0.9,
+                  c_in=1.0, c_out=0.0)
+    return ph, params
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16dev"])
+def test_protons_setup_and_trajectory(cuda_lib, storage):
+    """Protons in the ionomer of a QSGS layer: the active set (ionomer
+    6-connected to x = 0) is bit-exact, omega matches, and the field after
+    150 steps matches the oracle within the storage tolerance."""
+    ph, params = _proton_case()
+    o = oracle.OracleLBM(ph, **params)
+    with _solver(ph.shape, storage, **params) as s:
+        s.set_structure(ph)
+        su = s.setup()
+        act = o.active() > 0
+        np.testing.assert_array_equal(su["active"], o.active())
+        assert not act[ph != 2].any()
+        np.testing.assert_allclose(su["omega"][act], 1.0 / o.tau()[act], rtol=1e-6)
+        s.step(150)
+        o.step(150)
+        np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(storage, 150))
+
+
+def test_protons_effective_conductivity_against_finite_volume(cuda_lib):
+    """Converged effective proton conductivity (Sec. 5.2) of a 40 x 40 x 64
+    layer through the C ABI equals the finite-volume value on the same
+    ionomer cells (tau = 1 everywhere: uniform conductivity) to 2e-5."""
+    ph, params = _proton_case((40, 40, 64), 32)
+    params = dict(params, tau_ref=1.0)
+    act = oracle.active_mask(ph, protons=True).astype(bool)
+    with _solver(ph.shape, "fp32", check_every=500, tol_rel=1e-7, tol_flux=1e-6, max_steps=4_000_000,
+                 **params) as s:
+        s.set_structure(ph)
+        info = s.solve()
+        assert info["status"] == "CL_OK", info
+        d, ratio = s.effective_diffusivity()
+    fv = _fv_deff_uniform(~act)
+    assert ratio == pytest.approx(fv, rel=2e-5)
+    assert d == pytest.approx(fv * SIGMA, rel=2e-5)
+    assert 0 < ratio < (ph == 2).mean()  # below the ionomer volume fraction (tortuosity)
+
+
+def test_protons_reject_sink_or_missing_conductivity(cuda_lib):
+    from paper_1410_1914_gb300 import _lib as L
+    with pytest.raises(L.ClError):
+        _solver((4, 4, 8), "fp32", carrier=1, D_ionomer=0.0)
+    with pytest.raises(L.ClError):
+        _solver((4, 4, 8), "fp32", carrier=1, D_ionomer=1.0, k_ms=1.0)
