@@ -292,6 +292,12 @@ def run_converge(args):
     else:
         ph, react, params = inputs.make_workload("pt_cl_256", shape=shape, reactive=False)
         label = f"{shape[2]}x{shape[1]}x{shape[0]} Pt layer, 2 nm, Knudsen D, D_eff set-up"
+    if args.carrier == "proton":
+        # Eq. 16 in the ionomer alone (uniform conductivity, no source): the
+        # effective proton conductivity of Sec. 5.2; readouts are sigma_eff / sigma
+        params = dict(params, carrier=1, D_ionomer=1.0, k_ms=0.0)
+        react = None
+        label = label.replace("Knudsen D, D_eff set-up", "proton conduction in the ionomer (Eq. 16)")
     K = args.check_every
     max_steps = args.max_steps
 
@@ -307,7 +313,7 @@ def run_converge(args):
     arms = [("fp32pop", False), ("fp32", False), ("fp16dev", False)]
     net = None
     nz, ny, nx = ph.shape
-    if nz == ny == nx and nx % 8 == 0 and not args.no_warm:
+    if nz == ny == nx and nx % 8 == 0 and not args.no_warm and args.carrier == "o2":
         from paper_1410_1914_gb300 import warmstart as W
         if os.path.exists(W.WEIGHTS):
             net = W.load_pretrained()
@@ -337,7 +343,8 @@ def run_converge(args):
     plain = out["fp32pop"]["seconds_to_1e-3"]
     state32 = out["fp32"]["seconds_to_1e-3"]
     best = out.get("fp16dev+warm", out["fp16dev"])["seconds_to_1e-3"]
-    line = {"metric": "time-to-converged D_eff (rel 1e-3)", "unit": "s", "higher_is_better": False,
+    line = {"metric": "time-to-converged D_eff (rel 1e-3)" if args.carrier == "o2"
+            else "time-to-converged effective proton conductivity (rel 1e-3)", "unit": "s", "higher_is_better": False,
             "workload": label, "shape_zyx": list(ph.shape), "reference_D_eff_over_Db": ref, "check_every": K,
             "by_arm": out,
             "fp16_warm_vs_plain_fp32": (None if plain is None or best is None else plain / best),
@@ -478,6 +485,8 @@ def main():
     ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64", "converge", "unet_train"])
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--no-warm", action="store_true", help="converge workload: skip the learned warm-start arms")
+    ap.add_argument("--carrier", default="o2", choices=["o2", "proton"],
+                    help="converge workload: O2 in the pores (D_eff) or protons in the ionomer (sigma_eff)")
     args = ap.parse_args()
     if args.shape:
         args.shape = tuple(args.shape)
