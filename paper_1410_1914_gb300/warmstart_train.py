@@ -104,10 +104,12 @@ def train(net, groups, steps: int, lr: float = 1e-3, seed: int = 0, log_every: i
 
 
 def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = "fp32", check_every: int = 200,
-             max_steps: int = 6_000_000, rel: float = 1e-3):
+             max_steps: int = 6_000_000, rel: float = 1e-3, extra_arms=()):
     """Steps (and seconds) to D_eff within rel, from the ramp and from the
     warm start.  The ramp run is carried on to an extrapolated relative
-    change below 1e-9 and its last D_eff is the converged reference."""
+    change below 1e-9 and its last D_eff is the converged reference.
+    extra_arms: further (storage, warm) runs scored against the same
+    reference, reported as "<storage>+ramp" / "<storage>+warm"."""
     import torch
 
     from . import warmstart as W
@@ -137,6 +139,23 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
                          "final_rel_err": abs(float(val[-1]) - ref) / abs(ref)}
         if row["ramp"]["steps"] and row["warm"]["steps"]:
             row["steps_saved_frac"] = 1.0 - row["warm"]["steps"] / row["ramp"]["steps"]
+        for st_mode, warm in extra_arms:
+            s = Solver(ph.shape, storage=st_mode, check_every=check_every, **params)
+            s.set_structure(ph, react)
+            t_inf = 0.0
+            if warm:
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                W.warm_start(net, s)
+                torch.cuda.synchronize()
+                t_inf = time.perf_counter() - t1
+            # FP16 readouts carry ~1e-5 noise: the trace only has to outlast the band
+            st, sec, val = deff_trace(s, max_steps, check_every, stop_rel_change=1e-7)
+            s.close()
+            k, secs = time_to_tolerance(st, sec, val, ref, rel)
+            row[f"{st_mode}+{'warm' if warm else 'ramp'}"] = {
+                "steps": k, "seconds": None if secs is None else secs + t_inf, "inference_s": t_inf,
+                "final_rel_err": abs(float(val[-1]) - ref) / abs(ref)}
         rows.append(row)
     return rows
 
@@ -154,12 +173,29 @@ def main():
     ap.add_argument("--eval-size", type=int, nargs="+", default=[96])
     ap.add_argument("--n-eval", type=int, default=3)
     ap.add_argument("--out", default="warmstart_weights.npz")
+    ap.add_argument("--eval-only", default=None, help="weights to evaluate (no data, no training)")
+    ap.add_argument("--eval-seed0", type=int, default=5000)
+    ap.add_argument("--eval-fp16", action="store_true", help="also score FP16-state runs from the ramp and warm start")
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     import torch
 
-    from .warmstart import UNet
+    from .warmstart import UNet, load_pretrained
     torch.cuda.set_device(0)
+    arms = (("fp16dev", False), ("fp16dev", True)) if args.eval_fp16 else ()
+    if args.eval_only:
+        net = load_pretrained(args.eval_only)
+        rows = []
+        for size in args.eval_size:
+            r = evaluate(net, size, args.n_eval, seed0=args.eval_seed0, extra_arms=arms)
+            for x in r:
+                x["size"] = size
+            print(json.dumps({"eval": r}), flush=True)
+            rows += r
+        if args.report:
+            with open(args.report, "w") as fh:
+                json.dump({"eval": rows, "config": vars(args)}, fh, indent=1)
+        return
     groups, dstats = [], []
     data_net = None
     if args.data_warm:
@@ -179,7 +215,7 @@ def main():
     np.savez_compressed(args.out, **{k: v.astype(np.float16) for k, v in net.state_dict().items()})
     rows = []
     for size in args.eval_size:
-        r = evaluate(net, size, args.n_eval)
+        r = evaluate(net, size, args.n_eval, seed0=args.eval_seed0, extra_arms=arms)
         for x in r:
             x["size"] = size
         print(json.dumps({"eval": r}), flush=True)
