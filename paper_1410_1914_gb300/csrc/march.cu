@@ -518,8 +518,11 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty) {
 // empty[s] when every consumer warp has released it.  A consumer keeps the
 // z-1 values it needs (its own cells one plane below) in registers, so a
 // slot is live only while its plane is the current or the next one.
+// FP16 plain steps: 72 registers, which still fits three resident blocks per
+// SM (3 x 288 x 72 <= 65536) without the recomputation a tighter bound
+// forces; the other variants take what they need.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 3 : 1)
+__global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) == 2 && !REDUCE) ? 72 : 168)
     k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
     // Addressed directly (no integer round trip) so that every slot access
     // compiles to a shared-memory load.
