@@ -576,6 +576,222 @@ cudaError_t launch_conv3d_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16*
     return cudaGetLastError();
 }
 
+// ------------------------------------------------- forward, halo tiles
+// The same convolution with the 27 taps read from one gathered neighbourhood
+// instead of 27 gathers.  A CTA owns an 8 (x) x 16 (y) block of output
+// voxels at one z of one batch item: M row r = 8 yr + xr.  Per chunk of CK
+// input channels it stages the 10 x 18 x 3 halo of that block once, laid
+// out so that every tap's A operand is the same K-major core-matrix layout
+// at a shifted start address:
+//   halo voxel (xi, yj, zk), channel group g (8 channels, 16 bytes) at
+//   zk PZ + yj PY + g PC + xi 16,   PC = 10 x 16 B, PY = CK/8 PC, PZ = 18 PY;
+//   tap (dx, dy, dz): start = (1+dz) PZ + (1+dy) PY + (1+dx) 16,
+//   LBO = PC (next 8 channels), SBO = PY (next 8-row group = next y line).
+// Only the weights stream, one tap per ring stage.  x is zero padded; y and
+// z wrap (or are zero padded); rows outside the box are computed and dropped.
+constexpr int kHaloX = 10, kHaloY = 18, kHaloZ = 3;
+constexpr int kHaloStages = 4;                 // weight ring
+constexpr int kHaloLag = kHaloStages - 2;      // weight stages in flight per thread
+
+struct HaloShape {
+    int CK, ncols, halo_bytes, w_bytes, smem;
+};
+
+__host__ __device__ inline HaloShape halo_shape(int ci, int co) {
+    HaloShape s;
+    const int cands[4] = {64, 48, 32, 16};
+    s.CK = 16;
+    for (int i = 0; i < 4; ++i) {
+        const int ck = cands[i];
+        if (ck > ci || ci % ck) continue;
+        const int hb = kHaloX * kHaloY * kHaloZ * ck * 2, wb = co * ck * 2;
+        if (1024 + hb + kHaloStages * wb <= 200 * 1024) { s.CK = ck; break; }
+    }
+    int c = 32;
+    while (c < co) c <<= 1;
+    s.ncols = c;
+    s.halo_bytes = kHaloX * kHaloY * kHaloZ * s.CK * 2;
+    s.w_bytes = co * s.CK * 2;
+    s.smem = 1024 + s.halo_bytes + kHaloStages * s.w_bytes;
+    return s;
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_conv3d_halo(const __nv_bfloat16* __restrict__ in,
+                                                            const __nv_bfloat16* __restrict__ w,
+                                                            const float* __restrict__ bias,
+                                                            __nv_bfloat16* __restrict__ out, ConvGeom g, int relu,
+                                                            int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const HaloShape sh = halo_shape(g.ci, g.co);
+    uint64_t* wfull = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* wempty = wfull + kHaloStages;
+    uint64_t* hempty = wempty + kHaloStages;  // the halo may be refilled
+    uint64_t* done = hempty + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    unsigned char* halo = smem + 1024;
+    unsigned char* wring = halo + sh.halo_bytes;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int CK = sh.CK, kg = CK / 8;
+    const int nchunks = g.ci / CK;
+    const int ksteps = 27 * nchunks;  // one tap of one chunk per step
+    const uint32_t PC = 16u * kHaloX, PY = (uint32_t)kg * PC, PZ = (uint32_t)kHaloY * PY;
+    // output block
+    const int x0 = blockIdx.x * 8, y0 = blockIdx.y * 16;
+    const int zb = blockIdx.z % g.D;
+    const long long nb = blockIdx.z / g.D;
+
+    if (tid == 0) {
+        for (int s = 0; s < kHaloStages; ++s) {
+            bar_init(&wfull[s], 128);
+            bar_init(&wempty[s], 1);
+        }
+        bar_init(hempty, 1);
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(sh.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------ producers
+        bool ok = true;
+        int issued = 0, published = 0;
+        const uint32_t halo_s = smem_addr(halo);
+        const int nhalo = kHaloX * kHaloY * kHaloZ * kg;  // 16-byte chunks of one halo
+        for (int ks = 0; ks < ksteps && ok; ++ks) {
+            const int t = ks % 27, chunk = ks / 27;
+            if (t == 0) {
+                if (chunk > 0) {
+                    // publish every step still in flight, then wait until the
+                    // previous chunk's MMAs are done with the halo
+                    cp_async_wait<0>();
+                    fence_async_shared();
+                    for (; published < issued; ++published) bar_arrive(&wfull[published % kHaloStages]);
+                    if (!bar_wait(hempty, (chunk - 1) & 1)) { ok = false; break; }
+                }
+                const int c0 = chunk * CK;
+                for (int e = tid; e < nhalo; e += 128) {
+                    const int grp = e % kg;
+                    const int v = e / kg;
+                    const int xi = v % kHaloX, yj = (v / kHaloX) % kHaloY, zk = v / (kHaloX * kHaloY);
+                    const int qx = x0 - 1 + xi;
+                    int qy = y0 - 1 + yj, qz = zb - 1 + zk;
+                    bool valid = qx >= 0 && qx < g.W;
+                    if (g.periodic_yz) {
+                        qy = ((qy % g.H) + g.H) % g.H;
+                        qz = ((qz % g.D) + g.D) % g.D;
+                    } else {
+                        valid = valid && qy >= 0 && qy < g.H && qz >= 0 && qz < g.D;
+                    }
+                    const long long sv =
+                        valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nb)) : 0;
+                    const uint32_t dst = halo_s + (uint32_t)zk * PZ + (uint32_t)yj * PY + (uint32_t)grp * PC +
+                                         (uint32_t)xi * 16u;
+                    cp_async16(dst, in + sv * g.in_stride + g.in_off + c0 + 8 * grp, valid);
+                }
+            }
+            // the tap's weights into the ring
+            const int s = ks % kHaloStages;
+            if (ks >= kHaloStages && !bar_wait(&wempty[s], ((ks / kHaloStages) - 1) & 1)) { ok = false; break; }
+            if (*(volatile int*)abort_flag) { ok = false; break; }
+            const uint32_t wb = smem_addr(wring + s * sh.w_bytes);
+            const __nv_bfloat16* wt = w + (long long)t * g.co * g.ci + chunk * CK;
+            for (int e = tid; e < g.co * kg; e += 128) {
+                const int n = e / kg, h = e % kg;
+                cp_async16(wb + (uint32_t)(n >> 3) * (uint32_t)(kg * 128) + (uint32_t)h * 128u + (uint32_t)(n & 7) * 16u,
+                           wt + (long long)n * g.ci + 8 * h, true);
+            }
+            cp_async_commit();
+            ++issued;
+            if (issued - published > kHaloLag) {
+                // every earlier copy of this thread (the halo too) has landed
+                cp_async_wait<kHaloLag>();
+                fence_async_shared();
+                bar_arrive(&wfull[published % kHaloStages]);
+                ++published;
+            }
+        }
+        cp_async_wait<0>();
+        fence_async_shared();
+        for (; published < issued; ++published) bar_arrive(&wfull[published % kHaloStages]);
+        if (!ok) {
+            atomicOr(err, 64);
+            *(volatile int*)abort_flag = 1;
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16(kTcM, g.co);
+        const uint32_t halo_s = smem_addr(halo);
+        const uint32_t sbo_w = (uint32_t)kg * 128u;
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kHaloStages, t = ks % 27;
+            if (!bar_wait(&wfull[s], (ks / kHaloStages) & 1) || *(volatile int*)abort_flag) {
+                atomicOr(err, 64);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // tap offset + 1
+            const uint32_t a0 = halo_s + (uint32_t)dz * PZ + (uint32_t)dy * PY + (uint32_t)dx * 16u;
+            const uint32_t b0 = smem_addr(wring + s * sh.w_bytes);
+            for (int kk = 0; kk < CK / 16; ++kk) {
+                const uint64_t ad = sdesc(a0 + (uint32_t)kk * 2u * PC, PC, PY);
+                const uint64_t bd = sdesc(b0 + (uint32_t)kk * 256u, 128u, sbo_w);
+                mma_bf16_ss(tmem, ad, bd, idesc, (ks > 0 || kk > 0) ? 1u : 0u);
+            }
+            mma_commit(&wempty[s]);
+            if (t == 26) mma_commit(hempty);  // the chunk's halo is no longer read
+        }
+        mma_commit(done);
+    }
+
+    // ---------------------------------------------------------- epilogue
+    if (warp < 4) {
+        const bool ok = bar_wait(done, 0);
+        tc_fence_after();
+        if (!ok) atomicOr(err, 64);
+        const int r = tid, x = x0 + (r & 7), y = y0 + (r >> 3);
+        const bool store = ok && !*(volatile int*)abort_flag && x < g.W && y < g.H;
+        const long long v = x + (long long)g.W * (y + (long long)g.H * (zb + (long long)g.D * nb));
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < g.co; c += 16) {
+            uint32_t acc[16];
+            tmem_ld16(lane_base + (uint32_t)c, acc);
+            if (store) {
+                uint32_t pk[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    float a = __uint_as_float(acc[2 * j]) + (bias ? bias[c + 2 * j] : 0.f);
+                    float b = __uint_as_float(acc[2 * j + 1]) + (bias ? bias[c + 2 * j + 1] : 0.f);
+                    if (relu) { a = fmaxf(a, 0.f); b = fmaxf(b, 0.f); }
+                    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+                    pk[j] = *reinterpret_cast<uint32_t*>(&h);
+                }
+                uint4* dst = reinterpret_cast<uint4*>(out + v * g.out_stride + g.out_off + c);
+                dst[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                dst[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.ncols) : "memory");
+    }
+}
+
 bool conv3d_tc_supported(const ConvGeom& g) {
     return g.ci % 16 == 0 && g.co % 16 == 0 && g.co >= 16 && g.co <= 256 && g.in_stride % 8 == 0 &&
            g.in_off % 8 == 0 && g.out_stride % 8 == 0 && g.out_off % 8 == 0 && tc_shape(g.ci, g.co).smem <= 227 * 1024;
@@ -583,6 +799,14 @@ bool conv3d_tc_supported(const ConvGeom& g) {
 
 cudaError_t launch_conv3d_tc(const __nv_bfloat16* in, const __nv_bfloat16* w, const float* bias, __nv_bfloat16* out,
                              const ConvGeom& g, int relu, int* err, cudaStream_t s) {
+    const HaloShape hs = halo_shape(g.ci, g.co);
+    if (hs.smem <= 227 * 1024 && (long long)g.D * g.N <= 65535) {
+        cudaError_t e = cudaFuncSetAttribute(k_conv3d_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, hs.smem);
+        if (e != cudaSuccess) return e;
+        const dim3 grid((unsigned)((g.W + 7) / 8), (unsigned)((g.H + 15) / 16), (unsigned)(g.D * g.N));
+        k_conv3d_halo<<<grid, kTcThreads, hs.smem, s>>>(in, w, bias, out, g, relu, err);
+        return cudaGetLastError();
+    }
     const TcShape sh = tc_shape(g.ci, g.co);
     cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
     if (e != cudaSuccess) return e;
