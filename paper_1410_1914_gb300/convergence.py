@@ -54,7 +54,8 @@ class StopRule:
 
 
 def deff_trace(solver, max_steps: int, check_every: int, stop_rel_change: float = 1e-7):
-    """Run from the current state; return (steps, seconds, D_eff/D_b) per check.
+    """Run from the current state; return (steps, seconds, D_eff/D_b) per check
+    (sigma_eff / sigma for the proton carrier).
 
     Stops after max_steps or once the extrapolated relative change of the
     outlet flux has been below stop_rel_change at two checks in a row (the
@@ -63,7 +64,9 @@ def deff_trace(solver, max_steps: int, check_every: int, stop_rel_change: float 
     info = solver.info()
     nz, ny, nx = solver.shape
     p = solver.params
-    scale = nx / ((p.c_in - p.c_out) * ny * nz) * p.dx_m * p.dx_m / info["dt_s"] / info["D_b"]
+    # D_eff / D_b for O2; sigma_eff / sigma (the ionomer's own) for protons
+    ref = p.D_ionomer if getattr(p, "carrier", 0) == 1 else info["D_b"]
+    scale = nx / ((p.c_in - p.c_out) * ny * nz) * p.dx_m * p.dx_m / info["dt_s"] / ref
     steps, secs, vals = [], [], []
     rule = StopRule(stop_rel_change)
     t0 = time.perf_counter()

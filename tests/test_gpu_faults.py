@@ -72,9 +72,11 @@ def test_nonfinite_initial_field_diverges(cuda_lib):
         z, y, x = np.argwhere(act)[len(np.argwhere(act)) // 2]
         C0[z, y, x] = np.nan
         s.init(C0)
-        d = s.solve_budget(40)
-        assert d["status"] == "CL_ERR_DIVERGED"
-        assert d["steps"] == 10  # stopped at the first check
+        with pytest.raises(L.ClError) as ei:
+            s.solve_budget(40)
+        assert ei.value.status == L.CL_ERR_DIVERGED
+        assert "non-finite" in str(ei.value)
+        assert s.steps == 10  # stopped at the first check
 
 
 def test_step_budget_reports_not_converged(cuda_lib):
