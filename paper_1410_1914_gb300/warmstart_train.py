@@ -104,7 +104,7 @@ def train(net, groups, steps: int, lr: float = 1e-3, seed: int = 0, log_every: i
 
 
 def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = "fp32", check_every: int = 200,
-             max_steps: int = 6_000_000, rel: float = 1e-3, extra_arms=()):
+             max_steps: int = 6_000_000, rel: float = 1e-3, extra_arms=(), base_warm: bool = True):
     """Steps (and seconds) to D_eff within rel, from the ramp and from the
     warm start.  The ramp run is carried on to an extrapolated relative
     change below 1e-9 and its last D_eff is the converged reference.
@@ -119,7 +119,7 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
     rows = []
     for ph, react, params in work:
         row = {}
-        for mode in ("ramp", "warm"):
+        for mode in ("ramp", "warm") if base_warm else ("ramp",):
             s = Solver(ph.shape, storage=storage, check_every=check_every, **params)
             s.set_structure(ph, react)
             t_inf = 0.0
@@ -137,7 +137,7 @@ def evaluate(net, size: int = 96, n: int = 4, seed0: int = 5000, storage: str = 
             k, secs = time_to_tolerance(st, sec, val, ref, rel)
             row[mode] = {"steps": k, "seconds": None if secs is None else secs + t_inf, "inference_s": t_inf,
                          "final_rel_err": abs(float(val[-1]) - ref) / abs(ref)}
-        if row["ramp"]["steps"] and row["warm"]["steps"]:
+        if "warm" in row and row["ramp"]["steps"] and row["warm"]["steps"]:
             row["steps_saved_frac"] = 1.0 - row["warm"]["steps"] / row["ramp"]["steps"]
         for st_mode, warm in extra_arms:
             s = Solver(ph.shape, storage=st_mode, check_every=check_every, **params)
@@ -176,6 +176,8 @@ def main():
     ap.add_argument("--eval-only", default=None, help="weights to evaluate (no data, no training)")
     ap.add_argument("--eval-seed0", type=int, default=5000)
     ap.add_argument("--eval-fp16", action="store_true", help="also score FP16-state runs from the ramp and warm start")
+    ap.add_argument("--eval-no-fp32-warm", action="store_true", help="skip the FP32-state warm-start run")
+    ap.add_argument("--eval-check-every", type=int, default=200)
     ap.add_argument("--report", default=None)
     args = ap.parse_args()
     import torch
@@ -187,7 +189,8 @@ def main():
         net = load_pretrained(args.eval_only)
         rows = []
         for size in args.eval_size:
-            r = evaluate(net, size, args.n_eval, seed0=args.eval_seed0, extra_arms=arms)
+            r = evaluate(net, size, args.n_eval, seed0=args.eval_seed0, extra_arms=arms,
+                         base_warm=not args.eval_no_fp32_warm, check_every=args.eval_check_every)
             for x in r:
                 x["size"] = size
             print(json.dumps({"eval": r}), flush=True)
