@@ -792,6 +792,245 @@ __global__ void __launch_bounds__(kTcThreads) k_conv3d_halo(const __nv_bfloat16*
     }
 }
 
+// ------------------------------------------ weight gradient, halo tiles
+// dW[t][co][ci] over 8 x 16 voxel blocks: per block the input halo (as in
+// the forward kernel) and the block's output gradient dO are staged once;
+// every tap of the CTA's group is then a shifted descriptor into the halo.
+// GEMM per tap: D[m = co][n = ci chunk] += sum over the block's voxels,
+// A = dO (MN-major: 8 channels of a voxel in 16 bytes; voxel line yr of
+// the block at yr PYo, channel group g at g 128, voxel xr at xr 16),
+// B = the halo (MN-major; line stride PY, channel-group stride PC).  M is co
+// padded to 128 (rows co.. are never read back).  A CTA accumulates in
+// tensor memory over the blocks of its slice for TG taps x CN channels
+// (<= 256 columns) and writes one partial per slice; a second kernel sums
+// the slices in a fixed order.
+constexpr int kWhStages = 2;  // double-buffered block stages
+
+struct WgHaloShape {
+    int CN, TG, ngroups, nchunks, ncols, halo_bytes, do_bytes, stage, smem;
+};
+
+__host__ __device__ inline WgHaloShape wgh_shape(int ci, int co) {
+    WgHaloShape s;
+    s.CN = ci <= 64 ? ci : (ci % 64 == 0 ? 64 : (ci % 48 == 0 ? 48 : (ci % 32 == 0 ? 32 : 16)));
+    s.TG = 256 / s.CN;
+    if (s.TG > 27) s.TG = 27;
+    s.ngroups = (27 + s.TG - 1) / s.TG;
+    s.nchunks = ci / s.CN;
+    int c = 32;
+    while (c < s.TG * s.CN) c <<= 1;
+    s.ncols = c;
+    s.halo_bytes = kHaloX * kHaloY * kHaloZ * s.CN * 2;
+    // dO tile of 128 voxels x co, plus slack: the padded M rows of the A
+    // descriptor reach up to 15 x 128 bytes past a line
+    s.do_bytes = 128 * co * 2 + 2048;
+    s.stage = s.halo_bytes + s.do_bytes;
+    s.stage = (s.stage + 127) & ~127;
+    s.smem = 1024 + kWhStages * s.stage;
+    return s;
+}
+
+__host__ __device__ inline long long wgrad_halo_blocks(const ConvGeom& g) {
+    return (long long)((g.W + 7) / 8) * ((g.H + 15) / 16) * g.D * g.N;
+}
+
+int wgrad_halo_slices(const ConvGeom& g) {
+    const WgHaloShape s = wgh_shape(g.ci, g.co);
+    long long ns = 304 / (s.ngroups * s.nchunks);
+    if (ns < 1) ns = 1;
+    const long long nb = wgrad_halo_blocks(g);
+    return (int)(ns < nb ? ns : nb);
+}
+
+__global__ void __launch_bounds__(kTcThreads) k_conv3d_wgrad_halo(const __nv_bfloat16* __restrict__ in,
+                                                                  const __nv_bfloat16* __restrict__ dout,
+                                                                  float* __restrict__ partial, ConvGeom g,
+                                                                  int blocks_per_slice, int* err) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const WgHaloShape sh = wgh_shape(g.ci, g.co);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    uint64_t* empty = full + kWhStages;
+    uint64_t* done = empty + kWhStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+    unsigned char* stages = smem + 1024;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int CN = sh.CN, kg = CN / 8;
+    const int t0 = blockIdx.y * sh.TG;
+    const int ntap = 27 - t0 < sh.TG ? 27 - t0 : sh.TG;
+    const int c0 = blockIdx.z * CN;
+    const long long nblocks = wgrad_halo_blocks(g);
+    const long long b0 = (long long)blockIdx.x * blocks_per_slice;
+    const long long b1 = b0 + blocks_per_slice < nblocks ? b0 + blocks_per_slice : nblocks;
+    const int nb = b0 < b1 ? (int)(b1 - b0) : 0;
+    const int bxn = (g.W + 7) / 8, byn = (g.H + 15) / 16;
+    const uint32_t PC = 16u * kHaloX, PY = (uint32_t)kg * PC, PZ = (uint32_t)kHaloY * PY;
+    const uint32_t PYo = (uint32_t)(g.co / 8) * 128u;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWhStages; ++s) {
+            bar_init(&full[s], 128);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 4) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tmem_slot)),
+                     "r"(sh.ncols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp < 4) {
+        // ------------------------------------------------------ producers
+        bool ok = true;
+        int issued = 0;
+        for (int i = 0; i < nb; ++i) {
+            const int s = i % kWhStages;
+            if (i >= kWhStages && !bar_wait(&empty[s], ((i / kWhStages) - 1) & 1)) { ok = false; break; }
+            if (*(volatile int*)abort_flag) { ok = false; break; }
+            long long b = b0 + i;
+            const int bx = (int)(b % bxn);
+            b /= bxn;
+            const int by = (int)(b % byn);
+            b /= byn;
+            const int zb = (int)(b % g.D);
+            const long long nbt = b / g.D;
+            const int x0 = bx * 8, y0 = by * 16;
+            const uint32_t st = smem_addr(stages + s * sh.stage);
+            // halo of the input channels [c0, c0 + CN)
+            for (int e = tid; e < kHaloX * kHaloY * kHaloZ * kg; e += 128) {
+                const int grp = e % kg, v = e / kg;
+                const int xi = v % kHaloX, yj = (v / kHaloX) % kHaloY, zk = v / (kHaloX * kHaloY);
+                const int qx = x0 - 1 + xi;
+                int qy = y0 - 1 + yj, qz = zb - 1 + zk;
+                bool valid = qx >= 0 && qx < g.W;
+                if (g.periodic_yz) {
+                    qy = ((qy % g.H) + g.H) % g.H;
+                    qz = ((qz % g.D) + g.D) % g.D;
+                } else {
+                    valid = valid && qy >= 0 && qy < g.H && qz >= 0 && qz < g.D;
+                }
+                const long long sv =
+                    valid ? qx + (long long)g.W * (qy + (long long)g.H * (qz + (long long)g.D * nbt)) : 0;
+                cp_async16_ca(st + (uint32_t)zk * PZ + (uint32_t)yj * PY + (uint32_t)grp * PC + (uint32_t)xi * 16u,
+                              in + sv * g.in_stride + g.in_off + c0 + 8 * grp, valid);
+            }
+            // dO of the block's 128 voxels (zeros outside the box)
+            const uint32_t dst0 = st + (uint32_t)sh.halo_bytes;
+            for (int e = tid; e < 128 * (g.co / 8); e += 128) {
+                const int grp = e % (g.co / 8), r = e / (g.co / 8);
+                const int x = x0 + (r & 7), y = y0 + (r >> 3);
+                const bool valid = x < g.W && y < g.H;
+                const long long v = valid ? x + (long long)g.W * (y + (long long)g.H * (zb + (long long)g.D * nbt)) : 0;
+                cp_async16(dst0 + (uint32_t)(r >> 3) * PYo + (uint32_t)grp * 128u + (uint32_t)(r & 7) * 16u,
+                           dout + v * g.out_stride + g.out_off + 8 * grp, valid);
+            }
+            cp_async_commit();
+            ++issued;
+            // one block in flight behind this one (two stages)
+            cp_async_wait<1>();
+            fence_async_shared();
+            if (i >= 1) bar_arrive(&full[(i - 1) % kWhStages]);
+        }
+        cp_async_wait<0>();
+        fence_async_shared();
+        if (issued >= 1) bar_arrive(&full[(issued - 1) % kWhStages]);
+        if (!ok) {
+            atomicOr(err, 64);
+            *(volatile int*)abort_flag = 1;
+        }
+    } else if (lane == 0) {
+        // ------------------------------------------------------ MMA issuer
+        const uint32_t idesc = idesc_bf16(kTcM, CN) | (1u << 15) | (1u << 16);  // A, B MN-major
+        for (int i = 0; i < nb; ++i) {
+            const int s = i % kWhStages;
+            if (!bar_wait(&full[s], (i / kWhStages) & 1) || *(volatile int*)abort_flag) {
+                atomicOr(err, 64);
+                *(volatile int*)abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t st = smem_addr(stages + s * sh.stage);
+            const uint32_t a_base = st + (uint32_t)sh.halo_bytes;
+            for (int kk = 0; kk < 8; ++kk) {  // two lines of 8 voxels per K = 16
+                const uint64_t ad = sdesc(a_base + (uint32_t)(2 * kk) * PYo, PYo, 128u);
+                for (int j = 0; j < ntap; ++j) {
+                    const int t = t0 + j;
+                    const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;
+                    const uint32_t b = st + (uint32_t)dz * PZ + (uint32_t)(2 * kk + dy) * PY + (uint32_t)dx * 16u;
+                    mma_bf16_ss(tmem + (uint32_t)(j * CN), ad, sdesc(b, PY, PC), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+                }
+            }
+            mma_commit(&empty[s]);
+        }
+        mma_commit(done);
+    }
+
+    // ---------------------------------------------------------- epilogue
+    if (warp < 4) {
+        const bool ok = bar_wait(done, 0);
+        tc_fence_after();
+        if (!ok) atomicOr(err, 64);
+        const int m = tid;  // output channel of this lane
+        const bool store = ok && !*(volatile int*)abort_flag && m < g.co;
+        if (warp * 32 < g.co) {
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+            for (int j = 0; j < ntap; ++j) {
+                float* dst = partial + (((long long)blockIdx.x * 27 + t0 + j) * g.co + m) * g.ci + c0;
+                for (int c = 0; c < CN; c += 16) {
+                    uint32_t acc[16];
+                    tmem_ld16(lane_base + (uint32_t)(j * CN + c), acc);
+                    if (store) {
+                        float4* d4 = reinterpret_cast<float4*>(dst + c);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+                            d4[q] = nb > 0 ? make_float4(__uint_as_float(acc[4 * q]), __uint_as_float(acc[4 * q + 1]),
+                                                         __uint_as_float(acc[4 * q + 2]), __uint_as_float(acc[4 * q + 3]))
+                                           : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 4) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.ncols) : "memory");
+    }
+}
+
+bool conv3d_wgrad_halo_supported(const ConvGeom& g) {
+    const WgHaloShape s = wgh_shape(g.ci, g.co);
+    return g.ci % 16 == 0 && g.co % 16 == 0 && g.co <= 128 && g.in_stride % 8 == 0 && g.in_off % 8 == 0 &&
+           g.out_stride % 8 == 0 && g.out_off % 8 == 0 && s.smem <= 227 * 1024 && (long long)g.D * g.N <= (1LL << 30);
+}
+
+long long wgrad_halo_workspace_floats(const ConvGeom& g) {
+    return (long long)wgrad_halo_slices(g) * 27LL * g.co * g.ci;
+}
+
+cudaError_t launch_conv3d_wgrad_halo(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial,
+                                     const ConvGeom& g, int* err, int* nslices, cudaStream_t s) {
+    const WgHaloShape sh = wgh_shape(g.ci, g.co);
+    cudaError_t e = cudaFuncSetAttribute(k_conv3d_wgrad_halo, cudaFuncAttributeMaxDynamicSharedMemorySize, sh.smem);
+    if (e != cudaSuccess) return e;
+    const int ns = wgrad_halo_slices(g);
+    const long long nb = wgrad_halo_blocks(g);
+    const int per = (int)((nb + ns - 1) / ns);
+    *nslices = ns;
+    k_conv3d_wgrad_halo<<<dim3(ns, sh.ngroups, sh.nchunks), kTcThreads, sh.smem, s>>>(in, dout, partial, g, per, err);
+    return cudaGetLastError();
+}
+
 bool conv3d_tc_supported(const ConvGeom& g) {
     return g.ci % 16 == 0 && g.co % 16 == 0 && g.co >= 16 && g.co <= 256 && g.in_stride % 8 == 0 &&
            g.in_off % 8 == 0 && g.out_stride % 8 == 0 && g.out_off % 8 == 0 && tc_shape(g.ci, g.co).smem <= 227 * 1024;

@@ -29,4 +29,11 @@ long long wgrad_tc_workspace_floats(const ConvGeom& g);
 cudaError_t launch_conv3d_wgrad_tc(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial,
                                    const ConvGeom& g, int lbo_mn, int* err, int* nslices, cudaStream_t s);
 
+// weight gradient from halo tiles (preferred where supported); same
+// partial layout and slice sum as the kernel above
+bool conv3d_wgrad_halo_supported(const ConvGeom& g);
+long long wgrad_halo_workspace_floats(const ConvGeom& g);
+cudaError_t launch_conv3d_wgrad_halo(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial,
+                                     const ConvGeom& g, int* err, int* nslices, cudaStream_t s);
+
 }  // namespace cl

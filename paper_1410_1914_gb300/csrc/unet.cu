@@ -223,6 +223,16 @@ constexpr int kWgradLboMN = 0;
 cudaError_t launch_conv3d_wgrad(const __nv_bfloat16* in, const __nv_bfloat16* dout, float* partial, float* dw,
                                 const ConvGeom& g, cudaStream_t s) {
     if (g.ci % 16 || g.co % 16) return cudaErrorInvalidValue;
+    if (conv3d_wgrad_halo_supported(g)) {
+        int* err = nn_err_ptr();
+        if (!err) return cudaErrorInvalidValue;
+        int ns = 0;
+        cudaError_t e = launch_conv3d_wgrad_halo(in, dout, partial, g, err, &ns, s);
+        if (e != cudaSuccess) return e;
+        const long long n = 27LL * g.co * g.ci;
+        k_sum_slices<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(partial, ns, n, dw);
+        return cudaGetLastError();
+    }
     if (conv3d_wgrad_tc_supported(g)) {
         int* err = nn_err_ptr();
         if (!err) return cudaErrorInvalidValue;
@@ -621,8 +631,10 @@ long long cl_nn_wgrad_workspace(int N, int D, int H, int W, int ci, int co) {
     const long long M = (long long)N * D * H * W;
     const long long slice = wgrad_slice(g);
     const long long legacy = ((M + slice - 1) / slice) * 27LL * co * ci;
-    const long long tc = wgrad_tc_workspace_floats(g);
-    return (legacy > tc ? legacy : tc) * (long long)sizeof(float);
+    const long long tc = wgrad_tc_workspace_floats(g), halo = wgrad_halo_workspace_floats(g);
+    long long m = legacy > tc ? legacy : tc;
+    m = m > halo ? m : halo;
+    return m * (long long)sizeof(float);
 }
 
 cl_status cl_nn_conv3d_wgrad(const void* in, const void* dout, float* workspace, float* dw, int N, int D, int H, int W,
