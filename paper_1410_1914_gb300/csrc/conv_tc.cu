@@ -1,30 +1,34 @@
-// 3x3x3 convolution of the warm-start network on the 5th-generation tensor
-// cores (tcgen05.mma, BF16 operands, FP32 accumulator in tensor memory).
+// 3x3x3 convolutions of the warm-start network on the 5th-generation tensor
+// cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in tensor
+// memory).  Implicit GEMMs: out[v][n] = sum over taps t and input channels c
+// of in[shift(v, t)][c] * w[t][n][c]; the weight gradient is the GEMM over
+// voxels.  Three kernels:
 //
-// Implicit GEMM: out[v][n] = sum over taps t and input channels c of
-// in[shift(v, t)][c] * w[t][n][c].  One CTA computes 128 consecutive output
-// voxels (M = 128) for all output channels (N = co, 16..256); the reduction
-// runs over 27 taps x ci in k-steps of CK channels of one tap.
+//   k_conv3d_halo        forward / data gradient (the main path): one CTA per
+//                        8 x 16 block of output voxels; the 10 x 18 x 3 input
+//                        halo is staged once per channel chunk and every tap
+//                        is a shifted descriptor into it; weights stream.
+//   k_conv3d_wgrad_halo  weight gradient (the main path): per voxel block the
+//                        halo and the output-gradient tile are staged once,
+//                        every tap a shifted MN-major descriptor, accumulation
+//                        over a slice of blocks in tensor memory.
+//   k_conv3d_tc,         the same operations with one gather per tap and
+//   k_conv3d_wgrad_tc    voxel (128 rows of consecutive voxels); used where
+//                        a halo tile does not fit.
 //
-// Roles (160 threads):
-//   warps 0-3  producers: thread r gathers the CK input channels of voxel
-//              v0 + r shifted by the tap (x zero padded, y and z periodic or
-//              zero padded) and the tap's weight rows into a shared-memory
-//              stage with cp.async (zero fill outside the box), then arrives
-//              on the stage's `full` barrier once its copies have landed and
-//              have been made visible to the tensor core (async proxy);
-//              afterwards they run the epilogue: tcgen05.ld of their 32 TMEM
-//              lanes (warp w owns lanes 32w..32w+31), bias, ReLU, BF16 store;
-//   warp 4     allocates and frees the tensor memory; its lane 0 issues the
-//              MMAs of each stage and commits them to the stage's `empty`
-//              barrier (the stage can be refilled when they completed) and,
-//              after the last stage, to `done`.
+// Roles (160 threads): warps 0-3 stage operands with cp.async (zero fill
+// outside the box; y and z wrap by index), make them visible to the tensor
+// core (fence.proxy.async) and arrive on the stage's `full` barrier, then
+// run the epilogue (tcgen05.ld of their 32 TMEM lanes: warp w owns lanes
+// 32w..32w+31); warp 4 allocates and frees the tensor memory and its lane 0
+// issues the MMAs of each stage and commits them to the stage's `empty`
+// barrier and, after the last stage, to `done`.
 //
-// Shared-memory operand layout: K-major, no swizzle.  A tile of R rows x CK
-// columns is stored as 8x8 core matrices (8 rows of 16 bytes, contiguous):
-// element (r, k) at (r / 8) * SBO + (k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2
-// with SBO = CK / 8 * 128, so the leading-dimension offset (next core matrix
-// along K) is 128 bytes and one K = 16 instruction covers 256 bytes.
+// Shared-memory operands use the no-swizzle core-matrix layouts: 8 rows of
+// 16 bytes, contiguous.  K-major (forward): a row is 8 input channels of one
+// voxel; LBO steps to the next 8 channels, SBO to the next 8 rows.  MN-major
+// (weight gradient): a row is 8 channels of one voxel read along K = voxels;
+// LBO steps to the next 8 voxels, SBO to the next 8 channels.
 //
 // Every wait is bounded; on expiry the CTA records an error bit, stops
 // issuing work, waits (bounded) for the MMAs it issued, frees its tensor
