@@ -25,21 +25,27 @@ def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype).cuda().contiguous()
 
 
-@pytest.mark.parametrize("ci,co", [(16, 16), (16, 32), (48, 16), (96, 32), (192, 64), (64, 128), (64, 192), (16, 8)])
-def test_conv_forward(cuda_lib, ci, co):
+@pytest.mark.parametrize("ci,co,shape,periodic", [
+    (16, 16, (2, 4, 6, 10), 1), (16, 32, (2, 4, 6, 10), 1), (48, 16, (2, 4, 6, 10), 1),
+    (96, 32, (2, 4, 6, 10), 1), (192, 64, (2, 4, 6, 10), 1), (64, 128, (2, 4, 6, 10), 1),
+    (64, 192, (2, 4, 6, 10), 1), (16, 8, (2, 4, 6, 10), 1),
+    # several 8 x 16 output blocks with ragged edges, and zero padding in y, z
+    (32, 64, (1, 5, 37, 19), 1), (32, 64, (1, 5, 37, 19), 0), (16, 16, (3, 3, 17, 9), 0)])
+def test_conv_forward(cuda_lib, ci, co, shape, periodic):
     import torch
 
     from paper_1410_1914_gb300 import warmstart as W
-    rng = np.random.default_rng(ci * 1000 + co)
-    N, D, H, Wd = 2, 4, 6, 10
+    rng = np.random.default_rng(ci * 1000 + co + periodic)
+    N, D, H, Wd = shape
     x = _bf16(rng.standard_normal((N, D, H, Wd, ci)))
     w = _bf16(rng.standard_normal((27, co, ci)) / np.sqrt(27 * ci))
     b = rng.standard_normal(co)
-    ref = OU.conv3d(x, w, b)
+    ref = OU.conv3d(x, w, b, periodic_yz=bool(periodic))
     out = torch.empty(N, D, H, Wd, co, dtype=torch.bfloat16, device="cuda")
     # keep the device copies alive until the kernel has run
     xd, wd, bd = _dev(x, torch.bfloat16), _dev(w, torch.bfloat16), _dev(b, torch.float32)
-    W._call("cl_nn_conv3d", W._p(xd), W._p(wd), W._p(bd), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, 1, None)
+    W._call("cl_nn_conv3d", W._p(xd), W._p(wd), W._p(bd), W._p(out), N, D, H, Wd, ci, co, ci, 0, co, 0, 0, periodic,
+            None)
     W._call("cl_nn_check", None)
     got = out.float().cpu().numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-2, atol=1e-2 * np.abs(ref).max())
@@ -90,9 +96,11 @@ def test_conv_gradients_against_differences(cuda_lib, ci, co):
         assert gx[idx] == pytest.approx(fd, rel=2e-2, abs=2e-2 * (1 + abs(fd)))
 
 
-@pytest.mark.parametrize("ci,co,shape", [(16, 16, (1, 3, 5, 7)), (48, 16, (2, 4, 4, 6)), (96, 32, (1, 4, 6, 6)),
-                                          (192, 64, (1, 3, 4, 8)), (64, 128, (1, 5, 3, 9)), (16, 128, (2, 2, 2, 2))])
-def test_wgrad_full_tensor(cuda_lib, ci, co, shape):
+@pytest.mark.parametrize("ci,co,shape,periodic", [
+    (16, 16, (1, 3, 5, 7), 1), (48, 16, (2, 4, 4, 6), 1), (96, 32, (1, 4, 6, 6), 1), (192, 64, (1, 3, 4, 8), 1),
+    (64, 128, (1, 5, 3, 9), 1), (16, 128, (2, 2, 2, 2), 1), (16, 32, (1, 4, 21, 11), 1), (16, 16, (2, 3, 19, 9), 0),
+    (32, 32, (1, 3, 19, 9), 0)])
+def test_wgrad_full_tensor(cuda_lib, ci, co, shape, periodic):
     """Every entry of dW[t][o][i] = sum_v gy[v][o] x_t[v][i], where x_t (the
     input shifted by tap t, with the padding rules) comes from the oracle's
     convolution with an identity kernel at that tap.  Products of BF16
@@ -108,12 +116,13 @@ def test_wgrad_full_tensor(cuda_lib, ci, co, shape):
     for tap in range(27):
         wid = np.zeros((27, ci, ci))
         wid[tap] = np.eye(ci)
-        xt = OU.conv3d(x, wid, np.zeros(ci)).reshape(-1, ci)
+        xt = OU.conv3d(x, wid, np.zeros(ci), periodic_yz=bool(periodic)).reshape(-1, ci)
         exp[tap] = gy.reshape(-1, co).T @ xt
     ws = torch.empty(W._lib().cl_nn_wgrad_workspace(N, D, H, Wd, ci, co) // 4 + 1, dtype=torch.float32, device="cuda")
     dw = torch.empty(27, co, ci, dtype=torch.float32, device="cuda")
     xd, gd = _dev(x, torch.bfloat16), _dev(gy, torch.bfloat16)
-    W._call("cl_nn_conv3d_wgrad", W._p(xd), W._p(gd), W._p(ws), W._p(dw), N, D, H, Wd, ci, co, ci, 0, co, 0, 1, None)
+    W._call("cl_nn_conv3d_wgrad", W._p(xd), W._p(gd), W._p(ws), W._p(dw), N, D, H, Wd, ci, co, ci, 0, co, 0, periodic,
+            None)
     W._call("cl_nn_check", None)
     np.testing.assert_allclose(dw.cpu().numpy(), exp, rtol=0, atol=1e-5 * np.abs(exp).max() + 1e-6)
 
