@@ -176,7 +176,8 @@ template <class S, bool REDUCE>
 __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, float om, float hx, float lxs,
                                             const float (&dds)[6], const float (&nh)[6], const float (&nls)[6],
                                             const float (&nds)[6], int x, float& hnew, float& lnew_s,
-                                            float (&dns)[6], double (&rv)[RED_N], float csnap, float& csnap_out) {
+                                            float (&dns)[6], double (&rv)[RED_N], float (&rs)[4], float csnap,
+                                            float& csnap_out) {
     constexpr bool HALF = sizeof(typename S::T) == 2;
     const float inv_lo = HALF ? a.inv_lo : 1.0f, s_lo = HALF ? a.s_lo : 1.0f;
     const float s_d = HALF ? a.s_d : 1.0f, inv_d = HALF ? a.inv_d : 1.0f;
@@ -209,25 +210,32 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
 #pragma unroll
     for (int i = 0; i < 6; ++i) dns[i] = om1 * (av[i] - w * dCs);
     if (REDUCE) {
-        const double Cn = (double)hnew + (double)lnew;
+        // Fluxes and reaction in FP64 (boundary and catalytic cells only:
+        // the stopping rule resolves their changes down to 1e-9); the
+        // per-cell diagnostics in per-thread FP32 partials that the block
+        // sums in FP64 (GB300's FP64 rate is a small fraction of FP32)
         const double id = inv_d;
         if (x == 0 && a.bc_in == CL_BC_DIRICHLET)
-            rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - Cn) - 2.0 * (double)dns[1] * id;
+            rv[RED_JIN] += 2.0 * (double)w * ((double)a.c_in - ((double)hnew + (double)lnew)) -
+                           2.0 * (double)dns[1] * id;
         if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET)
-            rv[RED_JOUT] += 2.0 * (double)w * (Cn - (double)a.c_out) + 2.0 * (double)dns[0] * id;
+            rv[RED_JOUT] += 2.0 * (double)w * (((double)hnew + (double)lnew) - (double)a.c_out) +
+                            2.0 * (double)dns[0] * id;
         const unsigned rb = (m >> kReactShift) & 0x3fu;
         if (rb) {
+            const double Cn = (double)hnew + (double)lnew;
             double r = 0.0;
 #pragma unroll
             for (int d = 0; d < 6; ++d)
                 if (rb & (1u << d)) r += (double)w * Cn + (double)dns[d] * id;
             rv[RED_R] += (1.0 - (double)rf) * r;
         }
-        rv[RED_SUMC] += Cn;
-        rv[RED_DC] += fabs(Cn - (double)csnap);
-        rv[RED_ABSC] += fabs(Cn);
-        rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
-        csnap_out = (float)Cn;
+        const float Cf = hnew + lnew;  // the f32 rounding of the double-float C
+        rs[0] += Cf;
+        rs[1] += fabsf(Cf - csnap);
+        rs[2] += fabsf(Cf);
+        if (!isfinite(hnew)) rs[3] += 1.0f;
+        csnap_out = Cf;
     }
 }
 
@@ -337,6 +345,7 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
         return ok;
     }
     // ---------------------------------------------------------- consumers
+    float rs[4] = {0.f, 0.f, 0.f, 0.f};  // FP32 partials of sum C, sum |dC|, sum |C|, non-finite
     const int xa = x0 + 2 * tx;  // this lane's cells: xa, xa + 1
     const int y = y0 + ty;
     const bool row_ok = y < ny;
@@ -437,15 +446,18 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
             const float ndb[6] = {dp[0].x, dxr, dym.y, dyp.y, pd5.y, dzp.y};
             if (REDUCE) {
                 // the reductions must see active cells only
-                if (act_a) cell_update<S, true>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, cs.x, cso.x);
+                if (act_a)
+                    cell_update<S, true>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, rs, cs.x, cso.x);
                 if (act_b)
-                    cell_update<S, true>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+                    cell_update<S, true>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, rs, cs.y,
+                                         cso.y);
             } else {
                 // both cells of the pair without a branch; an inactive cell's
                 // result (finite: its neighbours and omega slots hold zeros or
                 // state values) is replaced by the zeros it keeps
-                cell_update<S, false>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, cs.x, cso.x);
-                cell_update<S, false>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, cs.y, cso.y);
+                cell_update<S, false>(a, ma, om.x, hx.x, lx.x, dda, nha, nla, nda, xa, hA, lA, dA, rv, rs, cs.x, cso.x);
+                cell_update<S, false>(a, mb, om.y, hx.y, lx.y, ddb, nhb, nlb, ndb, xa + 1, hB, lB, dB, rv, rs, cs.y,
+                                      cso.y);
                 if (!act_a) {
                     hA = 0.f; lA = 0.f;
 #pragma unroll
@@ -490,6 +502,12 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
         release(k);
     }
     if (ok) release(nplanes - 1);  // plane ze, read only as a z+1 neighbour
+    if (REDUCE) {
+        rv[RED_SUMC] += (double)rs[0];
+        rv[RED_DC] += (double)rs[1];
+        rv[RED_ABSC] += (double)rs[2];
+        rv[RED_NONFINITE] += (double)rs[3];
+    }
     return ok;
 }
 
@@ -520,9 +538,10 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty) {
 // slot is live only while its plane is the current or the next one.
 // FP16 plain steps: 72 registers, which still fits three resident blocks per
 // SM (3 x 288 x 72 <= 65536) without the recomputation a tighter bound
-// forces; the other variants take what they need.
+// forces; FP32 plain steps need fewer than 112; the reducing steps (one per
+// check) are capped at 112 so that two blocks fit per SM.
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) == 2 && !REDUCE) ? 72 : 168)
+__global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) == 2 && !REDUCE) ? 72 : 112)
     k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
     // Addressed directly (no integer round trip) so that every slot access
     // compiles to a shared-memory load.
