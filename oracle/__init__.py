@@ -1,4 +1,5 @@
-"""FP64 CPU oracle for the D3Q7 reactive-diffusion LBM of arXiv:1410.1914.
+"""FP64 CPU oracle for the reactive-diffusion LBM of arXiv:1410.1914 (D3Q7 and
+the paper's D3Q19 lattice).
 
 TEST INFRASTRUCTURE ONLY.  Imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``; never by the library.  It shares no
@@ -15,7 +16,7 @@ What each function follows:
   chord_counts         Sec. 2.1.3, 13-direction pore length
   active_mask          Sec. 2.1.3 connectivity, as a 6-connected flood from
                        the inlet plane
-  OracleLBM            Eq. 21, 23, 24 on D3Q7; boundaries of Sec. 3.5;
+  OracleLBM            Eq. 21, 23, 24 on D3Q7 or D3Q19 (Eq. 22); boundaries of Sec. 3.5;
                        Eq. 19 readout; Eq. 17b/18a kinetics as a surface sink
 
 Arrays are numpy with shape (nz, ny, nx), x fastest.
@@ -55,7 +56,7 @@ class _Params(ctypes.Structure):
         ("D_ionomer", ctypes.c_double), ("k_ms", ctypes.c_double),
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
-        ("carrier", ctypes.c_int),
+        ("carrier", ctypes.c_int), ("lattice", ctypes.c_int),
     ]
 
 
@@ -100,6 +101,7 @@ def lib():
                 "orc_lbm_get_D": (None, [_P, _P]),
                 "orc_lbm_get_active": (None, [_P, _P]),
                 "orc_lbm_get_react": (None, [_P, _P]),
+                "orc_lbm_q": (ctypes.c_int, [_P]),
                 "orc_num_threads": (ctypes.c_int, []),
             }
             for name, (res, args) in sig.items():
@@ -177,16 +179,20 @@ def active_mask(phase: np.ndarray, ionomer_transport: bool = False, protons: boo
 
 # ---------------------------------------------------------------- solver
 DEFAULTS = dict(dx_m=2e-9, T_K=353.0, p_atm=1.0, M_kgmol=0.032, D_bulk=0.0, D_ionomer=0.0,
-                k_ms=0.0, knudsen=0, bc_in=0, bc_out=0, c_in=1.0, c_out=0.0, tau_ref=1.0, carrier=0)
+                k_ms=0.0, knudsen=0, bc_in=0, bc_out=0, c_in=1.0, c_out=0.0, tau_ref=1.0, carrier=0,
+                lattice=0)
 
 
 class OracleLBM:
-    """Double-precision D3Q7 BGK solver (Eq. 21-24 with the D3Q7 lattice).
+    """Double-precision BGK solver (Eq. 21-24) on D3Q7 (``lattice=0``) or the
+    paper's D3Q19 (``lattice=1``, Eq. 22-23).
 
     ``phase`` (nz, ny, nx) uint8 codes 0 pore / 1 solid / 2 ionomer /
-    3 micropore.  ``react`` (same shape, uint8): bit i-1 marks the face
-    toward x + c_i as reactive (i = 1..6 = +x, -x, +y, -y, +z, -z).
+    3 micropore.  ``react`` (same shape, uint8): bit f marks the face toward
+    x + e_f as catalytic (f = 0..5 = +x, -x, +y, -y, +z, -z).
     ``D`` (same shape, float64): per-cell diffusivity override [m^2/s].
+    ``react()`` returns the derived per-link bits (uint32, bit i-1 = link
+    toward x + c_i reacts).
     """
 
     def __init__(self, phase, react=None, D=None, **params):
@@ -198,7 +204,9 @@ class OracleLBM:
         self.params = p
         cp = _Params(nx, ny, nz, p["dx_m"], p["T_K"], p["p_atm"], p["M_kgmol"], p["D_bulk"],
                      p["D_ionomer"], p["k_ms"], int(p["knudsen"]), int(p["bc_in"]), int(p["bc_out"]),
-                     p["c_in"], p["c_out"], p["tau_ref"], int(p["carrier"]))
+                     p["c_in"], p["c_out"], p["tau_ref"], int(p["carrier"]), int(p["lattice"]))
+        if int(p["lattice"]) not in (0, 1):
+            raise ValueError("lattice must be 0 (D3Q7) or 1 (D3Q19)")
         if int(p["carrier"]) == 1 and not (p["D_ionomer"] > 0 and p["k_ms"] == 0):
             raise ValueError("protons (carrier 1) need D_ionomer > 0 (the conductivity) and k_ms = 0")
         self._react = None if react is None else np.ascontiguousarray(react, dtype=np.uint8)
@@ -209,6 +217,7 @@ class OracleLBM:
         if not h:
             raise ValueError("no transport cell is connected to the inlet plane")
         self._h = h
+        self.q = lib().orc_lbm_q(h)
         self.init_linear()
 
     def __del__(self):
@@ -238,7 +247,7 @@ class OracleLBM:
         return out
 
     def populations(self):
-        out = np.zeros((7,) + self.shape)
+        out = np.zeros((self.q,) + self.shape)
         lib().orc_lbm_populations(self._h, _ptr(out))
         return out
 
@@ -298,6 +307,6 @@ class OracleLBM:
         return out
 
     def react(self):
-        out = np.zeros(self.shape, dtype=np.uint8)
+        out = np.zeros(self.shape, dtype=np.uint32)
         lib().orc_lbm_get_react(self._h, _ptr(out))
         return out

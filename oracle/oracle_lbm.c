@@ -18,8 +18,10 @@
  *   Eq. 7           bulk O2-N2 diffusivity (orc_bulk_diffusivity)
  *   Eq. 8           Knudsen diffusivity (orc_knudsen_diffusivity)
  *   Eq. 9           Bosanquet combination (orc_bosanquet)
- *   Eq. 21, 23, 24  BGK evolution, equilibrium, C = sum g, D <-> tau; here on
- *                   the D3Q7 lattice (w0 = 1/4, w1..6 = 1/8, cs^2 = 1/4)
+ *   Eq. 21, 23, 24  BGK evolution, equilibrium, C = sum g, D <-> tau, on
+ *                   either lattice: D3Q7 (w0 = 1/4, w1..6 = 1/8, cs^2 = 1/4)
+ *                   or the paper's D3Q19 (Eq. 22, 23: a0 = 1/3, 1/18 on the
+ *                   six axes, 1/36 on the twelve face diagonals, cs^2 = 1/3)
  *   Sec. 3.5.1      Dirichlet inlet/outlet in x, periodic y and z
  *   Sec. 3.5.2      zero-flux outlet (Eq. 20a), Dirichlet inlet (Eq. 20b)
  *   Eq. 17b + 18a   first-order kinetics with uniform ionomer potential,
@@ -30,7 +32,10 @@
  *                   source; the Eq. 19 readout then is the effective
  *                   conductivity, normalised by the ionomer's own
  *
- * Lattice directions: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z.
+ * Lattice directions: 0 rest, 1 +x, 2 -x, 3 +y, 4 -y, 5 +z, 6 -z; D3Q19 adds
+ * 7 (+1,+1,0), 8 (-1,-1,0), 9 (+1,-1,0), 10 (-1,+1,0), 11 (+1,0,+1),
+ * 12 (-1,0,-1), 13 (+1,0,-1), 14 (-1,0,+1), 15 (0,+1,+1), 16 (0,-1,-1),
+ * 17 (0,+1,-1), 18 (0,-1,+1).
  * Phase codes: 0 pore, 1 solid (carbon / Pt / catalyst), 2 ionomer,
  *              3 micropore (transports like pore, never reactive).
  * Cell index: x + nx*(y + ny*z)  (x fastest).
@@ -43,15 +48,42 @@
 #include <omp.h>
 #endif
 
-#define Q 7
+#define QMAX 19
 
-static const int CX[Q] = {0, 1, -1, 0, 0, 0, 0};
-static const int CY[Q] = {0, 0, 0, 1, -1, 0, 0};
-static const int CZ[Q] = {0, 0, 0, 0, 0, 1, -1};
-static const int OPP[Q] = {0, 2, 1, 4, 3, 6, 5};
-/* D3Q7 weights; sum = 1, sum w c_a^2 = 1/4 = cs^2 */
-static const double W[Q] = {0.25, 0.125, 0.125, 0.125, 0.125, 0.125, 0.125};
-static const double CS2 = 0.25;
+typedef struct {
+    int q;
+    int cx[QMAX], cy[QMAX], cz[QMAX], opp[QMAX];
+    double w[QMAX];
+    double cs2; /* sum_i w_i c_ia^2 */
+} orc_lattice;
+
+/* D3Q7: sum w = 1, sum w c_x^2 = 2/8 = 1/4 */
+static const orc_lattice LAT7 = {
+    7,
+    {0, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1},
+    {0, 2, 1, 4, 3, 6, 5},
+    {0.25, 0.125, 0.125, 0.125, 0.125, 0.125, 0.125},
+    0.25};
+
+/* D3Q19 (Eq. 22, 23): sum a = 1/3 + 6/18 + 12/36 = 1,
+   sum a c_x^2 = 2/18 + 8/36 = 1/3 */
+static const orc_lattice LAT19 = {
+    19,
+    {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1},
+    {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17},
+    {1.0 / 3, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18, 1.0 / 18,
+     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36,
+     1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36},
+    1.0 / 3};
+
+/* the six faces of a voxel, in the order of directions 1..6 above */
+static const int FX[6] = {1, -1, 0, 0, 0, 0};
+static const int FY[6] = {0, 0, 1, -1, 0, 0};
+static const int FZ[6] = {0, 0, 0, 0, 1, -1};
 
 typedef struct {
     int nx, ny, nz;
@@ -68,6 +100,7 @@ typedef struct {
     double tau_ref;     /* relaxation time of the most diffusive active cell */
     int carrier;        /* 0: O2 in the pore space (Eq. 6); 1: protons in the ionomer
                            (Eq. 16 with S_e = 0 and uniform conductivity D_ionomer) */
+    int lattice;        /* 0: D3Q7; 1: D3Q19 (Eq. 22) */
 } orc_params;
 
 static long idx3(int x, int y, int z, int nx, int ny) { return x + (long)nx * (y + (long)ny * z); }
@@ -213,10 +246,10 @@ long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int mode, uin
     while (head < tail) {
         long c = queue[head++];
         int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
-        for (int i = 1; i < Q; ++i) {
-            int qx = x + CX[i];
+        for (int d = 0; d < 6; ++d) {
+            int qx = x + FX[d];
             if (qx < 0 || qx >= nx) continue;
-            long n = idx3(qx, wrap(y + CY[i], ny), wrap(z + CZ[i], nz), nx, ny);
+            long n = idx3(qx, wrap(y + FY[d], ny), wrap(z + FZ[d], nz), nx, ny);
             if (!active[n] && is_transport(phase[n], mode)) {
                 active[n] = 1;
                 queue[tail++] = n;
@@ -251,31 +284,54 @@ double orc_cell_diffusivity(const orc_params* p, const uint8_t* phase, const uin
 
 /* ----------------------------------------------------------------------
  * LBM state.  g holds the pre-collision populations g_i(x, t) of Eq. 21,
- * array of Q planes of N doubles.  Inactive cells hold 0 and are never
+ * array of q planes of N doubles.  Inactive cells hold 0 and are never
  * touched.
  * ---------------------------------------------------------------------- */
 typedef struct {
     orc_params p;
+    const orc_lattice* L;
     long N;
     uint8_t* phase;
     uint8_t* active;
-    uint8_t* react;    /* 6 bits per cell: bit (i-1) = face toward x + c_i reactive */
+    uint32_t* react;   /* bit (i-1) = link toward x + c_i ends on a catalytic face */
     double* D;         /* m^2/s, 0 for inactive */
-    double* tau;       /* per-cell relaxation time, Eq. 24 with cs^2 = 1/4 */
+    double* tau;       /* per-cell relaxation time, Eq. 24 with the lattice's cs^2 */
     double* g;         /* current pre-collision populations */
     double* gn;        /* scratch for the next step */
     double D_b, D_max, dt, k_lu;
     long step;
 } orc_lbm;
 
+/*
+ * End cell of the link of cell c toward x + c_i.  *outside = -1 / +1 when the
+ * link leaves the box through x = 0 / x = L.  Beyond those faces the box
+ * continues as the mirror image of its first / last plane, so the end cell
+ * of a leaving link is then (x, y + c_iy, z + c_iz): the cell itself for the
+ * axis link, an in-plane neighbour for a D3Q19 diagonal.  A leaving link
+ * whose end cell is active is a boundary link (Dirichlet or zero flux);
+ * one whose end cell is not is a wall like any other, so that a wall that
+ * meets the inlet or outlet face stays a wall up to the face.
+ */
 static long orc_neighbor(const orc_lbm* s, long c, int i, int* outside)
 {
     int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
     int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
-    int qx = x + CX[i];
+    const orc_lattice* L = s->L;
+    int qx = x + L->cx[i];
     *outside = (qx < 0) ? -1 : (qx >= nx ? 1 : 0);
-    if (*outside) return -1;
-    return idx3(qx, wrap(y + CY[i], ny), wrap(z + CZ[i], nz), nx, ny);
+    if (*outside) qx = x;
+    return idx3(qx, wrap(y + L->cy[i], ny), wrap(z + L->cz[i], nz), nx, ny);
+}
+
+/* Face f (0..5, directions 1..6) of cell c is catalytic: marked in the input
+ * and its neighbour across the face is solid (code 1). */
+static int face_catalytic(const orc_lbm* s, const uint8_t* react_in, long c, int f)
+{
+    int nx = s->p.nx, ny = s->p.ny, nz = s->p.nz;
+    int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+    int qx = x + FX[f];
+    if (qx < 0 || qx >= nx || !(react_in[c] >> f & 1)) return 0;
+    return s->phase[idx3(qx, wrap(y + FY[f], ny), wrap(z + FZ[f], nz), nx, ny)] == 1;
 }
 
 /*
@@ -294,11 +350,12 @@ orc_lbm* orc_lbm_new(const orc_params* p, const uint8_t* phase, const uint8_t* r
     s->phase = (uint8_t*)malloc((size_t)N);
     memcpy(s->phase, phase, (size_t)N);
     s->active = (uint8_t*)malloc((size_t)N);
-    s->react = (uint8_t*)calloc((size_t)N, 1);
+    s->L = p->lattice == 1 ? &LAT19 : &LAT7;
+    s->react = (uint32_t*)calloc((size_t)N, sizeof(uint32_t));
     s->D = (double*)calloc((size_t)N, sizeof(double));
     s->tau = (double*)calloc((size_t)N, sizeof(double));
-    s->g = (double*)calloc((size_t)N * Q, sizeof(double));
-    s->gn = (double*)calloc((size_t)N * Q, sizeof(double));
+    s->g = (double*)calloc((size_t)N * s->L->q, sizeof(double));
+    s->gn = (double*)calloc((size_t)N * s->L->q, sizeof(double));
 
     long n_active = orc_active_mask(phase, p->nx, p->ny, p->nz, p->carrier == 1 ? 2 : (p->D_ionomer > 0),
                                     s->active);
@@ -319,24 +376,37 @@ orc_lbm* orc_lbm_new(const orc_params* p, const uint8_t* phase, const uint8_t* r
         free(counts);
         free(d_p);
     }
-    /* reactive faces: input bit set, cell active, neighbour is solid catalyst */
+    /* Reactive links.  A link of active cell c toward x + c_i reacts when its
+     * end cell is solid (code 1) and it leaves c through a catalytic face:
+     * one of the faces that c_i crosses (the axis faces of its non-zero
+     * components) is marked in the input and borders solid.  On D3Q7 each
+     * link crosses exactly its own face.  On D3Q19 a flat catalytic face is
+     * crossed by its axis link and four diagonals; a diagonal that only
+     * touches a solid edge between two open faces stays a plain wall. */
     if (react) {
+        const orc_lattice* L = s->L;
         for (long c = 0; c < N; ++c) {
             if (!s->active[c]) continue;
-            for (int i = 1; i < Q; ++i) {
+            for (int i = 1; i < L->q; ++i) {
                 int out;
                 long n = orc_neighbor(s, c, i, &out);
-                if (!out && (react[c] >> (i - 1) & 1) && phase[n] == 1) s->react[c] |= (uint8_t)(1u << (i - 1));
+                if (phase[n] != 1) continue;
+                int hit = 0;
+                if (L->cx[i]) hit |= face_catalytic(s, react, c, L->cx[i] > 0 ? 0 : 1);
+                if (L->cy[i]) hit |= face_catalytic(s, react, c, L->cy[i] > 0 ? 2 : 3);
+                if (L->cz[i]) hit |= face_catalytic(s, react, c, L->cz[i] > 0 ? 4 : 5);
+                if (hit) s->react[c] |= 1u << (i - 1);
             }
         }
     }
-    /* Eq. 24 on D3Q7: D = cs^2 (tau - 1/2) dx^2 / dt.  The most diffusive
-       active cell gets tau_ref; that fixes dt. */
+    /* Eq. 24: D = cs^2 (tau - 1/2) dx^2 / dt.  The most diffusive active cell
+       gets tau_ref; that fixes dt. */
+    const double cs2 = s->L->cs2;
     s->D_max = 0.0;
     for (long c = 0; c < N; ++c) if (s->active[c] && s->D[c] > s->D_max) s->D_max = s->D[c];
-    s->dt = (p->tau_ref - 0.5) * CS2 * p->dx_m * p->dx_m / s->D_max;
+    s->dt = (p->tau_ref - 0.5) * cs2 * p->dx_m * p->dx_m / s->D_max;
     for (long c = 0; c < N; ++c)
-        s->tau[c] = s->active[c] ? 0.5 + s->D[c] * s->dt / (CS2 * p->dx_m * p->dx_m) : 0.0;
+        s->tau[c] = s->active[c] ? 0.5 + s->D[c] * s->dt / (cs2 * p->dx_m * p->dx_m) : 0.0;
     s->k_lu = p->k_ms * s->dt / p->dx_m;
     return s;
 }
@@ -352,7 +422,7 @@ void orc_lbm_free(orc_lbm* s)
 void orc_lbm_init_field(orc_lbm* s, const double* C)
 {
     for (long c = 0; c < s->N; ++c)
-        for (int i = 0; i < Q; ++i) s->g[i * s->N + c] = s->active[c] ? W[i] * C[c] : 0.0;
+        for (int i = 0; i < s->L->q; ++i) s->g[i * s->N + c] = s->active[c] ? s->L->w[i] * C[c] : 0.0;
     s->step = 0;
 }
 
@@ -370,26 +440,38 @@ void orc_lbm_init_linear(orc_lbm* s)
 }
 
 /* post-collision populations of Eq. 21: g* = g - (g - g_eq) / tau */
-static void collide_cell(const orc_lbm* s, long c, double gs[Q])
+static void collide_cell(const orc_lbm* s, long c, double gs[QMAX])
 {
     double C = 0.0;
-    for (int i = 0; i < Q; ++i) C += s->g[i * s->N + c];
-    for (int i = 0; i < Q; ++i) {
+    for (int i = 0; i < s->L->q; ++i) C += s->g[i * s->N + c];
+    for (int i = 0; i < s->L->q; ++i) {
         double gi = s->g[i * s->N + c];
-        gs[i] = gi - (gi - W[i] * C) / s->tau[c];
+        gs[i] = gi - (gi - s->L->w[i] * C) / s->tau[c];
     }
 }
 
-static double reactive_factor(double w, double k_lu) { return (2.0 * w - k_lu) / (2.0 * w + k_lu); }
+/*
+ * Half-way first-order sink: a population g* that meets a catalytic face
+ * returns as r g*.  The wall value is the mean of the pair,
+ * C_w = (g* + r g*) / (2 w_i), and the amount the link delivers, (1 - r) g*,
+ * is its share of the face's rate k C_w.  The share is w_i over the weight
+ * sum of the links that cross one face (cs^2 / 2 on both lattices: 1/8 on
+ * D3Q7, 1/18 + 4/36 on D3Q19), so (1 - r) = k (1 + r) / cs^2 and
+ * r = (cs^2 - k) / (cs^2 + k) for every link; on D3Q7 that is
+ * (2w - k) / (2w + k).
+ */
+static double reactive_factor(const orc_lbm* s) { return (s->L->cs2 - s->k_lu) / (s->L->cs2 + s->k_lu); }
 
 /*
  * One time step in the order of Eq. 21: collide every active cell, then
  * stream each post-collision population to x + c_i.  Where the link leaves
  * the transport set, the population returns along the opposite direction:
- *   solid / inactive neighbour: bounce-back, times (2w - k)/(2w + k) if the
- *                               face is reactive (half-way first-order sink);
- *   beyond x = 0 or x = L:      anti-bounce-back -g* + 2 w C_bc (Dirichlet),
- *                               bounce-back (zero flux).
+ *   boundary link (leaves through x = 0 or x = L, end cell active, see
+ *   orc_neighbor):        anti-bounce-back -g* + 2 w_i C_bc (Dirichlet),
+ *                         bounce-back (zero flux);
+ *   wall link (end cell solid or inactive): bounce-back, times the reactive
+ *                         factor r if the link is reactive (half-way
+ *                         first-order sink).
  */
 void orc_lbm_step(orc_lbm* s, long nsteps)
 {
@@ -398,19 +480,20 @@ void orc_lbm_step(orc_lbm* s, long nsteps)
 #pragma omp parallel for schedule(static)
         for (long c = 0; c < N; ++c) {
             if (!s->active[c]) continue;
-            double gs[Q];
+            const orc_lattice* L = s->L;
+            double gs[QMAX];
             collide_cell(s, c, gs);
             s->gn[c] = gs[0];
-            for (int i = 1; i < Q; ++i) {
+            for (int i = 1; i < L->q; ++i) {
                 int out;
                 long n = orc_neighbor(s, c, i, &out);
-                if (out) {
+                if (out && s->active[n]) {
                     int bc = out < 0 ? s->p.bc_in : s->p.bc_out;
                     double cb = out < 0 ? s->p.c_in : s->p.c_out;
-                    s->gn[OPP[i] * N + c] = bc == 0 ? -gs[i] + 2.0 * W[i] * cb : gs[i];
+                    s->gn[L->opp[i] * N + c] = bc == 0 ? -gs[i] + 2.0 * L->w[i] * cb : gs[i];
                 } else if (!s->active[n]) {
-                    double r = (s->react[c] >> (i - 1) & 1) ? reactive_factor(W[i], s->k_lu) : 1.0;
-                    s->gn[OPP[i] * N + c] = r * gs[i];
+                    double r = (s->react[c] >> (i - 1) & 1) ? reactive_factor(s) : 1.0;
+                    s->gn[L->opp[i] * N + c] = r * gs[i];
                 } else {
                     s->gn[i * N + n] = gs[i];
                 }
@@ -426,15 +509,15 @@ void orc_lbm_concentration(const orc_lbm* s, double* C)
     for (long c = 0; c < s->N; ++c) {
         double sum = 0.0;
         if (s->active[c])
-            for (int i = 0; i < Q; ++i) sum += s->g[i * s->N + c];
+            for (int i = 0; i < s->L->q; ++i) sum += s->g[i * s->N + c];
         C[c] = sum;
     }
 }
 
-/* copy of the pre-collision populations, layout [Q][N] */
+/* copy of the pre-collision populations, layout [q][N] */
 void orc_lbm_populations(const orc_lbm* s, double* out)
 {
-    memcpy(out, s->g, sizeof(double) * Q * s->N);
+    memcpy(out, s->g, sizeof(double) * s->L->q * s->N);
 }
 
 /*
@@ -452,19 +535,20 @@ void orc_lbm_fluxes(const orc_lbm* s, double out[5])
     double jin = 0, jout = 0, R = 0, sc = 0, na = 0;
     for (long c = 0; c < s->N; ++c) {
         if (!s->active[c]) continue;
-        double gs[Q];
+        const orc_lattice* L = s->L;
+        double gs[QMAX];
         collide_cell(s, c, gs);
         double C = 0.0;
-        for (int i = 0; i < Q; ++i) C += s->g[i * s->N + c];
+        for (int i = 0; i < L->q; ++i) C += s->g[i * s->N + c];
         sc += C;
         na += 1;
-        for (int i = 1; i < Q; ++i) {
+        for (int i = 1; i < L->q; ++i) {
             int o;
             long n = orc_neighbor(s, c, i, &o);
-            if (o < 0 && s->p.bc_in == 0) jin += 2.0 * W[i] * s->p.c_in - 2.0 * gs[i];
-            if (o > 0 && s->p.bc_out == 0) jout += 2.0 * gs[i] - 2.0 * W[i] * s->p.c_out;
-            if (!o && !s->active[n] && (s->react[c] >> (i - 1) & 1))
-                R += (1.0 - reactive_factor(W[i], s->k_lu)) * gs[i];
+            if (o < 0 && s->active[n] && s->p.bc_in == 0) jin += 2.0 * L->w[i] * s->p.c_in - 2.0 * gs[i];
+            if (o > 0 && s->active[n] && s->p.bc_out == 0) jout += 2.0 * gs[i] - 2.0 * L->w[i] * s->p.c_out;
+            if (!s->active[n] && (s->react[c] >> (i - 1) & 1))
+                R += (1.0 - reactive_factor(s)) * gs[i];
         }
     }
     out[0] = jin; out[1] = jout; out[2] = R; out[3] = sc; out[4] = na;
@@ -506,16 +590,16 @@ double orc_lbm_reaction_rate(const orc_lbm* s, double* profile_R, double* profil
     for (long c = 0; c < s->N; ++c) {
         if (!s->active[c]) continue;
         int x = (int)(c % nx);
-        double gs[Q];
+        double gs[QMAX];
         collide_cell(s, c, gs);
         double C = 0.0;
-        for (int i = 0; i < Q; ++i) C += s->g[i * s->N + c];
+        for (int i = 0; i < s->L->q; ++i) C += s->g[i * s->N + c];
         if (profile_C) { profile_C[x] += C; cnt[x] += 1; }
-        for (int i = 1; i < Q; ++i) {
+        for (int i = 1; i < s->L->q; ++i) {
             int o;
             long n = orc_neighbor(s, c, i, &o);
-            if (!o && !s->active[n] && (s->react[c] >> (i - 1) & 1)) {
-                double r = (1.0 - reactive_factor(W[i], s->k_lu)) * gs[i] * scale;
+            if (!s->active[n] && (s->react[c] >> (i - 1) & 1)) {
+                double r = (1.0 - reactive_factor(s)) * gs[i] * scale;
                 total += r;
                 if (profile_R) profile_R[x] += r;
             }
@@ -562,7 +646,8 @@ double orc_lbm_k_lu(const orc_lbm* s) { return s->k_lu; }
 void orc_lbm_get_tau(const orc_lbm* s, double* out) { memcpy(out, s->tau, sizeof(double) * s->N); }
 void orc_lbm_get_D(const orc_lbm* s, double* out) { memcpy(out, s->D, sizeof(double) * s->N); }
 void orc_lbm_get_active(const orc_lbm* s, uint8_t* out) { memcpy(out, s->active, (size_t)s->N); }
-void orc_lbm_get_react(const orc_lbm* s, uint8_t* out) { memcpy(out, s->react, (size_t)s->N); }
+void orc_lbm_get_react(const orc_lbm* s, uint32_t* out) { memcpy(out, s->react, sizeof(uint32_t) * s->N); }
+int orc_lbm_q(const orc_lbm* s) { return s->L->q; }
 
 int orc_num_threads(void)
 {
