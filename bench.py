@@ -1,4 +1,5 @@
-"""Benchmark of the D3Q7 reactive-diffusion LBM hot path on one GB300.
+"""Benchmark of the reactive-diffusion LBM hot path on one GB300 (D3Q7 by
+default; `--lattice d3q19` times the paper's own 19-velocity lattice).
 
 Workload: the 256^3 Pt catalyst layer at 2 nm (seeded QSGS: pore 45 %,
 ionomer 18.87 %, solid 36.13 %; Knudsen diffusivity from the 13-direction
@@ -32,14 +33,15 @@ import hashlib
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
-KERNEL_SRCS = [os.path.join(ROOT, "paper_1410_1914_gb300", "csrc", f)
-               for f in ("march.cu", "march.cuh", "device_util.cuh")]
+_CSRC = os.path.join(ROOT, "paper_1410_1914_gb300", "csrc")
+KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("march.cu", "march.cuh", "device_util.cuh")]
+KERNEL_SRCS_Q19 = [os.path.join(_CSRC, f) for f in ("q19.cu", "internal.cuh", "device_util.cuh")]
 
 
-def kernel_src_sha256() -> str:
+def kernel_src_sha256(srcs=None) -> str:
     """sha256 over the step kernel's sources (the key of profiles/traffic.json)."""
     h = hashlib.sha256()
-    for f in KERNEL_SRCS:
+    for f in srcs or KERNEL_SRCS:
         with open(f, "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
@@ -52,13 +54,17 @@ WORKLOAD_DESC = ("256^3 Pt catalyst layer, 2 nm voxels, seeded QSGS (pore 0.45, 
                  "reservoir plane + fixed C inlet, zero-flux outlet, periodic y,z")
 
 
-def bytes_per_cell(storage: str) -> float:
+def bytes_per_cell(storage: str, lattice: str = "d3q7") -> float:
     """Algorithmic DRAM bytes of one fused step per box cell: the cell's state
     read once and written once, plus its relaxation rate (f32, 4 B) and link
-    mask (u16, 2 B).
+    mask (D3Q7: u16, 2 B; D3Q19: u32, 4 B).
       fp32     C as two f32 + 6 f32 deviations: 32 B state -> 2*32 + 6 = 70 B
       fp16dev  C f32 + f16 low word + 6 f16 deviations: 18 B -> 2*18 + 6 = 42 B
-      fp32pop  7 f32 populations: 28 B -> 2*28 + 6 = 62 B"""
+      fp32pop  7 f32 populations: 28 B -> 2*28 + 6 = 62 B
+      D3Q19    19 f32 populations: 76 B -> 2*76 + 8 = 160 B (the reactive-link
+               word, read only by cells with a catalytic link, is not counted)"""
+    if lattice == "d3q19":
+        return 2 * 76 + 8
     state = {"fp32": 32, "fp16dev": 18, "fp32pop": 28}[storage]
     return 2 * state + 6
 
@@ -119,14 +125,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def measured_traffic(storage: str, n_cells: int):
+def measured_traffic(storage: str, n_cells: int, lattice: str = "d3q7"):
     """DRAM bytes per launch of the step kernel from the committed ncu capture
     (profiles/traffic.json), scaled by the cells processed; None when the
     kernel source changed since the capture or no capture exists."""
+    key = "d3q19" if lattice == "d3q19" else storage
     try:
         with open(TRAFFIC_JSON) as fh:
-            rec = json.load(fh)[storage]
-        sha = kernel_src_sha256()
+            rec = json.load(fh)[key]
+        sha = kernel_src_sha256(KERNEL_SRCS_Q19 if lattice == "d3q19" else KERNEL_SRCS)
     except (OSError, KeyError, ValueError):
         return None, "no capture"
     if rec.get("src_sha256") != sha:
@@ -143,12 +150,12 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(ph, react, params, budget_s: float = 20.0):
+def cpu_baseline(ph, react, params, budget_s: float = 20.0, lattice: str = "d3q7"):
     """The FP64 oracle on the host cores: set-up, then as many whole steps as
     fit the budget (at least one).  Returns MLUPS and what was sampled."""
     import oracle
     t0 = time.perf_counter()
-    o = oracle.OracleLBM(ph, react=react, **params)
+    o = oracle.OracleLBM(ph, react=react, lattice=int(lattice == "d3q19"), **params)
     t_setup = time.perf_counter() - t0
     n = ph.size
     steps = 0
@@ -173,7 +180,7 @@ def run_reference(args):
     from paper_1410_1914_gb300 import inputs
     import oracle
     ph, react, params = inputs.make_workload(WORKLOAD, shape=args.shape)
-    o = oracle.OracleLBM(ph, react=react, **params)
+    o = oracle.OracleLBM(ph, react=react, lattice=int(args.lattice == "d3q19"), **params)
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
@@ -183,7 +190,8 @@ def run_reference(args):
     n = ph.size
     value = n * args.steps * args.ref_steps_per_step / el / 1e6
     line = {
-        "impl": "reference", "metric": "MLUPS (D3Q7 fused collide-stream step, all box cells)", "value": value,
+        "impl": "reference", "metric": "MLUPS (%s fused collide-stream step, all box cells)" % args.lattice.upper(),
+        "value": value,
         "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -473,6 +481,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="fp16dev", choices=["fp32", "fp16dev", "fp32pop"])
+    ap.add_argument("--lattice", default="d3q7", choices=["d3q7", "d3q19"],
+                    help="d3q19: the paper's 19-velocity lattice (19 f32 populations)")
     ap.add_argument("--no-other-storages", action="store_true",
                     help="skip the short timing of the other storage modes")
     ap.add_argument("--check-every", type=int, default=100)
@@ -492,6 +502,8 @@ def main():
         args.shape = tuple(args.shape)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.lattice == "d3q19":
+        args.storage = "fp32pop"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
@@ -519,7 +531,8 @@ def main():
     n_cells = ph.size
     K = args.check_every
     stream = torch.cuda.current_stream()
-    s = Solver(ph.shape, storage=args.storage, stream=int(stream.cuda_stream), check_every=K, **params)
+    s = Solver(ph.shape, storage=args.storage, stream=int(stream.cuda_stream), check_every=K,
+               lattice=args.lattice, **params)
     t0 = time.perf_counter()
     s.set_structure(ph, react)
     torch.cuda.synchronize()
@@ -550,19 +563,20 @@ def main():
     ms_per_step = elapsed_ms / args.steps
 
     # roofline of the fused step kernel (average launch = interval time / K)
-    launch_bytes = bytes_per_cell(args.storage) * n_cells
+    launch_bytes = bytes_per_cell(args.storage, args.lattice) * n_cells
     launch_s = ms_per_step * 1e-3 / K
     peak, peak_kind = measured_peak_gbs()
     achieved = launch_bytes / launch_s / 1e9
-    traffic, traffic_src = measured_traffic(args.storage, n_cells)
+    traffic, traffic_src = measured_traffic(args.storage, n_cells, args.lattice)
 
-    # the other storage modes on the same structure, for context (not the headline)
+    # the other storage modes and lattices on the same structure, for context (not the headline)
     others = {}
     if not args.no_other_storages:
-        for st in ("fp32", "fp16dev", "fp32pop"):
-            if st == args.storage:
+        for st, lat in (("fp32", "d3q7"), ("fp16dev", "d3q7"), ("fp32pop", "d3q7"), ("fp32pop", "d3q19")):
+            if st == args.storage and lat == args.lattice:
                 continue
-            so = Solver(ph.shape, storage=st, stream=int(stream.cuda_stream), check_every=K, **params)
+            so = Solver(ph.shape, storage=st, stream=int(stream.cuda_stream), check_every=K, lattice=lat,
+                        **params)
             so.set_structure(ph, react)
             for _ in range(3):
                 so.solve_budget(K)
@@ -576,7 +590,8 @@ def main():
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 5
             v = n_cells * K / (ms * 1e-3) / 1e6
-            others[st] = {"mlups": v, "hbm_frac": bytes_per_cell(st) * n_cells / (ms * 1e-3 / K) / 1e9 / peak}
+            others[st if lat == "d3q7" else f"{lat}_{st}"] = {
+                "mlups": v, "hbm_frac": bytes_per_cell(st, lat) * n_cells / (ms * 1e-3 / K) / 1e9 / peak}
             so.close()
 
     # ---------------------------------------------------------- end to end
@@ -604,14 +619,16 @@ def main():
                "lbm_steps_per_e2e_step": E, "includes": "structure upload + GPU set-up + steps + readout"}
 
     line = {
-        "metric": "MLUPS (D3Q7 fused collide-stream step, all box cells)",
+        "metric": "MLUPS (%s fused collide-stream step, all box cells)" % args.lattice.upper(),
         "value": mlups, "unit": "MLUPS", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_DESC, "shape_zyx": list(ph.shape), "storage": args.storage,
+                   "lattice": args.lattice,
                    "lbm_steps_per_bench_step": K, "active_fraction": info["n_active"] / n_cells,
                    "l2": "inputs larger than L2 (state buffers 2 x %.0f MB)" % (
-                       (bytes_per_cell(args.storage) - 6) / 2 * n_cells / 1e6),
+                       (bytes_per_cell(args.storage, args.lattice) - (8 if args.lattice == "d3q19" else 6))
+                       / 2 * n_cells / 1e6),
                    "parallelism": f"replicas x{world}", "setup_s": setup_s},
         "active_mlups": mlups * info["n_active"] / n_cells,
         "other_storages": others,
@@ -620,14 +637,15 @@ def main():
                      "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": launch_bytes,
-                     "kernel": "k_step_fp32" if args.storage == "fp32pop" else "k_march"},
+                     "kernel": ("k_step19" if args.lattice == "d3q19" else
+                                "k_step_fp32" if args.storage == "fp32pop" else "k_march")},
         "gpu_launches": args.steps * (K + 1),
         "clocks": clocks.summary(),
         "e2e": e2e,
         "last_check": {k: last[k] for k in ("J_in", "J_out", "R", "flux_balance", "resid")},
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(ph, react, params, args.cpu_budget)
+        line["cpu_baseline"] = cpu_baseline(ph, react, params, args.cpu_budget, args.lattice)
     s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -8,8 +8,10 @@
  * in the transport phase of a voxelised catalyst layer:
  *   - per-voxel diffusivity: Eq. 7 (bulk), Eq. 8 (Knudsen, from the
  *     13-direction local pore length of Sec. 2.1.3), Eq. 9 (Bosanquet);
- *   - relaxation time per voxel from Eq. 24, here on the D3Q7 lattice
- *     (weights 1/4 rest, 1/8 axis; cs^2 = 1/4; D = (tau - 1/2) dx^2 / (4 dt));
+ *   - relaxation time per voxel from Eq. 24 on one of two lattices: D3Q7
+ *     (weights 1/4 rest, 1/8 axis; cs^2 = 1/4; D = (tau - 1/2) dx^2 / (4 dt)),
+ *     the default and the fast path, or the paper's D3Q19 (Eq. 22-23:
+ *     1/3 rest, 1/18 axis, 1/36 face diagonal; cs^2 = 1/3);
  *   - BGK evolution Eq. 21 with equilibrium w_i C (Eq. 23);
  *   - boundaries of Sec. 3.5: fixed concentration (Eq. 19 setup, Eq. 20b)
  *     or zero flux (Eq. 20a) at the x faces, periodic in y and z,
@@ -23,7 +25,19 @@
  *   - Arrays are x-fastest: index = x + nx*(y + ny*z).
  *   - Phase codes: 0 pore, 1 solid (carbon/Pt/catalyst), 2 ionomer,
  *     3 micropore (transports like pore, never reactive).
- *   - Direction codes d = 1..6 are +x, -x, +y, -y, +z, -z.
+ *   - Direction codes d = 1..6 are +x, -x, +y, -y, +z, -z.  D3Q19 adds
+ *     7 (+1,+1,0), 8 (-1,-1,0), 9 (+1,-1,0), 10 (-1,+1,0), 11 (+1,0,+1),
+ *     12 (-1,0,-1), 13 (+1,0,-1), 14 (-1,0,+1), 15 (0,+1,+1), 16 (0,-1,-1),
+ *     17 (0,+1,-1), 18 (0,-1,+1); q = 7 or 19 populations per cell.
+ *   - Link classes.  The link of an active cell toward x + c_i ends in the
+ *     cell x + c_i, or, when it leaves the box through x = 0 or x = L, in
+ *     the mirror image (x, y + c_y, z + c_z) of the end plane.  It is a wall
+ *     (bounce-back) when that end cell is not active, a boundary link
+ *     (fixed value or zero flux) when it leaves the box and its end cell is
+ *     active, and open otherwise.  A wall link reacts when its end cell is
+ *     solid (1) and it leaves through a catalytic face: one of the faces
+ *     that its non-zero components cross is marked (set_structure) and
+ *     borders solid.  On D3Q7 every link crosses exactly its own face.
  *   - A pointer argument documented "host or device" is read or written with
  *     cudaMemcpyAsync on the handle's stream; `ptr_is_device` says which.
  *   - Calls are ordered on the handle's CUDA stream.  Calls that return
@@ -65,10 +79,15 @@ typedef enum {
     CL_STORE_FP32 = 0,
     /* C as f32 + a scaled f16 low word, deviations as scaled f16; FP32 arithmetic */
     CL_STORE_FP16DEV = 1,
-    /* plain 7 x f32 populations per cell (reference layout; its steady state
-       carries an FP32 rounding floor that grows with the box) */
+    /* plain q x f32 populations per cell (reference layout; its steady state
+       carries an FP32 rounding floor that grows with the box); the one
+       storage of the D3Q19 lattice */
     CL_STORE_FP32POP = 2
 } cl_storage;
+
+/* Velocity set (Eq. 22).  D3Q19 needs storage CL_STORE_FP32POP and cannot
+   join a batch. */
+typedef enum { CL_LATTICE_D3Q7 = 0, CL_LATTICE_D3Q19 = 1 } cl_lattice;
 
 /* What the solve transports.  O2: the pore space (pore 0 and micropore 3,
    plus ionomer 2 when D_ionomer > 0), Eq. 6 / Eq. 15.  PROTON: the ionomer
@@ -103,6 +122,7 @@ typedef struct {
     int storage;           /* cl_storage */
     int react_rule;        /* cl_react_rule */
     int carrier;           /* cl_carrier; PROTON needs D_ionomer > 0 and k_ms = 0 */
+    int lattice;           /* cl_lattice */
     int check_every;       /* steps between convergence checks in cl_lbm_solve (even, >= 2) */
     double tol_flux;       /* |J_in - J_out - R| / |J_in| below this ... */
     double tol_rel;        /* ... and the extrapolated relative error of the tracked readout
@@ -123,7 +143,7 @@ typedef struct {
     long long n_cells;        /* nx*ny*nz */
     long long n_transport;    /* transport-phase cells */
     long long n_active;       /* transport cells 6-connected to the inlet plane */
-    long long n_wall_links;   /* active-cell faces toward inactive cells */
+    long long n_wall_links;   /* wall links of active cells (see "Link classes") */
     long long n_react_links;  /* of those, reactive */
     double D_b;               /* bulk diffusivity used [m^2/s] */
     double D_max;             /* largest active-cell diffusivity [m^2/s] */
@@ -223,8 +243,9 @@ cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, do
    inactive cells). */
 cl_status cl_lbm_get_field(cl_handle h, float* C, int ptr_is_device);
 
-/* Current post-collision populations as f32, layout [7][nz][ny][nx], host
-   or device (decoded from FP16 storage if used; 0 on inactive cells). */
+/* Current post-collision populations as f32, layout [q][nz][ny][nx] in the
+   direction order above, host or device (decoded from FP16 storage if
+   used; 0 on inactive cells). */
 cl_status cl_lbm_get_populations(cl_handle h, float* g, int ptr_is_device);
 
 /* Set-up products: active (nx*ny*nz bytes, 0/1), omega (nx*ny*nz floats,
@@ -234,6 +255,13 @@ cl_status cl_lbm_get_populations(cl_handle h, float* g, int ptr_is_device);
    reactive, 12 active).  Any pointer may be NULL; all are host or device. */
 cl_status cl_lbm_get_setup(cl_handle h, uint8_t* active, float* omega, int32_t* chord,
                            uint16_t* link_mask, int ptr_is_device);
+
+/* Link classes of the loaded structure (nx*ny*nz uint32 each, host or
+   device; either may be NULL): wall[c] bit i-1 = the link of cell c toward
+   x + c_i is a wall, reactive[c] bit i-1 = that wall link is a catalytic
+   sink, for i = 1..q-1 of the handle's lattice (see "Link classes" above);
+   0 on inactive cells. */
+cl_status cl_lbm_get_links(cl_handle h, uint32_t* wall, uint32_t* reactive, int ptr_is_device);
 
 cl_status cl_lbm_get_info(cl_handle h, cl_structure_info* info);
 

@@ -25,6 +25,7 @@ CL_BC_DIRICHLET, CL_BC_ZERO_FLUX = 0, 1
 CL_STORE_FP32, CL_STORE_FP16DEV, CL_STORE_FP32POP = 0, 1, 2
 CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID = 0, 1
 CL_CARRIER_O2, CL_CARRIER_PROTON = 0, 1
+CL_LATTICE_D3Q7, CL_LATTICE_D3Q19 = 0, 1
 
 cl_alloc_fn = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 cl_free_fn = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
@@ -39,7 +40,7 @@ class cl_params(ctypes.Structure):
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
         ("storage", ctypes.c_int), ("react_rule", ctypes.c_int), ("carrier", ctypes.c_int),
-        ("check_every", ctypes.c_int),
+        ("lattice", ctypes.c_int), ("check_every", ctypes.c_int),
         ("tol_flux", ctypes.c_double), ("tol_rel", ctypes.c_double),
         ("max_steps", ctypes.c_longlong),
         ("cuda_stream", ctypes.c_void_p),
@@ -90,6 +91,7 @@ SIGNATURES = {
     "cl_lbm_get_field": (_S, [_H, _P, _I]),
     "cl_lbm_get_populations": (_S, [_H, _P, _I]),
     "cl_lbm_get_setup": (_S, [_H, _P, _P, _P, _P, _I]),
+    "cl_lbm_get_links": (_S, [_H, _P, _P, _I]),
     "cl_lbm_get_info": (_S, [_H, ctypes.POINTER(cl_structure_info)]),
     "cl_lbm_get_step": (_S, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "cl_status_str": (ctypes.c_char_p, [_I]),
@@ -311,6 +313,15 @@ def cl_lbm_get_setup(h: int, active=None, omega=None, chord=None, link_mask=None
     if len(devs) > 1:
         raise ValueError("outputs must all be host or all be device")
     _check(load().cl_lbm_get_setup(h, a, o, c, m, devs.pop() if devs else 0), "cl_lbm_get_setup")
+
+
+def cl_lbm_get_links(h: int, wall=None, reactive=None) -> None:
+    w, d1, _k1 = _arr(wall, np.uint32, writable=True)
+    r, d2, _k2 = _arr(reactive, np.uint32, writable=True)
+    devs = {d for d, x in ((d1, wall), (d2, reactive)) if x is not None}
+    if len(devs) > 1:
+        raise ValueError("outputs must both be host or both be device")
+    _check(load().cl_lbm_get_links(h, w, r, devs.pop() if devs else 0), "cl_lbm_get_links")
 
 
 def cl_lbm_get_info(h: int) -> cl_structure_info:

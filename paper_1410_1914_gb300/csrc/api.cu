@@ -29,7 +29,12 @@ int transport_phases(const cl_params& p) {
     if (p.carrier == CL_CARRIER_PROTON) return 1 << 2;           // ionomer (Eq. 16)
     return (1 << 0) | (1 << 3) | (p.D_ionomer > 0 ? 1 << 2 : 0);  // pore, micropore (+ ionomer, Eq. 15)
 }
+// Half-way first-order sink (the pair of a link meets the wall value
+// C_w = (g* + r g*) / (2 a_i); the link's share of the face's rate k C_w is
+// a_i over the weight of all links crossing one face, cs^2 / 2):
+// r = (cs^2 - k) / (cs^2 + k); on D3Q7 (cs^2 = 2w = 1/4) that is (2w - k) / (2w + k).
 float reactive_factor(const cl_lbm* h) {
+    if (h->q == 19) return (float)((1.0 / 3.0 - h->k_lu) / (1.0 / 3.0 + h->k_lu));
     const double w = 0.125;
     return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
 }
@@ -140,6 +145,26 @@ StepArgs make_args(cl_lbm* h) {
 }
 
 
+Q19Args make_args19(cl_lbm* h) {
+    Q19Args a;
+    a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px19;
+    a.NP = h->NP19;
+    a.mask = h->mask19;
+    a.react = h->react19;
+    a.omega = h->omega19;
+    a.rfac = reactive_factor(h);
+    a.c_in = (float)h->p.c_in;
+    a.c_out = (float)h->p.c_out;
+    a.c_in_d = h->p.c_in;
+    a.c_out_d = h->p.c_out;
+    a.bc_in = h->p.bc_in;
+    a.bc_out = h->p.bc_out;
+    a.Csnap = h->Csnap;
+    a.partials = h->partials;
+    return a;
+}
+
+
 cl_status make_map(CUtensorMap* m, CUtensorMapDataType dt, int el, void* ptr, int px, int rows, int nz, int bx,
                    int by) {
     EncodeTiledFn fn = encode_fn();
@@ -223,6 +248,13 @@ cl_status enqueue_steps(cl_lbm* h, long long n, bool reduce, cudaStream_t s, int
             CK(launch_march(h->p.storage, red, h->maps[*parity], a, h->mgrid, s));
             *parity ^= 1;
         }
+    } else if (h->q == 19) {
+        Q19Args a = make_args19(h);
+        for (long long i = 0; i < n; ++i) {
+            const bool red = reduce && i == n - 1;
+            CK(launch_step19(h->pop[*parity], h->pop[*parity ^ 1], a, red, s));
+            *parity ^= 1;
+        }
     } else {
         StepArgs a = make_args(h);
         for (long long i = 0; i < n; ++i) {
@@ -289,8 +321,9 @@ cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
     if (h->info.n_active == 0) { set_msg_txt("no transport cell is connected to the inlet plane"); return CL_ERR_NO_PATH; }
     h->D_max = st[6];
     if (!(h->D_max > 0) || !isfinite(h->D_max)) { set_msg_txt("largest diffusivity is not positive"); return CL_ERR_ARG; }
-    // Eq. 24 on D3Q7 (cs^2 = 1/4): D = (tau - 1/2) dx^2 / (4 dt); tau_ref at D_max.
-    h->dt = (h->p.tau_ref - 0.5) * 0.25 * h->p.dx_m * h->p.dx_m / h->D_max;
+    // Eq. 24: D = cs^2 (tau - 1/2) dx^2 / dt, cs^2 = 1/4 (D3Q7) or 1/3 (D3Q19); tau_ref at D_max.
+    const double cs2 = h->q == 19 ? 1.0 / 3.0 : 0.25;
+    h->dt = (h->p.tau_ref - 0.5) * cs2 * h->p.dx_m * h->p.dx_m / h->D_max;
     h->k_lu = h->p.k_ms * h->dt / h->p.dx_m;
     h->info.D_b = h->D_b;
     h->info.D_max = h->D_max;
@@ -299,6 +332,17 @@ cl_status derive_relaxation(cl_lbm* h, bool with_dp) {
     CK(launch_omega(h->active, h->D, h->N, h->p.tau_ref, stat_out + 6, h->omega, h->s));
     if (h->march)
         CK(launch_pad_static(h->mask, h->omega, h->nx, h->ny, h->nz, h->px, h->mask_p, h->omega_p, h->s));
+    if (h->q == 19) {
+        CK(launch_pad_omega19(h->omega, h->nx, h->ny, h->nz, h->px19, h->omega19, h->s));
+        // wall and reactive link counts of the 19-velocity stencil
+        double* lc = h->d_red + 8;
+        CK(launch_linkcount19(h->mask19, h->react19, h->NP19, h->partials, h->nblk_stats, lc, h->s));
+        double cnt[2];
+        CK(cudaMemcpyAsync(cnt, lc, sizeof(cnt), cudaMemcpyDeviceToHost, h->s));
+        CK(cudaStreamSynchronize(h->s));
+        h->info.n_wall_links = (long long)cnt[0];
+        h->info.n_react_links = (long long)cnt[1];
+    }
     drop_graphs(h);  // the reactive factor is baked into captured kernel arguments
     return CL_OK;
 }
@@ -334,6 +378,10 @@ cl_status do_init(cl_lbm* h, const float* C0dev) {
         for (int i = 0; i < 6; ++i) CK(cudaMemsetAsync(o.d[i], 0, (size_t)h->el * h->NP, h->s));
         MarchArgs a = make_margs(h, 0);
         CK(launch_state_init(h->p.storage, a, h->mask_p, C0dev, h->s));
+    } else if (h->q == 19) {
+        CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 19 * (size_t)h->NP19, h->s));
+        CK(launch_init19(h->pop[0], h->mask19, C0dev, h->nx, h->ny, h->nz, h->px19, h->p.c_in, h->p.c_out, h->Csnap,
+                         h->s));
     } else {
         CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)h->N, h->s));
         CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap, h->s));
@@ -346,6 +394,9 @@ cl_status plane_readout(cl_lbm* h, double* tot /* [5] */) {
     if (h->march) {
         MarchArgs a = make_margs(h, h->cur);
         CK(launch_state_readout(h->p.storage, a, h->mask_p, h->d_plane, h->s));
+    } else if (h->q == 19) {
+        Q19Args a = make_args19(h);
+        CK(launch_readout19(h->pop[h->cur], a, h->d_plane, h->s));
     } else {
         StepArgs a = make_args(h);
         CK(launch_readout_fp32(h->pop[h->cur], a, h->d_plane, h->s));
@@ -400,7 +451,7 @@ const char* cl_status_str(cl_status s) {
 
 const char* cl_last_error_message(void) { return g_msg; }
 
-const char* cl_version(void) { return "cl_lbm 0.2 (D3Q7, sm_103a)"; }
+const char* cl_version(void) { return "cl_lbm 0.3 (D3Q7 and D3Q19, sm_103a)"; }
 
 cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (!out || !p) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
@@ -414,6 +465,11 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (p->storage != CL_STORE_FP32 && p->storage != CL_STORE_FP16DEV && p->storage != CL_STORE_FP32POP) { set_msg_txt("bad storage mode"); return CL_ERR_ARG; }
     if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
     if (p->carrier != CL_CARRIER_O2 && p->carrier != CL_CARRIER_PROTON) { set_msg_txt("bad carrier"); return CL_ERR_ARG; }
+    if (p->lattice != CL_LATTICE_D3Q7 && p->lattice != CL_LATTICE_D3Q19) { set_msg_txt("bad lattice"); return CL_ERR_ARG; }
+    if (p->lattice == CL_LATTICE_D3Q19 && p->storage != CL_STORE_FP32POP) {
+        set_msg_txt("the D3Q19 lattice stores its 19 populations: storage must be CL_STORE_FP32POP");
+        return CL_ERR_ARG;
+    }
     if (p->carrier == CL_CARRIER_PROTON && !(p->D_ionomer > 0 && p->k_ms == 0)) {
         set_msg_txt("the proton carrier needs D_ionomer > 0 (its conductivity) and k_ms = 0");
         return CL_ERR_ARG;
@@ -426,6 +482,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     h->p = *p;
     h->nx = p->nx; h->ny = p->ny; h->nz = p->nz; h->N = N;
     h->march = p->storage != CL_STORE_FP32POP;
+    h->q = p->lattice == CL_LATTICE_D3Q19 ? 19 : 7;
     h->el = p->storage == CL_STORE_FP16DEV ? 2 : 4;
     h->s = (cudaStream_t)p->cuda_stream;
     memset(&h->info, 0, sizeof(h->info));
@@ -448,6 +505,14 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         h->NP = (long long)h->px * (h->ny + 2) * h->nz;
         choose_march_grid(h);
         h->nblk_step = (int)(h->mgrid.x * h->mgrid.y * h->mgrid.z);
+    } else if (h->q == 19) {
+        // row pitch a multiple of 32 cells: every row starts on a 128-byte
+        // line, and the 8 lanes of each 32-byte sector hold one row's cells
+        h->px19 = (h->nx + 31) / 32 * 32;
+        h->NP19 = (long long)h->px19 * h->ny * h->nz;
+        Q19Args a;
+        a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px19;
+        h->nblk_step = step19_blocks(a);
     } else {
         StepArgs a;
         a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;
@@ -482,6 +547,18 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         if ((st = dalloc_n(h, &h->Csnap_p, h->NP)) != CL_OK) return fail(st);
         if ((st = build_maps(h)) != CL_OK) return fail(st);
         e = cudaMemsetAsync(h->mask_p, 0, sizeof(uint16_t) * h->NP, h->s);
+        if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
+    } else if (h->q == 19) {
+        const long long NP = h->NP19;
+        if ((st = dalloc_n(h, &h->pop[0], 19 * NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->pop[1], 19 * NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->Csnap, NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->mask19, NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->react19, NP)) != CL_OK) return fail(st);
+        if ((st = dalloc_n(h, &h->omega19, NP)) != CL_OK) return fail(st);
+        e = cudaMemsetAsync(h->pop[0], 0, sizeof(float) * 19 * (size_t)NP, h->s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 19 * (size_t)NP, h->s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->mask19, 0, sizeof(uint32_t) * (size_t)NP, h->s);
         if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
     } else {
         if ((st = dalloc_n(h, &h->pop[0], 7 * N)) != CL_OK) return fail(st);
@@ -534,6 +611,9 @@ cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t*
                           h->p.D_ionomer, h->p.knudsen, nullptr, h->D, h->dp, nullptr, h->s));
     CK(launch_masks(h->phase, h->active, h->have_react ? h->react : nullptr, h->p.react_rule, h->nx, h->ny,
                     h->nz, h->mask, h->s));
+    if (h->q == 19)
+        CK(launch_masks19(h->phase, h->active, h->have_react ? h->react : nullptr, h->p.react_rule, h->nx, h->ny,
+                          h->nz, h->px19, h->mask19, h->react19, h->s));
     CKS(derive_relaxation(h, true));
     CKS(do_init(h, nullptr));
     CK(cudaStreamSynchronize(h->s));
@@ -713,6 +793,25 @@ static cl_status state_out(cl_lbm* h, float* C, float* g, int ptr_is_device) {
             cudaFreeAsync(tmp, h->s);
             if (e != cudaSuccess) { set_msg("populations", e); return from_cuda(e); }
         }
+    } else if (h->q == 19) {
+        if (C) {
+            float* dstp = ptr_is_device ? C : h->fbuf;
+            CK(launch_out19(h->pop[h->cur], h->mask19, h->nx, h->ny, h->nz, h->px19, dstp, nullptr, h->s));
+            if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * N, cudaMemcpyDeviceToHost, h->s));
+        }
+        if (g) {
+            float* gd = g;
+            void* tmp = nullptr;
+            if (!ptr_is_device) {
+                CK(cudaMallocAsync(&tmp, sizeof(float) * 19 * N, h->s));
+                gd = (float*)tmp;
+            }
+            cudaError_t e = launch_out19(h->pop[h->cur], h->mask19, h->nx, h->ny, h->nz, h->px19, nullptr, gd, h->s);
+            if (e == cudaSuccess && !ptr_is_device)
+                e = cudaMemcpyAsync(g, gd, sizeof(float) * 19 * N, cudaMemcpyDeviceToHost, h->s);
+            if (tmp) cudaFreeAsync(tmp, h->s);
+            if (e != cudaSuccess) { set_msg("populations", e); return from_cuda(e); }
+        }
     } else {
         if (C) {
             float* dstp = ptr_is_device ? C : h->fbuf;
@@ -757,6 +856,31 @@ cl_status cl_lbm_get_setup(cl_handle h, uint8_t* active, float* omega, int32_t* 
         if (tmp) cudaFreeAsync(tmp, h->s);
         if (e != cudaSuccess) { set_msg("chords", e); return from_cuda(e); }
     }
+    CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+cl_status cl_lbm_get_links(cl_handle h, uint32_t* wall, uint32_t* reactive, int ptr_is_device) {
+    CKS(need_structure(h));
+    if (!wall && !reactive) return CL_OK;
+    const size_t N = (size_t)h->N;
+    uint32_t* dw = wall;
+    uint32_t* dr = reactive;
+    void* tmp = nullptr;
+    if (!ptr_is_device) {
+        CK(cudaMallocAsync(&tmp, 2 * N * sizeof(uint32_t), h->s));
+        dw = wall ? (uint32_t*)tmp : nullptr;
+        dr = reactive ? (uint32_t*)tmp + N : nullptr;
+    }
+    cudaError_t e = h->q == 19
+                        ? launch_links_out(h->mask19, h->react19, nullptr, h->nx, h->ny, h->nz, h->px19, dw, dr, h->s)
+                        : launch_links_out(nullptr, nullptr, h->mask, h->nx, h->ny, h->nz, 0, dw, dr, h->s);
+    if (e == cudaSuccess && !ptr_is_device && wall)
+        e = cudaMemcpyAsync(wall, dw, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s);
+    if (e == cudaSuccess && !ptr_is_device && reactive)
+        e = cudaMemcpyAsync(reactive, dr, N * sizeof(uint32_t), cudaMemcpyDeviceToHost, h->s);
+    if (tmp) cudaFreeAsync(tmp, h->s);
+    if (e != cudaSuccess) { set_msg("links", e); return from_cuda(e); }
     CK(cudaStreamSynchronize(h->s));
     return CL_OK;
 }

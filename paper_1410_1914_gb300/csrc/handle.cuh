@@ -46,7 +46,8 @@ struct cl_lbm {
     cl_params p;
     int nx, ny, nz;
     long long N;
-    bool march = true;  // (C, delta) storage; false: 7 f32 populations
+    bool march = true;  // (C, delta) storage; false: q f32 populations
+    int q = 7;          // lattice: 7 (D3Q7) or 19 (D3Q19, Eq. 22)
     int px = 0;         // padded row pitch
     long long NP = 0;   // padded, ghosted cell count
     int el = 4;         // bytes per stored deviation
@@ -60,9 +61,13 @@ struct cl_lbm {
     double *D = nullptr, *dp = nullptr;
     float* omega = nullptr;
     uint16_t* mask = nullptr;
-    // population layout
+    // population layout (D3Q19: 19 planes of the padded px19 x ny x nz box)
     float* pop[2] = {nullptr, nullptr};
     float* Csnap = nullptr;
+    int px19 = 0;
+    long long NP19 = 0;
+    uint32_t *mask19 = nullptr, *react19 = nullptr;
+    float* omega19 = nullptr;
     // (C, delta) layout
     cl::MState st[2];
     uint16_t* mask_p = nullptr;

@@ -35,6 +35,41 @@ struct StepArgs {
     double* partials;    // [blocks][RED_N] (reduction)
 };
 
+// ---- D3Q19 (q19.cu) ----
+constexpr int kQ19Threads = 128;
+constexpr uint32_t kQ19LinkBits = (1u << 18) - 1;  // bit i-1: link toward x + c_i
+constexpr uint32_t kQ19HasReact = 1u << 18;
+constexpr uint32_t kQ19Active = 1u << 19;
+
+struct Q19Args {
+    int nx, ny, nz, px;   // px: padded row pitch (multiple of 32 cells)
+    long long NP;         // px * ny * nz
+    const uint32_t* __restrict__ mask;
+    const uint32_t* __restrict__ react;
+    const float* __restrict__ omega;
+    float rfac;           // (cs^2 - k_lu) / (cs^2 + k_lu), cs^2 = 1/3
+    float c_in, c_out;
+    double c_in_d, c_out_d;
+    int bc_in, bc_out;
+    float* Csnap;         // padded (reduction)
+    double* partials;     // [blocks][RED_N] (reduction)
+};
+
+cudaError_t launch_masks19(const uint8_t* phase, const uint8_t* active, const uint8_t* react_in, int rule,
+                           int nx, int ny, int nz, int px, uint32_t* mask, uint32_t* react, cudaStream_t s);
+cudaError_t launch_pad_omega19(const float* omega, int nx, int ny, int nz, int px, float* out, cudaStream_t s);
+cudaError_t launch_linkcount19(const uint32_t* mask, const uint32_t* react, long long NP, double* partials,
+                               int nblocks, double* out, cudaStream_t s);
+cudaError_t launch_init19(float* pop, const uint32_t* mask, const float* C0, int nx, int ny, int nz, int px,
+                          double c_in, double c_out, float* Csnap, cudaStream_t s);
+int step19_blocks(const Q19Args& a);
+cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool reduce, cudaStream_t s);
+cudaError_t launch_readout19(const float* pop, const Q19Args& a, double* out, cudaStream_t s);
+cudaError_t launch_out19(const float* pop, const uint32_t* mask, int nx, int ny, int nz, int px, float* C, float* g,
+                         cudaStream_t s);
+cudaError_t launch_links_out(const uint32_t* mask19, const uint32_t* react19, const uint16_t* mask7, int nx, int ny,
+                             int nz, int px, uint32_t* wall, uint32_t* react, cudaStream_t s);
+
 // ---- setup (kernels.cu) ----
 cudaError_t launch_validate(const uint8_t* phase, long long N, int* d_err, cudaStream_t s);
 cudaError_t launch_percolation(const uint8_t* phase, int nx, int ny, int nz, int transport_phase_mask,

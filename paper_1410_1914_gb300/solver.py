@@ -6,10 +6,12 @@ import numpy as np
 from . import _lib as L
 
 _STORAGE = {"fp32": L.CL_STORE_FP32, "fp16dev": L.CL_STORE_FP16DEV, "fp32pop": L.CL_STORE_FP32POP}
+_LATTICE = {"d3q7": L.CL_LATTICE_D3Q7, "d3q19": L.CL_LATTICE_D3Q19}
 
 
 class Solver:
-    """One D3Q7 solver on one box.  Parameters are the cl_params fields.
+    """One solver on one box.  Parameters are the cl_params fields; the
+    ``lattice`` may also be given by name ("d3q7", "d3q19").
 
     ``shape`` is (nz, ny, nx).  ``stream``: a cudaStream_t (int); default is
     torch's current stream when torch has initialised CUDA, else the legacy
@@ -24,8 +26,11 @@ class Solver:
         self.n = nx * ny * nz
         p = L.cl_params_default(nx=nx, ny=ny, nz=nz)
         p.storage = _STORAGE[storage]
+        if isinstance(params.get("lattice"), str):
+            params["lattice"] = _LATTICE[params["lattice"]]
         for k, v in params.items():
             setattr(p, k, v)
+        self.q = 19 if p.lattice == L.CL_LATTICE_D3Q19 else 7
         p.cuda_stream = L.current_torch_stream() if stream is None else stream
         self._alloc = None
         if torch_alloc:
@@ -92,7 +97,7 @@ class Solver:
         return out
 
     def populations(self):
-        out = np.zeros((7,) + self.shape, dtype=np.float32)
+        out = np.zeros((self.q,) + self.shape, dtype=np.float32)
         L.cl_lbm_get_populations(self.h, out)
         return out
 
@@ -103,6 +108,13 @@ class Solver:
         ch = np.zeros(self.shape + (13,), dtype=np.int32) if chord else None
         L.cl_lbm_get_setup(self.h, active, omega, ch, mask)
         return dict(active=active, omega=omega, chord=ch, mask=mask)
+
+    def links(self):
+        """(wall, reactive) link bit sets per cell, uint32 (bit i-1: link toward x + c_i)."""
+        wall = np.zeros(self.shape, dtype=np.uint32)
+        react = np.zeros(self.shape, dtype=np.uint32)
+        L.cl_lbm_get_links(self.h, wall, react)
+        return wall, react
 
     def info(self):
         i = L.cl_lbm_get_info(self.h)
