@@ -16,6 +16,8 @@ What each function follows:
   chord_counts         Sec. 2.1.3, 13-direction pore length
   active_mask          Sec. 2.1.3 connectivity, as a 6-connected flood from
                        the inlet plane
+  phase_connectivity   Sec. 2.1.3 connected-phase labelling (26 or 6
+                       neighbours), transport / dead portions, surface area
   OracleLBM            Eq. 21, 23, 24 on D3Q7 or D3Q19 (Eq. 22); boundaries of Sec. 3.5;
                        Eq. 19 readout; Eq. 17b/18a kinetics as a surface sink
 
@@ -80,6 +82,8 @@ def lib():
                 "orc_chord_counts": (None, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
                 "orc_pore_diameter": (None, [_P, _L, _D, _P]),
                 "orc_active_mask": (_L, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
+                "orc_phase_connectivity": (None, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint,
+                                                  ctypes.c_int, ctypes.c_int, _P, _P]),
                 "orc_lbm_new": (_P, [ctypes.POINTER(_Params), _P, _P, _P]),
                 "orc_lbm_free": (None, [_P]),
                 "orc_lbm_init_field": (None, [_P, _P]),
@@ -175,6 +179,29 @@ def active_mask(phase: np.ndarray, ionomer_transport: bool = False, protons: boo
     mode = 2 if protons else int(bool(ionomer_transport))
     lib().orc_active_mask(_ptr(phase), nx, ny, nz, mode, _ptr(out))
     return out
+
+
+STAT_KEYS = ("n_cells", "n_portions", "n_transport_portions", "n_transport_cells", "surface_faces",
+             "transport_surface_faces", "largest_portion")
+
+
+def phase_connectivity(phase: np.ndarray, phase_set, neighbours: int = 26, periodic_yz: bool = False):
+    """Sec. 2.1.3 connected-phase labelling of the cells whose code is in
+    ``phase_set`` (iterable of codes): (labels, stats).  labels (int32, shape
+    of phase): the smallest cell index of the cell's portion, -1 outside the
+    set.  stats: dict with STAT_KEYS (portions, "transport" portions touching
+    both x end planes, their cells, surface faces to other phases, largest
+    portion)."""
+    phase = np.ascontiguousarray(phase, dtype=np.uint8)
+    nz, ny, nx = phase.shape
+    mask = 0
+    for k in phase_set:
+        mask |= 1 << int(k)
+    labels = np.zeros(phase.shape, dtype=np.int32)
+    out = np.zeros(7, dtype=np.int64)
+    lib().orc_phase_connectivity(_ptr(phase), nx, ny, nz, mask, int(neighbours), int(bool(periodic_yz)),
+                                 _ptr(labels), _ptr(out))
+    return labels, {k: int(v) for k, v in zip(STAT_KEYS, out)}
 
 
 # ---------------------------------------------------------------- solver

@@ -261,6 +261,77 @@ long orc_active_mask(const uint8_t* phase, int nx, int ny, int nz, int mode, uin
 }
 
 /* ----------------------------------------------------------------------
+ * Sec. 2.1.3 connected-phase labelling and its statistics.  The cells whose
+ * phase code is in `set_mask` (bit k = code k) are grouped into portions:
+ * maximal sets connected through the 26 neighbours of Fig. 4a (or the 6
+ * face neighbours); y and z wrap when periodic_yz, x never does.  A portion
+ * is "transport" when it has cells on both end planes x = 0 and x = nx - 1,
+ * "dead" otherwise.  Plain breadth-first search in scan order, so each
+ * portion's label is the smallest cell index in it (-1 outside the set).
+ * out[0] cells in the set, [1] portions, [2] transport portions,
+ * [3] transport cells, [4] faces between a set cell and an in-box cell of
+ * another phase (the surface area in dx^2), [5] those faces of transport
+ * cells, [6] cells of the largest portion.
+ * ---------------------------------------------------------------------- */
+void orc_phase_connectivity(const uint8_t* phase, int nx, int ny, int nz, unsigned set_mask, int neighbours,
+                            int periodic_yz, int32_t* labels, long long out[7])
+{
+    long N = (long)nx * ny * nz;
+    int off[26][3], noff = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                int m = abs(dx) + abs(dy) + abs(dz);
+                if (m == 0 || (neighbours == 6 && m != 1)) continue;
+                off[noff][0] = dx; off[noff][1] = dy; off[noff][2] = dz; ++noff;
+            }
+    long* queue = (long*)malloc(sizeof(long) * (N > 0 ? N : 1));
+    unsigned char* ends = (unsigned char*)calloc((size_t)(N > 0 ? N : 1), 1);
+    long* size = (long*)calloc((size_t)(N > 0 ? N : 1), sizeof(long));
+    for (long c = 0; c < N; ++c) labels[c] = -1;
+    for (int k = 0; k < 7; ++k) out[k] = 0;
+    for (long s = 0; s < N; ++s) {
+        if (labels[s] >= 0 || !(set_mask >> phase[s] & 1u)) continue;
+        long head = 0, tail = 0;
+        labels[s] = (int32_t)s;
+        queue[tail++] = s;
+        while (head < tail) {
+            long c = queue[head++];
+            int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+            if (x == 0) ends[s] |= 1;
+            if (x == nx - 1) ends[s] |= 2;
+            for (int k = 0; k < noff; ++k) {
+                int qx = x + off[k][0], qy = y + off[k][1], qz = z + off[k][2];
+                if (qx < 0 || qx >= nx) continue;
+                if (periodic_yz) { qy = wrap(qy, ny); qz = wrap(qz, nz); }
+                else if (qy < 0 || qy >= ny || qz < 0 || qz >= nz) continue;
+                long n = idx3(qx, qy, qz, nx, ny);
+                if (labels[n] < 0 && (set_mask >> phase[n] & 1u)) { labels[n] = (int32_t)s; queue[tail++] = n; }
+            }
+        }
+        size[s] = tail;
+        out[1] += 1;
+        if (ends[s] == 3) { out[2] += 1; out[3] += tail; }
+        if (tail > out[6]) out[6] = tail;
+        out[0] += tail;
+    }
+    for (long c = 0; c < N; ++c) {
+        if (labels[c] < 0) continue;
+        int x = (int)(c % nx), y = (int)((c / nx) % ny), z = (int)(c / ((long)nx * ny));
+        for (int f = 0; f < 6; ++f) {
+            int qx = x + FX[f], qy = y + FY[f], qz = z + FZ[f];
+            if (qx < 0 || qx >= nx) continue;
+            if (periodic_yz) { qy = wrap(qy, ny); qz = wrap(qz, nz); }
+            else if (qy < 0 || qy >= ny || qz < 0 || qz >= nz) continue;
+            if (set_mask >> phase[idx3(qx, qy, qz, nx, ny)] & 1u) continue;
+            out[4] += 1;
+            if (ends[labels[c]] == 3) out[5] += 1;
+        }
+    }
+    free(queue); free(ends); free(size);
+}
+
+/* ----------------------------------------------------------------------
  * Per-cell diffusivity [m^2/s] of active cells (0 elsewhere):
  *   pore / micropore: Eq. 9 of Eq. 8 (d_p from the 13-direction lengths) and
  *                     D_b (Eq. 7 unless given); D_b alone without Knudsen;
