@@ -341,6 +341,38 @@ cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* 
 cl_status cl_active_mask_noalloc(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
                                  uint8_t* active, void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Structure statistics: the connected-phase labelling of Sec. 2.1.3.
+ * The cells whose phase code is in phase_set (bit k = code k, e.g. 0x2 for
+ * C/Pt, 0x9 for the void phase of pores and micropores, 0x4 for ionomer)
+ * are grouped into portions connected through the 26 neighbours of Fig. 4a
+ * (neighbours = 26) or the 6 face neighbours (neighbours = 6); y and z wrap
+ * when periodic_yz, x never does.  A portion with cells on both end planes
+ * x = 0 and x = L is "transport", the others are "dead".
+ * --------------------------------------------------------------------- */
+typedef struct {
+    long long n_cells;                 /* cells of the phase set */
+    long long n_portions;              /* connected portions */
+    long long n_transport_portions;    /* portions touching x = 0 and x = L */
+    long long n_transport_cells;       /* cells of those portions */
+    long long surface_faces;           /* faces between a set cell and an in-box cell of
+                                          another phase (surface area in dx^2) */
+    long long transport_surface_faces; /* of those, faces of transport cells */
+    long long largest_portion;         /* cells of the largest portion */
+} cl_phase_stats;
+
+/* Label and count, on the GPU.  phase: nx*ny*nz codes 0..3 (host or
+   device); labels (nullable, nx*ny*nz int32, same side as phase): the
+   smallest cell index of the cell's portion, -1 outside the set; out: host.
+   Allocates its scratch (about 12 B per cell) on the stream with
+   cudaMallocAsync and frees it before returning; synchronises the stream.
+   Errors: CL_ERR_ARG (NULL, sizes, neighbours not 6 or 26, empty or
+   invalid phase_set, a phase code > 3), CL_ERR_OOM, CL_ERR_CUDA,
+   CL_ERR_TIMEOUT (labelling iteration bound). */
+cl_status cl_phase_connectivity(const uint8_t* phase, int nx, int ny, int nz, unsigned phase_set,
+                                int neighbours, int periodic_yz, int32_t* labels, cl_phase_stats* out,
+                                int ptr_is_device, void* cuda_stream);
+
 /* Library version string. */
 const char* cl_version(void);
 

@@ -58,6 +58,12 @@ class cl_structure_info(ctypes.Structure):
     ]
 
 
+class cl_phase_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_longlong) for k in (
+        "n_cells", "n_portions", "n_transport_portions", "n_transport_cells", "surface_faces",
+        "transport_surface_faces", "largest_portion")]
+
+
 class cl_solve_info(ctypes.Structure):
     _fields_ = [
         ("steps", ctypes.c_longlong), ("converged", ctypes.c_int),
@@ -98,6 +104,8 @@ SIGNATURES = {
     "cl_last_error_message": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_char_p, []),
     "cl_active_mask_noalloc": (_S, [_P, _I, _I, _I, _I, _P, _P]),
+    "cl_phase_connectivity": (_S, [_P, _I, _I, _I, ctypes.c_uint, _I, _I, _P, ctypes.POINTER(cl_phase_stats),
+                                   _I, _P]),
     "cl_batch_create": (_S, [ctypes.POINTER(_H), ctypes.POINTER(_H), _I, _I]),
     "cl_batch_destroy": (None, [_H]),
     "cl_batch_step": (_S, [_H, ctypes.c_longlong]),
@@ -322,6 +330,27 @@ def cl_lbm_get_links(h: int, wall=None, reactive=None) -> None:
     if len(devs) > 1:
         raise ValueError("outputs must both be host or both be device")
     _check(load().cl_lbm_get_links(h, w, r, devs.pop() if devs else 0), "cl_lbm_get_links")
+
+
+def cl_phase_connectivity(phase, phase_set, neighbours: int = 26, periodic_yz: bool = False, labels=None,
+                          stream: int | None = None) -> dict:
+    """Sec. 2.1.3 connected-phase labelling on the GPU.  phase: (nz, ny, nx)
+    uint8 (numpy or torch); phase_set: iterable of codes; labels: optional
+    int32 output of the same shape and side.  Returns the statistics."""
+    nz, ny, nx = (int(v) for v in phase.shape)
+    n = nx * ny * nz
+    pp, pdev, _k1 = _arr(phase, np.uint8, n)
+    lp, ldev, _k2 = _arr(labels, np.int32, n, writable=True)
+    if labels is not None and ldev != pdev:
+        raise ValueError("phase and labels must be on the same side")
+    mask = 0
+    for k in phase_set:
+        mask |= 1 << int(k)
+    st = current_torch_stream() if stream is None else stream
+    out = cl_phase_stats()
+    _check(load().cl_phase_connectivity(pp, nx, ny, nz, mask, int(neighbours), int(bool(periodic_yz)), lp,
+                                        ctypes.byref(out), pdev, st), "cl_phase_connectivity")
+    return {k: getattr(out, k) for k, _ in out._fields_}
 
 
 def cl_lbm_get_info(h: int) -> cl_structure_info:

@@ -4,6 +4,7 @@
 
 #include "device_util.cuh"
 #include "internal.cuh"
+#include "uf.cuh"
 
 namespace cl {
 
@@ -27,35 +28,7 @@ cudaError_t launch_validate(const uint8_t* phase, long long N, int* d_err, cudaS
 
 // ------------------------------------------------ percolation (union-find)
 // Transport cells 6-connected (y, z periodic) to the inlet plane x = 0.
-// Lock-free union-find: a root is only ever linked to a smaller index, so
-// parent chains strictly decrease and every find terminates; each failed
-// CAS means another thread linked that root, so the retry loop makes
-// global progress.  Both loops still carry an iteration cap that raises
-// an error bit instead of spinning.
-constexpr int kUfMaxIter = 1 << 24;
-
-__device__ int uf_find(volatile int* L, int a, int* err) {
-    int it = 0;
-    int p = L[a];
-    while (p != a) {
-        a = p;
-        p = L[a];
-        if (++it > kUfMaxIter) { atomicOr(err, 2); break; }
-    }
-    return a;
-}
-
-__device__ void uf_union(int* L, int a, int b, int* err) {
-    for (int it = 0; it < kUfMaxIter; ++it) {
-        a = uf_find(L, a, err);
-        b = uf_find(L, b, err);
-        if (a == b) return;
-        if (a < b) { int t = a; a = b; b = t; }
-        int old = atomicCAS(L + a, a, b);
-        if (old == a) return;
-    }
-    atomicOr(err, 2);
-}
+// Union-find helpers: uf.cuh.
 
 __global__ void k_uf_init(const uint8_t* __restrict__ phase, long long N, int tmask, int* L,
                           uint8_t* touch) {

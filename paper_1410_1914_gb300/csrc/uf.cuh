@@ -1,0 +1,38 @@
+// Lock-free union-find over cell indices, shared by the connectivity
+// kernels.  A root is only ever linked to a smaller index, so parent chains
+// strictly decrease, every find terminates, and the final root of a set is
+// its smallest index; each failed CAS means another thread linked that
+// root, so the retry loop makes global progress.  Both loops still carry an
+// iteration cap that raises bit 2 of *err instead of spinning.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace cl {
+
+constexpr int kUfMaxIter = 1 << 24;
+
+__device__ __forceinline__ int uf_find(volatile int* L, int a, int* err) {
+    int it = 0;
+    int p = L[a];
+    while (p != a) {
+        a = p;
+        p = L[a];
+        if (++it > kUfMaxIter) { atomicOr(err, 2); break; }
+    }
+    return a;
+}
+
+__device__ __forceinline__ void uf_union(int* L, int a, int b, int* err) {
+    for (int it = 0; it < kUfMaxIter; ++it) {
+        a = uf_find(L, a, err);
+        b = uf_find(L, b, err);
+        if (a == b) return;
+        if (a < b) { int t = a; a = b; b = t; }
+        int old = atomicCAS(L + a, a, b);
+        if (old == a) return;
+    }
+    atomicOr(err, 2);
+}
+
+}  // namespace cl
