@@ -373,6 +373,43 @@ cl_status cl_phase_connectivity(const uint8_t* phase, int nx, int ny, int nz, un
                                 int neighbours, int periodic_yz, int32_t* labels, cl_phase_stats* out,
                                 int ptr_is_device, void* cuda_stream);
 
+/* ---------------------------------------------------------------------
+ * Structure generation on the GPU (input generation, Sec. 2.1.2 and 5.3),
+ * bit-identical to the host generator shipped with the inputs module.
+ * Random numbers: SplitMix64 folded over (seed, stream, a, b); a uniform
+ * draw is the top 53 bits of the hash times 2^-53.  All arrays are device
+ * arrays of nx*ny*nz cells; calls synchronise the stream.
+ * --------------------------------------------------------------------- */
+
+/* QSGS growth of phase `code` in place until `target` cells carry it
+   (Sec. 2.1.2.1): seeds once with probability c_d on cells whose phase is
+   in allowed_mask (and region[c] != 0 when region is given), then
+   synchronous sweeps: an allowed cell with grown 6-neighbours (phases in
+   grown_mask; x, y, z wrap) converts when it has two or more (rule 2a),
+   else with probability p_alpha (rule 2b); the sweep that would overshoot
+   converts only its candidates with the smallest (priority hash, cell
+   index).  At most max_sweeps sweeps; *final_count (nullable) gets the
+   resulting count.  Scratch: 12 B per cell, allocated on the stream.
+   Errors: CL_ERR_ARG (NULL, sizes, code not in 0..3 or not in grown_mask),
+   CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_qsgs_grow(uint8_t* phase, int nx, int ny, int nz, int code, unsigned allowed_mask,
+                       unsigned grown_mask, const uint8_t* region, long long target, double c_d,
+                       double p_alpha, uint64_t seed, uint64_t stream, int max_sweeps,
+                       long long* final_count, void* cuda_stream);
+
+/* region[c] = 1 where phase[c] == code and no 6-neighbour (all axes wrap)
+   has phase `avoid` (the solid that may hold micropores, Sec. 5.3). */
+cl_status cl_qsgs_region_not_adjacent(const uint8_t* phase, int nx, int ny, int nz, int code, int avoid,
+                                      uint8_t* region, void* cuda_stream);
+
+/* out[c] bit d-1 (d = 1..6: +x, -x, +y, -y, +z, -z): cell c has phase
+   from_code, its neighbour across face d (y, z wrap, x does not) has phase
+   to_code, and the face is drawn with probability `fraction` (>= 1: all);
+   *n_faces (nullable) = faces set. */
+cl_status cl_qsgs_reactive_faces(const uint8_t* phase, int nx, int ny, int nz, int from_code, int to_code,
+                                 double fraction, uint64_t seed, uint8_t* out, long long* n_faces,
+                                 void* cuda_stream);
+
 /* Library version string. */
 const char* cl_version(void);
 

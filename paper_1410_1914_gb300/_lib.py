@@ -106,6 +106,12 @@ SIGNATURES = {
     "cl_active_mask_noalloc": (_S, [_P, _I, _I, _I, _I, _P, _P]),
     "cl_phase_connectivity": (_S, [_P, _I, _I, _I, ctypes.c_uint, _I, _I, _P, ctypes.POINTER(cl_phase_stats),
                                    _I, _P]),
+    "cl_qsgs_grow": (_S, [_P, _I, _I, _I, _I, ctypes.c_uint, ctypes.c_uint, _P, ctypes.c_longlong,
+                          ctypes.c_double, ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, _I,
+                          ctypes.POINTER(ctypes.c_longlong), _P]),
+    "cl_qsgs_region_not_adjacent": (_S, [_P, _I, _I, _I, _I, _I, _P, _P]),
+    "cl_qsgs_reactive_faces": (_S, [_P, _I, _I, _I, _I, _I, ctypes.c_double, ctypes.c_uint64, _P,
+                                    ctypes.POINTER(ctypes.c_longlong), _P]),
     "cl_batch_create": (_S, [ctypes.POINTER(_H), ctypes.POINTER(_H), _I, _I]),
     "cl_batch_destroy": (None, [_H]),
     "cl_batch_step": (_S, [_H, ctypes.c_longlong]),
@@ -351,6 +357,41 @@ def cl_phase_connectivity(phase, phase_set, neighbours: int = 26, periodic_yz: b
     _check(load().cl_phase_connectivity(pp, nx, ny, nz, mask, int(neighbours), int(bool(periodic_yz)), lp,
                                         ctypes.byref(out), pdev, st), "cl_phase_connectivity")
     return {k: getattr(out, k) for k, _ in out._fields_}
+
+
+def _dev_u8(x, what):
+    p, dev, _k = _arr(x, np.uint8, None, writable=True)
+    if not dev:
+        raise ValueError(f"{what} must be a CUDA uint8 tensor")
+    return p
+
+
+def cl_qsgs_grow(phase, code: int, allowed_mask: int, grown_mask: int, target: int, c_d: float, p_alpha: float,
+                 seed: int, stream_id: int, region=None, max_sweeps: int = 100000) -> int:
+    """QSGS growth in place on a CUDA uint8 tensor (nz, ny, nx); returns the final count."""
+    nz, ny, nx = (int(v) for v in phase.shape)
+    out = ctypes.c_longlong(0)
+    _check(load().cl_qsgs_grow(_dev_u8(phase, "phase"), nx, ny, nz, int(code), int(allowed_mask), int(grown_mask),
+                               None if region is None else _dev_u8(region, "region"), int(target), float(c_d),
+                               float(p_alpha), seed & (2**64 - 1), stream_id & (2**64 - 1), int(max_sweeps),
+                               ctypes.byref(out), current_torch_stream()), "cl_qsgs_grow")
+    return out.value
+
+
+def cl_qsgs_region_not_adjacent(phase, code: int, avoid: int, region) -> None:
+    nz, ny, nx = (int(v) for v in phase.shape)
+    _check(load().cl_qsgs_region_not_adjacent(_dev_u8(phase, "phase"), nx, ny, nz, int(code), int(avoid),
+                                              _dev_u8(region, "region"), current_torch_stream()),
+           "cl_qsgs_region_not_adjacent")
+
+
+def cl_qsgs_reactive_faces(phase, from_code: int, to_code: int, fraction: float, seed: int, out) -> int:
+    nz, ny, nx = (int(v) for v in phase.shape)
+    n = ctypes.c_longlong(0)
+    _check(load().cl_qsgs_reactive_faces(_dev_u8(phase, "phase"), nx, ny, nz, int(from_code), int(to_code),
+                                         float(fraction), seed & (2**64 - 1), _dev_u8(out, "out"),
+                                         ctypes.byref(n), current_torch_stream()), "cl_qsgs_reactive_faces")
+    return n.value
 
 
 def cl_lbm_get_info(h: int) -> cl_structure_info:
