@@ -281,6 +281,64 @@ def run_batch(args):
     return 0
 
 
+def run_structures(args):
+    """Structure generation and labelling on the GPU: the Pt-layer recipe
+    (QSGS solid then ionomer, Sec. 2.1.2) at 464^3 = 1e8 voxels, then the
+    connected-phase statistics of Sec. 2.1.3 for its three phases (26
+    neighbours).  One step = one structure generated and labelled (seed
+    1000 + step).  The host generator of the inputs module, timed on the
+    same recipe at a bounded size, is the CPU baseline."""
+    import torch
+    from paper_1410_1914_gb300 import inputs, structures
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    n = args.shape[0] if args.shape else 464
+    shape = (n, n, n)
+    pore, ion = 0.45, inputs.EQ4_EPS045_IONOMER
+
+    def one(seed):
+        ph = structures.pt_cl(shape, seed, pore, ion)
+        return ph, structures.connectivity(ph)
+
+    for w in range(args.warmup):
+        one(900 + w)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    with ClockSampler(0) as clocks:
+        ev0.record(stream)
+        for k in range(args.steps):
+            ph, stats = one(1000 + k)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = ev0.elapsed_time(ev1)
+    vox = ph.numel()
+    line = {
+        "metric": "Mvoxel/s (QSGS Pt layer generated + three phases labelled, Sec. 2.1.2-2.1.3)",
+        "value": vox * args.steps / (ms * 1e-3) / 1e6, "unit": "Mvoxel/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"Pt layer {n}^3, porosity {pore}, ionomer {ion:.4f}, c_d 0.01, P_alpha 0.01; "
+                               "26-neighbour labelling of C/Pt, void, ionomer", "voxels": vox},
+        "host_wall_s_per_step": wall / args.steps,
+        "last_stats": stats,
+        "gpu_launches": None,
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline:
+        m = 256
+        t0 = time.perf_counter()
+        inputs.pt_cl((m, m, m), 1000, pore, ion)
+        el = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": m ** 3 / el / 1e6, "unit": "Mvoxel/s (generation only)",
+                                "cores": os.cpu_count(), "kind": "host generator",
+                                "sample": f"one {m}^3 Pt layer by the host QSGS ({el:.1f} s), no labelling"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_converge(args):
     """Time-to-converged D_eff (Eq. 19 readout within 1e-3, and staying there)
     per storage mode, from the linear ramp and from the learned warm start,
@@ -492,7 +550,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-steps-per-step", type=int, default=1)
     ap.add_argument("--shape", type=int, nargs=3, default=None, help="override (nz ny nx)")
-    ap.add_argument("--workload", default="pt_cl_256", choices=["pt_cl_256", "batch64", "converge", "unet_train"])
+    ap.add_argument("--workload", default="pt_cl_256",
+                    choices=["pt_cl_256", "batch64", "converge", "unet_train", "structures"])
     ap.add_argument("--max-steps", type=int, default=3_000_000)
     ap.add_argument("--no-warm", action="store_true", help="converge workload: skip the learned warm-start arms")
     ap.add_argument("--carrier", default="o2", choices=["o2", "proton"],
@@ -512,6 +571,8 @@ def main():
         return run_converge(args)
     if args.workload == "unet_train":
         return run_unet(args)
+    if args.workload == "structures":
+        return run_structures(args)
 
     import torch
     rank = int(os.environ.get("RANK", "0"))
