@@ -36,6 +36,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(ROOT, "paper_1410_1914_gb300", "csrc")
 KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("march.cu", "march.cuh", "device_util.cuh")]
 KERNEL_SRCS_Q19 = [os.path.join(_CSRC, f) for f in ("q19.cu", "internal.cuh", "device_util.cuh")]
+KERNEL_SRCS_Q19S = [os.path.join(_CSRC, f) for f in ("q19s.cu", "internal.cuh", "device_util.cuh")]
 
 
 def kernel_src_sha256(srcs=None) -> str:
@@ -61,10 +62,13 @@ def bytes_per_cell(storage: str, lattice: str = "d3q7") -> float:
       fp32     C as two f32 + 6 f32 deviations: 32 B state -> 2*32 + 6 = 70 B
       fp16dev  C f32 + f16 low word + 6 f16 deviations: 18 B -> 2*18 + 6 = 42 B
       fp32pop  7 f32 populations: 28 B -> 2*28 + 6 = 62 B
-      D3Q19    19 f32 populations: 76 B -> 2*76 + 8 = 160 B (the reactive-link
-               word, read only by cells with a catalytic link, is not counted)"""
+      D3Q19 (u32 link word + f32 omega = 8 B of static data; the reactive-link
+      word, read only by cells with a catalytic link, is not counted):
+        fp32pop  19 f32 populations: 76 B -> 2*76 + 8 = 160 B
+        fp32     C as two f32 + 18 f32 deviations: 80 B -> 2*80 + 8 = 168 B
+        fp16dev  C f32 + f16 low word + 18 f16 deviations: 42 B -> 2*42 + 8 = 92 B"""
     if lattice == "d3q19":
-        return 2 * 76 + 8
+        return 2 * {"fp32pop": 76, "fp32": 80, "fp16dev": 42}[storage] + 8
     state = {"fp32": 32, "fp16dev": 18, "fp32pop": 28}[storage]
     return 2 * state + 6
 
@@ -129,11 +133,12 @@ def measured_traffic(storage: str, n_cells: int, lattice: str = "d3q7"):
     """DRAM bytes per launch of the step kernel from the committed ncu capture
     (profiles/traffic.json), scaled by the cells processed; None when the
     kernel source changed since the capture or no capture exists."""
-    key = "d3q19" if lattice == "d3q19" else storage
+    key = f"d3q19_{storage}" if lattice == "d3q19" else storage
+    srcs = (KERNEL_SRCS if lattice != "d3q19" else KERNEL_SRCS_Q19 if storage == "fp32pop" else KERNEL_SRCS_Q19S)
     try:
         with open(TRAFFIC_JSON) as fh:
             rec = json.load(fh)[key]
-        sha = kernel_src_sha256(KERNEL_SRCS_Q19 if lattice == "d3q19" else KERNEL_SRCS)
+        sha = kernel_src_sha256(srcs)
     except (OSError, KeyError, ValueError):
         return None, "no capture"
     if rec.get("src_sha256") != sha:
@@ -561,8 +566,6 @@ def main():
         args.shape = tuple(args.shape)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    if args.lattice == "d3q19":
-        args.storage = "fp32pop"
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch64":
@@ -633,7 +636,8 @@ def main():
     # the other storage modes and lattices on the same structure, for context (not the headline)
     others = {}
     if not args.no_other_storages:
-        for st, lat in (("fp32", "d3q7"), ("fp16dev", "d3q7"), ("fp32pop", "d3q7"), ("fp32pop", "d3q19")):
+        for st, lat in (("fp32", "d3q7"), ("fp16dev", "d3q7"), ("fp32pop", "d3q7"), ("fp32", "d3q19"),
+                        ("fp16dev", "d3q19"), ("fp32pop", "d3q19")):
             if st == args.storage and lat == args.lattice:
                 continue
             so = Solver(ph.shape, storage=st, stream=int(stream.cuda_stream), check_every=K, lattice=lat,
@@ -698,7 +702,8 @@ def main():
                      "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": launch_bytes,
-                     "kernel": ("k_step19" if args.lattice == "d3q19" else
+                     "kernel": ("k_step19" if args.lattice == "d3q19" and args.storage == "fp32pop" else
+                                "k_step19s" if args.lattice == "d3q19" else
                                 "k_step_fp32" if args.storage == "fp32pop" else "k_march")},
         "gpu_launches": args.steps * (K + 1),
         "clocks": clocks.summary(),

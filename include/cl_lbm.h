@@ -74,19 +74,18 @@ typedef enum {
 typedef enum { CL_BC_DIRICHLET = 0, CL_BC_ZERO_FLUX = 1 } cl_bc;
 
 typedef enum {
-    /* C as a double-float (two f32) + 6 post-collision deviations from w_i C
-       as f32; FP32 arithmetic on small quantities only */
+    /* C as a double-float (two f32) + the q-1 post-collision deviations from
+       w_i C as f32 (delta_0 implied); FP32 arithmetic on small quantities only */
     CL_STORE_FP32 = 0,
     /* C as f32 + a scaled f16 low word, deviations as scaled f16; FP32 arithmetic */
     CL_STORE_FP16DEV = 1,
     /* plain q x f32 populations per cell (reference layout; its steady state
-       carries an FP32 rounding floor that grows with the box); the one
-       storage of the D3Q19 lattice */
+       carries an FP32 rounding floor that grows with the box) */
     CL_STORE_FP32POP = 2
 } cl_storage;
 
-/* Velocity set (Eq. 22).  D3Q19 needs storage CL_STORE_FP32POP and cannot
-   join a batch. */
+/* Velocity set (Eq. 22).  Both lattices take every storage mode; D3Q19
+   handles cannot join a batch. */
 typedef enum { CL_LATTICE_D3Q7 = 0, CL_LATTICE_D3Q19 = 1 } cl_lattice;
 
 /* What the solve transports.  O2: the pore space (pore 0 and micropore 3,

@@ -161,6 +161,10 @@ Q19Args make_args19(cl_lbm* h) {
     a.bc_out = h->p.bc_out;
     a.Csnap = h->Csnap;
     a.partials = h->partials;
+    a.s_lo = h->s_lo;
+    a.inv_lo = 1.0f / h->s_lo;
+    a.s_d = h->s_d;
+    a.inv_d = 1.0f / h->s_d;
     return a;
 }
 
@@ -246,6 +250,13 @@ cl_status enqueue_steps(cl_lbm* h, long long n, bool reduce, cudaStream_t s, int
             const bool red = reduce && i == n - 1;
             MarchArgs a = make_margs(h, *parity ^ 1);
             CK(launch_march(h->p.storage, red, h->maps[*parity], a, h->mgrid, s));
+            *parity ^= 1;
+        }
+    } else if (h->q19s) {
+        Q19Args a = make_args19(h);
+        for (long long i = 0; i < n; ++i) {
+            const bool red = reduce && i == n - 1;
+            CK(launch_step19s(h->p.storage, h->st19[*parity], h->st19[*parity ^ 1], a, red, s));
             *parity ^= 1;
         }
     } else if (h->q == 19) {
@@ -378,6 +389,16 @@ cl_status do_init(cl_lbm* h, const float* C0dev) {
         for (int i = 0; i < 6; ++i) CK(cudaMemsetAsync(o.d[i], 0, (size_t)h->el * h->NP, h->s));
         MarchArgs a = make_margs(h, 0);
         CK(launch_state_init(h->p.storage, a, h->mask_p, C0dev, h->s));
+    } else if (h->q19s) {
+        set_scales(h, cmax);
+        drop_graphs(h);  // the scales are baked into captured kernel arguments
+        // the other time level must hold zeros on inactive cells: sectors without an active cell are never written
+        const Q19State& o = h->st19[1];
+        CK(cudaMemsetAsync(o.chi, 0, sizeof(float) * (size_t)h->NP19, h->s));
+        CK(cudaMemsetAsync(o.clo, 0, (size_t)h->el * h->NP19, h->s));
+        CK(cudaMemsetAsync(o.d, 0, (size_t)h->el * 18 * h->NP19, h->s));
+        Q19Args a = make_args19(h);
+        CK(launch_init19s(h->p.storage, h->st19[0], a, C0dev, h->s));
     } else if (h->q == 19) {
         CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 19 * (size_t)h->NP19, h->s));
         CK(launch_init19(h->pop[0], h->mask19, C0dev, h->nx, h->ny, h->nz, h->px19, h->p.c_in, h->p.c_out, h->Csnap,
@@ -394,6 +415,9 @@ cl_status plane_readout(cl_lbm* h, double* tot /* [5] */) {
     if (h->march) {
         MarchArgs a = make_margs(h, h->cur);
         CK(launch_state_readout(h->p.storage, a, h->mask_p, h->d_plane, h->s));
+    } else if (h->q19s) {
+        Q19Args a = make_args19(h);
+        CK(launch_readout19s(h->p.storage, h->st19[h->cur], a, h->d_plane, h->s));
     } else if (h->q == 19) {
         Q19Args a = make_args19(h);
         CK(launch_readout19(h->pop[h->cur], a, h->d_plane, h->s));
@@ -466,10 +490,6 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
     if (p->carrier != CL_CARRIER_O2 && p->carrier != CL_CARRIER_PROTON) { set_msg_txt("bad carrier"); return CL_ERR_ARG; }
     if (p->lattice != CL_LATTICE_D3Q7 && p->lattice != CL_LATTICE_D3Q19) { set_msg_txt("bad lattice"); return CL_ERR_ARG; }
-    if (p->lattice == CL_LATTICE_D3Q19 && p->storage != CL_STORE_FP32POP) {
-        set_msg_txt("the D3Q19 lattice stores its 19 populations: storage must be CL_STORE_FP32POP");
-        return CL_ERR_ARG;
-    }
     if (p->carrier == CL_CARRIER_PROTON && !(p->D_ionomer > 0 && p->k_ms == 0)) {
         set_msg_txt("the proton carrier needs D_ionomer > 0 (its conductivity) and k_ms = 0");
         return CL_ERR_ARG;
@@ -481,8 +501,9 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     cl_lbm* h = new cl_lbm();
     h->p = *p;
     h->nx = p->nx; h->ny = p->ny; h->nz = p->nz; h->N = N;
-    h->march = p->storage != CL_STORE_FP32POP;
     h->q = p->lattice == CL_LATTICE_D3Q19 ? 19 : 7;
+    h->march = h->q == 7 && p->storage != CL_STORE_FP32POP;
+    h->q19s = h->q == 19 && p->storage != CL_STORE_FP32POP;
     h->el = p->storage == CL_STORE_FP16DEV ? 2 : 4;
     h->s = (cudaStream_t)p->cuda_stream;
     memset(&h->info, 0, sizeof(h->info));
@@ -550,15 +571,30 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
     } else if (h->q == 19) {
         const long long NP = h->NP19;
-        if ((st = dalloc_n(h, &h->pop[0], 19 * NP)) != CL_OK) return fail(st);
-        if ((st = dalloc_n(h, &h->pop[1], 19 * NP)) != CL_OK) return fail(st);
+        if (h->q19s) {
+            for (int b = 0; b < 2; ++b) {
+                if ((st = dalloc_n(h, &h->st19[b].chi, NP)) != CL_OK) return fail(st);
+                if ((st = dalloc(h, &h->st19[b].clo, (size_t)h->el * NP)) != CL_OK) return fail(st);
+                if ((st = dalloc(h, &h->st19[b].d, (size_t)h->el * 18 * NP)) != CL_OK) return fail(st);
+            }
+        } else {
+            if ((st = dalloc_n(h, &h->pop[0], 19 * NP)) != CL_OK) return fail(st);
+            if ((st = dalloc_n(h, &h->pop[1], 19 * NP)) != CL_OK) return fail(st);
+        }
         if ((st = dalloc_n(h, &h->Csnap, NP)) != CL_OK) return fail(st);
         if ((st = dalloc_n(h, &h->mask19, NP)) != CL_OK) return fail(st);
         if ((st = dalloc_n(h, &h->react19, NP)) != CL_OK) return fail(st);
         if ((st = dalloc_n(h, &h->omega19, NP)) != CL_OK) return fail(st);
-        e = cudaMemsetAsync(h->pop[0], 0, sizeof(float) * 19 * (size_t)NP, h->s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 19 * (size_t)NP, h->s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(h->mask19, 0, sizeof(uint32_t) * (size_t)NP, h->s);
+        e = cudaMemsetAsync(h->mask19, 0, sizeof(uint32_t) * (size_t)NP, h->s);
+        for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+            if (h->q19s) {
+                e = cudaMemsetAsync(h->st19[b].chi, 0, sizeof(float) * (size_t)NP, h->s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(h->st19[b].clo, 0, (size_t)h->el * NP, h->s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(h->st19[b].d, 0, (size_t)h->el * 18 * NP, h->s);
+            } else {
+                e = cudaMemsetAsync(h->pop[b], 0, sizeof(float) * 19 * (size_t)NP, h->s);
+            }
+        }
         if (e != cudaSuccess) { set_msg("memset", e); return fail(from_cuda(e)); }
     } else {
         if ((st = dalloc_n(h, &h->pop[0], 7 * N)) != CL_OK) return fail(st);
@@ -791,6 +827,26 @@ static cl_status state_out(cl_lbm* h, float* C, float* g, int ptr_is_device) {
             cudaError_t e = launch_state_out(h->p.storage, a, h->mask_p, nullptr, (float*)tmp, h->s);
             if (e == cudaSuccess) e = cudaMemcpyAsync(g, tmp, sizeof(float) * 7 * N, cudaMemcpyDeviceToHost, h->s);
             cudaFreeAsync(tmp, h->s);
+            if (e != cudaSuccess) { set_msg("populations", e); return from_cuda(e); }
+        }
+    } else if (h->q19s) {
+        Q19Args a = make_args19(h);
+        if (C) {
+            float* dstp = ptr_is_device ? C : h->fbuf;
+            CK(launch_out19s(h->p.storage, h->st19[h->cur], a, dstp, nullptr, h->s));
+            if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * N, cudaMemcpyDeviceToHost, h->s));
+        }
+        if (g) {
+            float* gd = g;
+            void* tmp = nullptr;
+            if (!ptr_is_device) {
+                CK(cudaMallocAsync(&tmp, sizeof(float) * 19 * N, h->s));
+                gd = (float*)tmp;
+            }
+            cudaError_t e = launch_out19s(h->p.storage, h->st19[h->cur], a, nullptr, gd, h->s);
+            if (e == cudaSuccess && !ptr_is_device)
+                e = cudaMemcpyAsync(g, gd, sizeof(float) * 19 * N, cudaMemcpyDeviceToHost, h->s);
+            if (tmp) cudaFreeAsync(tmp, h->s);
             if (e != cudaSuccess) { set_msg("populations", e); return from_cuda(e); }
         }
     } else if (h->q == 19) {

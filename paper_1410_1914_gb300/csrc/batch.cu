@@ -169,6 +169,7 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
         const cl_lbm* h = members[i];
         if (!h) { set_msg_txt("NULL member"); return CL_ERR_ARG; }
         if (!h->have_structure) { set_msg_txt("member without a structure"); return CL_ERR_STATE; }
+        if (h->q != 7) { set_msg_txt("batch members must use the D3Q7 lattice"); return CL_ERR_ARG; }
         if (!h->march) { set_msg_txt("batch members need FP32 or FP16 (C, delta) storage"); return CL_ERR_ARG; }
         if (h->p.storage != h0->p.storage || h->p.check_every != h0->p.check_every) {
             set_msg_txt("batch members must share storage mode and check_every");

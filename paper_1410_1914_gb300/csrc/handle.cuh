@@ -68,6 +68,8 @@ struct cl_lbm {
     long long NP19 = 0;
     uint32_t *mask19 = nullptr, *react19 = nullptr;
     float* omega19 = nullptr;
+    bool q19s = false;  // D3Q19 on the (C, delta) state (FP32 or FP16 storage)
+    cl::Q19State st19[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     // (C, delta) layout
     cl::MState st[2];
     uint16_t* mask_p = nullptr;

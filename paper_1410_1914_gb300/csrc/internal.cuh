@@ -53,6 +53,15 @@ struct Q19Args {
     int bc_in, bc_out;
     float* Csnap;         // padded (reduction)
     double* partials;     // [blocks][RED_N] (reduction)
+    float s_lo, inv_lo, s_d, inv_d;  // FP16 state scales (1 otherwise)
+};
+
+// One time level of the D3Q19 (C, delta) state in the padded layout:
+// hi f32, lo (f32 | f16 * s_lo), 18 deviation planes (f32 | f16 * s_d).
+struct Q19State {
+    float* chi;
+    void* clo;
+    void* d;
 };
 
 cudaError_t launch_masks19(const uint8_t* phase, const uint8_t* active, const uint8_t* react_in, int rule,
@@ -67,6 +76,11 @@ cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool r
 cudaError_t launch_readout19(const float* pop, const Q19Args& a, double* out, cudaStream_t s);
 cudaError_t launch_out19(const float* pop, const uint32_t* mask, int nx, int ny, int nz, int px, float* C, float* g,
                          cudaStream_t s);
+cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst, const Q19Args& a, bool reduce,
+                           cudaStream_t s);
+cudaError_t launch_init19s(int storage, const Q19State& st, const Q19Args& a, const float* C0, cudaStream_t s);
+cudaError_t launch_readout19s(int storage, const Q19State& st, const Q19Args& a, double* out, cudaStream_t s);
+cudaError_t launch_out19s(int storage, const Q19State& st, const Q19Args& a, float* C, float* g, cudaStream_t s);
 cudaError_t launch_links_out(const uint32_t* mask19, const uint32_t* react19, const uint16_t* mask7, int nx, int ny,
                              int nz, int px, uint32_t* wall, uint32_t* react, cudaStream_t s);
 

@@ -172,17 +172,22 @@ cudaError_t launch_init19(float* pop, const uint32_t* mask, const float* C0, int
 // arriving at x is pulled from x - c_i (open link), or rebuilt from the
 // cell's own post-collision population of the opposite direction (wall or
 // boundary link); then C = sum g_i and g*_i = g_i - omega (g_i - a_i C).
+// Each link first selects the element to read (the neighbour's population,
+// or its own opposite one) and loads it unconditionally, so the 18 loads of
+// a cell are independent and all in flight at once; the boundary rules are
+// applied to the loaded values afterwards.  Element offsets are 32-bit
+// (I = uint32_t) while 19 padded planes fit, 64-bit otherwise.
 // Stores: the lanes of a 32-byte sector (8 cells; the pitch is a multiple
 // of 32 cells) all store when any of them is active, none otherwise, so
 // that no sector is written in part (inactive cells store their zeros).
-template <bool REDUCE>
+template <bool REDUCE, class I>
 __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict__ src, float* __restrict__ dst,
                                                         Q19Args a) {
     const int x = blockIdx.x * kQ19Threads + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
-    const long long NP = a.NP;
-    const long long c = x + (long long)px * (y + (long long)ny * z);
+    const I NP = (I)a.NP;
+    const I c = (I)x + (I)px * ((I)y + (I)ny * (I)z);
     const bool in_row = x < px;
     const uint32_t m = in_row ? a.mask[c] : 0u;
     const bool act = (m & kQ19Active) != 0;
@@ -195,30 +200,38 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
     if (act) {
         const uint32_t rb = (m & kQ19HasReact) ? a.react[c] : 0u;
-        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-        float g[19];
-        g[0] = src[c];
+        // offsets of the rows y -+ 1 and planes z -+ 1 (periodic), relative to c
+        const I plane = (I)px * (I)ny;
+        const I oym = y == 0 ? (I)(ny - 1) * (I)px : (I)0 - (I)px;  // row y - 1
+        const I oyp = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)px : (I)px;
+        const I ozm = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
+        const I ozp = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
+        float v[19];
+        bool own[19];
+        v[0] = src[c];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const int j = q19_opp(i);  // the population arrives through the link toward x + c_j = x - c_i
             const int cx = q19_cx(i), cy = q19_cy(i), cz = q19_cz(i);
+            own[i] = ((m >> (j - 1)) & 1u) || (cx > 0 && x == 0) || (cx < 0 && x == nx - 1);
+            const I s = c - (I)cx + (cy > 0 ? oym : (cy < 0 ? oyp : (I)0)) + (cz > 0 ? ozm : (cz < 0 ? ozp : (I)0));
+            const I e = own[i] ? (I)j * NP + c : (I)i * NP + s;
+            v[i] = src[e];
+        }
+        float g[19];
+        g[0] = v[0];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int j = q19_opp(i);
+            const int cx = q19_cx(i);
             const float wi = q19_w(i);
-            if (m & (1u << (j - 1))) {
-                const float o = src[(long long)j * NP + c];
-                g[i] = (rb & (1u << (j - 1))) ? a.rfac * o : o;
-            } else if (cx > 0 && x == 0) {
-                const float o = src[(long long)j * NP + c];
-                g[i] = a.bc_in == CL_BC_DIRICHLET ? 2.f * wi * a.c_in - o : o;
-            } else if (cx < 0 && x == nx - 1) {
-                const float o = src[(long long)j * NP + c];
-                g[i] = a.bc_out == CL_BC_DIRICHLET ? 2.f * wi * a.c_out - o : o;
-            } else {
-                const int sy = cy > 0 ? ym : (cy < 0 ? yp : y);
-                const int sz = cz > 0 ? zm : (cz < 0 ? zp : z);
-                const long long s = (x - cx) + (long long)px * (sy + (long long)ny * sz);
-                g[i] = src[(long long)i * NP + s];
+            float o = v[i];
+            if (own[i]) {
+                if ((m >> (j - 1)) & 1u) o = ((rb >> (j - 1)) & 1u) ? a.rfac * o : o;
+                else if (cx > 0) o = a.bc_in == CL_BC_DIRICHLET ? 2.f * wi * a.c_in - o : o;
+                else o = a.bc_out == CL_BC_DIRICHLET ? 2.f * wi * a.c_out - o : o;
             }
+            g[i] = o;
         }
         // C = sum g_i in a fixed pairwise order
         const float C = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) +
@@ -252,7 +265,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
     const unsigned vote = __ballot_sync(0xffffffffu, act);
     if (in_row && ((vote >> (lane & ~7u)) & 0xFFu)) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) dst[(long long)i * NP + c] = h[i];
+        for (int i = 0; i < 19; ++i) dst[(I)i * NP + c] = h[i];
     }
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
@@ -269,8 +282,15 @@ int step19_blocks(const Q19Args& a) {
 
 cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool reduce, cudaStream_t s) {
     const dim3 g = step19_grid(a);
-    if (reduce) k_step19<true><<<g, kQ19Threads, 0, s>>>(src, dst, a);
-    else k_step19<false><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+    // 32-bit element offsets while every offset into the 19 planes fits
+    const bool narrow = 19LL * a.NP < (1LL << 32);
+    if (narrow) {
+        if (reduce) k_step19<true, uint32_t><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+        else k_step19<false, uint32_t><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+    } else {
+        if (reduce) k_step19<true, unsigned long long><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+        else k_step19<false, unsigned long long><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+    }
     return cudaGetLastError();
 }
 

@@ -2,10 +2,14 @@
 C ABI (gpu).
 
 Integer set-up products (active set, wall and reactive link classes) must
-match bit for bit; floating-point results within the FP32 rounding of the 19
-stored populations (ulps of O(1) values per step, as for the D3Q7
-population storage).  Sizes span several 128-cell x blocks and 8-cell
-store sectors with ragged tails.
+match bit for bit; floating-point results within the bounds of each storage
+mode, as for D3Q7:
+  fp32     C as double-float, 18 f32 deviations: the f32 rounding of the
+           returned O(1) field;
+  fp16dev  deviations as scaled f16 (11-bit significand);
+  fp32pop  19 plain f32 populations: ulps of O(1) values per step.
+Sizes span several 128-cell x blocks and 8-cell store sectors with ragged
+tails.
 """
 import json
 import os
@@ -19,24 +23,25 @@ from paper_1410_1914_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-STORAGE = "fp32pop"
+STORAGES = ["fp32", "fp16dev", "fp32pop"]
 C19 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1),
        (1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1),
        (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
 A19 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
 
 
-def _solver(shape, **params):
+def _solver(shape, storage="fp32pop", **params):
     from paper_1410_1914_gb300 import Solver
-    return Solver(shape, storage=STORAGE, lattice="d3q19", **params)
+    return Solver(shape, storage=storage, lattice="d3q19", **params)
 
 
 def _oracle(ph, react=None, **params):
     return oracle.OracleLBM(ph, react=react, lattice=1, **params)
 
 
-def _tol(steps):
-    return 2e-6 + 1e-7 * steps
+def _tol(steps, storage="fp32pop"):
+    return {"fp32": 1e-7 + 1e-10 * steps, "fp16dev": 8e-5 + 1e-7 * steps,
+            "fp32pop": 2e-6 + 1e-7 * steps}[storage]
 
 
 CASES = {
@@ -101,35 +106,38 @@ def test_all_pore_solid_rule_equals_the_full_mask(cuda_lib):
     assert a.links()[1].any()
 
 
+@pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("name", sorted(CASES))
 @pytest.mark.parametrize("steps", [1, 2, 10, 150])
-def test_trajectory(cuda_lib, name, steps):
+def test_trajectory(cuda_lib, storage, name, steps):
     ph, react, params = _case(name)
-    s = _solver(ph.shape, **params)
+    s = _solver(ph.shape, storage, **params)
     s.set_structure(ph, react)
     s.step(steps)
     o = _oracle(ph, react, **params)
     o.step(steps)
-    tol = _tol(steps)
+    tol = _tol(steps, storage)
     np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=tol)
     fg, fo = s.fluxes(), o.fluxes()
     nyz = ph.shape[0] * ph.shape[1]
-    floor = 6e-8 * nyz + 1e-7
+    ftol = {"fp32": 1e-6, "fp16dev": 5e-4, "fp32pop": 2e-5}[storage]
+    floor = {"fp32": 1e-9, "fp16dev": 2e-6, "fp32pop": 6e-8}[storage] * nyz + 1e-7
     assert fg["n_active"] == fo["n_active"]
     for k in ("J_in", "J_out"):
-        assert abs(fg[k] - fo[k]) <= 2e-5 * max(abs(fo["J_in"]), 1e-30) + floor
-    assert abs(fg["R"] - fo["R"]) <= 2e-5 * max(abs(fo["R"]), 1e-30) + floor
-    assert fg["sum_C"] == pytest.approx(fo["sum_C"], rel=2e-5)
+        assert abs(fg[k] - fo[k]) <= ftol * max(abs(fo["J_in"]), 1e-30) + floor
+    assert abs(fg["R"] - fo["R"]) <= ftol * max(abs(fo["R"]), 1e-30) + floor
+    assert fg["sum_C"] == pytest.approx(fo["sum_C"], rel=max(ftol, 1e-6))
     tg, pRg, pCg = s.reaction_rate()
     to, pRo, pCo = o.reaction_rate()
-    assert tg == pytest.approx(to, rel=2e-5, abs=1e-30)
+    assert tg == pytest.approx(to, rel=ftol, abs=1e-30)
     np.testing.assert_allclose(pCg, pCo, atol=tol)
     s.close()
 
 
+@pytest.mark.parametrize("storage", STORAGES)
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 5), (2, 1, 33), (5, 9, 1), (4, 8, 32), (1, 16, 128),
                                    (2, 3, 129)])
-def test_degenerate_boxes(cuda_lib, shape):
+def test_degenerate_boxes(cuda_lib, storage, shape):
     """Single cells, single rows and planes (a diagonal then wraps onto its
     own row), rows of exactly one block or one cell over."""
     rng = np.random.default_rng(sum(shape))
@@ -137,20 +145,21 @@ def test_degenerate_boxes(cuda_lib, shape):
     ph[..., 0] = 0
     react = rng.integers(0, 64, shape).astype(np.uint8)
     params = dict(dx_m=1e-8, D_bulk=1e-5, k_ms=40.0, c_in=1.0, c_out=0.25)
-    s = _solver(shape, **params)
+    s = _solver(shape, storage, **params)
     s.set_structure(ph, react)
     s.step(37)
     o = _oracle(ph, react, **params)
     o.step(37)
-    np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(37))
+    np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(37, storage))
 
 
-def test_populations_layout_and_seed_spread(cuda_lib):
+@pytest.mark.parametrize("storage", STORAGES)
+def test_populations_layout_and_seed_spread(cuda_lib, storage):
     """Populations come back as [19][nz][ny][nx] in the order of Eq. 22 as
     listed in the header: after one step from a single seeded cell at tau = 1
     cell x + c_i holds a_i C0 in population i (the Eq. 23 weights)."""
     ph = np.zeros((7, 7, 40), np.uint8)
-    s = _solver(ph.shape, dx_m=1e-8, D_bulk=1e-5, tau_ref=1.0, bc_in=1, bc_out=1)
+    s = _solver(ph.shape, storage, dx_m=1e-8, D_bulk=1e-5, tau_ref=1.0, bc_in=1, bc_out=1)
     s.set_structure(ph)
     C0 = np.zeros(ph.shape, np.float32)
     C0[3, 3, 20] = 1.0
@@ -161,45 +170,74 @@ def test_populations_layout_and_seed_spread(cuda_lib):
     # post-collision populations at tau = 1 are a_j C at each cell: cell
     # x + c_i received C = a_i, so its population j holds a_j a_i
     for i, (cx, cy, cz) in enumerate(C19):
-        np.testing.assert_allclose(g[:, 3 + cz, 3 + cy, 20 + cx], A19 * A19[i], rtol=1e-6)
+        np.testing.assert_allclose(g[:, 3 + cz, 3 + cy, 20 + cx], A19 * A19[i], rtol=1e-6 if storage != "fp16dev" else 2e-3,
+                                   atol=1e-12 if storage != "fp16dev" else 1e-6)
     np.testing.assert_allclose(g.sum(axis=0), s.field(), atol=1e-7)
     assert abs(s.field().sum() - 1.0) < 1e-6
 
 
-def test_custom_init_and_step_counter(cuda_lib):
+@pytest.mark.parametrize("storage", STORAGES)
+def test_custom_init_and_step_counter(cuda_lib, storage):
     ph, react, params = _case("pt_deff")
     rng = np.random.default_rng(0)
     C0 = rng.random(ph.shape).astype(np.float32)
-    s = _solver(ph.shape, **params)
+    s = _solver(ph.shape, storage, **params)
     s.set_structure(ph, react)
     s.init(C0)
     s.step(65)  # one 64-step graph + one single step
     o = _oracle(ph, react, **params)
     o.init_field(C0.astype(np.float64))
     o.step(65)
-    np.testing.assert_allclose(s.field(), o.concentration(), atol=_tol(65) * 10)
+    np.testing.assert_allclose(s.field(), o.concentration(), atol=_tol(65, storage) * 10)
     assert s.steps == 65
 
 
-def test_storage_and_batch_limits(cuda_lib):
+def test_lattice_and_batch_limits(cuda_lib):
     from paper_1410_1914_gb300 import Solver
+    from paper_1410_1914_gb300.batch import Batch
     from paper_1410_1914_gb300._lib import ClError
     with pytest.raises(ClError):
-        Solver((4, 4, 8), storage="fp32", lattice="d3q19")
-    with pytest.raises(ClError):
         Solver((4, 4, 8), storage="fp32pop", lattice=2)
+    ph, react, params = _case("thin")
+    s = _solver(ph.shape, "fp32", **params)
+    s.set_structure(ph, react)
+    with pytest.raises(ClError):
+        Batch([s])
 
 
-def test_converged_deff_small_workload(cuda_lib):
-    """48^3 plain-method workload on D3Q19: GPU solve vs the converged FP64
-    oracle D_eff (tests/golden/c1_deff_d3q19.json) to 1e-3 relative."""
+@pytest.mark.parametrize("storage,rel", [("fp32", 1e-3), ("fp16dev", 5e-3)])
+def test_converged_deff_small_workload_state(cuda_lib, storage, rel):
+    """48^3 plain-method workload on D3Q19 with the (C, delta) state: the
+    stopping rule fires and the GPU D_eff matches the converged FP64
+    oracle (tests/golden/c1_deff_d3q19.json): 1e-3 relative for FP32, 5e-3
+    for FP16 storage."""
     with open(os.path.join(HERE, "golden", "c1_deff_d3q19.json")) as fh:
         gold = json.load(fh)
     ph, react, params = inputs.make_workload("pt_cl_48")
-    s = _solver(ph.shape, check_every=200, tol_rel=1e-5, tol_flux=1e-4, max_steps=3_000_000, **params)
+    s = _solver(ph.shape, storage, check_every=200, tol_rel=1e-5, tol_flux=1e-4, max_steps=3_000_000, **params)
     s.set_structure(ph, react)
     info = s.solve()
     assert info["converged"] == 1, info
+    d, ratio = s.effective_diffusivity()
+    assert ratio == pytest.approx(gold["D_eff_over_Db"], rel=rel)
+    assert d == pytest.approx(gold["D_eff_m2s"], rel=rel)
+
+
+def test_converged_deff_small_workload(cuda_lib):
+    """48^3 plain-method workload on D3Q19: D_eff after 300,000 steps (ten
+    times what the FP64 oracle needs to a relative change of 1e-8 per 100
+    steps) against the converged FP64 oracle (tests/golden/c1_deff_d3q19.json),
+    1e-3 relative.  The 19 plain f32 populations stall at an FP32 rounding
+    floor: the outlet flux is right to ~2e-4, but the inlet and outlet
+    fluxes keep a ~6e-4 imbalance, so the flux-balance test of the stopping
+    rule (1e-4) does not fire, as for the D3Q7 populations."""
+    with open(os.path.join(HERE, "golden", "c1_deff_d3q19.json")) as fh:
+        gold = json.load(fh)
+    ph, react, params = inputs.make_workload("pt_cl_48")
+    s = _solver(ph.shape, check_every=200, tol_rel=1e-5, tol_flux=1e-4, **params)
+    s.set_structure(ph, react)
+    info = s.solve_budget(300_000)
+    assert info["steps"] == 300_000
     d, ratio = s.effective_diffusivity()
     assert ratio == pytest.approx(gold["D_eff_over_Db"], rel=1e-3)
     assert d == pytest.approx(gold["D_eff_m2s"], rel=1e-3)
@@ -253,21 +291,22 @@ def _stencil_deff_uniform(solid):
 
 def test_sphere_in_cube_96(cuda_lib):
     """The validation geometry of Sec. 5.1, which the paper computed on this
-    lattice (0.3317 at 200^3): at 96^3 the converged GPU D_eff equals the
-    lattice's own tau = 1 steady state to the FP32 population floor and lies
-    within 4 % of the printed value."""
+    lattice (0.3317 at 200^3): at 96^3 the converged GPU D_eff (FP32 state)
+    equals the lattice's own tau = 1 steady state to 5e-5 and lies within
+    4 % of the printed value."""
     n = 96
     c = (np.arange(n) + 0.5) - n / 2
     z, y, x = np.meshgrid(c, c, c, indexing="ij")
     solid = (x * x + y * y + z * z) < (n / 2) ** 2
     ph = solid.astype(np.uint8)
-    with _solver(ph.shape, D_bulk=1e-5, knudsen=0, tau_ref=1.0, check_every=500, tol_rel=1e-7, tol_flux=1e-6,
-                 max_steps=3_000_000) as s:
+    with _solver(ph.shape, "fp32", D_bulk=1e-5, knudsen=0, tau_ref=1.0, check_every=500, tol_rel=1e-7,
+                 tol_flux=1e-6, max_steps=3_000_000) as s:
         s.set_structure(ph)
         info = s.solve()
+        assert info["status"] == "CL_OK", info
         _, d_rel = s.effective_diffusivity()
     ref_stencil = _stencil_deff_uniform(solid)
-    assert d_rel == pytest.approx(ref_stencil, rel=1e-3), (info, d_rel, ref_stencil)
+    assert d_rel == pytest.approx(ref_stencil, rel=5e-5), (info, d_rel, ref_stencil)
     with open(os.path.join(HERE, "golden", "paper_values.json")) as fh:
         ref = json.load(fh)["sphere_in_cube_deff"]["value"]
     assert d_rel == pytest.approx(ref, rel=0.04)
