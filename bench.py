@@ -372,8 +372,12 @@ def run_converge(args):
     K = args.check_every
     max_steps = args.max_steps
 
+    if args.lattice == "d3q19":
+        label += ", D3Q19 lattice"
+
     def solver(storage):
-        s = Solver(ph.shape, storage=storage, stream=int(stream.cuda_stream), check_every=K, **params)
+        s = Solver(ph.shape, storage=storage, stream=int(stream.cuda_stream), check_every=K, lattice=args.lattice,
+                   **params)
         s.set_structure(ph, react)
         return s
 
@@ -416,7 +420,8 @@ def run_converge(args):
     best = out.get("fp16dev+warm", out["fp16dev"])["seconds_to_1e-3"]
     line = {"metric": "time-to-converged D_eff (rel 1e-3)" if args.carrier == "o2"
             else "time-to-converged effective proton conductivity (rel 1e-3)", "unit": "s", "higher_is_better": False,
-            "workload": label, "shape_zyx": list(ph.shape), "reference_D_eff_over_Db": ref, "check_every": K,
+            "workload": label, "shape_zyx": list(ph.shape), "lattice": args.lattice, "reference_D_eff_over_Db": ref,
+            "check_every": K,
             "by_arm": out,
             "fp16_warm_vs_plain_fp32": (None if plain is None or best is None else plain / best),
             "fp16_warm_vs_fp32_state_ramp": (None if state32 is None or best is None else state32 / best),
