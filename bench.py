@@ -708,7 +708,7 @@ def main():
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": launch_bytes,
                      "kernel": ("k_step19" if args.lattice == "d3q19" and args.storage == "fp32pop" else
-                                "k_march19s" if args.lattice == "d3q19" else
+                                "k_step19s" if args.lattice == "d3q19" else
                                 "k_step_fp32" if args.storage == "fp32pop" else "k_march")},
         "gpu_launches": args.steps * (K + 1),
         "clocks": clocks.summary(),

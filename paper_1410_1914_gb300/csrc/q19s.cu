@@ -16,10 +16,9 @@
 //     delta'_i = (1 - omega) (e_i - a_i dC)
 // which is the BGK step rewritten exactly; delta_0 is implied, so the mass
 // of a cell is exact by construction.  Link classes, layout and store
-// sectors as in q19.cu.  Each link reads the (hi, lo) of the cell its
-// population comes from (its own cell for wall and boundary links) from a
-// shared-memory ring of planes, and that cell's deviation from global
-// memory, unconditionally, so a cell's loads are all in flight together.
+// sectors as in q19.cu; each link loads (hi, lo, delta) of the cell its
+// population comes from (its own cell for wall and boundary links)
+// unconditionally, so a cell's loads are all in flight together.
 #include <cuda_fp16.h>
 #include <math.h>
 
@@ -76,183 +75,126 @@ __device__ __forceinline__ void df_add19(float hi, float lo, float d, float& ho,
 
 }  // namespace
 
-// ------------------------------------------------------- plane-marching step
+// ------------------------------------------------------------------- step
 // Values stay in storage units inside the update: lo scaled by s_lo and the
 // deviations by s_d (both 1 for FP32), so nothing is rescaled on its way in
-// or out.  The (hi, lo) of the source cells come from shared memory: a
-// block owns a 32 x 8 column of cells and marches along z through
-// a chunk of planes, keeping the (hi, lo) of planes z - 1, z, z + 1 of its
-// column plus a one-cell halo (y and z wrap) in a ring of three slots.
-// Each plane is loaded once per block by all threads (coalesced, about 1.3
-// loads a cell), so a cell's own work is its 18 own and 18 source
-// deviations from global memory and 36 shared-memory reads.  Only block
-// barriers order the ring; nothing waits on a flag.
-constexpr int kM19X = 32, kM19Y = 8, kM19HX = kM19X + 2, kM19HY = kM19Y + 2;
-
+// or out.
 template <class S, bool REDUCE, class I>
-__global__ void __launch_bounds__(kM19X * kM19Y) k_march19s(Q19State src, Q19State dst, Q19Args a, int z_chunk) {
+__global__ void __launch_bounds__(kQ19Threads) k_step19s(Q19State src, Q19State dst, Q19Args a) {
     using T = typename S::T;
     constexpr bool HALF = sizeof(T) == 2;
-    __shared__ float hs[3][kM19HY][kM19HX];
-    __shared__ float ls[3][kM19HY][kM19HX];
-    const int tx = threadIdx.x, ty = threadIdx.y, tid = tx + kM19X * ty;
-    const int x0 = blockIdx.x * kM19X, y0 = blockIdx.y * kM19Y;
-    const int z0 = blockIdx.z * z_chunk;
+    const int x = blockIdx.x * kQ19Threads + threadIdx.x;
+    const int y = blockIdx.y, z = blockIdx.z;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
-    const int z1 = min(nz, z0 + z_chunk);
-    const int x = x0 + tx, y = y0 + ty;
-    const bool in_tile = x < px && y < ny;
     const I NP = (I)a.NP;
+    const I c = (I)x + (I)px * ((I)y + (I)ny * (I)z);
+    const bool in_row = x < px;
+    const uint32_t m = in_row ? a.mask[c] : 0u;
+    const bool act = (m & kQ19Active) != 0;
     const float inv_lo = HALF ? a.inv_lo : 1.f, s_lo = HALF ? a.s_lo : 1.f;
     const float s_d = HALF ? a.s_d : 1.f, inv_d = HALF ? a.inv_d : 1.f;
     const T* __restrict__ slo = reinterpret_cast<const T*>(src.clo);
     const T* __restrict__ sd = reinterpret_cast<const T*>(src.d);
-    T* __restrict__ dlo = reinterpret_cast<T*>(dst.clo);
-    T* __restrict__ ddv = reinterpret_cast<T*>(dst.d);
+    float hnew = 0.f, lnew_s = 0.f;
+    float dn[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) dn[i] = 0.f;
     double rv[RED_N];
     if (REDUCE)
 #pragma unroll
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
-
-    // (hi, lo) of plane zz into ring slot k: cells x0-1 .. x0+32, y0-1 .. y0+8
-    auto load_plane = [&](int k, int zz) {
-        const int gz = ((zz % nz) + nz) % nz;
-        for (int idx = tid; idx < kM19HX * kM19HY; idx += kM19X * kM19Y) {
-            const int lyy = idx / kM19HX, lxx = idx - lyy * kM19HX;
-            const int gx = x0 - 1 + lxx;
-            const int gy = (((y0 - 1 + lyy) % ny) + ny) % ny;
-            float h = 0.f, l = 0.f;
-            if (gx >= 0 && gx < px) {
-                const I p = (I)gx + (I)px * ((I)gy + (I)ny * (I)gz);
-                h = src.chi[p];
-                l = S::ld(slo[p]);
+    if (act) {
+        const uint32_t rb = (m & kQ19HasReact) ? a.react[c] : 0u;
+        const I plane = (I)px * (I)ny;
+        const I oym = y == 0 ? (I)(ny - 1) * (I)px : (I)0 - (I)px;
+        const I oyp = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)px : (I)px;
+        const I ozm = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
+        const I ozp = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
+        const float hx = src.chi[c];
+        const float lxs = S::ld(slo[c]);
+        const float lx = lxs * inv_lo;
+        const float Cx = hx + lx;
+        const float rf = a.rfac;
+        // own deviations: their sum is -delta_0
+        float sdd = 0.f;
+#pragma unroll
+        for (int i = 0; i < 18; ++i) sdd += S::ld(sd[(I)i * NP + c]);
+        // per link: (hi, lo, delta) of the cell the population comes from, then e_i
+        float ev[18];
+#pragma unroll
+        for (int i = 1; i < 19; ++i) {
+            const int j = s19_opp(i);
+            const int cx = s19_cx(i), cy = s19_cy(i), cz = s19_cz(i);
+            const bool wall = (m >> (j - 1)) & 1u;
+            const bool own = wall || (cx > 0 && x == 0) || (cx < 0 && x == nx - 1);
+            const I s = c - (I)cx + (cy > 0 ? oym : (cy < 0 ? oyp : (I)0)) + (cz > 0 ? ozm : (cz < 0 ? ozp : (I)0));
+            const I e = own ? c : s;
+            const float nh = src.chi[e];
+            const float nl = S::ld(slo[e]);
+            const float nd = S::ld(sd[(I)((own ? j : i) - 1) * NP + e]);
+            const float ws = s19_w(i) * s_d;
+            // open link; for an own link nh = hx, nl = lxs and nd = delta_opp: the inert wall value
+            float ei = ws * ((nh - hx) + (nl - lxs) * inv_lo) + nd;
+            if (own) {
+                if (wall) {
+                    if ((rb >> (j - 1)) & 1u) ei = fmaf(rf, nd, -(1.0f - rf) * ws * Cx);
+                } else if (cx > 0) {
+                    if (a.bc_in == CL_BC_DIRICHLET) ei = 2.0f * ws * ((a.c_in - hx) - lx) - nd;
+                } else {
+                    if (a.bc_out == CL_BC_DIRICHLET) ei = 2.0f * ws * ((a.c_out - hx) - lx) - nd;
+                }
             }
-            hs[k][lyy][lxx] = h;
-            ls[k][lyy][lxx] = l;
+            ev[i - 1] = ei;
         }
-    };
-    load_plane(0, z0 - 1);
-    load_plane(1, z0);
-    const int ym = y == 0 ? ny - 1 : y - 1, yp = y >= ny - 1 ? 0 : y + 1;
-    for (int z = z0; z < z1; ++z) {
-        const int kc = (z - z0 + 1) % 3, km = (z - z0) % 3, kp = (z - z0 + 2) % 3;
-        load_plane(kp, z + 1);
-        __syncthreads();
-        const I c = (I)x + (I)px * ((I)y + (I)ny * (I)z);
-        const uint32_t m = in_tile ? a.mask[c] : 0u;
-        const bool act = (m & kQ19Active) != 0;
-        float hnew = 0.f, lnew_s = 0.f;
-        float dn[18];
+        float se = 0.f;
 #pragma unroll
-        for (int i = 0; i < 18; ++i) dn[i] = 0.f;
-        if (act) {
-            const uint32_t rb = (m & kQ19HasReact) ? a.react[c] : 0u;
-            const I plane = (I)px * (I)ny;
-            const I oym = (I)ym * (I)px - (I)y * (I)px;  // row y - 1 relative to row y (mod 2^bits)
-            const I oyp = (I)yp * (I)px - (I)y * (I)px;
-            const I ozm = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
-            const I ozp = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
-            const float hx = hs[kc][ty + 1][tx + 1];
-            const float lxs = ls[kc][ty + 1][tx + 1];
-            const float lx = lxs * inv_lo;
-            const float Cx = hx + lx;
-            const float rf = a.rfac;
-            float sdd = 0.f;
+        for (int i = 0; i < 18; ++i) se += ev[i];
+        const float dCs = se - sdd;  // sum e_i + delta_0, storage units
+        float lnew;
+        df_add19(hx, lx, dCs * inv_d, hnew, lnew);
+        lnew_s = lnew * s_lo;
+        const float om1 = 1.0f - a.omega[c];
 #pragma unroll
-            for (int i = 0; i < 18; ++i) sdd += S::ld(sd[(I)i * NP + c]);
-            float ev[18];
+        for (int i = 1; i < 19; ++i) dn[i - 1] = om1 * (ev[i - 1] - s19_w(i) * dCs);
+        if (REDUCE) {
+            const double id = inv_d;
+            const double Cn = (double)hnew + (double)lnew;
+            double jin = 0.0, jout = 0.0, r = 0.0;
 #pragma unroll
             for (int i = 1; i < 19; ++i) {
-                const int j = s19_opp(i);
-                const int cx = s19_cx(i), cy = s19_cy(i), cz = s19_cz(i);
-                const bool wall = (m >> (j - 1)) & 1u;
-                const bool own = wall || (cx > 0 && x == 0) || (cx < 0 && x == nx - 1);
-                const I s = c - (I)cx + (cy > 0 ? oym : (cy < 0 ? oyp : (I)0)) + (cz > 0 ? ozm : (cz < 0 ? ozp : (I)0));
-                const int kk = cz > 0 ? km : (cz < 0 ? kp : kc);
-                const float nh = own ? hx : hs[kk][ty + 1 - cy][tx + 1 - cx];
-                const float nl = own ? lxs : ls[kk][ty + 1 - cy][tx + 1 - cx];
-                const float nd = S::ld(sd[(I)((own ? j : i) - 1) * NP + (own ? c : s)]);
-                const float ws = s19_w(i) * s_d;
-                float ei = ws * ((nh - hx) + (nl - lxs) * inv_lo) + nd;
-                if (own) {
-                    if (wall) {
-                        if ((rb >> (j - 1)) & 1u) ei = fmaf(rf, nd, -(1.0f - rf) * ws * Cx);
-                    } else if (cx > 0) {
-                        if (a.bc_in == CL_BC_DIRICHLET) ei = 2.0f * ws * ((a.c_in - hx) - lx) - nd;
-                    } else {
-                        if (a.bc_out == CL_BC_DIRICHLET) ei = 2.0f * ws * ((a.c_out - hx) - lx) - nd;
-                    }
-                }
-                ev[i - 1] = ei;
+                const bool wall = (m >> (i - 1)) & 1u;
+                const double gs = (double)s19_w(i) * Cn + (double)dn[i - 1] * id;  // g*_i
+                if (s19_cx(i) < 0 && x == 0 && !wall && a.bc_in == CL_BC_DIRICHLET)
+                    jin += 2.0 * ((double)s19_w(i) * a.c_in_d - gs);
+                if (s19_cx(i) > 0 && x == nx - 1 && !wall && a.bc_out == CL_BC_DIRICHLET)
+                    jout += 2.0 * (gs - (double)s19_w(i) * a.c_out_d);
+                if (rb & (1u << (i - 1))) r += gs;
             }
-            float se = 0.f;
-#pragma unroll
-            for (int i = 0; i < 18; ++i) se += ev[i];
-            const float dCs = se - sdd;
-            float lnew;
-            df_add19(hx, lx, dCs * inv_d, hnew, lnew);
-            lnew_s = lnew * s_lo;
-            const float om1 = 1.0f - a.omega[c];
-#pragma unroll
-            for (int i = 1; i < 19; ++i) dn[i - 1] = om1 * (ev[i - 1] - s19_w(i) * dCs);
-            if (REDUCE) {
-                const double id = inv_d;
-                const double Cn = (double)hnew + (double)lnew;
-                double jin = 0.0, jout = 0.0, r = 0.0;
-#pragma unroll
-                for (int i = 1; i < 19; ++i) {
-                    const bool wl = (m >> (i - 1)) & 1u;
-                    const double gs = (double)s19_w(i) * Cn + (double)dn[i - 1] * id;
-                    if (s19_cx(i) < 0 && x == 0 && !wl && a.bc_in == CL_BC_DIRICHLET)
-                        jin += 2.0 * ((double)s19_w(i) * a.c_in_d - gs);
-                    if (s19_cx(i) > 0 && x == nx - 1 && !wl && a.bc_out == CL_BC_DIRICHLET)
-                        jout += 2.0 * (gs - (double)s19_w(i) * a.c_out_d);
-                    if (rb & (1u << (i - 1))) r += gs;
-                }
-                rv[RED_JIN] += jin;
-                rv[RED_JOUT] += jout;
-                rv[RED_R] += (1.0 - (double)rf) * r;
-                const float Cf = hnew + lnew;
-                rv[RED_SUMC] += Cf;
-                rv[RED_DC] += fabs((double)Cf - (double)a.Csnap[c]);
-                rv[RED_ABSC] += fabs((double)Cf);
-                rv[RED_NONFINITE] += isfinite(hnew) ? 0.0 : 1.0;
-                a.Csnap[c] = Cf;
-            }
+            rv[RED_JIN] = jin;
+            rv[RED_JOUT] = jout;
+            rv[RED_R] = (1.0 - (double)rf) * r;
+            const float Cf = hnew + lnew;
+            rv[RED_SUMC] = Cf;
+            rv[RED_DC] = fabs((double)Cf - (double)a.Csnap[c]);
+            rv[RED_ABSC] = fabs((double)Cf);
+            rv[RED_NONFINITE] = isfinite(hnew) ? 0.0 : 1.0;
+            a.Csnap[c] = Cf;
         }
-        // a warp is one row of the tile: the 8 lanes of a sector vote as in k_step19
-        const unsigned lane = tid & 31u;
-        const unsigned vote = __ballot_sync(0xffffffffu, act);
-        if (in_tile && ((vote >> (lane & ~7u)) & 0xFFu)) {
-            dst.chi[c] = hnew;
-            dlo[c] = S::st(lnew_s);
+    }
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned vote = __ballot_sync(0xffffffffu, act);
+    if (in_row && ((vote >> (lane & ~7u)) & 0xFFu)) {
+        T* dlo = reinterpret_cast<T*>(dst.clo);
+        T* ddv = reinterpret_cast<T*>(dst.d);
+        dst.chi[c] = hnew;
+        dlo[c] = S::st(lnew_s);
 #pragma unroll
-            for (int i = 0; i < 18; ++i) ddv[(I)i * NP + c] = S::st(dn[i]);
-        }
-        __syncthreads();  // the slot of plane z - 1 is reloaded next
+        for (int i = 0; i < 18; ++i) ddv[(I)i * NP + c] = S::st(dn[i]);
     }
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         block_sum_store<RED_N>(rv, a.partials + blk * RED_N);
     }
-}
-
-// grid of the plane-marching kernel: column tiles x z-chunks, the chunk
-// length chosen so that the grid holds at least two waves of 4 blocks per SM
-dim3 march19s_grid(int px, int ny, int nz, int* z_chunk) {
-    const int gx = (px + kM19X - 1) / kM19X, gy = (ny + kM19Y - 1) / kM19Y;
-    const long long cols = (long long)gx * gy;
-    long long want = (2LL * 152 * 4 + cols - 1) / cols;
-    const int max_chunks = nz >= 16 ? nz / 8 : 1;
-    const int chunks = (int)(want < 1 ? 1 : (want > max_chunks ? max_chunks : want));
-    *z_chunk = (nz + chunks - 1) / chunks;
-    return dim3(gx, gy, (nz + *z_chunk - 1) / *z_chunk);
-}
-
-int march19s_blocks(int px, int ny, int nz) {
-    int zc = 0;
-    const dim3 g = march19s_grid(px, ny, nz, &zc);
-    return (int)(g.x * g.y * g.z);
 }
 
 // ----------------------------------------------------------- init / readout
@@ -350,11 +292,9 @@ __global__ void k_out19s(Q19State st, Q19Args a, float* __restrict__ C, float* _
 // -------------------------------------------------------------- launchers
 cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst, const Q19Args& a, bool reduce,
                            cudaStream_t s) {
-    int zc = 0;
-    const dim3 g = march19s_grid(a.px, a.ny, a.nz, &zc);
-    const dim3 b(kM19X, kM19Y);
+    const dim3 g((a.px + kQ19Threads - 1) / kQ19Threads, a.ny, a.nz);
     const bool narrow = 19LL * a.NP < (1LL << 32);
-#define CL_Q19S(SS, R, II) k_march19s<SS, R, II><<<g, b, 0, s>>>(src, dst, a, zc)
+#define CL_Q19S(SS, R, II) k_step19s<SS, R, II><<<g, kQ19Threads, 0, s>>>(src, dst, a)
     if (storage == CL_STORE_FP16DEV) {
         if (narrow) { if (reduce) CL_Q19S(SF16, true, uint32_t); else CL_Q19S(SF16, false, uint32_t); }
         else { if (reduce) CL_Q19S(SF16, true, unsigned long long); else CL_Q19S(SF16, false, unsigned long long); }
