@@ -390,87 +390,75 @@ cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, 
 //   outlet (x = L,  i = -x): -g*_{+x} + 2 w C_out or g*_{+x}
 //   wall:  g*_{opp}(x) times (2w - k)/(2w + k) if catalytic, else 1.
 // Collide: C = sum g_i, g*_i = g_i - omega (g_i - w_i C).
-template <bool REDUCE>
+// Each population first selects the element it reads (the neighbour's, or
+// the cell's own opposite one across a closed face) and loads it
+// unconditionally, so the six loads of a cell are in flight together; the
+// boundary rules act on the loaded values.  Offsets are 32-bit (I) while
+// the seven planes fit.
+template <bool REDUCE, class I>
 __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src, float* __restrict__ dst,
                                                    StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const long long N = a.N;
+    const I N = (I)a.N;
     double rv[RED_N];
     if (REDUCE)
 #pragma unroll
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
     if (x < nx) {
-        const long long plane = (long long)nx * ny;
-        const long long c = x + (long long)nx * y + plane * z;
+        const I plane = (I)nx * (I)ny;
+        const I c = (I)x + (I)nx * (I)y + plane * (I)z;
         const uint16_t m = a.mask[c];
         if (m & kActiveBit) {
-            const float* s0 = src;
-            const float* s1 = src + N;
-            const float* s2 = src + 2 * N;
-            const float* s3 = src + 3 * N;
-            const float* s4 = src + 4 * N;
-            const float* s5 = src + 5 * N;
-            const float* s6 = src + 6 * N;
             const float rf = a.rfac;
-            float g0 = s0[c];
-            float g1, g2, g3, g4, g5, g6;
-            // +x population arrives from x-1 through the -x face (d = 2, bit 1)
-            if (m & (1u << 1)) {
-                const float o = s2[c];
-                if (x == 0) g1 = a.bc_in == CL_BC_DIRICHLET ? a.abb_in - o : o;
-                else g1 = (m & (1u << (kReactShift + 1))) ? rf * o : o;
-            } else g1 = s1[c - 1];
-            // -x population from x+1 through the +x face (d = 1, bit 0)
-            if (m & (1u << 0)) {
-                const float o = s1[c];
-                if (x == nx - 1) g2 = a.bc_out == CL_BC_DIRICHLET ? a.abb_out - o : o;
-                else g2 = (m & (1u << (kReactShift + 0))) ? rf * o : o;
-            } else g2 = s2[c + 1];
-            // +y from y-1 through the -y face (d = 4, bit 3)
-            if (m & (1u << 3)) { const float o = s4[c]; g3 = (m & (1u << (kReactShift + 3))) ? rf * o : o; }
-            else g3 = s3[y == 0 ? c + (long long)(ny - 1) * nx : c - nx];
-            // -y from y+1 through the +y face (d = 3, bit 2)
-            if (m & (1u << 2)) { const float o = s3[c]; g4 = (m & (1u << (kReactShift + 2))) ? rf * o : o; }
-            else g4 = s4[y == ny - 1 ? c - (long long)(ny - 1) * nx : c + nx];
-            // +z from z-1 through the -z face (d = 6, bit 5)
-            if (m & (1u << 5)) { const float o = s6[c]; g5 = (m & (1u << (kReactShift + 5))) ? rf * o : o; }
-            else g5 = s5[z == 0 ? c + (long long)(nz - 1) * plane : c - plane];
-            // -z from z+1 through the +z face (d = 5, bit 4)
-            if (m & (1u << 4)) { const float o = s5[c]; g6 = (m & (1u << (kReactShift + 4))) ? rf * o : o; }
-            else g6 = s6[z == nz - 1 ? c - (long long)(nz - 1) * plane : c + plane];
-
-            const float C = ((g0 + g1) + (g2 + g3)) + ((g4 + g5) + g6);
+            // source of population i (1..6 = +x, -x, +y, -y, +z, -z): x - c_i, y and z periodic
+            const I sy_m = y == 0 ? (I)(ny - 1) * (I)nx : (I)0 - (I)nx;            // row y - 1
+            const I sy_p = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)nx : (I)nx;       // row y + 1
+            const I sz_m = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
+            const I sz_p = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
+            const I srcoff[7] = {0, (I)0 - (I)1, (I)1, sy_m, sy_p, sz_m, sz_p};
+            float v[7];
+            v[0] = src[c];
+#pragma unroll
+            for (int i = 1; i < 7; ++i) {
+                const int o = ((i - 1) ^ 1) + 1;          // opposite direction
+                const bool closed = (m >> (o - 1)) & 1u;  // the face the population arrives through
+                const I e = closed ? (I)o * N + c : (I)i * N + c + srcoff[i];
+                v[i] = src[e];
+            }
+            float g[7];
+            g[0] = v[0];
+#pragma unroll
+            for (int i = 1; i < 7; ++i) {
+                const int o = ((i - 1) ^ 1) + 1;
+                float gi = v[i];
+                if ((m >> (o - 1)) & 1u) {
+                    if (i == 1 && x == 0) gi = a.bc_in == CL_BC_DIRICHLET ? a.abb_in - gi : gi;
+                    else if (i == 2 && x == nx - 1) gi = a.bc_out == CL_BC_DIRICHLET ? a.abb_out - gi : gi;
+                    else if (m & (1u << (kReactShift + o - 1))) gi = rf * gi;
+                }
+                g[i] = gi;
+            }
+            const float C = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
             const float om = a.omega[c];
             const float e0 = kW0 * C, e1 = kW1 * C;
-            const float h0 = g0 - om * (g0 - e0);
-            const float h1 = g1 - om * (g1 - e1);
-            const float h2 = g2 - om * (g2 - e1);
-            const float h3 = g3 - om * (g3 - e1);
-            const float h4 = g4 - om * (g4 - e1);
-            const float h5 = g5 - om * (g5 - e1);
-            const float h6 = g6 - om * (g6 - e1);
-            dst[c] = h0;
-            dst[N + c] = h1;
-            dst[2 * N + c] = h2;
-            dst[3 * N + c] = h3;
-            dst[4 * N + c] = h4;
-            dst[5 * N + c] = h5;
-            dst[6 * N + c] = h6;
+            float h[7];
+            h[0] = g[0] - om * (g[0] - e0);
+#pragma unroll
+            for (int i = 1; i < 7; ++i) h[i] = g[i] - om * (g[i] - e1);
+#pragma unroll
+            for (int i = 0; i < 7; ++i) dst[(I)i * N + c] = h[i];
             if (REDUCE) {
-                if (x == 0 && a.bc_in == CL_BC_DIRICHLET) rv[RED_JIN] = 2.0 * ((double)a.w_cin - (double)h2);
-                if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h1 - (double)a.w_cout);
+                if (x == 0 && a.bc_in == CL_BC_DIRICHLET) rv[RED_JIN] = 2.0 * ((double)a.w_cin - (double)h[2]);
+                if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h[1] - (double)a.w_cout);
                 const unsigned rb = (m >> kReactShift) & 0x3fu;
                 if (rb) {
                     const double sink = 1.0 - (double)rf;
                     double r = 0.0;
-                    if (rb & 1u) r += h1;
-                    if (rb & 2u) r += h2;
-                    if (rb & 4u) r += h3;
-                    if (rb & 8u) r += h4;
-                    if (rb & 16u) r += h5;
-                    if (rb & 32u) r += h6;
+#pragma unroll
+                    for (int d = 0; d < 6; ++d)
+                        if (rb & (1u << d)) r += h[d + 1];
                     rv[RED_R] = sink * r;
                 }
                 const double Cd = C;
@@ -497,8 +485,13 @@ int step_fp32_blocks(const StepArgs& a) {
 
 cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce, cudaStream_t s) {
     const dim3 g = step_grid(a);
-    if (reduce) k_step_fp32<true><<<g, 128, 0, s>>>(src, dst, a);
-    else k_step_fp32<false><<<g, 128, 0, s>>>(src, dst, a);
+    if (7LL * a.N < (1LL << 32)) {
+        if (reduce) k_step_fp32<true, uint32_t><<<g, 128, 0, s>>>(src, dst, a);
+        else k_step_fp32<false, uint32_t><<<g, 128, 0, s>>>(src, dst, a);
+    } else {
+        if (reduce) k_step_fp32<true, unsigned long long><<<g, 128, 0, s>>>(src, dst, a);
+        else k_step_fp32<false, unsigned long long><<<g, 128, 0, s>>>(src, dst, a);
+    }
     return cudaGetLastError();
 }
 
