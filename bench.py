@@ -37,6 +37,7 @@ _CSRC = os.path.join(ROOT, "paper_1410_1914_gb300", "csrc")
 KERNEL_SRCS = [os.path.join(_CSRC, f) for f in ("march.cu", "march.cuh", "device_util.cuh")]
 KERNEL_SRCS_Q19 = [os.path.join(_CSRC, f) for f in ("q19.cu", "internal.cuh", "device_util.cuh")]
 KERNEL_SRCS_Q19S = [os.path.join(_CSRC, f) for f in ("q19s.cu", "internal.cuh", "device_util.cuh")]
+KERNEL_SRCS_POP = [os.path.join(_CSRC, f) for f in ("kernels.cu", "internal.cuh", "device_util.cuh")]
 
 
 def kernel_src_sha256(srcs=None) -> str:
@@ -134,7 +135,10 @@ def measured_traffic(storage: str, n_cells: int, lattice: str = "d3q7"):
     (profiles/traffic.json), scaled by the cells processed; None when the
     kernel source changed since the capture or no capture exists."""
     key = f"d3q19_{storage}" if lattice == "d3q19" else storage
-    srcs = (KERNEL_SRCS if lattice != "d3q19" else KERNEL_SRCS_Q19 if storage == "fp32pop" else KERNEL_SRCS_Q19S)
+    if lattice == "d3q19":
+        srcs = KERNEL_SRCS_Q19 if storage == "fp32pop" else KERNEL_SRCS_Q19S
+    else:
+        srcs = KERNEL_SRCS_POP if storage == "fp32pop" else KERNEL_SRCS
     try:
         with open(TRAFFIC_JSON) as fh:
             rec = json.load(fh)[key]
