@@ -238,6 +238,13 @@ cl_status cl_lbm_effective_diffusivity(cl_handle h, double* d_eff_m2s, double* d
    (0 where none). */
 cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, double* profile_C);
 
+/* Eq. 25: the discharge current density the reaction carries,
+   i_d = 4 F R / A_cross, with R the total rate above (O2 in mol/s when C is
+   in mol/m^3), four electrons per O2 (ORR), F = 96485.33212 C/mol and
+   A_cross = ny nz dx^2 the cross-section of the layer; A/m^2.
+   CL_ERR_STATE for the PROTON carrier (it has no sink). */
+cl_status cl_lbm_current_density(cl_handle h, double* i_d);
+
 /* Current concentration C = sum_i g_i (nx*ny*nz floats, host or device; 0 on
    inactive cells). */
 cl_status cl_lbm_get_field(cl_handle h, float* C, int ptr_is_device);

@@ -94,6 +94,7 @@ def lib():
                 "orc_lbm_fluxes": (None, [_P, _P]),
                 "orc_lbm_effective_diffusivity": (None, [_P, _P]),
                 "orc_lbm_reaction_rate": (_D, [_P, _P, _P]),
+                "orc_lbm_current_density": (_D, [_P]),
                 "orc_lbm_solve": (_L, [_P, _D, _L, _L]),
                 "orc_lbm_n": (_L, [_P]),
                 "orc_lbm_step_count": (_L, [_P]),
@@ -296,6 +297,10 @@ class OracleLBM:
         pc = np.zeros(nx)
         tot = lib().orc_lbm_reaction_rate(self._h, _ptr(pr), _ptr(pc))
         return float(tot), pr, pc
+
+    def current_density(self):
+        """Eq. 25: i_d = 4 F R / A_cross [A/m^2]."""
+        return lib().orc_lbm_current_density(self._h)
 
     # scalars and maps
     @property

@@ -683,6 +683,18 @@ double orc_lbm_reaction_rate(const orc_lbm* s, double* profile_R, double* profil
 }
 
 /*
+ * Eq. 25: the discharge current density carried by the reaction,
+ * i_d = (integral of the local current over the reactive surface) / A_cross
+ *     = 4 F R / A_cross, four electrons per O2 and A_cross = ny nz dx^2 [A/m^2].
+ */
+double orc_lbm_current_density(const orc_lbm* s)
+{
+    const double F = 96485.33212;
+    double R = orc_lbm_reaction_rate(s, NULL, NULL);
+    return 4.0 * F * R / ((double)s->p.ny * s->p.nz * s->p.dx_m * s->p.dx_m);
+}
+
+/*
  * Run until the relative change r = sum|C(t) - C(t-K)| / sum|C(t)| over one
  * check interval K drops below tol, or max_steps.  Returns the steps taken
  * (negative if max_steps was reached first).

@@ -94,6 +94,7 @@ SIGNATURES = {
     "cl_lbm_fluxes": (_S, [_H, _P]),
     "cl_lbm_effective_diffusivity": (_S, [_H, _P, _P]),
     "cl_lbm_reaction_rate": (_S, [_H, _P, _P, _P]),
+    "cl_lbm_current_density": (_S, [_H, ctypes.POINTER(ctypes.c_double)]),
     "cl_lbm_get_field": (_S, [_H, _P, _I]),
     "cl_lbm_get_populations": (_S, [_H, _P, _I]),
     "cl_lbm_get_setup": (_S, [_H, _P, _P, _P, _P, _I]),
@@ -306,6 +307,12 @@ def cl_lbm_reaction_rate(h: int, nx: int) -> tuple[float, np.ndarray, np.ndarray
     _check(load().cl_lbm_reaction_rate(h, ctypes.byref(tot), pr.ctypes.data_as(ctypes.c_void_p),
                                        pc.ctypes.data_as(ctypes.c_void_p)), "cl_lbm_reaction_rate")
     return tot.value, pr, pc
+
+
+def cl_lbm_current_density(h: int) -> float:
+    v = ctypes.c_double()
+    _check(load().cl_lbm_current_density(h, ctypes.byref(v)), "cl_lbm_current_density")
+    return v.value
 
 
 def cl_lbm_get_field(h: int, out) -> None:

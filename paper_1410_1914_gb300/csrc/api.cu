@@ -812,6 +812,17 @@ cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, do
     return CL_OK;
 }
 
+cl_status cl_lbm_current_density(cl_handle h, double* i_d) {
+    CKS(need_structure(h));
+    if (!i_d) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    if (h->p.carrier == CL_CARRIER_PROTON) { set_msg_txt("the proton carrier has no reaction"); return CL_ERR_STATE; }
+    double R = 0.0;
+    CKS(cl_lbm_reaction_rate(h, &R, nullptr, nullptr));
+    const double F = 96485.33212;  // C/mol
+    *i_d = 4.0 * F * R / ((double)h->ny * h->nz * h->p.dx_m * h->p.dx_m);  // Eq. 25, A_cross = ny nz dx^2
+    return CL_OK;
+}
+
 static cl_status state_out(cl_lbm* h, float* C, float* g, int ptr_is_device) {
     const size_t N = (size_t)h->N;
     if (h->march) {

@@ -91,6 +91,10 @@ class Solver:
     def reaction_rate(self):
         return L.cl_lbm_reaction_rate(self.h, self.shape[2])
 
+    def current_density(self):
+        """Eq. 25: i_d = 4 F R / A_cross [A/m^2]."""
+        return L.cl_lbm_current_density(self.h)
+
     def field(self):
         out = np.zeros(self.shape, dtype=np.float32)
         L.cl_lbm_get_field(self.h, out)

@@ -114,6 +114,7 @@ def test_trajectory(cuda_lib, storage, name, steps):
     to, pRo, pCo = o.reaction_rate()
     assert tg == pytest.approx(to, rel=ftol, abs=1e-30)
     np.testing.assert_allclose(pCg, pCo, atol=tol)
+    assert s.current_density() == pytest.approx(o.current_density(), rel=ftol, abs=1e-30)
     s.close()
 
 

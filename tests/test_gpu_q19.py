@@ -131,6 +131,7 @@ def test_trajectory(cuda_lib, storage, name, steps):
     to, pRo, pCo = o.reaction_rate()
     assert tg == pytest.approx(to, rel=ftol, abs=1e-30)
     np.testing.assert_allclose(pCg, pCo, atol=tol)
+    assert s.current_density() == pytest.approx(o.current_density(), rel=ftol, abs=1e-30)
     s.close()
 
 
@@ -310,3 +311,23 @@ def test_sphere_in_cube_96(cuda_lib):
     with open(os.path.join(HERE, "golden", "paper_values.json")) as fh:
         ref = json.load(fh)["sphere_in_cube_deff"]["value"]
     assert d_rel == pytest.approx(ref, rel=0.04)
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_protons_on_d3q19(cuda_lib, storage):
+    """Proton conduction in the ionomer (Eq. 16) on the D3Q19 lattice: the
+    ionomer active set and its link classes bit for bit, and the trajectory
+    against the oracle."""
+    ph = inputs.pt_cl((16, 20, 70), 31, 0.45, 0.1887)
+    params = dict(dx_m=2e-9, D_bulk=2.9e-5, knudsen=1, D_ionomer=2.5, carrier=1, tau_ref=0.9, c_in=1.0, c_out=0.0)
+    s = _solver(ph.shape, storage, **params)
+    s.set_structure(ph)
+    o = _oracle(ph, **params)
+    act = o.active() > 0
+    np.testing.assert_array_equal(s.setup()["active"], o.active())
+    np.testing.assert_array_equal(s.links()[0], _walls_from_active(act))
+    s.step(60)
+    o.step(60)
+    np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(60, storage))
+    with pytest.raises(Exception):
+        s.current_density()  # no sink for protons

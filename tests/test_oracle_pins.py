@@ -96,6 +96,8 @@ def test_reactive_wall_1d(tau_ref, k):
     assert prof_R[nx - 1] == pytest.approx(R, rel=1e-12) and np.all(prof_R[: nx - 1] == 0)
     f = o.fluxes()
     assert f["J_in"] == pytest.approx(f["R"], rel=1e-10)  # steady state: inflow = consumption
+    # Eq. 25: i_d = 4 F (rate per area), here 4 F k D c0 / (D + k L)
+    assert o.current_density() == pytest.approx(4 * 96485.33212 * k * DB * 0.7 / (DB + k * L), rel=1e-10)
 
 
 # ---------------------------------------------------------------- FV pin
