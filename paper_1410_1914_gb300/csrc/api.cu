@@ -533,7 +533,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         h->NP19 = (long long)h->px19 * h->ny * h->nz;
         Q19Args a;
         a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px19;
-        h->nblk_step = step19_blocks(a);
+        h->nblk_step = h->q19s ? step19s_blocks(h->px19, h->ny, h->nz) : step19_blocks(a);
     } else {
         StepArgs a;
         a.nx = h->nx; a.ny = h->ny; a.nz = h->nz;

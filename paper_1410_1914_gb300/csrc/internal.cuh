@@ -76,6 +76,7 @@ cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool r
 cudaError_t launch_readout19(const float* pop, const Q19Args& a, double* out, cudaStream_t s);
 cudaError_t launch_out19(const float* pop, const uint32_t* mask, int nx, int ny, int nz, int px, float* C, float* g,
                          cudaStream_t s);
+int step19s_blocks(int px, int ny, int nz);
 cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst, const Q19Args& a, bool reduce,
                            cudaStream_t s);
 cudaError_t launch_init19s(int storage, const Q19State& st, const Q19Args& a, const float* C0, cudaStream_t s);

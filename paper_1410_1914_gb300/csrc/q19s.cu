@@ -76,19 +76,23 @@ __device__ __forceinline__ void df_add19(float hi, float lo, float d, float& ho,
 }  // namespace
 
 // ------------------------------------------------------------------- step
-// Values stay in storage units inside the update: lo scaled by s_lo and the
+// A block is a 32 x 4 tile of cells (x, y) of one plane: a warp is one row,
+// and the y-neighbour rows a cell reads are mostly the block's own rows,
+// already in L1.  Values stay in storage units inside the update: lo scaled by s_lo and the
 // deviations by s_d (both 1 for FP32), so nothing is rescaled on its way in
 // or out.
+constexpr int kS19X = 32, kS19Y = 4;
+
 template <class S, bool REDUCE, class I>
-__global__ void __launch_bounds__(kQ19Threads) k_step19s(Q19State src, Q19State dst, Q19Args a) {
+__global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19State dst, Q19Args a) {
     using T = typename S::T;
     constexpr bool HALF = sizeof(T) == 2;
-    const int x = blockIdx.x * kQ19Threads + threadIdx.x;
-    const int y = blockIdx.y, z = blockIdx.z;
+    const int x = blockIdx.x * kS19X + threadIdx.x;
+    const int y = blockIdx.y * kS19Y + threadIdx.y, z = blockIdx.z;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
     const I NP = (I)a.NP;
     const I c = (I)x + (I)px * ((I)y + (I)ny * (I)z);
-    const bool in_row = x < px;
+    const bool in_row = x < px && y < ny;
     const uint32_t m = in_row ? a.mask[c] : 0u;
     const bool act = (m & kQ19Active) != 0;
     const float inv_lo = HALF ? a.inv_lo : 1.f, s_lo = HALF ? a.s_lo : 1.f;
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19s(Q19State src, Q19State 
             a.Csnap[c] = Cf;
         }
     }
-    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lane = threadIdx.x;  // blockDim.x = 32: the lane
     const unsigned vote = __ballot_sync(0xffffffffu, act);
     if (in_row && ((vote >> (lane & ~7u)) & 0xFFu)) {
         T* dlo = reinterpret_cast<T*>(dst.clo);
@@ -292,9 +296,10 @@ __global__ void k_out19s(Q19State st, Q19Args a, float* __restrict__ C, float* _
 // -------------------------------------------------------------- launchers
 cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst, const Q19Args& a, bool reduce,
                            cudaStream_t s) {
-    const dim3 g((a.px + kQ19Threads - 1) / kQ19Threads, a.ny, a.nz);
+    const dim3 g((a.px + kS19X - 1) / kS19X, (a.ny + kS19Y - 1) / kS19Y, a.nz);
+    const dim3 b(kS19X, kS19Y);
     const bool narrow = 19LL * a.NP < (1LL << 32);
-#define CL_Q19S(SS, R, II) k_step19s<SS, R, II><<<g, kQ19Threads, 0, s>>>(src, dst, a)
+#define CL_Q19S(SS, R, II) k_step19s<SS, R, II><<<g, b, 0, s>>>(src, dst, a)
     if (storage == CL_STORE_FP16DEV) {
         if (narrow) { if (reduce) CL_Q19S(SF16, true, uint32_t); else CL_Q19S(SF16, false, uint32_t); }
         else { if (reduce) CL_Q19S(SF16, true, unsigned long long); else CL_Q19S(SF16, false, unsigned long long); }
@@ -304,6 +309,10 @@ cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst
     }
 #undef CL_Q19S
     return cudaGetLastError();
+}
+
+int step19s_blocks(int px, int ny, int nz) {
+    return ((px + kS19X - 1) / kS19X) * ((ny + kS19Y - 1) / kS19Y) * nz;
 }
 
 cudaError_t launch_init19s(int storage, const Q19State& st, const Q19Args& a, const float* C0, cudaStream_t s) {
