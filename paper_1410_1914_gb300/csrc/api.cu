@@ -141,6 +141,7 @@ StepArgs make_args(cl_lbm* h) {
     a.bc_out = h->p.bc_out;
     a.Csnap = h->Csnap;
     a.partials = h->partials;
+    a.wide = h->wide;
     return a;
 }
 
@@ -165,6 +166,7 @@ Q19Args make_args19(cl_lbm* h) {
     a.inv_lo = 1.0f / h->s_lo;
     a.s_d = h->s_d;
     a.inv_d = 1.0f / h->s_d;
+    a.wide = h->wide;
     return a;
 }
 
@@ -504,6 +506,9 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     h->q = p->lattice == CL_LATTICE_D3Q19 ? 19 : 7;
     h->march = h->q == 7 && p->storage != CL_STORE_FP32POP;
     h->q19s = h->q == 19 && p->storage != CL_STORE_FP32POP;
+    // the population kernels switch to 64-bit element offsets once 32 bits
+    // no longer hold every offset; this override takes that path on any box
+    if (const char* e = getenv("CL_LBM_WIDE_INDEX")) h->wide = atoi(e) != 0;
     h->el = p->storage == CL_STORE_FP16DEV ? 2 : 4;
     h->s = (cudaStream_t)p->cuda_stream;
     memset(&h->info, 0, sizeof(h->info));

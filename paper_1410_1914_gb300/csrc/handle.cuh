@@ -69,6 +69,7 @@ struct cl_lbm {
     uint32_t *mask19 = nullptr, *react19 = nullptr;
     float* omega19 = nullptr;
     bool q19s = false;  // D3Q19 on the (C, delta) state (FP32 or FP16 storage)
+    int wide = 0;       // force 64-bit element offsets (test of the large-box path)
     cl::Q19State st19[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     // (C, delta) layout
     cl::MState st[2];

@@ -33,6 +33,7 @@ struct StepArgs {
     int bc_in, bc_out;   // cl_bc
     float* Csnap;        // C at the previous check (reduction)
     double* partials;    // [blocks][RED_N] (reduction)
+    int wide;            // 1: 64-bit element offsets even where 32-bit ones fit
 };
 
 // ---- D3Q19 (q19.cu) ----
@@ -54,6 +55,7 @@ struct Q19Args {
     float* Csnap;         // padded (reduction)
     double* partials;     // [blocks][RED_N] (reduction)
     float s_lo, inv_lo, s_d, inv_d;  // FP16 state scales (1 otherwise)
+    int wide;             // 1: 64-bit element offsets even where 32-bit ones fit
 };
 
 // One time level of the D3Q19 (C, delta) state in the padded layout:

@@ -485,7 +485,7 @@ int step_fp32_blocks(const StepArgs& a) {
 
 cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce, cudaStream_t s) {
     const dim3 g = step_grid(a);
-    if (7LL * a.N < (1LL << 32)) {
+    if (!a.wide && 7LL * a.N < (1LL << 32)) {
         if (reduce) k_step_fp32<true, uint32_t><<<g, 128, 0, s>>>(src, dst, a);
         else k_step_fp32<false, uint32_t><<<g, 128, 0, s>>>(src, dst, a);
     } else {

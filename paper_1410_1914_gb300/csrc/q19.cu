@@ -283,7 +283,7 @@ int step19_blocks(const Q19Args& a) {
 cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool reduce, cudaStream_t s) {
     const dim3 g = step19_grid(a);
     // 32-bit element offsets while every offset into the 19 planes fits
-    const bool narrow = 19LL * a.NP < (1LL << 32);
+    const bool narrow = !a.wide && 19LL * a.NP < (1LL << 32);
     if (narrow) {
         if (reduce) k_step19<true, uint32_t><<<g, kQ19Threads, 0, s>>>(src, dst, a);
         else k_step19<false, uint32_t><<<g, kQ19Threads, 0, s>>>(src, dst, a);

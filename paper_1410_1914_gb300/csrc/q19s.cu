@@ -298,7 +298,7 @@ cudaError_t launch_step19s(int storage, const Q19State& src, const Q19State& dst
                            cudaStream_t s) {
     const dim3 g((a.px + kS19X - 1) / kS19X, (a.ny + kS19Y - 1) / kS19Y, a.nz);
     const dim3 b(kS19X, kS19Y);
-    const bool narrow = 19LL * a.NP < (1LL << 32);
+    const bool narrow = !a.wide && 19LL * a.NP < (1LL << 32);
 #define CL_Q19S(SS, R, II) k_step19s<SS, R, II><<<g, b, 0, s>>>(src, dst, a)
     if (storage == CL_STORE_FP16DEV) {
         if (narrow) { if (reduce) CL_Q19S(SF16, true, uint32_t); else CL_Q19S(SF16, false, uint32_t); }

@@ -331,3 +331,25 @@ def test_protons_on_d3q19(cuda_lib, storage):
     np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(60, storage))
     with pytest.raises(Exception):
         s.current_density()  # no sink for protons
+
+
+@pytest.mark.parametrize("storage", STORAGES)
+def test_wide_offsets(cuda_lib, storage, monkeypatch):
+    """Boxes whose 19 planes exceed 2^32 elements (about 610^3 cells) take
+    64-bit element offsets; CL_LBM_WIDE_INDEX=1 forces that path here, on a
+    small box, against the oracle (and the D3Q7 population kernel with it)."""
+    monkeypatch.setenv("CL_LBM_WIDE_INDEX", "1")
+    ph, react, params = _case("pt_ragged")
+    s = _solver(ph.shape, storage, **params)
+    s.set_structure(ph, react)
+    s.step(10)
+    o = _oracle(ph, react, **params)
+    o.step(10)
+    np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(10, storage))
+    from paper_1410_1914_gb300 import Solver
+    s7 = Solver(ph.shape, storage="fp32pop", **params)
+    s7.set_structure(ph, react)
+    s7.step(10)
+    o7 = oracle.OracleLBM(ph, react=react, **params)
+    o7.step(10)
+    np.testing.assert_allclose(s7.field(), o7.concentration(), rtol=0, atol=_tol(10, "fp32pop"))
