@@ -147,12 +147,14 @@ cl_status cl_nn_to_bf16(const float* a, void* b, long long n, void* stream);
 cl_status cl_lbm_features(cl_handle h, void* feat);
 
 /* Training target from the handle's current field: target[v] (FP32) =
-   C[v] - ramp(x) on active cells, 0 elsewhere.  Synchronises the stream. */
+   (C[v] - ramp(x)) nx / (c_in - c_out) on active cells, 0 elsewhere (a
+   scale-free deviation from the ramp).  Synchronises the stream. */
 cl_status cl_lbm_target(cl_handle h, float* target);
 
-/* Initialise the handle's state (as cl_lbm_init) from C0 = ramp(x) +
-   pred[v] on active cells, 0 elsewhere; pred is FP32 on the device, in
-   concentration units.  Errors as cl_lbm_init. */
+/* Initialise the handle's state (as cl_lbm_init) from
+   C0 = ramp(x) + pred[v] (c_in - c_out) / nx on active cells, 0 elsewhere:
+   pred is FP32 on the device, in the units of cl_lbm_target (the network's
+   output).  Errors as cl_lbm_init. */
 cl_status cl_lbm_init_warm(cl_handle h, const float* pred);
 
 #ifdef __cplusplus

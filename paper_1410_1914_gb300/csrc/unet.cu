@@ -576,22 +576,26 @@ __global__ void k_features(const uint8_t* __restrict__ phase, const uint16_t* __
 }
 
 // target of the network: (C - ramp) on active cells, 0 elsewhere
+// training target (C - ramp) nx / (c_in - c_out): scale-free
 __global__ void k_target(const float* __restrict__ C, const uint16_t* __restrict__ mask, int nx, long long N, float c_in,
                          float c_out, float* __restrict__ t) {
+    const float scale = (float)nx / (c_in - c_out);
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx);
         const float ramp = c_in + (c_out - c_in) * (x + 0.5f) / nx;
-        t[c] = (mask[c] & kActiveBit) ? C[c] - ramp : 0.f;
+        t[c] = (mask[c] & kActiveBit) ? (C[c] - ramp) * scale : 0.f;
     }
 }
 
-// warm start: C0 = ramp + prediction on active cells
+// warm start: C0 = ramp + pred (c_in - c_out) / nx: the prediction is in the units of
+// the training target, (C - ramp) nx / (c_in - c_out)
 __global__ void k_warm_field(const float* __restrict__ pred, const uint16_t* __restrict__ mask, int nx, long long N,
                              float c_in, float c_out, float* __restrict__ C0) {
+    const float scale = (c_in - c_out) / (float)nx;
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(c % nx);
         const float ramp = c_in + (c_out - c_in) * (x + 0.5f) / nx;
-        C0[c] = (mask[c] & kActiveBit) ? ramp + pred[c] : 0.f;
+        C0[c] = (mask[c] & kActiveBit) ? fmaf(pred[c], scale, ramp) : 0.f;
     }
 }
 

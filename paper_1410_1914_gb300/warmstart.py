@@ -315,8 +315,7 @@ def target(solver):
     import torch
     t = torch.empty(solver.n, dtype=torch.float32, device="cuda")
     _call("cl_lbm_target", ctypes.c_void_p(solver.h), _p(t))
-    nx = solver.shape[2]
-    return t.mul_(float(nx) / (solver.params.c_in - solver.params.c_out))
+    return t
 
 
 def active_mask(solver):
@@ -332,5 +331,4 @@ def warm_start(net: UNet, solver):
     f = features(solver)
     pred = net.forward(f, 1, nx)
     net.check()
-    pred = pred.mul(float(solver.params.c_in - solver.params.c_out) / nx)
     _call("cl_lbm_init_warm", ctypes.c_void_p(solver.h), _p(pred))

@@ -229,10 +229,10 @@ def test_features_target_and_warm_field(cuda_lib):
         C = s.field()
         t = W.target(s).cpu().numpy().reshape(ph.shape)
         np.testing.assert_allclose(t, np.where(act, (C - ramp) * nx, 0.0), rtol=1e-6, atol=1e-5)
-        # warm field: ramp + prediction on active cells, 0 elsewhere
-        pred = np.random.default_rng(0).standard_normal(ph.size).astype(np.float32) * 0.01
+        # warm field: ramp + prediction (target units: times (c_in - c_out) / nx) on active cells, 0 elsewhere
+        pred = np.random.default_rng(0).standard_normal(ph.size).astype(np.float32)
         pd = torch.from_numpy(pred).cuda()
         W._call("cl_lbm_init_warm", __import__("ctypes").c_void_p(s.h), W._p(pd))
         torch.cuda.synchronize()
         C0 = s.field()
-        np.testing.assert_allclose(C0, np.where(act, ramp + pred.reshape(ph.shape), 0.0), rtol=0, atol=1e-7)
+        np.testing.assert_allclose(C0, np.where(act, ramp + pred.reshape(ph.shape) / nx, 0.0), rtol=0, atol=1e-6)
