@@ -160,12 +160,158 @@ __global__ void k_diffusivity(const uint8_t* __restrict__ phase, const uint8_t* 
     }
 }
 
+// ---- 13-direction lengths line by line ----
+// Every cell lies on exactly one line of each direction.  One thread walks
+// one line and adds, to each pore cell of a run, the run's length times
+// |e_d| dx; the 13 directions run in the order of c_dir13, so that the sum
+// (then / 13) is formed in the same order as a cell-by-cell evaluation.
+// Lines with an x component start on the plane x = 0 and end at x = L
+// (x is bounded); lines without one are closed loops of period P in their
+// x-plane, and an all-pore loop gives every cell the length P.
+
+// one step along (e_x, e_y, e_z) with y and z wrapping
+__device__ __forceinline__ void chord_step(int ey, int ez, int ny, int nz, int& yy, int& zz) {
+    yy += ey;
+    yy = yy == ny ? 0 : (yy < 0 ? ny - 1 : yy);
+    zz += ez;
+    zz = zz == nz ? 0 : (zz < 0 ? nz - 1 : zz);
+}
+
+// lines with e_x = 1: one per (y0, z0) of the plane x = 0
+__global__ void k_chord_xlines(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ey, int ez, double len,
+                               double dx, double* __restrict__ acc) {
+    const long long nlines = (long long)ny * nz;
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < nlines;
+         l += (long long)gridDim.x * blockDim.x) {
+        int t = 0, yy = (int)(l % ny), zz = (int)(l / ny);
+        while (t < nx) {
+            if (!is_pore(phase[t + (long long)nx * (yy + (long long)ny * zz)])) {
+                ++t;
+                chord_step(ey, ez, ny, nz, yy, zz);
+                continue;
+            }
+            const int s = t, ys = yy, zs = zz;
+            while (t < nx && is_pore(phase[t + (long long)nx * (yy + (long long)ny * zz)])) {
+                ++t;
+                chord_step(ey, ez, ny, nz, yy, zz);
+            }
+            const double add = ((double)(t - s) * len) * dx;
+            int uy = ys, uz = zs;
+            for (int u = s; u < t; ++u) {
+                acc[u + (long long)nx * (uy + (long long)ny * uz)] += add;
+                chord_step(ey, ez, ny, nz, uy, uz);
+            }
+        }
+    }
+}
+
+// loops with e_x = 0 in each x-plane: nloops per plane, loop k starting at
+// (y, z) = (k, 0) when e_y = 0, else (0, k); period P
+__global__ void k_chord_loops(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ey, int ez, long long P,
+                              int nloops, double len, double dx, double* __restrict__ acc) {
+    const long long total = (long long)nloops * nx;
+    for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < total;
+         l += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(l % nx), k = (int)(l / nx);
+        auto at = [&](int yy, int zz) { return x + (long long)nx * (yy + (long long)ny * zz); };
+        int yy = ey == 0 ? k : 0, zz = ey == 0 ? 0 : k;
+        long long t0 = -1;
+        for (long long t = 0; t < P; ++t) {
+            if (!is_pore(phase[at(yy, zz)])) { t0 = t; break; }
+            chord_step(ey, ez, ny, nz, yy, zz);
+        }
+        if (t0 < 0) {  // an all-pore loop: every cell gets the period (yy, zz are back at the start)
+            const double add = ((double)P * len) * dx;
+            for (long long t = 0; t < P; ++t) {
+                acc[at(yy, zz)] += add;
+                chord_step(ey, ez, ny, nz, yy, zz);
+            }
+            continue;
+        }
+        // (yy, zz) is the non-pore cell t0; walk the other P - 1 cells, runs cannot wrap past it
+        chord_step(ey, ez, ny, nz, yy, zz);
+        long long t = t0 + 1;
+        const long long end = t0 + P;
+        while (t < end) {
+            if (!is_pore(phase[at(yy, zz)])) {
+                ++t;
+                chord_step(ey, ez, ny, nz, yy, zz);
+                continue;
+            }
+            const long long s = t;
+            const int ys = yy, zs = zz;
+            while (t < end && is_pore(phase[at(yy, zz)])) {
+                ++t;
+                chord_step(ey, ez, ny, nz, yy, zz);
+            }
+            const double add = ((double)(t - s) * len) * dx;
+            int uy = ys, uz = zs;
+            for (long long u = s; u < t; ++u) {
+                acc[at(uy, uz)] += add;
+                chord_step(ey, ez, ny, nz, uy, uz);
+            }
+        }
+    }
+}
+
+// D from the accumulated lengths: d_p = sum / 13 on pore cells (Sec. 2.1.3), Eq. 7-9
+__global__ void k_diffusivity_dp(const uint8_t* __restrict__ phase, const uint8_t* __restrict__ active, long long N,
+                                 double T, double M, double D_b, double D_ion, int knudsen, double* D, double* dp) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint8_t ph = phase[c];
+        const double dpc = is_pore(ph) ? dp[c] / 13.0 : 0.0;
+        double dcell = 0.0;
+        if (active[c]) {
+            if (ph == 2) dcell = D_ion;
+            else if (knudsen) {
+                const double R = 8.314462618;
+                const double D_kn = dpc / 3.0 * sqrt(8.0 * R * T / (M_PI * M));  // Eq. 8
+                dcell = 1.0 / (1.0 / D_kn + 1.0 / D_b);                           // Eq. 9
+            } else dcell = D_b;
+        }
+        D[c] = dcell;
+        dp[c] = dpc;
+    }
+}
+
+static long long gcd_host(long long a, long long b) {
+    while (b) { const long long t = a % b; a = b; b = t; }
+    return a;
+}
+
 cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int nx, int ny, int nz,
                                double dx, double T, double M, double D_b, double D_ionomer, int knudsen,
                                const double* D_override, double* D, double* dp, int32_t* chord13,
                                cudaStream_t s) {
-    k_diffusivity<<<152 * 16, 128, 0, s>>>(phase, active, nx, ny, nz, dx, T, M, D_b, D_ionomer, knudsen,
-                                           D_override, D, dp, chord13);
+    if (!dp || D_override || chord13) {
+        k_diffusivity<<<152 * 16, 128, 0, s>>>(phase, active, nx, ny, nz, dx, T, M, D_b, D_ionomer, knudsen,
+                                               D_override, D, dp, chord13);
+        return cudaGetLastError();
+    }
+    const long long N = (long long)nx * ny * nz;
+    cudaError_t e = cudaMemsetAsync(dp, 0, sizeof(double) * (size_t)N, s);
+    if (e != cudaSuccess) return e;
+    const int dirs[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
+                             {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
+                             {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
+    for (int d = 0; d < 13; ++d) {
+        const int ex = dirs[d][0], ey = dirs[d][1], ez = dirs[d][2];
+        const double len = sqrt((double)(ex * ex + ey * ey + ez * ez));
+        if (ex) {
+            const long long nl = (long long)ny * nz;
+            const int grid = (int)((nl + 127) / 128 < 152 * 16 ? (nl + 127) / 128 : 152 * 16);
+            k_chord_xlines<<<grid, 128, 0, s>>>(phase, nx, ny, nz, ey, ez, len, dx, dp);
+        } else {
+            const long long py = ey ? ny : 1, pz = ez ? nz : 1;
+            const long long P = py / gcd_host(py, pz) * pz;
+            const int nloops = (int)((long long)ny * nz / P);
+            const long long nl = (long long)nloops * nx;
+            const int grid = (int)((nl + 127) / 128 < 152 * 16 ? (nl + 127) / 128 : 152 * 16);
+            k_chord_loops<<<grid, 128, 0, s>>>(phase, nx, ny, nz, ey, ez, P, nloops, len, dx, dp);
+        }
+    }
+    k_diffusivity_dp<<<152 * 16, 128, 0, s>>>(phase, active, N, T, M, D_b, D_ionomer, knudsen, D, dp);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,10 @@ def test_setup_bit_exact(cuda_lib, name):
     info = s.info()
     assert info["n_active"] == int(act.sum())
     assert info["D_max"] == pytest.approx(o.D_max, rel=1e-12)
+    # the 13-direction pore lengths of Sec. 2.1.3 (walked line by line on the GPU)
+    pore = (ph == 0) | (ph == 3)
+    d_p = oracle.pore_diameter(ph, params["dx_m"])
+    assert info["mean_pore_diameter_m"] == pytest.approx(d_p[pore].mean(), rel=1e-12)
     assert info["dt_s"] == pytest.approx(o.dt, rel=1e-12)
     assert info["k_lu"] == pytest.approx(o.k_lu, rel=1e-12)
     s.close()
