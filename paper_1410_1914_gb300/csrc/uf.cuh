@@ -12,11 +12,17 @@ namespace cl {
 
 constexpr int kUfMaxIter = 1 << 24;
 
+// Find with path halving: each visited node is pointed at its grandparent.
+// Any ancestor is a valid parent (sets only ever merge, and parents stay
+// smaller than children), and only nodes already seen to be non-roots are
+// written, so the halving never races with the CAS that links a root.
 __device__ __forceinline__ int uf_find(volatile int* L, int a, int* err) {
     int it = 0;
     int p = L[a];
     while (p != a) {
-        a = p;
+        const int gp = L[p];
+        if (gp != p) L[a] = gp;
+        a = gp;
         p = L[a];
         if (++it > kUfMaxIter) { atomicOr(err, 2); break; }
     }
