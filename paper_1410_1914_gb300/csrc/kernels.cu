@@ -205,6 +205,72 @@ __global__ void k_chord_xlines(const uint8_t* __restrict__ phase, int nx, int ny
     }
 }
 
+// The same for lines with e_x = 1, one warp per line: the lanes read 32
+// cells of the line at a time and keep the line's pore bits as 32-bit chunk
+// masks in shared memory; each pore cell then finds the ends of its run in
+// the masks (leading / trailing ones, continued through whole chunks).
+// Lines of up to 32 * kChordChunks cells.
+constexpr int kChordWarps = 4, kChordChunks = 64;
+
+__global__ void __launch_bounds__(32 * kChordWarps) k_chord_xlines_warp(const uint8_t* __restrict__ phase, int nx, int ny,
+                                                                         int nz, int ey, int ez, double len, double dx,
+                                                                         double* __restrict__ acc) {
+    __shared__ uint32_t mk[kChordWarps][kChordChunks];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long nlines = (long long)ny * nz;
+    const int nch = (nx + 31) >> 5;
+    for (long long l = (long long)blockIdx.x * kChordWarps + w; l < nlines; l += (long long)gridDim.x * kChordWarps) {
+        const int y0 = (int)(l % ny), z0 = (int)(l / ny);
+        auto cell = [&](int t) -> long long {
+            int yy = (int)(((long long)y0 + (long long)t * ey) % ny);
+            int zz = (int)(((long long)z0 + (long long)t * ez) % nz);
+            yy += yy < 0 ? ny : 0;
+            zz += zz < 0 ? nz : 0;
+            return t + (long long)nx * (yy + (long long)ny * zz);
+        };
+        for (int k = 0; k < nch; ++k) {
+            const int t = (k << 5) + lane;
+            const bool p = t < nx && is_pore(phase[cell(t)]);
+            const uint32_t b = __ballot_sync(0xffffffffu, p);
+            if (lane == 0) mk[w][k] = b;
+        }
+        __syncwarp();
+        for (int k = 0; k < nch; ++k) {
+            const int t = (k << 5) + lane;
+            const uint32_t m = mk[w][k];
+            if (t >= nx || !((m >> lane) & 1u)) continue;
+            // run cells at or below this one
+            const uint32_t zl = ~m & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+            int left;
+            if (zl) {
+                left = lane - (31 - __clz(zl));
+            } else {
+                left = lane + 1;
+                for (int j = k - 1; j >= 0; --j) {
+                    const uint32_t mj = mk[w][j];
+                    if (mj == 0xffffffffu) left += 32;
+                    else { left += __clz(~mj); break; }
+                }
+            }
+            // run cells at or above this one (bits past the line end are 0)
+            const uint32_t zr = ~m & ~((1u << lane) - 1u);
+            int right;
+            if (zr) {
+                right = (__ffs(zr) - 1) - lane;
+            } else {
+                right = 32 - lane;
+                for (int j = k + 1; j < nch; ++j) {
+                    const uint32_t mj = mk[w][j];
+                    if (mj == 0xffffffffu) right += 32;
+                    else { right += __ffs(~mj) - 1; break; }
+                }
+            }
+            acc[cell(t)] += ((double)(left + right - 1) * len) * dx;
+        }
+        __syncwarp();  // the next line overwrites this warp's masks
+    }
+}
+
 // loops with e_x = 0 in each x-plane: nloops per plane, loop k starting at
 // (y, z) = (k, 0) when e_y = 0, else (0, k); period P
 __global__ void k_chord_loops(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ey, int ez, long long P,
@@ -298,7 +364,12 @@ cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int 
     for (int d = 0; d < 13; ++d) {
         const int ex = dirs[d][0], ey = dirs[d][1], ez = dirs[d][2];
         const double len = sqrt((double)(ex * ex + ey * ey + ez * ez));
-        if (ex) {
+        if (ex && nx <= 32 * kChordChunks) {
+            const long long nl = (long long)ny * nz;
+            const long long blocks = (nl + kChordWarps - 1) / kChordWarps;
+            const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+            k_chord_xlines_warp<<<grid, 32 * kChordWarps, 0, s>>>(phase, nx, ny, nz, ey, ez, len, dx, dp);
+        } else if (ex) {
             const long long nl = (long long)ny * nz;
             const int grid = (int)((nl + 127) / 128 < 152 * 16 ? (nl + 127) / 128 : 152 * 16);
             k_chord_xlines<<<grid, 128, 0, s>>>(phase, nx, ny, nz, ey, ez, len, dx, dp);
