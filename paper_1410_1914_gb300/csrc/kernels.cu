@@ -271,6 +271,78 @@ __global__ void __launch_bounds__(32 * kChordWarps) k_chord_xlines_warp(const ui
     }
 }
 
+// Loops without an x component, one warp per loop: the loop is read from
+// its first non-pore cell on, so that in that order no run wraps around,
+// and then handled as an x-line; an all-pore loop gives every cell the
+// period P.  Loops of up to 32 * kChordChunks cells.
+__global__ void __launch_bounds__(32 * kChordWarps) k_chord_loops_warp(const uint8_t* __restrict__ phase, int nx, int ny,
+                                                                        int nz, int ey, int ez, int P, int nloops,
+                                                                        double len, double dx, double* __restrict__ acc) {
+    __shared__ uint32_t mk[kChordWarps][kChordChunks];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long total = (long long)nloops * nx;
+    const int nch = (P + 31) >> 5;
+    for (long long l = (long long)blockIdx.x * kChordWarps + w; l < total; l += (long long)gridDim.x * kChordWarps) {
+        const int x = (int)(l % nx), kl = (int)(l / nx);
+        const int y0 = ey == 0 ? kl : 0, z0 = ey == 0 ? 0 : kl;
+        auto cell = [&](int t) -> long long {  // 0 <= t < P
+            const int yy = (int)(((long long)y0 + (long long)t * (ey < 0 ? ny - 1 : ey)) % ny);
+            const int zz = (int)(((long long)z0 + (long long)t * (ez < 0 ? nz - 1 : ez)) % nz);
+            return x + (long long)nx * (yy + (long long)ny * zz);
+        };
+        int t0 = -1;
+        for (int k = 0; k < nch && t0 < 0; ++k) {
+            const int t = (k << 5) + lane;
+            const uint32_t b = __ballot_sync(0xffffffffu, t < P && !is_pore(phase[cell(t)]));
+            if (b) t0 = (k << 5) + __ffs(b) - 1;
+        }
+        if (t0 < 0) {
+            const double add = ((double)P * len) * dx;
+            for (int t = lane; t < P; t += 32) acc[cell(t)] += add;
+            continue;
+        }
+        auto tu = [&](int u) { const int t = t0 + u; return t >= P ? t - P : t; };
+        for (int k = 0; k < nch; ++k) {
+            const int u = (k << 5) + lane;
+            const bool p = u < P && is_pore(phase[cell(tu(u))]);
+            const uint32_t b = __ballot_sync(0xffffffffu, p);
+            if (lane == 0) mk[w][k] = b;
+        }
+        __syncwarp();
+        for (int k = 0; k < nch; ++k) {
+            const int u = (k << 5) + lane;
+            const uint32_t m = mk[w][k];
+            if (u >= P || !((m >> lane) & 1u)) continue;
+            const uint32_t zl = ~m & (lane == 31 ? 0xffffffffu : ((2u << lane) - 1u));
+            int left;
+            if (zl) {
+                left = lane - (31 - __clz(zl));
+            } else {
+                left = lane + 1;
+                for (int j = k - 1; j >= 0; --j) {
+                    const uint32_t mj = mk[w][j];
+                    if (mj == 0xffffffffu) left += 32;
+                    else { left += __clz(~mj); break; }
+                }
+            }
+            const uint32_t zr = ~m & ~((1u << lane) - 1u);
+            int right;
+            if (zr) {
+                right = (__ffs(zr) - 1) - lane;
+            } else {
+                right = 32 - lane;
+                for (int j = k + 1; j < nch; ++j) {
+                    const uint32_t mj = mk[w][j];
+                    if (mj == 0xffffffffu) right += 32;
+                    else { right += __ffs(~mj) - 1; break; }
+                }
+            }
+            acc[cell(tu(u))] += ((double)(left + right - 1) * len) * dx;
+        }
+        __syncwarp();
+    }
+}
+
 // loops with e_x = 0 in each x-plane: nloops per plane, loop k starting at
 // (y, z) = (k, 0) when e_y = 0, else (0, k); period P
 __global__ void k_chord_loops(const uint8_t* __restrict__ phase, int nx, int ny, int nz, int ey, int ez, long long P,
@@ -378,8 +450,15 @@ cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int 
             const long long P = py / gcd_host(py, pz) * pz;
             const int nloops = (int)((long long)ny * nz / P);
             const long long nl = (long long)nloops * nx;
-            const int grid = (int)((nl + 127) / 128 < 152 * 16 ? (nl + 127) / 128 : 152 * 16);
-            k_chord_loops<<<grid, 128, 0, s>>>(phase, nx, ny, nz, ey, ez, P, nloops, len, dx, dp);
+            if (P <= 32 * kChordChunks) {
+                const long long blocks = (nl + kChordWarps - 1) / kChordWarps;
+                const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
+                k_chord_loops_warp<<<grid, 32 * kChordWarps, 0, s>>>(phase, nx, ny, nz, ey, ez, (int)P, nloops, len,
+                                                                      dx, dp);
+            } else {
+                const int grid = (int)((nl + 127) / 128 < 152 * 16 ? (nl + 127) / 128 : 152 * 16);
+                k_chord_loops<<<grid, 128, 0, s>>>(phase, nx, ny, nz, ey, ez, P, nloops, len, dx, dp);
+            }
         }
     }
     k_diffusivity_dp<<<152 * 16, 128, 0, s>>>(phase, active, N, T, M, D_b, D_ionomer, knudsen, D, dp);
