@@ -702,11 +702,14 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
     if (REDUCE)
 #pragma unroll
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
-    if (x < nx) {
-        const I plane = (I)nx * (I)ny;
-        const I c = (I)x + (I)nx * (I)y + plane * (I)z;
-        const uint16_t m = a.mask[c];
-        if (m & kActiveBit) {
+    const bool in_row = x < nx;
+    const I plane = (I)nx * (I)ny;
+    const I c = (I)x + (I)nx * (I)y + plane * (I)z;
+    const uint16_t m = in_row ? a.mask[c] : (uint16_t)0;
+    const bool act = (m & kActiveBit) != 0;
+    float h[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        if (act) {
             const float rf = a.rfac;
             // source of population i (1..6 = +x, -x, +y, -y, +z, -z): x - c_i, y and z periodic
             const I sy_m = y == 0 ? (I)(ny - 1) * (I)nx : (I)0 - (I)nx;            // row y - 1
@@ -739,12 +742,9 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
             const float C = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
             const float om = a.omega[c];
             const float e0 = kW0 * C, e1 = kW1 * C;
-            float h[7];
             h[0] = g[0] - om * (g[0] - e0);
 #pragma unroll
             for (int i = 1; i < 7; ++i) h[i] = g[i] - om * (g[i] - e1);
-#pragma unroll
-            for (int i = 0; i < 7; ++i) dst[(I)i * N + c] = h[i];
             if (REDUCE) {
                 if (x == 0 && a.bc_in == CL_BC_DIRICHLET) rv[RED_JIN] = 2.0 * ((double)a.w_cin - (double)h[2]);
                 if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h[1] - (double)a.w_cout);
@@ -765,6 +765,17 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
                 a.Csnap[c] = C;
             }
         }
+    }
+    // The lanes whose cells share a 32-byte sector (the rows are not padded,
+    // so the groups come from matching sector numbers) store together when
+    // any of their cells is active, so that no sector is written in part;
+    // inactive cells store the zeros they already hold.
+    const unsigned long long sector = in_row ? (unsigned long long)(c >> 3) : ~0ULL;
+    const unsigned group = __match_any_sync(0xffffffffu, sector);
+    const unsigned vote = __ballot_sync(0xffffffffu, act);
+    if (in_row && (vote & group)) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i) dst[(I)i * N + c] = h[i];
     }
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
