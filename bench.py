@@ -67,9 +67,9 @@ def bytes_per_cell(storage: str, lattice: str = "d3q7") -> float:
       word, read only by cells with a catalytic link, is not counted):
         fp32pop  19 f32 populations: 76 B -> 2*76 + 8 = 160 B
         fp32     C as two f32 + 18 f32 deviations: 80 B -> 2*80 + 8 = 168 B
-        fp16dev  C f32 + f16 low word + 18 f16 deviations: 42 B -> 2*42 + 8 = 92 B"""
+        fp16dev  C as two f32 + 18 f16 deviations: 44 B -> 2*44 + 8 = 96 B"""
     if lattice == "d3q19":
-        return 2 * {"fp32pop": 76, "fp32": 80, "fp16dev": 42}[storage] + 8
+        return 2 * {"fp32pop": 76, "fp32": 80, "fp16dev": 44}[storage] + 8
     state = {"fp32": 32, "fp16dev": 18, "fp32pop": 28}[storage]
     return 2 * state + 6
 

@@ -396,8 +396,7 @@ cl_status do_init(cl_lbm* h, const float* C0dev) {
         drop_graphs(h);  // the scales are baked into captured kernel arguments
         // the other time level must hold zeros on inactive cells: sectors without an active cell are never written
         const Q19State& o = h->st19[1];
-        CK(cudaMemsetAsync(o.chi, 0, sizeof(float) * (size_t)h->NP19, h->s));
-        CK(cudaMemsetAsync(o.clo, 0, (size_t)h->el * h->NP19, h->s));
+        CK(cudaMemsetAsync(o.hl, 0, sizeof(float2) * (size_t)h->NP19, h->s));
         CK(cudaMemsetAsync(o.d, 0, (size_t)h->el * 18 * h->NP19, h->s));
         Q19Args a = make_args19(h);
         CK(launch_init19s(h->p.storage, h->st19[0], a, C0dev, h->s));
@@ -578,8 +577,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         const long long NP = h->NP19;
         if (h->q19s) {
             for (int b = 0; b < 2; ++b) {
-                if ((st = dalloc_n(h, &h->st19[b].chi, NP)) != CL_OK) return fail(st);
-                if ((st = dalloc(h, &h->st19[b].clo, (size_t)h->el * NP)) != CL_OK) return fail(st);
+                if ((st = dalloc_n(h, &h->st19[b].hl, NP)) != CL_OK) return fail(st);
                 if ((st = dalloc(h, &h->st19[b].d, (size_t)h->el * 18 * NP)) != CL_OK) return fail(st);
             }
         } else {
@@ -593,8 +591,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         e = cudaMemsetAsync(h->mask19, 0, sizeof(uint32_t) * (size_t)NP, h->s);
         for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
             if (h->q19s) {
-                e = cudaMemsetAsync(h->st19[b].chi, 0, sizeof(float) * (size_t)NP, h->s);
-                if (e == cudaSuccess) e = cudaMemsetAsync(h->st19[b].clo, 0, (size_t)h->el * NP, h->s);
+                e = cudaMemsetAsync(h->st19[b].hl, 0, sizeof(float2) * (size_t)NP, h->s);
                 if (e == cudaSuccess) e = cudaMemsetAsync(h->st19[b].d, 0, (size_t)h->el * 18 * NP, h->s);
             } else {
                 e = cudaMemsetAsync(h->pop[b], 0, sizeof(float) * 19 * (size_t)NP, h->s);

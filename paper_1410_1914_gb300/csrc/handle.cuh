@@ -70,7 +70,7 @@ struct cl_lbm {
     float* omega19 = nullptr;
     bool q19s = false;  // D3Q19 on the (C, delta) state (FP32 or FP16 storage)
     int wide = 0;       // force 64-bit element offsets (test of the large-box path)
-    cl::Q19State st19[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+    cl::Q19State st19[2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     // (C, delta) layout
     cl::MState st[2];
     uint16_t* mask_p = nullptr;

@@ -59,10 +59,9 @@ struct Q19Args {
 };
 
 // One time level of the D3Q19 (C, delta) state in the padded layout:
-// hi f32, lo (f32 | f16 * s_lo), 18 deviation planes (f32 | f16 * s_d).
+// (hi, lo) of C side by side as float2, 18 deviation planes (f32 | f16 * s_d).
 struct Q19State {
-    float* chi;
-    void* clo;
+    float2* hl;
     void* d;
 };
 

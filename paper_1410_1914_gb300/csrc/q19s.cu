@@ -5,8 +5,9 @@
 // State per active cell after a step (post-collision, Eq. 21 with the
 // equilibrium a_i C of Eq. 23):
 //     g*_i = a_i C + delta_i,   i = 1..18,   delta_0 = -(delta_1 + ... + delta_18)
-// C is an unevaluated sum hi + lo of two floats (hi f32; lo f32, or f16
-// scaled by s_lo); the deviations are f32 (or f16 scaled by s_d).  With e_i
+// C is an unevaluated sum hi + lo of two floats, stored side by side (one
+// 8-byte load per source cell); the deviations are f32 (or f16 scaled by
+// s_d).  With e_i
 // the arriving population minus a_i C(x):
 //     open link:   e_i = a_i (C(x - c_i) - C(x)) + delta_i(x - c_i)
 //     wall:        e_i = r delta_opp(x) - (1 - r) a_i C(x)   (r = 1 unless reactive)
@@ -16,7 +17,7 @@
 //     delta'_i = (1 - omega) (e_i - a_i dC)
 // which is the BGK step rewritten exactly; delta_0 is implied, so the mass
 // of a cell is exact by construction.  Link classes, layout and store
-// sectors as in q19.cu; each link loads (hi, lo, delta) of the cell its
+// sectors as in q19.cu; each link loads (hi, lo) and delta of the cell its
 // population comes from (its own cell for wall and boundary links)
 // unconditionally, so a cell's loads are all in flight together.
 #include <cuda_fp16.h>
@@ -78,9 +79,8 @@ __device__ __forceinline__ void df_add19(float hi, float lo, float d, float& ho,
 // ------------------------------------------------------------------- step
 // A block is a 32 x 4 tile of cells (x, y) of one plane: a warp is one row,
 // and the y-neighbour rows a cell reads are mostly the block's own rows,
-// already in L1.  Values stay in storage units inside the update: lo scaled by s_lo and the
-// deviations by s_d (both 1 for FP32), so nothing is rescaled on its way in
-// or out.
+// already in L1.  Deviations stay in storage units inside the update
+// (scaled by s_d, 1 for FP32), so nothing is rescaled on its way in or out.
 constexpr int kS19X = 32, kS19Y = 4;
 
 template <class S, bool REDUCE, class I>
@@ -95,11 +95,10 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
     const bool in_row = x < px && y < ny;
     const uint32_t m = in_row ? a.mask[c] : 0u;
     const bool act = (m & kQ19Active) != 0;
-    const float inv_lo = HALF ? a.inv_lo : 1.f, s_lo = HALF ? a.s_lo : 1.f;
     const float s_d = HALF ? a.s_d : 1.f, inv_d = HALF ? a.inv_d : 1.f;
-    const T* __restrict__ slo = reinterpret_cast<const T*>(src.clo);
+    const float2* __restrict__ shl = src.hl;
     const T* __restrict__ sd = reinterpret_cast<const T*>(src.d);
-    float hnew = 0.f, lnew_s = 0.f;
+    float hnew = 0.f, lnew = 0.f;
     float dn[18];
 #pragma unroll
     for (int i = 0; i < 18; ++i) dn[i] = 0.f;
@@ -114,9 +113,8 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
         const I oyp = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)px : (I)px;
         const I ozm = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
         const I ozp = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
-        const float hx = src.chi[c];
-        const float lxs = S::ld(slo[c]);
-        const float lx = lxs * inv_lo;
+        const float2 own_hl = shl[c];
+        const float hx = own_hl.x, lx = own_hl.y;
         const float Cx = hx + lx;
         const float rf = a.rfac;
         // own deviations: their sum is -delta_0
@@ -133,12 +131,11 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
             const bool own = wall || (cx > 0 && x == 0) || (cx < 0 && x == nx - 1);
             const I s = c - (I)cx + (cy > 0 ? oym : (cy < 0 ? oyp : (I)0)) + (cz > 0 ? ozm : (cz < 0 ? ozp : (I)0));
             const I e = own ? c : s;
-            const float nh = src.chi[e];
-            const float nl = S::ld(slo[e]);
+            const float2 nhl = shl[e];
             const float nd = S::ld(sd[(I)((own ? j : i) - 1) * NP + e]);
             const float ws = s19_w(i) * s_d;
-            // open link; for an own link nh = hx, nl = lxs and nd = delta_opp: the inert wall value
-            float ei = ws * ((nh - hx) + (nl - lxs) * inv_lo) + nd;
+            // open link; for an own link (hi, lo) are the cell's own and nd = delta_opp: the inert wall value
+            float ei = ws * ((nhl.x - hx) + (nhl.y - lx)) + nd;
             if (own) {
                 if (wall) {
                     if ((rb >> (j - 1)) & 1u) ei = fmaf(rf, nd, -(1.0f - rf) * ws * Cx);
@@ -154,9 +151,7 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
 #pragma unroll
         for (int i = 0; i < 18; ++i) se += ev[i];
         const float dCs = se - sdd;  // sum e_i + delta_0, storage units
-        float lnew;
         df_add19(hx, lx, dCs * inv_d, hnew, lnew);
-        lnew_s = lnew * s_lo;
         const float om1 = 1.0f - a.omega[c];
 #pragma unroll
         for (int i = 1; i < 19; ++i) dn[i - 1] = om1 * (ev[i - 1] - s19_w(i) * dCs);
@@ -188,10 +183,8 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
     const unsigned lane = threadIdx.x;  // blockDim.x = 32: the lane
     const unsigned vote = __ballot_sync(0xffffffffu, act);
     if (in_row && ((vote >> (lane & ~7u)) & 0xFFu)) {
-        T* dlo = reinterpret_cast<T*>(dst.clo);
         T* ddv = reinterpret_cast<T*>(dst.d);
-        dst.chi[c] = hnew;
-        dlo[c] = S::st(lnew_s);
+        dst.hl[c] = make_float2(hnew, lnew);
 #pragma unroll
         for (int i = 0; i < 18; ++i) ddv[(I)i * NP + c] = S::st(dn[i]);
     }
@@ -217,8 +210,7 @@ __global__ void k_init19s(Q19State st, Q19Args a, const float* __restrict__ C0) 
             hi = (float)C;
             lo = (float)(C - (double)hi);
         }
-        st.chi[p] = hi;
-        reinterpret_cast<T*>(st.clo)[p] = S::st(lo * (sizeof(T) == 2 ? a.s_lo : 1.f));
+        st.hl[p] = make_float2(hi, lo);
         for (int i = 0; i < 18; ++i) reinterpret_cast<T*>(st.d)[i * NP + p] = S::st(0.f);
         a.Csnap[p] = hi + lo;
     }
@@ -229,8 +221,7 @@ template <class S>
 __device__ __forceinline__ double state_cell(const Q19State& st, const Q19Args& a, long long p, float (&g)[19]) {
     using T = typename S::T;
     constexpr bool HALF = sizeof(T) == 2;
-    const double C = (double)st.chi[p] +
-                     (double)S::ld(reinterpret_cast<const T*>(st.clo)[p]) * (HALF ? (double)a.inv_lo : 1.0);
+    const double C = (double)st.hl[p].x + (double)st.hl[p].y;
     float s = 0.f;
     for (int i = 1; i < 19; ++i) {
         const float d = S::ld(reinterpret_cast<const T*>(st.d)[(i - 1) * a.NP + p]) * (HALF ? a.inv_d : 1.f);
