@@ -1,6 +1,7 @@
 // Set-up kernels and the FP32 fused collide-stream kernel of the D3Q7
 // reactive-diffusion LBM (arXiv:1410.1914, Sec. 2.1.3, Eq. 7-9, 19, 21-24).
 #include <math.h>
+#include <stdlib.h>
 
 #include "device_util.cuh"
 #include "internal.cuh"
@@ -430,13 +431,19 @@ cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int 
     const long long N = (long long)nx * ny * nz;
     cudaError_t e = cudaMemsetAsync(dp, 0, sizeof(double) * (size_t)N, s);
     if (e != cudaSuccess) return e;
+    // lines longer than the warp kernels' masks hold take one thread per line;
+    // CL_LBM_LINE_THREADS=1 takes that path on any box (it is tested that way)
+    static const bool force_threads = [] {
+        const char* e = getenv("CL_LBM_LINE_THREADS");
+        return e && atoi(e) != 0;
+    }();
     const int dirs[13][3] = {{1, 0, 0},  {0, 1, 0},  {0, 0, 1},  {1, 1, 0},  {1, -1, 0},
                              {1, 0, 1},  {1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {1, 1, 1},
                              {1, 1, -1}, {1, -1, 1}, {1, -1, -1}};
     for (int d = 0; d < 13; ++d) {
         const int ex = dirs[d][0], ey = dirs[d][1], ez = dirs[d][2];
         const double len = sqrt((double)(ex * ex + ey * ey + ez * ez));
-        if (ex && nx <= 32 * kChordChunks) {
+        if (ex && nx <= 32 * kChordChunks && !force_threads) {
             const long long nl = (long long)ny * nz;
             const long long blocks = (nl + kChordWarps - 1) / kChordWarps;
             const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
@@ -450,7 +457,7 @@ cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int 
             const long long P = py / gcd_host(py, pz) * pz;
             const int nloops = (int)((long long)ny * nz / P);
             const long long nl = (long long)nloops * nx;
-            if (P <= 32 * kChordChunks) {
+            if (P <= 32 * kChordChunks && !force_threads) {
                 const long long blocks = (nl + kChordWarps - 1) / kChordWarps;
                 const int grid = (int)(blocks < 152 * 32 ? blocks : 152 * 32);
                 k_chord_loops_warp<<<grid, 32 * kChordWarps, 0, s>>>(phase, nx, ny, nz, ey, ez, (int)P, nloops, len,

@@ -307,3 +307,26 @@ def test_protons_reject_sink_or_missing_conductivity(cuda_lib):
         _solver((4, 4, 8), "fp32", carrier=1, D_ionomer=0.0)
     with pytest.raises(L.ClError):
         _solver((4, 4, 8), "fp32", carrier=1, D_ionomer=1.0, k_ms=1.0)
+
+
+def test_pore_lengths_by_thread_per_line(cuda_lib):
+    """Lines longer than the warp kernels' masks (2048 cells) are walked one
+    thread per line; CL_LBM_LINE_THREADS=1 forces that path, which must give
+    the same set-up (a subprocess: the switch is read once per process)."""
+    import subprocess
+    import sys
+    code = (
+        "import json, numpy as np\n"
+        "from paper_1410_1914_gb300 import Solver, inputs\n"
+        "ph, react, params = inputs.make_workload('pt_cl_256', shape=(13, 17, 291), seed=21)\n"
+        "s = Solver(ph.shape, **params); s.set_structure(ph, react); i = s.info()\n"
+        "print(json.dumps([i['mean_pore_diameter_m'], i['D_max']]))\n")
+    env = dict(os.environ, CL_LBM_LINE_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True,
+                         cwd=os.path.dirname(HERE))
+    mean_dp, dmax = json.loads(out.stdout.strip().splitlines()[-1])
+    ph, react, params = inputs.make_workload("pt_cl_256", shape=(13, 17, 291), seed=21)
+    pore = (ph == 0) | (ph == 3)
+    assert mean_dp == pytest.approx(oracle.pore_diameter(ph, params["dx_m"])[pore].mean(), rel=1e-12)
+    o = oracle.OracleLBM(ph, react=react, **params)
+    assert dmax == pytest.approx(o.D_max, rel=1e-12)
