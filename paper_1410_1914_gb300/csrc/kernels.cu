@@ -394,8 +394,11 @@ __global__ void k_chord_loops(const uint8_t* __restrict__ phase, int nx, int ny,
 }
 
 // D from the accumulated lengths: d_p = sum / 13 on pore cells (Sec. 2.1.3), Eq. 7-9
+// vkn = sqrt(8 R T / (pi M)) and inv_Db = 1 / D_b come from the host (the
+// same correctly rounded values a cell-by-cell evaluation forms)
 __global__ void k_diffusivity_dp(const uint8_t* __restrict__ phase, const uint8_t* __restrict__ active, long long N,
-                                 double T, double M, double D_b, double D_ion, int knudsen, double* D, double* dp) {
+                                 double vkn, double inv_Db, double D_b, double D_ion, int knudsen, double* D,
+                                 double* dp) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         const uint8_t ph = phase[c];
@@ -404,9 +407,8 @@ __global__ void k_diffusivity_dp(const uint8_t* __restrict__ phase, const uint8_
         if (active[c]) {
             if (ph == 2) dcell = D_ion;
             else if (knudsen) {
-                const double R = 8.314462618;
-                const double D_kn = dpc / 3.0 * sqrt(8.0 * R * T / (M_PI * M));  // Eq. 8
-                dcell = 1.0 / (1.0 / D_kn + 1.0 / D_b);                           // Eq. 9
+                const double D_kn = dpc / 3.0 * vkn;   // Eq. 8
+                dcell = 1.0 / (1.0 / D_kn + inv_Db);   // Eq. 9
             } else dcell = D_b;
         }
         D[c] = dcell;
@@ -468,7 +470,8 @@ cudaError_t launch_diffusivity(const uint8_t* phase, const uint8_t* active, int 
             }
         }
     }
-    k_diffusivity_dp<<<152 * 16, 128, 0, s>>>(phase, active, N, T, M, D_b, D_ionomer, knudsen, D, dp);
+    const double vkn = sqrt(8.0 * 8.314462618 * T / (M_PI * M));
+    k_diffusivity_dp<<<152 * 16, 128, 0, s>>>(phase, active, N, vkn, 1.0 / D_b, D_b, D_ionomer, knudsen, D, dp);
     return cudaGetLastError();
 }
 
