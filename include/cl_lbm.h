@@ -122,6 +122,9 @@ typedef struct {
     int react_rule;        /* cl_react_rule */
     int carrier;           /* cl_carrier; PROTON needs D_ionomer > 0 and k_ms = 0 */
     int lattice;           /* cl_lattice */
+    int ionomer_o2;        /* 1: O2 dissolved in the ionomer (Eq. 10-15): the ionomer transports
+                              the gas-equivalent C with D = D_e(T) (Eq. 13) times RT/H (Eq. 10-11),
+                              replacing D_ionomer; O2 carrier only, T > 283.7 K */
     int check_every;       /* steps between convergence checks in cl_lbm_solve (even, >= 2) */
     double tol_flux;       /* |J_in - J_out - R| / |J_in| below this ... */
     double tol_rel;        /* ... and the extrapolated relative error of the tracked readout
@@ -415,6 +418,32 @@ cl_status cl_qsgs_region_not_adjacent(const uint8_t* phase, int nx, int ny, int 
 cl_status cl_qsgs_reactive_faces(const uint8_t* phase, int nx, int ny, int nz, int from_code, int to_code,
                                  double fraction, uint64_t seed, uint8_t* out, long long* n_faces,
                                  void* cuda_stream);
+
+/* ---------------------------------------------------------------------
+ * Property formulas of Sec. 3 (host arithmetic, SI units).
+ * --------------------------------------------------------------------- */
+
+/* Eq. 11: Henry's constant of O2 in the ionomer, H [Pa m^3 / mol]. */
+double cl_henry_constant(double T_K);
+
+/* Eq. 13: diffusivity of dissolved O2 in the ionomer, D_e [m^2/s]
+   (positive above 283.7 K). */
+double cl_ionomer_o2_diffusivity(double T_K);
+
+/* Diffusivity that the ionomer carries in the gas-equivalent variable of
+   Eq. 14-15: the dissolved concentration is C_e = C RT/H (Eq. 10), so the
+   molar flux D_e grad C_e equals (D_e RT/H) grad C, and with this D the
+   flux stays continuous across the pore-ionomer interface. [m^2/s] */
+double cl_ionomer_effective_diffusivity(double T_K);
+
+/* First-order surface rate constant k [m/s] of the gas-equivalent C for the
+   uniform-potential Tafel rate (Eq. 17b with Eq. 10, four electrons per O2):
+   the local current i = i0m (C RT/H / c_ref) exp(alpha F phi_e / (R T))
+   consumes O2 at i / (4F) per unit reactive area, i.e. k C with
+   k = i0m exp(alpha F phi_e / (R T)) (RT/H) / (4 F c_ref).
+   i0m [A/m^2], phi_e [V], c_ref [mol/m^3] (Table 1 gives 0.01, 0.61, 0.6,
+   333 K, 40.96). */
+double cl_tafel_rate_constant(double i0m, double alpha, double phi_e, double T_K, double c_ref);
 
 /* Library version string. */
 const char* cl_version(void);

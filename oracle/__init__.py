@@ -58,7 +58,7 @@ class _Params(ctypes.Structure):
         ("D_ionomer", ctypes.c_double), ("k_ms", ctypes.c_double),
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
-        ("carrier", ctypes.c_int), ("lattice", ctypes.c_int),
+        ("carrier", ctypes.c_int), ("lattice", ctypes.c_int), ("ionomer_o2", ctypes.c_int),
     ]
 
 
@@ -79,6 +79,8 @@ def lib():
                 "orc_bulk_diffusivity": (_D, [_D, _D]),
                 "orc_knudsen_diffusivity": (_D, [_D, _D, _D]),
                 "orc_bosanquet": (_D, [_D, _D]),
+                "orc_henry_constant": (_D, [_D]),
+                "orc_ionomer_o2_diffusivity": (_D, [_D]),
                 "orc_chord_counts": (None, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
                 "orc_pore_diameter": (None, [_P, _L, _D, _P]),
                 "orc_active_mask": (_L, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P]),
@@ -153,6 +155,16 @@ def bosanquet(D_kn, D_b):
     return lib().orc_bosanquet(D_kn, D_b)
 
 
+def henry_constant(T_K):
+    """Eq. 11 [Pa m^3/mol]."""
+    return lib().orc_henry_constant(T_K)
+
+
+def ionomer_o2_diffusivity(T_K):
+    """Eq. 13 [m^2/s]."""
+    return lib().orc_ionomer_o2_diffusivity(T_K)
+
+
 def chord_counts(phase: np.ndarray) -> np.ndarray:
     """13-direction pore run lengths in cells, shape (nz, ny, nx, 13)."""
     phase = np.ascontiguousarray(phase, dtype=np.uint8)
@@ -208,7 +220,7 @@ def phase_connectivity(phase: np.ndarray, phase_set, neighbours: int = 26, perio
 # ---------------------------------------------------------------- solver
 DEFAULTS = dict(dx_m=2e-9, T_K=353.0, p_atm=1.0, M_kgmol=0.032, D_bulk=0.0, D_ionomer=0.0,
                 k_ms=0.0, knudsen=0, bc_in=0, bc_out=0, c_in=1.0, c_out=0.0, tau_ref=1.0, carrier=0,
-                lattice=0)
+                lattice=0, ionomer_o2=0)
 
 
 class OracleLBM:
@@ -232,7 +244,10 @@ class OracleLBM:
         self.params = p
         cp = _Params(nx, ny, nz, p["dx_m"], p["T_K"], p["p_atm"], p["M_kgmol"], p["D_bulk"],
                      p["D_ionomer"], p["k_ms"], int(p["knudsen"]), int(p["bc_in"]), int(p["bc_out"]),
-                     p["c_in"], p["c_out"], p["tau_ref"], int(p["carrier"]), int(p["lattice"]))
+                     p["c_in"], p["c_out"], p["tau_ref"], int(p["carrier"]), int(p["lattice"]),
+                     int(p["ionomer_o2"]))
+        if int(p["ionomer_o2"]) and (int(p["carrier"]) != 0 or not ionomer_o2_diffusivity(p["T_K"]) > 0):
+            raise ValueError("ionomer_o2 needs the O2 carrier and T_K > 283.7 K (Eq. 13)")
         if int(p["lattice"]) not in (0, 1):
             raise ValueError("lattice must be 0 (D3Q7) or 1 (D3Q19)")
         if int(p["carrier"]) == 1 and not (p["D_ionomer"] > 0 and p["k_ms"] == 0):

@@ -101,6 +101,8 @@ typedef struct {
     int carrier;        /* 0: O2 in the pore space (Eq. 6); 1: protons in the ionomer
                            (Eq. 16 with S_e = 0 and uniform conductivity D_ionomer) */
     int lattice;        /* 0: D3Q7; 1: D3Q19 (Eq. 22) */
+    int ionomer_o2;     /* 1: the ionomer carries the gas-equivalent C of Eq. 14-15 with
+                           D = D_e(T) RT / H (Eq. 10, 11, 13), replacing D_ionomer */
 } orc_params;
 
 static long idx3(int x, int y, int z, int nx, int ny) { return x + (long)nx * (y + (long)ny * z); }
@@ -137,6 +139,18 @@ double orc_knudsen_diffusivity(double d_p_m, double T_K, double M_kgmol)
 {
     const double R = 8.314462618;
     return d_p_m / 3.0 * sqrt(8.0 * R * T_K / (M_PI * M_kgmol));
+}
+
+/* Eq. 11: H = 0.101325 exp(-666/T + 14.1)   [Pa m^3/mol] */
+double orc_henry_constant(double T_K)
+{
+    return 1.01325e-1 * exp(-666.0 / T_K + 14.1);
+}
+
+/* Eq. 13: D_e = 1e-10 (0.1543 (T - 273) - 1.65)   [m^2/s] */
+double orc_ionomer_o2_diffusivity(double T_K)
+{
+    return 1e-10 * (0.1543 * (T_K - 273.0) - 1.65);
 }
 
 /* Eq. 9: 1/D = 1/D_Kn + 1/D_b */
@@ -422,6 +436,14 @@ orc_lbm* orc_lbm_new(const orc_params* p, const uint8_t* phase, const uint8_t* r
     memcpy(s->phase, phase, (size_t)N);
     s->active = (uint8_t*)malloc((size_t)N);
     s->L = p->lattice == 1 ? &LAT19 : &LAT7;
+    if (p->ionomer_o2) {
+        /* Eq. 10: the dissolved concentration is C_e = C RT/H, so the molar
+           flux in the ionomer, D_e grad C_e, is (D_e RT/H) grad C: the
+           gas-equivalent C of Eq. 14-15 diffuses there with D_e RT/H */
+        const double R = 8.314462618;
+        s->p.D_ionomer = orc_ionomer_o2_diffusivity(p->T_K) * R * p->T_K / orc_henry_constant(p->T_K);
+        p = &s->p;
+    }
     s->react = (uint32_t*)calloc((size_t)N, sizeof(uint32_t));
     s->D = (double*)calloc((size_t)N, sizeof(double));
     s->tau = (double*)calloc((size_t)N, sizeof(double));

@@ -40,7 +40,7 @@ class cl_params(ctypes.Structure):
         ("knudsen", ctypes.c_int), ("bc_in", ctypes.c_int), ("bc_out", ctypes.c_int),
         ("c_in", ctypes.c_double), ("c_out", ctypes.c_double), ("tau_ref", ctypes.c_double),
         ("storage", ctypes.c_int), ("react_rule", ctypes.c_int), ("carrier", ctypes.c_int),
-        ("lattice", ctypes.c_int), ("check_every", ctypes.c_int),
+        ("lattice", ctypes.c_int), ("ionomer_o2", ctypes.c_int), ("check_every", ctypes.c_int),
         ("tol_flux", ctypes.c_double), ("tol_rel", ctypes.c_double),
         ("max_steps", ctypes.c_longlong),
         ("cuda_stream", ctypes.c_void_p),
@@ -102,6 +102,10 @@ SIGNATURES = {
     "cl_lbm_get_info": (_S, [_H, ctypes.POINTER(cl_structure_info)]),
     "cl_lbm_get_step": (_S, [_H, ctypes.POINTER(ctypes.c_longlong)]),
     "cl_status_str": (ctypes.c_char_p, [_I]),
+    "cl_henry_constant": (ctypes.c_double, [ctypes.c_double]),
+    "cl_ionomer_o2_diffusivity": (ctypes.c_double, [ctypes.c_double]),
+    "cl_ionomer_effective_diffusivity": (ctypes.c_double, [ctypes.c_double]),
+    "cl_tafel_rate_constant": (ctypes.c_double, [ctypes.c_double] * 5),
     "cl_last_error_message": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_char_p, []),
     "cl_active_mask_noalloc": (_S, [_P, _I, _I, _I, _I, _P, _P]),

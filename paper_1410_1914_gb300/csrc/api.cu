@@ -476,6 +476,20 @@ const char* cl_status_str(cl_status s) {
 
 const char* cl_last_error_message(void) { return g_msg; }
 
+double cl_henry_constant(double T_K) { return 1.01325e-1 * exp(-666.0 / T_K + 14.1); }  // Eq. 11
+
+double cl_ionomer_o2_diffusivity(double T_K) { return 1e-10 * (0.1543 * (T_K - 273.0) - 1.65); }  // Eq. 13
+
+double cl_ionomer_effective_diffusivity(double T_K) {
+    const double R = 8.314462618;
+    return cl_ionomer_o2_diffusivity(T_K) * R * T_K / cl_henry_constant(T_K);  // Eq. 10: C_e = C RT/H
+}
+
+double cl_tafel_rate_constant(double i0m, double alpha, double phi_e, double T_K, double c_ref) {
+    const double R = 8.314462618, F = 96485.33212;
+    return i0m * exp(alpha * F * phi_e / (R * T_K)) * (R * T_K / cl_henry_constant(T_K)) / (4.0 * F * c_ref);
+}
+
 const char* cl_version(void) { return "cl_lbm 0.3 (D3Q7 and D3Q19, sm_103a)"; }
 
 cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
@@ -491,6 +505,10 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
     if (p->carrier != CL_CARRIER_O2 && p->carrier != CL_CARRIER_PROTON) { set_msg_txt("bad carrier"); return CL_ERR_ARG; }
     if (p->lattice != CL_LATTICE_D3Q7 && p->lattice != CL_LATTICE_D3Q19) { set_msg_txt("bad lattice"); return CL_ERR_ARG; }
+    if (p->ionomer_o2 && (p->carrier != CL_CARRIER_O2 || !(cl_ionomer_o2_diffusivity(p->T_K) > 0))) {
+        set_msg_txt("ionomer_o2 needs the O2 carrier and T_K > 283.7 K (Eq. 13)");
+        return CL_ERR_ARG;
+    }
     if (p->carrier == CL_CARRIER_PROTON && !(p->D_ionomer > 0 && p->k_ms == 0)) {
         set_msg_txt("the proton carrier needs D_ionomer > 0 (its conductivity) and k_ms = 0");
         return CL_ERR_ARG;
@@ -501,6 +519,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
 
     cl_lbm* h = new cl_lbm();
     h->p = *p;
+    if (p->ionomer_o2) h->p.D_ionomer = cl_ionomer_effective_diffusivity(p->T_K);  // Eq. 10-15
     h->nx = p->nx; h->ny = p->ny; h->nz = p->nz; h->N = N;
     h->q = p->lattice == CL_LATTICE_D3Q19 ? 19 : 7;
     h->march = h->q == 7 && p->storage != CL_STORE_FP32POP;

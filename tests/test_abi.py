@@ -128,3 +128,35 @@ def test_null_handle_calls(lib):
     info = _lib.cl_solve_info()
     assert lib.cl_lbm_solve(None, ctypes.byref(info)) == _lib.CL_ERR_ARG
     lib.cl_lbm_destroy(None)  # ignored
+
+
+def test_property_formulas_match_the_oracle(lib):
+    """Eq. 10, 11, 13 and the Tafel rate constant as host functions of the
+    library equal the oracle's own evaluation (two independent statements of
+    the printed formulas); no device work."""
+    import math
+    import oracle
+    R, F = 8.314462618, 96485.33212
+    for T in (300.0, 333.0, 353.0):
+        assert lib.cl_henry_constant(T) == oracle.henry_constant(T)
+        assert lib.cl_ionomer_o2_diffusivity(T) == oracle.ionomer_o2_diffusivity(T)
+        assert lib.cl_ionomer_effective_diffusivity(T) == pytest.approx(
+            oracle.ionomer_o2_diffusivity(T) * R * T / oracle.henry_constant(T), rel=1e-15)
+    # Table 1 (Pt): i0m 0.01 A/m^2, alpha 0.61, phi_e 0.6 V, 333 K, c_ref 40.96 mol/m^3
+    k = lib.cl_tafel_rate_constant(0.01, 0.61, 0.6, 333.0, 40.96)
+    i_per_C = 0.01 * math.exp(0.61 * F * 0.6 / (R * 333.0)) * (R * 333.0 / oracle.henry_constant(333.0)) / 40.96
+    assert k == pytest.approx(i_per_C / (4 * F), rel=1e-14)
+    assert 1e-5 < k < 1e-4  # about 3.3e-5 m/s
+
+
+def test_ionomer_o2_argument_checks(lib):
+    from paper_1410_1914_gb300 import _lib as L
+    p = L.cl_params_default(nx=4, ny=4, nz=4)
+    p.ionomer_o2 = 1
+    p.T_K = 280.0   # Eq. 13 is not positive below 283.7 K
+    h = ctypes.c_void_p()
+    assert lib.cl_lbm_create(ctypes.byref(h), ctypes.byref(p)) == L.CL_ERR_ARG
+    p.T_K = 353.0
+    p.carrier = L.CL_CARRIER_PROTON
+    p.D_ionomer = 1.0
+    assert lib.cl_lbm_create(ctypes.byref(h), ctypes.byref(p)) == L.CL_ERR_ARG

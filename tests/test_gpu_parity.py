@@ -330,3 +330,25 @@ def test_pore_lengths_by_thread_per_line(cuda_lib):
     assert mean_dp == pytest.approx(oracle.pore_diameter(ph, params["dx_m"])[pore].mean(), rel=1e-12)
     o = oracle.OracleLBM(ph, react=react, **params)
     assert dmax == pytest.approx(o.D_max, rel=1e-12)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16dev"])
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_ionomer_o2_trajectory(cuda_lib, storage, lattice):
+    """O2 dissolved in the ionomer (Eq. 10-15, ionomer_o2 = 1): the ionomer
+    joins the transport set with D = D_e RT/H, about 2e5 times below the
+    bulk D here (relaxation near 1/2 in the ionomer); set-up and trajectory
+    against the oracle."""
+    ph, react, params = _case("pt_deff")
+    params = dict(params, ionomer_o2=1, k_ms=5e3)
+    s = _solver(ph.shape, storage, lattice=lattice, **params)
+    s.set_structure(ph, react)
+    o = oracle.OracleLBM(ph, react=react, lattice=lattice, **params)
+    act = o.active() > 0
+    np.testing.assert_array_equal(s.setup()["active"], o.active())
+    assert (act & (ph == 2)).any()   # ionomer cells carry O2
+    np.testing.assert_allclose(s.setup()["omega"][act], 1.0 / o.tau()[act], rtol=1e-6)
+    s.step(60)
+    o.step(60)
+    np.testing.assert_allclose(s.field(), o.concentration(), rtol=0, atol=_tol(storage, 60))
+    s.close()
