@@ -166,7 +166,8 @@ typedef struct {
 
 /* Create a solver for a box of p->nx * p->ny * p->nz voxels.  Allocates all
    device buffers (through p->alloc if given).  *out is set only on CL_OK.
-   Errors: CL_ERR_ARG (bad sizes/parameters), CL_ERR_OOM, CL_ERR_CUDA. */
+   Errors: CL_ERR_ARG (bad sizes/parameters, e.g. an unknown lattice or
+   storage, ionomer_o2 with the proton carrier), CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_lbm_create(cl_handle* out, const cl_params* p);
 
 /* Free every buffer of the handle (NULL is ignored). */
@@ -180,7 +181,9 @@ void cl_lbm_destroy(cl_handle h);
      reactive_faces: nx*ny*nz bytes, bit d-1 = face toward x + c_d is
                      catalytic, or NULL (no reaction unless react_rule says
                      otherwise); copied.  A face reacts only if it is marked,
-                     belongs to an active cell and its neighbour is solid (1).
+                     belongs to an active cell and its neighbour is solid (1);
+                     on D3Q19 the links that cross such a face react (see
+                     "Link classes").
    Errors: CL_ERR_ARG (phase code > 3), CL_ERR_NO_PATH, CL_ERR_CUDA. */
 cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t* reactive_faces,
                                int ptr_is_device);
