@@ -221,6 +221,35 @@ cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info);
    returns CL_ERR_NOT_CONVERGED with that interval's readouts in info. */
 cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* info);
 
+/* Steady state by a Krylov method instead of the time march, then the
+   stopping rule above as its certificate.  The steady state the march of
+   Eq. 21-24 approaches is the fixed point x = S(x) of one step S on the
+   stored post-collision populations; S is affine, S(x) = A x + b (A: the
+   step with zero boundary concentrations, b: the Dirichlet terms), so the
+   fixed point solves (I - A) x = b.  Mixed-precision refinement: the
+   iterate is held in FP64 and its residual r = S(x) - x (the change one
+   more step would make) is taken with the FP64 step; each correction
+   solves (I - A) e = r with BiCGSTAB on f32 vectors and the f32 step
+   kernel (two applications per iteration) to 1e-3 of |r|, restarted from
+   the true residual on breakdown (at most 4 restarts); x += e.  It stops
+   when |r| (2-norm over all populations, FP64) falls to tol times its
+   initial value, when max_iter BiCGSTAB iterations are spent, or when a
+   correction no longer halves |r|.  The result, rounded to f32, replaces
+   the state, and cl_lbm_solve_budget(h, max_steps, info) then runs the
+   time march from it: the return value and info are those of the stopping
+   rule (max_steps 0: no step, CL_ERR_NOT_CONVERGED with the readouts of
+   the Krylov state), except that info->seconds covers the whole call.
+     tol:        > 0, relative to the initial residual norm.
+     max_iter:   >= 0 BiCGSTAB iterations in all.
+     iterations: nullable; the iterations taken.
+   Needs storage CL_STORAGE_FP32POP (either lattice), else CL_ERR_STATE.
+   Allocates 8 f32 and 2 FP64 population-sized vectors for the call
+   (through p->alloc if given) and frees them before returning.
+   Errors: CL_ERR_ARG (tol <= 0, max_iter < 0, max_steps < 0), CL_ERR_STATE,
+   CL_ERR_OOM, CL_ERR_CUDA, and the codes of cl_lbm_solve_budget. */
+cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
+                              int* iterations);
+
 /* Lattice-unit fluxes of the current state, FP64 sums:
    out[0] J_in  net amount entering through x = 0 per step,
    out[1] J_out net amount leaving through x = L per step,

@@ -93,6 +93,7 @@ def lib():
                 "orc_lbm_step": (None, [_P, _L]),
                 "orc_lbm_concentration": (None, [_P, _P]),
                 "orc_lbm_populations": (None, [_P, _P]),
+                "orc_lbm_set_populations": (None, [_P, _P]),
                 "orc_lbm_fluxes": (None, [_P, _P]),
                 "orc_lbm_effective_diffusivity": (None, [_P, _P]),
                 "orc_lbm_reaction_rate": (_D, [_P, _P, _P]),
@@ -293,6 +294,12 @@ class OracleLBM:
         out = np.zeros((self.q,) + self.shape)
         lib().orc_lbm_populations(self._h, _ptr(out))
         return out
+
+    def set_populations(self, g):
+        """Replace the pre-collision populations, shape (q, nz, ny, nx);
+        entries of inactive cells are ignored (kept 0)."""
+        g = np.ascontiguousarray(g, dtype=np.float64).reshape((self.q,) + self.shape)
+        lib().orc_lbm_set_populations(self._h, _ptr(g))
 
     def fluxes(self):
         out = np.zeros(5)

@@ -613,6 +613,13 @@ void orc_lbm_populations(const orc_lbm* s, double* out)
     memcpy(out, s->g, sizeof(double) * s->L->q * s->N);
 }
 
+/* replace the pre-collision populations (layout [q][N]); inactive cells stay 0 */
+void orc_lbm_set_populations(orc_lbm* s, const double* g)
+{
+    for (int i = 0; i < s->L->q; ++i)
+        for (long c = 0; c < s->N; ++c) s->g[i * s->N + c] = s->active[c] ? g[i * s->N + c] : 0.0;
+}
+
 /*
  * Lattice-unit fluxes of the current state (computed from its post-collision
  * populations, i.e. what the next streaming moves):

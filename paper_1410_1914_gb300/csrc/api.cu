@@ -33,11 +33,11 @@ int transport_phases(const cl_params& p) {
 // C_w = (g* + r g*) / (2 a_i); the link's share of the face's rate k C_w is
 // a_i over the weight of all links crossing one face, cs^2 / 2):
 // r = (cs^2 - k) / (cs^2 + k); on D3Q7 (cs^2 = 2w = 1/4) that is (2w - k) / (2w + k).
-float reactive_factor(const cl_lbm* h) {
-    if (h->q == 19) return (float)((1.0 / 3.0 - h->k_lu) / (1.0 / 3.0 + h->k_lu));
-    const double w = 0.125;
-    return (float)((2.0 * w - h->k_lu) / (2.0 * w + h->k_lu));
+double reactive_factor_d(const cl_lbm* h) {
+    const double cs2 = h->q == 19 ? 1.0 / 3.0 : 0.25;
+    return (cs2 - h->k_lu) / (cs2 + h->k_lu);
 }
+float reactive_factor(const cl_lbm* h) { return (float)reactive_factor_d(h); }
 
 MarchArgs make_margs(cl_lbm* h, int dst) {
     MarchArgs a;
@@ -133,8 +133,11 @@ StepArgs make_args(cl_lbm* h) {
     a.omega = h->omega;
     const double w = 0.125;
     a.rfac = reactive_factor(h);
+    a.rfac_d = reactive_factor_d(h);
     a.abb_in = (float)(2.0 * w * h->p.c_in);
     a.abb_out = (float)(2.0 * w * h->p.c_out);
+    a.abb_in_d = 2.0 * w * h->p.c_in;
+    a.abb_out_d = 2.0 * w * h->p.c_out;
     a.w_cin = (float)(w * h->p.c_in);
     a.w_cout = (float)(w * h->p.c_out);
     a.bc_in = h->p.bc_in;
@@ -154,6 +157,7 @@ Q19Args make_args19(cl_lbm* h) {
     a.react = h->react19;
     a.omega = h->omega19;
     a.rfac = reactive_factor(h);
+    a.rfac_d = reactive_factor_d(h);
     a.c_in = (float)h->p.c_in;
     a.c_out = (float)h->p.c_out;
     a.c_in_d = h->p.c_in;
@@ -786,6 +790,174 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
     inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = inf;
     return result;
+}
+
+namespace {
+
+// Scratch of one call, freed when the call returns.
+struct Scratch {
+    cl_lbm* h;
+    std::vector<std::pair<void*, size_t>> bufs;
+    explicit Scratch(cl_lbm* hh) : h(hh) {}
+    cl_status get(void** out, size_t bytes) {
+        void* ptr = nullptr;
+        if (h->p.alloc) {
+            ptr = h->p.alloc(bytes, (void*)h->s, h->p.alloc_ctx);
+            if (!ptr) { set_msg_txt("allocator callback returned NULL"); return CL_ERR_OOM; }
+        } else {
+            cudaError_t e = cudaMallocAsync(&ptr, bytes, h->s);
+            if (e != cudaSuccess) { set_msg("cudaMallocAsync", e); return from_cuda(e); }
+        }
+        bufs.emplace_back(ptr, bytes);
+        *out = ptr;
+        return CL_OK;
+    }
+    ~Scratch() {
+        cudaStreamSynchronize(h->s);
+        for (auto& b : bufs) {
+            if (h->p.free) h->p.free(b.first, b.second, (void*)h->s, h->p.alloc_ctx);
+            else cudaFreeAsync(b.first, h->s);
+        }
+    }
+};
+
+// One step of the lattice's plain-population kernel from src to dst; with
+// `linear` the boundary concentrations are taken as zero, which leaves the
+// linear part A of the affine step map S(x) = A x + b.
+cudaError_t step_pop(cl_lbm* h, const float* src, float* dst, bool linear) {
+    if (h->q == 19) {
+        Q19Args a = make_args19(h);
+        if (linear) { a.c_in = a.c_out = 0.f; a.c_in_d = a.c_out_d = 0.0; }
+        return launch_step19(src, dst, a, false, h->s);
+    }
+    StepArgs a = make_args(h);
+    if (linear) { a.abb_in = a.abb_out = 0.f; a.w_cin = a.w_cout = 0.f; }
+    return launch_step_fp32(src, dst, a, false, h->s);
+}
+
+// The affine step S in FP64 on FP64 populations.
+cudaError_t step_f64(cl_lbm* h, const double* src, double* dst) {
+    if (h->q == 19) return launch_step19_f64(src, dst, make_args19(h), h->s);
+    return launch_step_f64(src, dst, make_args(h), h->s);
+}
+
+// Each f32 BiCGSTAB solve of the refinement reduces the residual to this
+// fraction (the f32 vectors reach a few 1e-6 at best).
+constexpr double kKryInnerTol = 1e-3;
+
+}  // namespace
+
+cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
+                              int* iterations) {
+    CKS(need_structure(h));
+    if (h->march || h->q19s) {
+        set_msg_txt("the Krylov solve needs the plain f32 population storage (CL_STORAGE_FP32POP)");
+        return CL_ERR_STATE;
+    }
+    if (!(tol > 0.0) || max_iter < 0 || max_steps < 0) {
+        set_msg_txt("tol must be > 0, max_iter and max_steps >= 0");
+        return CL_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const long long L = h->q == 19 ? 19 * h->NP19 : 7 * h->N;
+    const int nblk = kry_blocks();
+    int iters = 0;
+    {
+        Scratch sc(h);
+        // f32: r, rh, p, v, s, t of BiCGSTAB, the correction e and its right-hand side c
+        float* vec[8];
+        for (int k = 0; k < 8; ++k) {
+            CKS(sc.get((void**)&vec[k], sizeof(float) * (size_t)L));
+            CK(cudaMemsetAsync(vec[k], 0, sizeof(float) * (size_t)L, h->s));
+        }
+        float *r = vec[0], *rh = vec[1], *pv = vec[2], *v = vec[3], *sv = vec[4], *t = vec[5], *e = vec[6],
+              *c = vec[7];
+        double *x64 = nullptr, *y64 = nullptr, *part = nullptr;
+        KryScalars* ks = nullptr;
+        CKS(sc.get((void**)&x64, sizeof(double) * (size_t)L));
+        CKS(sc.get((void**)&y64, sizeof(double) * (size_t)L));
+        CK(cudaMemsetAsync(y64, 0, sizeof(double) * (size_t)L, h->s));
+        CKS(sc.get((void**)&part, sizeof(double) * 2 * (size_t)nblk));
+        CKS(sc.get((void**)&ks, sizeof(KryScalars)));
+        CK(cudaMemsetAsync(ks, 0, sizeof(KryScalars), h->s));
+        float* x = h->pop[h->cur];
+        float* u = h->pop[h->cur ^ 1];  // A(.) output; the next step of the march rewrites it
+        // the f32 vector kernels move float4s
+        uintptr_t bits = (uintptr_t)x | (uintptr_t)u;
+        for (int k = 0; k < 8; ++k) bits |= (uintptr_t)vec[k];
+        if (bits & 15u) {
+            set_msg_txt("population buffers must be 16-byte aligned for the Krylov solve");
+            return CL_ERR_STATE;
+        }
+        KryScalars hs;
+        auto read = [&]() -> cl_status {
+            CK(cudaMemcpyAsync(&hs, ks, sizeof(hs), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            return CL_OK;
+        };
+        // BiCGSTAB in f32 on (I - A) e = c from e = 0, to tol_in times |c|
+        auto correct = [&](double tol_in) -> cl_status {
+            const double tol2 = tol_in * tol_in;
+            const int kBatch = 8;        // iterations between host reads of the scalars
+            const int kMaxRestarts = 4;  // restarts from the true residual (breakdown, drift of the recurrence)
+            double rr0 = -1.0;
+            CK(cudaMemsetAsync(e, 0, sizeof(float) * (size_t)L, h->s));
+            for (int restart = 0;; ++restart) {
+                // true residual c - (I - A) e = c + A e - e
+                if (restart == 0) CK(launch_kry_start(e, c, nullptr, r, rh, pv, L, nblk, part, ks, h->s));
+                else {
+                    CK(step_pop(h, e, u, true));
+                    CK(launch_kry_start(e, u, c, r, rh, pv, L, nblk, part, ks, h->s));
+                }
+                CKS(read());
+                if (rr0 < 0.0) rr0 = hs.rr;
+                if (hs.bad == 1 || hs.rr <= tol2 * rr0 || restart >= kMaxRestarts || iters >= max_iter) break;
+                while (iters < max_iter) {
+                    const int n = std::min(kBatch, max_iter - iters);
+                    for (int k = 0; k < n; ++k) {
+                        CK(step_pop(h, pv, u, true));
+                        CK(launch_kry_v(pv, u, rh, v, L, nblk, part, ks, h->s));
+                        CK(launch_kry_s(r, v, sv, L, nblk, ks, h->s));
+                        CK(step_pop(h, sv, u, true));
+                        CK(launch_kry_t(sv, u, t, L, nblk, part, ks, h->s));
+                        CK(launch_kry_xr(e, pv, sv, t, rh, r, L, nblk, part, ks, h->s));
+                        CK(launch_kry_p(r, v, pv, L, nblk, ks, h->s));
+                    }
+                    CKS(read());
+                    iters = hs.iters;
+                    if (hs.bad || hs.rr <= tol2 * rr0) break;
+                }
+            }
+            return CL_OK;
+        };
+        // Mixed-precision refinement: the iterate x64 and its residual S(x64) - x64 in FP64 (the FP64 step),
+        // the correction in f32, so the result is not held to the rounding floor of f32 populations.
+        CK(launch_kry_to64(x, x64, L, nblk, h->s));
+        const double tol2 = tol * tol;
+        const int kMaxRefine = 30;
+        double rr0 = -1.0, rr_prev = INFINITY;
+        for (int ref = 0; ref < kMaxRefine; ++ref) {
+            CK(step_f64(h, x64, y64));
+            CK(launch_kry_res64(x64, y64, c, L, nblk, part, ks, h->s));
+            CKS(read());
+            if (!isfinite(hs.rr)) break;
+            if (rr0 < 0.0) rr0 = hs.rr;
+            // converged, out of iterations, or no longer gaining (the f32 corrections stopped helping)
+            if (hs.rr <= tol2 * rr0 || iters >= max_iter || !(hs.rr < 0.25 * rr_prev)) break;
+            rr_prev = hs.rr;
+            CKS(correct(kKryInnerTol));
+            CK(launch_kry_add64(x64, e, L, nblk, h->s));
+        }
+        CK(launch_kry_to32(x64, x, L, nblk, h->s));
+    }
+    if (iterations) *iterations = iters;
+    // certify with the stopping rule of the time march from the Krylov state
+    cl_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    cl_status st = cl_lbm_solve_budget(h, max_steps, &inf);
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return st;
 }
 
 cl_status cl_lbm_fluxes(cl_handle h, double out[5]) {

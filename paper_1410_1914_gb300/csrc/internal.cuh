@@ -30,6 +30,7 @@ struct StepArgs {
     float abb_in;        // 2 w C_in
     float abb_out;       // 2 w C_out
     float w_cin, w_cout; // w C_in, w C_out (reduction)
+    double rfac_d, abb_in_d, abb_out_d;  // the same three in FP64 (FP64 step)
     int bc_in, bc_out;   // cl_bc
     float* Csnap;        // C at the previous check (reduction)
     double* partials;    // [blocks][RED_N] (reduction)
@@ -49,6 +50,7 @@ struct Q19Args {
     const uint32_t* __restrict__ react;
     const float* __restrict__ omega;
     float rfac;           // (cs^2 - k_lu) / (cs^2 + k_lu), cs^2 = 1/3
+    double rfac_d;        // the same in FP64 (FP64 step)
     float c_in, c_out;
     double c_in_d, c_out_d;
     int bc_in, bc_out;
@@ -74,6 +76,8 @@ cudaError_t launch_init19(float* pop, const uint32_t* mask, const float* C0, int
                           double c_in, double c_out, float* Csnap, cudaStream_t s);
 int step19_blocks(const Q19Args& a);
 cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool reduce, cudaStream_t s);
+// the same step in FP64 on FP64 populations (no reduction)
+cudaError_t launch_step19_f64(const double* src, double* dst, const Q19Args& a, cudaStream_t s);
 cudaError_t launch_readout19(const float* pop, const Q19Args& a, double* out, cudaStream_t s);
 cudaError_t launch_out19(const float* pop, const uint32_t* mask, int nx, int ny, int nz, int px, float* C, float* g,
                          cudaStream_t s);
@@ -114,6 +118,8 @@ cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, 
                              int nz, double c_in, double c_out, float* Csnap, cudaStream_t s);
 cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce,
                              cudaStream_t s);
+// the same step in FP64 on FP64 populations (no reduction)
+cudaError_t launch_step_f64(const double* src, double* dst, const StepArgs& a, cudaStream_t s);
 int step_fp32_blocks(const StepArgs& a);
 cudaError_t launch_absmax(const float* v, long long N, double* partials, int nblocks, double* out,
                           cudaStream_t s);
@@ -123,5 +129,39 @@ cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long 
                               cudaStream_t s);
 // per-plane readout: out[5*nx]: sumC, count, R, J_in part, J_out part
 cudaError_t launch_readout_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s);
+
+// ---- Krylov steady solve (krylov.cu) ----
+enum KryFin { KRY_START = 0, KRY_ALPHA, KRY_OMEGA, KRY_BETA };
+struct KryScalars {
+    double rho, alpha, omega, beta;
+    double rr;  // r.r of the latest residual
+    int bad;    // 0 running; 1 breakdown or non-finite; 2 nothing left to solve
+    int iters;  // BiCGSTAB iterations completed
+};
+int kry_blocks();
+// r = c + sx - x (c nullable), rh = p = r; scalars from r.r
+cudaError_t launch_kry_start(const float* x, const float* sx, const float* c, float* r, float* rh, float* p,
+                             long long L, int nblk, double* part, KryScalars* ks, cudaStream_t s);
+// v = p - Ap; alpha = rho / rh.v
+cudaError_t launch_kry_v(const float* p, const float* ap, const float* rh, float* v, long long L, int nblk,
+                         double* part, KryScalars* ks, cudaStream_t s);
+// s = r - alpha v
+cudaError_t launch_kry_s(const float* r, const float* v, float* sv, long long L, int nblk, const KryScalars* ks,
+                         cudaStream_t s);
+// t = s - As; omega = t.s / t.t
+cudaError_t launch_kry_t(const float* sv, const float* as_, float* t, long long L, int nblk, double* part,
+                         KryScalars* ks, cudaStream_t s);
+// x += alpha p + omega s; r = s - omega t; beta, rho from rh.r; rr = r.r
+cudaError_t launch_kry_xr(float* x, const float* p, const float* sv, const float* t, const float* rh, float* r,
+                          long long L, int nblk, double* part, KryScalars* ks, cudaStream_t s);
+// p = r + beta (p - omega v)
+cudaError_t launch_kry_p(const float* r, const float* v, float* p, long long L, int nblk, const KryScalars* ks,
+                         cudaStream_t s);
+// mixed precision: b = a (f32 -> f64), b = (f32) a, x += e, and c = (f32)(sx - x) with ks->rr = |sx - x|^2 (FP64)
+cudaError_t launch_kry_to64(const float* a, double* b, long long L, int nblk, cudaStream_t s);
+cudaError_t launch_kry_to32(const double* a, float* b, long long L, int nblk, cudaStream_t s);
+cudaError_t launch_kry_add64(double* x, const float* e, long long L, int nblk, cudaStream_t s);
+cudaError_t launch_kry_res64(const double* x, const double* sx, float* c, long long L, int nblk, double* part,
+                             KryScalars* ks, cudaStream_t s);
 
 }  // namespace cl

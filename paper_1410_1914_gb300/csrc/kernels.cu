@@ -701,8 +701,11 @@ cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, 
 // unconditionally, so the six loads of a cell are in flight together; the
 // boundary rules act on the loaded values.  Offsets are 32-bit (I) while
 // the seven planes fit.
-template <bool REDUCE, class I>
-__global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src, float* __restrict__ dst,
+// T = double is the same step in FP64 arithmetic on FP64 populations (FP64
+// boundary values and reactive factor; omega as stored), used for the
+// residual of the mixed-precision steady solve.
+template <bool REDUCE, class I, class T = float>
+__global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T* __restrict__ dst,
                                                    StepArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -717,17 +720,19 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
     const I c = (I)x + (I)nx * (I)y + plane * (I)z;
     const uint16_t m = in_row ? a.mask[c] : (uint16_t)0;
     const bool act = (m & kActiveBit) != 0;
-    float h[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    constexpr bool kF64 = sizeof(T) == 8;
+    T h[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     {
         if (act) {
-            const float rf = a.rfac;
+            const T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
+            const T abb_in = kF64 ? (T)a.abb_in_d : (T)a.abb_in, abb_out = kF64 ? (T)a.abb_out_d : (T)a.abb_out;
             // source of population i (1..6 = +x, -x, +y, -y, +z, -z): x - c_i, y and z periodic
             const I sy_m = y == 0 ? (I)(ny - 1) * (I)nx : (I)0 - (I)nx;            // row y - 1
             const I sy_p = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)nx : (I)nx;       // row y + 1
             const I sz_m = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
             const I sz_p = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
             const I srcoff[7] = {0, (I)0 - (I)1, (I)1, sy_m, sy_p, sz_m, sz_p};
-            float v[7];
+            T v[7];
             v[0] = src[c];
 #pragma unroll
             for (int i = 1; i < 7; ++i) {
@@ -736,22 +741,22 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
                 const I e = closed ? (I)o * N + c : (I)i * N + c + srcoff[i];
                 v[i] = src[e];
             }
-            float g[7];
+            T g[7];
             g[0] = v[0];
 #pragma unroll
             for (int i = 1; i < 7; ++i) {
                 const int o = ((i - 1) ^ 1) + 1;
-                float gi = v[i];
+                T gi = v[i];
                 if ((m >> (o - 1)) & 1u) {
-                    if (i == 1 && x == 0) gi = a.bc_in == CL_BC_DIRICHLET ? a.abb_in - gi : gi;
-                    else if (i == 2 && x == nx - 1) gi = a.bc_out == CL_BC_DIRICHLET ? a.abb_out - gi : gi;
+                    if (i == 1 && x == 0) gi = a.bc_in == CL_BC_DIRICHLET ? abb_in - gi : gi;
+                    else if (i == 2 && x == nx - 1) gi = a.bc_out == CL_BC_DIRICHLET ? abb_out - gi : gi;
                     else if (m & (1u << (kReactShift + o - 1))) gi = rf * gi;
                 }
                 g[i] = gi;
             }
-            const float C = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
-            const float om = a.omega[c];
-            const float e0 = kW0 * C, e1 = kW1 * C;
+            const T C = ((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + g[6]);
+            const T om = (T)a.omega[c];
+            const T e0 = (T)kW0 * C, e1 = (T)kW1 * C;
             h[0] = g[0] - om * (g[0] - e0);
 #pragma unroll
             for (int i = 1; i < 7; ++i) h[i] = g[i] - om * (g[i] - e1);
@@ -772,7 +777,7 @@ __global__ void __launch_bounds__(128) k_step_fp32(const float* __restrict__ src
                 rv[RED_DC] = fabs(Cd - (double)a.Csnap[c]);
                 rv[RED_ABSC] = fabs(Cd);
                 rv[RED_NONFINITE] = isfinite(C) ? 0.0 : 1.0;
-                a.Csnap[c] = C;
+                a.Csnap[c] = (float)C;
             }
         }
     }
@@ -809,6 +814,13 @@ cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bo
         if (reduce) k_step_fp32<true, unsigned long long><<<g, 128, 0, s>>>(src, dst, a);
         else k_step_fp32<false, unsigned long long><<<g, 128, 0, s>>>(src, dst, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_f64(const double* src, double* dst, const StepArgs& a, cudaStream_t s) {
+    const dim3 g = step_grid(a);
+    if (!a.wide && 7LL * a.N < (1LL << 32)) k_step_fp32<false, uint32_t, double><<<g, 128, 0, s>>>(src, dst, a);
+    else k_step_fp32<false, unsigned long long, double><<<g, 128, 0, s>>>(src, dst, a);
     return cudaGetLastError();
 }
 

@@ -48,6 +48,11 @@ __host__ __device__ constexpr float q19_w(int i) {
     return i == 0 ? 1.f / 3.f : (i <= 6 ? 1.f / 18.f : 1.f / 36.f);
 }
 
+template <class T>
+__host__ __device__ constexpr T q19_wt(int i) {
+    return i == 0 ? T(1) / T(3) : (i <= 6 ? T(1) / T(18) : T(1) / T(36));
+}
+
 __device__ __forceinline__ int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 }  // namespace
@@ -180,8 +185,11 @@ cudaError_t launch_init19(float* pop, const uint32_t* mask, const float* C0, int
 // Stores: the lanes of a 32-byte sector (8 cells; the pitch is a multiple
 // of 32 cells) all store when any of them is active, none otherwise, so
 // that no sector is written in part (inactive cells store their zeros).
-template <bool REDUCE, class I>
-__global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict__ src, float* __restrict__ dst,
+// T = double is the same step in FP64 arithmetic on FP64 populations (with
+// the FP64 weights, boundary values and reactive factor; omega as stored),
+// used for the residual of the mixed-precision steady solve.
+template <bool REDUCE, class I, class T = float>
+__global__ void __launch_bounds__(kQ19Threads) k_step19(const T* __restrict__ src, T* __restrict__ dst,
                                                         Q19Args a) {
     const int x = blockIdx.x * kQ19Threads + threadIdx.x;
     const int y = blockIdx.y, z = blockIdx.z;
@@ -191,9 +199,10 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
     const bool in_row = x < px;
     const uint32_t m = in_row ? a.mask[c] : 0u;
     const bool act = (m & kQ19Active) != 0;
-    float h[19];
+    constexpr bool kF64 = sizeof(T) == 8;
+    T h[19];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) h[i] = 0.f;
+    for (int i = 0; i < 19; ++i) h[i] = T(0);
     double rv[RED_N];
     if (REDUCE)
 #pragma unroll
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
         const I oyp = y == ny - 1 ? (I)0 - (I)(ny - 1) * (I)px : (I)px;
         const I ozm = z == 0 ? (I)(nz - 1) * plane : (I)0 - plane;
         const I ozp = z == nz - 1 ? (I)0 - (I)(nz - 1) * plane : plane;
-        float v[19];
+        T v[19];
         bool own[19];
         v[0] = src[c];
 #pragma unroll
@@ -218,28 +227,30 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
             const I e = own[i] ? (I)j * NP + c : (I)i * NP + s;
             v[i] = src[e];
         }
-        float g[19];
+        const T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
+        const T cin = kF64 ? (T)a.c_in_d : (T)a.c_in, cout = kF64 ? (T)a.c_out_d : (T)a.c_out;
+        T g[19];
         g[0] = v[0];
 #pragma unroll
         for (int i = 1; i < 19; ++i) {
             const int j = q19_opp(i);
             const int cx = q19_cx(i);
-            const float wi = q19_w(i);
-            float o = v[i];
+            const T wi = q19_wt<T>(i);
+            T o = v[i];
             if (own[i]) {
-                if ((m >> (j - 1)) & 1u) o = ((rb >> (j - 1)) & 1u) ? a.rfac * o : o;
-                else if (cx > 0) o = a.bc_in == CL_BC_DIRICHLET ? 2.f * wi * a.c_in - o : o;
-                else o = a.bc_out == CL_BC_DIRICHLET ? 2.f * wi * a.c_out - o : o;
+                if ((m >> (j - 1)) & 1u) o = ((rb >> (j - 1)) & 1u) ? rf * o : o;
+                else if (cx > 0) o = a.bc_in == CL_BC_DIRICHLET ? T(2) * wi * cin - o : o;
+                else o = a.bc_out == CL_BC_DIRICHLET ? T(2) * wi * cout - o : o;
             }
             g[i] = o;
         }
         // C = sum g_i in a fixed pairwise order
-        const float C = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) +
+        const T C = (((g[0] + g[1]) + (g[2] + g[3])) + ((g[4] + g[5]) + (g[6] + g[7]))) +
                         (((g[8] + g[9]) + (g[10] + g[11])) + ((g[12] + g[13]) + (g[14] + g[15]))) +
                         ((g[16] + g[17]) + g[18]);
-        const float om = a.omega[c];
+        const T om = (T)a.omega[c];
 #pragma unroll
-        for (int i = 0; i < 19; ++i) h[i] = g[i] - om * (g[i] - q19_w(i) * C);
+        for (int i = 0; i < 19; ++i) h[i] = g[i] - om * (g[i] - q19_wt<T>(i) * C);
         if (REDUCE) {
             double jin = 0.0, jout = 0.0, r = 0.0;
 #pragma unroll
@@ -258,7 +269,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const float* __restrict_
             rv[RED_DC] = fabs((double)C - (double)a.Csnap[c]);
             rv[RED_ABSC] = fabs((double)C);
             rv[RED_NONFINITE] = isfinite(C) ? 0.0 : 1.0;
-            a.Csnap[c] = C;
+            a.Csnap[c] = (float)C;
         }
     }
     const unsigned lane = threadIdx.x & 31u;
@@ -291,6 +302,13 @@ cudaError_t launch_step19(const float* src, float* dst, const Q19Args& a, bool r
         if (reduce) k_step19<true, unsigned long long><<<g, kQ19Threads, 0, s>>>(src, dst, a);
         else k_step19<false, unsigned long long><<<g, kQ19Threads, 0, s>>>(src, dst, a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step19_f64(const double* src, double* dst, const Q19Args& a, cudaStream_t s) {
+    const dim3 g = step19_grid(a);
+    if (!a.wide && 19LL * a.NP < (1LL << 32)) k_step19<false, uint32_t, double><<<g, kQ19Threads, 0, s>>>(src, dst, a);
+    else k_step19<false, unsigned long long, double><<<g, kQ19Threads, 0, s>>>(src, dst, a);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,20 @@ class Solver:
         d["status"] = L.status_str(status)
         return d
 
+    def solve_krylov(self, tol: float = 1e-8, max_iter: int = 20000, max_steps: int | None = None):
+        """Mixed-precision Krylov solve of the fixed-point equation of the
+        step map (plain f32 populations only), then the stopping rule of the
+        time march from its result with at most max_steps steps (default:
+        the handle's max_steps).  Returns the solve info with "iterations"
+        (BiCGSTAB iterations) added."""
+        if max_steps is None:
+            max_steps = self.params.max_steps
+        status, info, it = L.cl_lbm_solve_krylov(self.h, tol, max_iter, max_steps)
+        d = info.as_dict()
+        d["status"] = L.status_str(status)
+        d["iterations"] = it
+        return d
+
     # ------------------------------------------------------------ readouts
     def fluxes(self):
         f = L.cl_lbm_fluxes(self.h)

@@ -1,0 +1,89 @@
+"""The fixed-point form of the steady state, on the FP64 oracle (no GPU).
+
+The Krylov steady solve of the library rests on two facts about the scheme
+of Eq. 21-24 with the boundaries of Sec. 3.5:
+  * one step S on the stored populations is affine, and its linear part A
+    is the same step with zero boundary concentrations:
+    S(x) = A x + S(0);
+  * the state the time march converges to is the solution of
+    (I - A) x = S(0), so a Krylov method on that system reaches the same
+    D_eff (Eq. 19) and reaction rate as the march, in far fewer
+    applications of the step.
+Both are checked here with the oracle's own step (scipy's BiCGSTAB as the
+library routine), on both lattices and on a reactive case.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_1914_gb300 import inputs
+
+SHAPE = (16, 18, 24)
+
+
+def _oracle(lattice, **extra):
+    ph, react, params = inputs.make_workload("pt_cl_48", shape=SHAPE, seed=51)
+    params.update(extra)
+    return oracle.OracleLBM(ph, react=react, lattice=lattice, **params), ph, react, params
+
+
+def _apply(o, x):
+    o.set_populations(x)
+    o.step(1)
+    return o.populations()
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_step_is_affine_with_zero_boundary_linear_part(lattice):
+    o, ph, react, params = _oracle(lattice)
+    o0 = oracle.OracleLBM(ph, react=react, lattice=lattice, **dict(params, c_in=0.0, c_out=0.0))
+    rng = np.random.default_rng(5)
+    shape = (o.q,) + o.shape
+    act = o.active().astype(bool)
+    x = rng.uniform(0.0, 0.2, shape) * act
+    y = rng.uniform(-0.1, 0.1, shape) * act
+    b = _apply(o, np.zeros(shape))
+    assert np.abs(b).max() > 0  # the Dirichlet terms
+    Ax = _apply(o0, x)
+    np.testing.assert_allclose(_apply(o, x) - b, Ax, rtol=0, atol=1e-15)
+    # linear: A(2x + y) = 2 Ax + Ay
+    np.testing.assert_allclose(_apply(o0, 2 * x + y), 2 * Ax + _apply(o0, y), rtol=0, atol=1e-15)
+    # inactive cells stay zero
+    assert np.all(Ax[:, ~act] == 0)
+
+
+@pytest.mark.parametrize("lattice,extra,readout", [
+    (0, {}, "deff"),
+    (1, {}, "deff"),
+    (0, dict(k_ms=2e4, bc_out=1), "R"),
+])
+def test_krylov_fixed_point_is_the_marched_steady_state(lattice, extra, readout):
+    from scipy.sparse.linalg import LinearOperator, bicgstab
+
+    march, ph, react, params = _oracle(lattice, **extra)
+    steps = march.solve(tol=1e-11, check_every=100, max_steps=2_000_000)
+    assert steps > 0
+    o, _, _, _ = _oracle(lattice, **extra)
+    o0 = oracle.OracleLBM(ph, react=react, lattice=lattice, **dict(params, c_in=0.0, c_out=0.0))
+    shape = (o.q,) + o.shape
+    n = int(np.prod(shape))
+    b = _apply(o, np.zeros(shape)).ravel()
+    count = [0]
+
+    def mv(v):
+        count[0] += 1
+        return v - _apply(o0, v.reshape(shape)).ravel()
+
+    o.init_linear()
+    x0 = o.populations().ravel()
+    x, info = bicgstab(LinearOperator((n, n), matvec=mv), b, x0=x0, rtol=1e-11, maxiter=5000)
+    assert info == 0
+    # the fixed point: one more step changes nothing
+    o.set_populations(x.reshape(shape))
+    assert np.linalg.norm(_apply(o, x.reshape(shape)).ravel() - x) <= 1e-9 * np.linalg.norm(x)
+    o.set_populations(x.reshape(shape))
+    if readout == "deff":
+        assert o.effective_diffusivity()[1] == pytest.approx(march.effective_diffusivity()[1], rel=1e-8)
+    else:
+        assert o.fluxes()["R"] == pytest.approx(march.fluxes()["R"], rel=1e-8)
+    assert count[0] * 10 < steps
