@@ -895,23 +895,31 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
             CK(cudaStreamSynchronize(h->s));
             return CL_OK;
         };
-        // BiCGSTAB in f32 on (I - A) e = c from e = 0, to tol_in times |c|
+        // BiCGSTAB in f32 on (I - A) e = c from e = 0, to tol_in times |c|.  Every pass starts from the
+        // true residual c - (I - A) e = c + A e - e; a pass ends on convergence of the recurrence, a breakdown,
+        // or growth of the recurrence residual (divergence), and the next pass (at most kMaxPasses) checks
+        // the true residual again.  A correction whose true residual is not below |c| is dropped (e = 0).
         auto correct = [&](double tol_in) -> cl_status {
             const double tol2 = tol_in * tol_in;
-            const int kBatch = 8;        // iterations between host reads of the scalars
-            const int kMaxRestarts = 4;  // restarts from the true residual (breakdown, drift of the recurrence)
+            const int kBatch = 8;       // iterations between host reads of the scalars
+            const int kMaxPasses = 5;
             double rr0 = -1.0;
             CK(cudaMemsetAsync(e, 0, sizeof(float) * (size_t)L, h->s));
-            for (int restart = 0;; ++restart) {
-                // true residual c - (I - A) e = c + A e - e
-                if (restart == 0) CK(launch_kry_start(e, c, nullptr, r, rh, pv, L, nblk, part, ks, h->s));
+            for (int pass = 0;; ++pass) {
+                if (pass == 0) CK(launch_kry_start(e, c, nullptr, r, rh, pv, L, nblk, part, ks, h->s));
                 else {
                     CK(step_pop(h, e, u, true));
                     CK(launch_kry_start(e, u, c, r, rh, pv, L, nblk, part, ks, h->s));
                 }
                 CKS(read());
                 if (rr0 < 0.0) rr0 = hs.rr;
-                if (hs.bad == 1 || hs.rr <= tol2 * rr0 || restart >= kMaxRestarts || iters >= max_iter) break;
+                if (hs.bad == 1 || (pass > 0 && !(hs.rr < rr0))) {
+                    // no better than e = 0
+                    CK(cudaMemsetAsync(e, 0, sizeof(float) * (size_t)L, h->s));
+                    break;
+                }
+                if (hs.rr <= tol2 * rr0 || pass + 1 >= kMaxPasses || iters >= max_iter) break;
+                double best = hs.rr;
                 while (iters < max_iter) {
                     const int n = std::min(kBatch, max_iter - iters);
                     for (int k = 0; k < n; ++k) {
@@ -925,13 +933,15 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
                     }
                     CKS(read());
                     iters = hs.iters;
-                    if (hs.bad || hs.rr <= tol2 * rr0) break;
+                    if (hs.bad || !isfinite(hs.rr) || hs.rr <= tol2 * rr0 || hs.rr > 1e4 * best) break;
+                    best = std::min(best, hs.rr);
                 }
             }
             return CL_OK;
         };
         // Mixed-precision refinement: the iterate x64 and its residual S(x64) - x64 in FP64 (the FP64 step),
-        // the correction in f32, so the result is not held to the rounding floor of f32 populations.
+        // the correction in f32, so the result is not held to the rounding floor of f32 populations.  A
+        // correction that does not reduce the FP64 residual is taken back, and the refinement stops.
         CK(launch_kry_to64(x, x64, L, nblk, h->s));
         const double tol2 = tol * tol;
         const int kMaxRefine = 30;
@@ -940,13 +950,16 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
             CK(step_f64(h, x64, y64));
             CK(launch_kry_res64(x64, y64, c, L, nblk, part, ks, h->s));
             CKS(read());
-            if (!isfinite(hs.rr)) break;
+            if (!(hs.rr < rr_prev)) {
+                if (ref > 0) CK(launch_kry_add64(x64, e, -1.0, L, nblk, h->s));
+                break;
+            }
             if (rr0 < 0.0) rr0 = hs.rr;
-            // converged, out of iterations, or no longer gaining (the f32 corrections stopped helping)
+            // converged, out of iterations, or gaining too little to go on
             if (hs.rr <= tol2 * rr0 || iters >= max_iter || !(hs.rr < 0.25 * rr_prev)) break;
             rr_prev = hs.rr;
             CKS(correct(kKryInnerTol));
-            CK(launch_kry_add64(x64, e, L, nblk, h->s));
+            CK(launch_kry_add64(x64, e, 1.0, L, nblk, h->s));
         }
         CK(launch_kry_to32(x64, x, L, nblk, h->s));
     }

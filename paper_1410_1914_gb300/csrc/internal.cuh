@@ -157,10 +157,10 @@ cudaError_t launch_kry_xr(float* x, const float* p, const float* sv, const float
 // p = r + beta (p - omega v)
 cudaError_t launch_kry_p(const float* r, const float* v, float* p, long long L, int nblk, const KryScalars* ks,
                          cudaStream_t s);
-// mixed precision: b = a (f32 -> f64), b = (f32) a, x += e, and c = (f32)(sx - x) with ks->rr = |sx - x|^2 (FP64)
+// mixed precision: b = a (f32 -> f64), b = (f32) a, x += sign e, and c = (f32)(sx - x) with ks->rr = |sx - x|^2 (FP64)
 cudaError_t launch_kry_to64(const float* a, double* b, long long L, int nblk, cudaStream_t s);
 cudaError_t launch_kry_to32(const double* a, float* b, long long L, int nblk, cudaStream_t s);
-cudaError_t launch_kry_add64(double* x, const float* e, long long L, int nblk, cudaStream_t s);
+cudaError_t launch_kry_add64(double* x, const float* e, double sign, long long L, int nblk, cudaStream_t s);
 cudaError_t launch_kry_res64(const double* x, const double* sx, float* c, long long L, int nblk, double* part,
                              KryScalars* ks, cudaStream_t s);
 

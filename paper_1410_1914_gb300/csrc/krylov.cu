@@ -239,9 +239,9 @@ __global__ void k_kry_to32(const double* __restrict__ a, float* __restrict__ b, 
         b[i] = (float)a[i];
 }
 
-__global__ void k_kry_add64(double* __restrict__ x, const float* __restrict__ e, long long L) {
+__global__ void k_kry_add64(double* __restrict__ x, const float* __restrict__ e, double sign, long long L) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L; i += (long long)gridDim.x * blockDim.x)
-        x[i] += e[i];
+        x[i] += sign * (double)e[i];
 }
 
 // c = S(x) - x in FP64 (sx = S(x)), stored as f32; partial |S(x) - x|^2 in FP64
@@ -317,8 +317,8 @@ cudaError_t launch_kry_to32(const double* a, float* b, long long L, int nblk, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_kry_add64(double* x, const float* e, long long L, int nblk, cudaStream_t s) {
-    k_kry_add64<<<nblk, kKryThreads, 0, s>>>(x, e, L);
+cudaError_t launch_kry_add64(double* x, const float* e, double sign, long long L, int nblk, cudaStream_t s) {
+    k_kry_add64<<<nblk, kKryThreads, 0, s>>>(x, e, sign, L);
     return cudaGetLastError();
 }
 
