@@ -242,6 +242,12 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
      tol:        > 0, relative to the initial residual norm.
      max_iter:   >= 0 BiCGSTAB iterations in all.
      iterations: nullable; the iterations taken.
+   Where it pays: with uniform relaxation times (bulk diffusivity, no
+   Knudsen term) the 48^3 Pt layer converges in about 330 iterations, far
+   fewer step applications than the march needs.  With the Knudsen term the
+   relaxation times spread over (1/2, 1], the unpreconditioned iteration
+   stalls after the first correction, and the call returns a state of lower
+   residual that is not converged: give max_steps for the march to finish.
    Needs storage CL_STORAGE_FP32POP (either lattice), else CL_ERR_STATE.
    Allocates 8 f32 and 2 FP64 population-sized vectors for the call
    (through p->alloc if given) and frees them before returning.
