@@ -1,5 +1,5 @@
-"""GB300-native D3Q7 reactive-diffusion lattice Boltzmann for catalyst layers
-(after Chen et al., arXiv:1410.1914).
+"""GB300-native reactive-diffusion lattice Boltzmann (D3Q7 and the paper's
+D3Q19) for catalyst layers (after Chen et al., arXiv:1410.1914).
 
 The solver is the CUDA library behind include/cl_lbm.h; ``Solver`` and the
 ``cl_*`` functions of ``_lib`` are its Python binding.  ``inputs`` generates
