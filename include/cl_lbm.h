@@ -256,6 +256,27 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
 cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
                               int* iterations);
 
+/* cl_lbm_solve_krylov with each f32 correction found by flexible GMRES(30)
+   with a diffusion preconditioner, for D3Q7 only.  The slow modes of the
+   step map are diffusive: a correction of equilibrium shape w_i eps changes
+   the cell sums by L eps in one step, L being the Laplacian of the active
+   cells with link weight 1/8 (2/8 on a fixed-concentration face, (1 - r)/8
+   on a catalytic face, 0 on a bounce-back face).  The preconditioner
+   P v = v + w_i eps with L eps = sum_i v_i (diagonal-preconditioned
+   conjugate gradients to 1e-2) keeps the number of step applications from
+   growing with the box or with the spread of relaxation times (Knudsen).
+   Each GMRES cycle (at most 10 per correction) restarts from the true
+   residual.  Refinement, stopping and certification as in
+   cl_lbm_solve_krylov.
+     iterations:       nullable; GMRES iterations (step applications).
+     inner_iterations: nullable; conjugate-gradient iterations in all.
+   Needs D3Q7 and CL_STORAGE_FP32POP, else CL_ERR_STATE.  Allocates 64 f32
+   and 2 FP64 population-sized vectors plus 6 f32 cell fields for the call
+   (through p->alloc if given) and frees them before returning.
+   Errors: as cl_lbm_solve_krylov. */
+cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
+                                  int* iterations, long long* inner_iterations);
+
 /* Lattice-unit fluxes of the current state, FP64 sums:
    out[0] J_in  net amount entering through x = 0 per step,
    out[1] J_out net amount leaving through x = L per step,

@@ -93,6 +93,9 @@ SIGNATURES = {
     "cl_lbm_solve_budget": (_S, [_H, ctypes.c_longlong, ctypes.POINTER(cl_solve_info)]),
     "cl_lbm_solve_krylov": (_S, [_H, ctypes.c_double, ctypes.c_int, ctypes.c_longlong,
                                  ctypes.POINTER(cl_solve_info), ctypes.POINTER(ctypes.c_int)]),
+    "cl_lbm_solve_krylov_dsa": (_S, [_H, ctypes.c_double, ctypes.c_int, ctypes.c_longlong,
+                                     ctypes.POINTER(cl_solve_info), ctypes.POINTER(ctypes.c_int),
+                                     ctypes.POINTER(ctypes.c_longlong)]),
     "cl_lbm_fluxes": (_S, [_H, _P]),
     "cl_lbm_effective_diffusivity": (_S, [_H, _P, _P]),
     "cl_lbm_reaction_rate": (_S, [_H, _P, _P, _P]),
@@ -300,6 +303,17 @@ def cl_lbm_solve_krylov(h: int, tol: float, max_iter: int, max_steps: int) -> tu
     if s not in (CL_OK, CL_ERR_NOT_CONVERGED):
         _check(s, "cl_lbm_solve_krylov")
     return s, info, it.value
+
+
+def cl_lbm_solve_krylov_dsa(h: int, tol: float, max_iter: int, max_steps: int) -> tuple[int, cl_solve_info, int, int]:
+    info = cl_solve_info()
+    it = ctypes.c_int(0)
+    inner = ctypes.c_longlong(0)
+    s = load().cl_lbm_solve_krylov_dsa(h, float(tol), int(max_iter), int(max_steps), ctypes.byref(info),
+                                       ctypes.byref(it), ctypes.byref(inner))
+    if s not in (CL_OK, CL_ERR_NOT_CONVERGED):
+        _check(s, "cl_lbm_solve_krylov_dsa")
+    return s, info, it.value, inner.value
 
 
 def cl_lbm_fluxes(h: int) -> np.ndarray:

@@ -973,6 +973,192 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
     return st;
 }
 
+cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
+                                  int* iterations, long long* inner_iterations) {
+    CKS(need_structure(h));
+    if (h->march || h->q19s || h->q != 7) {
+        set_msg_txt("the preconditioned Krylov solve needs D3Q7 with the plain f32 population storage");
+        return CL_ERR_STATE;
+    }
+    if (!(tol > 0.0) || max_iter < 0 || max_steps < 0) {
+        set_msg_txt("tol must be > 0, max_iter and max_steps >= 0");
+        return CL_ERR_ARG;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    const long long N = h->N, L = 7 * h->N;
+    const int nblk = kry_blocks();
+    constexpr int kM = 30;           // Krylov vectors per GMRES cycle
+    constexpr int kMaxCycles = 10;   // cycles per correction
+    constexpr int kCgBatch = 8;      // CG iterations between host reads
+    constexpr int kMaxCg = 4000;     // CG iterations per preconditioner application
+    const double kCgTol = 1e-2;      // relative residual of the inner CG solve
+    int iters = 0;
+    long long cg_total = 0;
+    {
+        Scratch sc(h);
+        float* V[kM + 1];
+        float* Z[kM];
+        for (int k = 0; k <= kM; ++k) CKS(sc.get((void**)&V[k], sizeof(float) * (size_t)L));
+        for (int k = 0; k < kM; ++k) CKS(sc.get((void**)&Z[k], sizeof(float) * (size_t)L));
+        float *wv = nullptr, *e = nullptr, *c = nullptr;
+        CKS(sc.get((void**)&wv, sizeof(float) * (size_t)L));
+        CKS(sc.get((void**)&e, sizeof(float) * (size_t)L));
+        CKS(sc.get((void**)&c, sizeof(float) * (size_t)L));
+        float* cell[6];  // eps, r, z, p, q of the inner CG, and 1/diag(L)
+        for (int k = 0; k < 6; ++k) {
+            CKS(sc.get((void**)&cell[k], sizeof(float) * (size_t)N));
+            CK(cudaMemsetAsync(cell[k], 0, sizeof(float) * (size_t)N, h->s));
+        }
+        float *eps = cell[0], *rc = cell[1], *zc = cell[2], *pc = cell[3], *qc = cell[4], *dinv = cell[5];
+        double *x64 = nullptr, *y64 = nullptr, *part = nullptr, *dH = nullptr, *dnrm = nullptr, *dy = nullptr;
+        KryScalars* ks = nullptr;
+        CgScalars* cs = nullptr;
+        CKS(sc.get((void**)&x64, sizeof(double) * (size_t)L));
+        CKS(sc.get((void**)&y64, sizeof(double) * (size_t)L));
+        CK(cudaMemsetAsync(y64, 0, sizeof(double) * (size_t)L, h->s));
+        CKS(sc.get((void**)&part, sizeof(double) * 2 * (size_t)nblk));
+        CKS(sc.get((void**)&dH, sizeof(double) * (kM + 1) * kM));
+        CKS(sc.get((void**)&dnrm, sizeof(double)));
+        CKS(sc.get((void**)&dy, sizeof(double) * kM));
+        CKS(sc.get((void**)&ks, sizeof(KryScalars)));
+        CKS(sc.get((void**)&cs, sizeof(CgScalars)));
+        CK(cudaMemsetAsync(ks, 0, sizeof(KryScalars), h->s));
+        CK(cudaMemsetAsync(cs, 0, sizeof(CgScalars), h->s));
+        float* x = h->pop[h->cur];
+        float* u = h->pop[h->cur ^ 1];  // A(.) output; the next step of the march rewrites it
+        DsaArgs da;
+        da.nx = h->nx; da.ny = h->ny; da.nz = h->nz; da.N = N;
+        da.mask = h->mask;
+        da.rfac = reactive_factor(h);
+        da.bc_in = h->p.bc_in; da.bc_out = h->p.bc_out;
+        CK(launch_lap_dinv(da, dinv, nblk, h->s));
+        auto host_double = [&](const double* dptr, double* out, int n) -> cl_status {
+            CK(cudaMemcpyAsync(out, dptr, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            return CL_OK;
+        };
+        // P v = v + w_i eps, L eps = sum_i v_i to kCgTol by diagonal-preconditioned CG
+        auto precondition = [&](const float* v, float* zout) -> cl_status {
+            CK(launch_cg_start(da, v, dinv, eps, rc, zc, pc, nblk, part, cs, h->s));
+            CgScalars hc;
+            CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            while (!hc.bad && hc.iters < kMaxCg && hc.rr > kCgTol * kCgTol * hc.rr0) {
+                for (int k = 0; k < kCgBatch; ++k) CK(launch_cg_iter(da, dinv, eps, rc, zc, pc, qc, nblk, part, cs, h->s));
+                CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, h->s));
+                CK(cudaStreamSynchronize(h->s));
+            }
+            cg_total += hc.iters;
+            CK(launch_prec_out(N, v, eps, zout, nblk, h->s));
+            return CL_OK;
+        };
+        // flexible GMRES(kM) in f32 on (I - A) e = c from e = 0, to tol_in times |c|
+        auto correct = [&](double tol_in) -> cl_status {
+            CK(cudaMemsetAsync(e, 0, sizeof(float) * (size_t)L, h->s));
+            double beta0 = 0.0;
+            CK(launch_dot_dev(c, c, L, nblk, part, dnrm, 1, h->s));
+            CKS(host_double(dnrm, &beta0, 1));
+            if (!(beta0 > 0.0) || !isfinite(beta0)) return CL_OK;
+            double H[kM + 1][kM], cs_[kM], sn_[kM], g[kM + 1], col[kM + 1], y[kM];
+            for (int cyc = 0; cyc < kMaxCycles && iters < max_iter; ++cyc) {
+                double beta = 0.0;
+                if (cyc == 0) {
+                    CK(launch_scale_dev(V[0], c, dnrm, L, nblk, h->s));
+                    beta = beta0;
+                } else {
+                    CK(step_pop(h, e, u, true));
+                    CK(launch_comb(c, e, u, wv, L, nblk, h->s));  // c - (I - A) e
+                    CK(launch_dot_dev(wv, wv, L, nblk, part, dnrm, 1, h->s));
+                    CKS(host_double(dnrm, &beta, 1));
+                    if (!isfinite(beta)) break;
+                    if (beta <= tol_in * beta0) break;
+                    CK(launch_scale_dev(V[0], wv, dnrm, L, nblk, h->s));
+                }
+                for (int k = 0; k <= kM; ++k) g[k] = 0.0;
+                g[0] = beta;
+                int jend = 0;
+                double resid = beta;
+                for (int j = 0; j < kM && iters < max_iter; ++j) {
+                    CKS(precondition(V[j], Z[j]));
+                    CK(step_pop(h, Z[j], u, true));
+                    CK(launch_comb(Z[j], u, nullptr, wv, L, nblk, h->s));  // (I - A) Z_j
+                    ++iters;
+                    // modified Gram-Schmidt, coefficients kept on the device
+                    for (int k = 0; k <= j; ++k) {
+                        double* hk = dH + k + (kM + 1) * j;
+                        CK(launch_dot_dev(V[k], wv, L, nblk, part, hk, 0, h->s));
+                        CK(launch_axpy_dev(wv, V[k], hk, -1.f, L, nblk, h->s));
+                    }
+                    double* hn = dH + (j + 1) + (kM + 1) * j;
+                    CK(launch_dot_dev(wv, wv, L, nblk, part, hn, 1, h->s));
+                    CK(launch_scale_dev(V[j + 1], wv, hn, L, nblk, h->s));
+                    CKS(host_double(dH + (kM + 1) * j, col, j + 2));
+                    // Givens rotations: the earlier ones, then a new one that zeroes col[j + 1]
+                    for (int k = 0; k < j; ++k) {
+                        const double a = cs_[k] * col[k] + sn_[k] * col[k + 1];
+                        col[k + 1] = -sn_[k] * col[k] + cs_[k] * col[k + 1];
+                        col[k] = a;
+                    }
+                    const double den = sqrt(col[j] * col[j] + col[j + 1] * col[j + 1]);
+                    jend = j + 1;
+                    if (!(den > 0.0) || !isfinite(den)) { jend = j; break; }
+                    cs_[j] = col[j] / den;
+                    sn_[j] = col[j + 1] / den;
+                    col[j] = den;
+                    col[j + 1] = 0.0;
+                    g[j + 1] = -sn_[j] * g[j];
+                    g[j] = cs_[j] * g[j];
+                    for (int k = 0; k <= j; ++k) H[k][j] = col[k];
+                    resid = fabs(g[j + 1]);
+                    if (resid <= tol_in * beta0) break;
+                }
+                if (jend == 0) break;
+                // back substitution R y = g, then e += sum_k y_k Z_k
+                for (int k = jend - 1; k >= 0; --k) {
+                    double t = g[k];
+                    for (int l = k + 1; l < jend; ++l) t -= H[k][l] * y[l];
+                    y[k] = t / H[k][k];
+                }
+                CK(cudaMemcpyAsync(dy, y, sizeof(double) * jend, cudaMemcpyHostToDevice, h->s));
+                for (int k = 0; k < jend; ++k) CK(launch_axpy_dev(e, Z[k], dy + k, 1.f, L, nblk, h->s));
+                CK(cudaStreamSynchronize(h->s));  // y lives on the host stack
+                if (resid <= tol_in * beta0) break;
+            }
+            return CL_OK;
+        };
+        // mixed-precision refinement, as in cl_lbm_solve_krylov
+        CK(launch_kry_to64(x, x64, L, nblk, h->s));
+        const double tol2 = tol * tol;
+        const int kMaxRefine = 30;
+        double rr0 = -1.0, rr_prev = INFINITY;
+        KryScalars hs;
+        for (int ref = 0; ref < kMaxRefine; ++ref) {
+            CK(step_f64(h, x64, y64));
+            CK(launch_kry_res64(x64, y64, c, L, nblk, part, ks, h->s));
+            CK(cudaMemcpyAsync(&hs, ks, sizeof(hs), cudaMemcpyDeviceToHost, h->s));
+            CK(cudaStreamSynchronize(h->s));
+            if (!(hs.rr < rr_prev)) {
+                if (ref > 0) CK(launch_kry_add64(x64, e, -1.0, L, nblk, h->s));
+                break;
+            }
+            if (rr0 < 0.0) rr0 = hs.rr;
+            if (hs.rr <= tol2 * rr0 || iters >= max_iter || !(hs.rr < 0.25 * rr_prev)) break;
+            rr_prev = hs.rr;
+            CKS(correct(kKryInnerTol));
+            CK(launch_kry_add64(x64, e, 1.0, L, nblk, h->s));
+        }
+        CK(launch_kry_to32(x64, x, L, nblk, h->s));
+    }
+    if (iterations) *iterations = iters;
+    if (inner_iterations) *inner_iterations = cg_total;
+    cl_solve_info inf;
+    memset(&inf, 0, sizeof(inf));
+    cl_status st = cl_lbm_solve_budget(h, max_steps, &inf);
+    inf.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = inf;
+    return st;
+}
+
 cl_status cl_lbm_fluxes(cl_handle h, double out[5]) {
     CKS(need_structure(h));
     if (!out) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }

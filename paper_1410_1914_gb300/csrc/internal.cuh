@@ -164,4 +164,39 @@ cudaError_t launch_kry_add64(double* x, const float* e, double sign, long long L
 cudaError_t launch_kry_res64(const double* x, const double* sx, float* c, long long L, int nblk, double* part,
                              KryScalars* ks, cudaStream_t s);
 
+// ---- diffusion preconditioner and flexible GMRES (dsa.cu), D3Q7
+struct DsaArgs {
+    int nx, ny, nz;
+    long long N;
+    const uint16_t* __restrict__ mask;
+    float rfac;          // reactive factor r of a catalytic face
+    int bc_in, bc_out;   // cl_bc
+};
+enum CgFin { CG_START = 0, CG_ALPHA, CG_BETA };
+struct CgScalars {
+    double rz, alpha, beta;
+    double rr, rr0;  // r.r now and at the start
+    int iters;       // iterations of this solve
+    int bad;         // 0 running; 1 breakdown or non-finite; 2 nothing left to solve
+};
+// dinv = 1 / diag(L) on active cells (0 elsewhere)
+cudaError_t launch_lap_dinv(const DsaArgs& a, float* dinv, int nblk, cudaStream_t s);
+// eps = 0, r = sum_i v_i (v: 7 population planes), z = dinv r, p = z; scalars
+cudaError_t launch_cg_start(const DsaArgs& a, const float* v, const float* dinv, float* eps, float* r, float* zc,
+                            float* p, int nblk, double* part, CgScalars* cs, cudaStream_t s);
+// one CG iteration on L eps = r0
+cudaError_t launch_cg_iter(const DsaArgs& a, const float* dinv, float* eps, float* r, float* zc, float* p, float* q,
+                           int nblk, double* part, CgScalars* cs, cudaStream_t s);
+// zout_i = v_i + w_i eps
+cudaError_t launch_prec_out(long long N, const float* v, const float* eps, float* zout, int nblk, cudaStream_t s);
+// *out = x.y (or its square root) in FP64, on the device
+cudaError_t launch_dot_dev(const float* x, const float* y, long long L, int nblk, double* part, double* out,
+                           int take_sqrt, cudaStream_t s);
+// y += sign * coef[0] * x; y = x / nrm[0]; out = a - b (+ c)
+cudaError_t launch_axpy_dev(float* y, const float* x, const double* coef, float sign, long long L, int nblk,
+                            cudaStream_t s);
+cudaError_t launch_scale_dev(float* y, const float* x, const double* nrm, long long L, int nblk, cudaStream_t s);
+cudaError_t launch_comb(const float* a, const float* b, const float* c, float* out, long long L, int nblk,
+                        cudaStream_t s);
+
 }  // namespace cl

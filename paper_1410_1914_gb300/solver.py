@@ -94,6 +94,20 @@ class Solver:
         d["iterations"] = it
         return d
 
+    def solve_krylov_dsa(self, tol: float = 1e-8, max_iter: int = 20000, max_steps: int | None = None):
+        """solve_krylov with flexible GMRES and the diffusion preconditioner
+        (D3Q7, plain f32 populations).  Adds "iterations" (step
+        applications) and "inner_iterations" (conjugate-gradient
+        iterations) to the solve info."""
+        if max_steps is None:
+            max_steps = self.params.max_steps
+        status, info, it, inner = L.cl_lbm_solve_krylov_dsa(self.h, tol, max_iter, max_steps)
+        d = info.as_dict()
+        d["status"] = L.status_str(status)
+        d["iterations"] = it
+        d["inner_iterations"] = inner
+        return d
+
     # ------------------------------------------------------------ readouts
     def fluxes(self):
         f = L.cl_lbm_fluxes(self.h)
