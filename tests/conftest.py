@@ -11,8 +11,6 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built CUDA library")
     config.addinivalue_line("markers", "slow: long-running case")
-    config.addinivalue_line("markers", "gpu_staged: needs a CUDA GPU; a path not yet run on one, kept out of "
-                                       "-m gpu until it has passed there (run with -m gpu_staged)")
 
 
 @pytest.fixture(scope="session", autouse=True)

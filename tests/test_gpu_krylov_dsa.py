@@ -1,9 +1,5 @@
 """The diffusion-preconditioned Krylov steady solve
-(cl_lbm_solve_krylov_dsa) against the FP64 oracle, through the C ABI.
-
-Marked gpu_staged: this path has not run on a GPU yet, so `-m gpu` does not
-select it; run it with `python -m pytest tests -m gpu_staged`.  On the CPU
-the cuda_lib fixture skips it.
+(cl_lbm_solve_krylov_dsa) against the FP64 oracle, through the C ABI (gpu).
 
 Cases: the bulk-D 48^3 layer against the golden converged D_eff (1e-3);
 a Knudsen Pt layer, where the unpreconditioned solve stalls, against the
@@ -19,7 +15,7 @@ import pytest
 import oracle
 from paper_1410_1914_gb300 import inputs
 
-pytestmark = pytest.mark.gpu_staged
+pytestmark = pytest.mark.gpu
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 
