@@ -87,3 +87,59 @@ def test_krylov_fixed_point_is_the_marched_steady_state(lattice, extra, readout)
     else:
         assert o.fluxes()["R"] == pytest.approx(march.fluxes()["R"], rel=1e-8)
     assert count[0] * 10 < steps
+
+
+C7 = [(0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+C19 = C7 + [(1, 1, 0), (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 0, 1), (-1, 0, -1), (1, 0, -1), (-1, 0, 1),
+            (0, 1, 1), (0, -1, -1), (0, 1, -1), (0, -1, 1)]
+
+
+def _link_laplacian(o, params):
+    """L eps in numpy from the link classes: an open link moves w_i (eps_c -
+    eps_end) out of a cell, a fixed-concentration boundary link 2 w_i eps_c,
+    a catalytic wall link (1 - r) w_i eps_c, a bounce-back link nothing."""
+    q = o.q
+    c = C19 if q == 19 else C7
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12) if q == 19 else np.array([0.25] + [0.125] * 6)
+    cs2 = 1 / 3 if q == 19 else 0.25
+    r = (cs2 - o.k_lu) / (cs2 + o.k_lu)
+    act = o.active().astype(bool)
+    react = o.react()
+    nz, ny, nx = o.shape
+
+    def apply(eps):
+        out = np.zeros(o.shape)
+        for z, y, x in zip(*np.nonzero(act)):
+            for i in range(1, q):
+                cx, cy, cz = c[i]
+                ex, ey, ez = x + cx, (y + cy) % ny, (z + cz) % nz
+                leaves = not 0 <= ex < nx
+                end = (ez, ey, x) if leaves else (ez, ey, ex)  # mirror end cell for a link that leaves in x
+                if act[end] and not leaves:
+                    out[z, y, x] += w[i] * (eps[z, y, x] - eps[end])
+                elif act[end]:
+                    bc = params["bc_in"] if cx < 0 else params["bc_out"]
+                    out[z, y, x] += 2 * w[i] * eps[z, y, x] if bc == 0 else 0.0
+                elif (react[z, y, x] >> (i - 1)) & 1:
+                    out[z, y, x] += (1 - r) * w[i] * eps[z, y, x]
+        return out
+    return apply
+
+
+@pytest.mark.parametrize("lattice", [0, 1])
+def test_one_step_mass_response_is_the_link_laplacian(lattice):
+    """The operator behind the diffusion preconditioner: from an
+    equilibrium-shaped state w_i eps, one step with zero boundary values
+    changes the cell sums by exactly -L eps."""
+    ph, _, params = inputs.make_workload("pt_cl_256", shape=(6, 7, 12), seed=61)
+    react = inputs.reactive_faces(ph, 0.5, 3)
+    params = dict(params, k_ms=3e4, bc_out=0, c_in=0.0, c_out=0.0)
+    o = oracle.OracleLBM(ph, react=react, lattice=lattice, **params)
+    act = o.active().astype(bool)
+    assert ((o.react() != 0) & act).any()
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12) if o.q == 19 else np.array([0.25] + [0.125] * 6)
+    eps = np.random.default_rng(7).uniform(0.2, 1.0, o.shape) * act
+    o.set_populations(w[:, None, None, None] * eps[None])
+    o.step(1)
+    dC = o.populations().sum(axis=0) - eps
+    np.testing.assert_allclose(dC, -_link_laplacian(o, params)(eps), rtol=0, atol=1e-14)
