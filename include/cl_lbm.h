@@ -263,10 +263,11 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
    cells with link weight 1/8 (2/8 on a fixed-concentration face, (1 - r)/8
    on a catalytic face, 0 on a bounce-back face).  The preconditioner
    P v = v + w_i eps with L eps = sum_i v_i (diagonal-preconditioned
-   conjugate gradients to 1e-2) keeps the number of step applications from
-   growing with the box or with the spread of relaxation times (Knudsen):
-   15 for the bulk-D 48^3 Pt layer, about 80 for Knudsen layers of 24^3 and
-   32^3, where the unpreconditioned solve stalls.
+   conjugate gradients to 1e-2) keeps the number of step applications
+   small as the box grows (it levels off near 100) and with a spread of
+   relaxation times (Knudsen): 15 for the bulk-D 48^3 Pt layer, about 80
+   for Knudsen layers of 24^3 and 32^3, where the unpreconditioned solve
+   stalls.
    Each GMRES cycle (at most 10 per correction) restarts from the true
    residual.  Refinement, stopping and certification as in
    cl_lbm_solve_krylov.

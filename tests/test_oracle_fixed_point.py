@@ -143,3 +143,82 @@ def test_one_step_mass_response_is_the_link_laplacian(lattice):
     o.step(1)
     dC = o.populations().sum(axis=0) - eps
     np.testing.assert_allclose(dC, -_link_laplacian(o, params)(eps), rtol=0, atol=1e-14)
+
+
+def _laplacian_matrix(o, params):
+    """The D3Q7 link Laplacian of _link_laplacian as a sparse matrix over the
+    active cells (vectorised; periodic y, z)."""
+    import scipy.sparse as sp
+    act = o.active().astype(bool)
+    nz, ny, nx = o.shape
+    r = (0.25 - o.k_lu) / (0.25 + o.k_lu)
+    react = o.react()
+    idx = -np.ones(o.shape, np.int64)
+    idx[act] = np.arange(act.sum())
+    zz, yy, xx = np.nonzero(act)
+    me = idx[zz, yy, xx]
+    rows, cols, vals = [], [], []
+    for i, (cx, cy, cz) in enumerate(C7[1:], start=1):
+        ex, ey, ez = xx + cx, (yy + cy) % ny, (zz + cz) % nz
+        leaves = (ex < 0) | (ex >= nx)
+        end = idx[ez, ey, np.clip(ex, 0, nx - 1)]
+        open_ = ~leaves & (end >= 0)
+        rows += [me[open_], me[open_]]
+        cols += [me[open_], end[open_]]
+        vals += [np.full(open_.sum(), 0.125), np.full(open_.sum(), -0.125)]
+        bc = params["bc_in"] if cx < 0 else params["bc_out"]
+        if bc == 0:
+            rows.append(me[leaves]); cols.append(me[leaves]); vals.append(np.full(leaves.sum(), 0.25))
+        sink = ~leaves & (end < 0) & (((react[zz, yy, xx] >> (i - 1)) & 1) == 1)
+        rows.append(me[sink]); cols.append(me[sink]); vals.append(np.full(sink.sum(), (1 - r) * 0.125))
+    n = int(act.sum())
+    return sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+def test_diffusion_preconditioner_count_does_not_grow_with_the_box():
+    """GMRES on (I - A) x = b, right-preconditioned by P v = v + w_i eps
+    with L eps = sum_i v_i (exact inner solve), on Knudsen Pt layers: the
+    step applications grow less than the edge from 16^3 to 32^3 (they
+    level off near 100 beyond that), stay far below the unpreconditioned
+    count, and the result is the march's fixed point."""
+    from scipy.sparse.linalg import LinearOperator, bicgstab, gmres, splu
+
+    w = np.array([0.25] + [0.125] * 6)
+    counts = {}
+    for edge in (16, 32):
+        ph, react, params = inputs.make_workload("pt_cl_256", shape=(edge, edge, edge), reactive=False)
+        o = oracle.OracleLBM(ph, react=react, **params)
+        o0 = oracle.OracleLBM(ph, react=react, **dict(params, c_in=0.0, c_out=0.0))
+        act = o.active().astype(bool)
+        lu = splu(_laplacian_matrix(o, params))
+        shape = (7,) + o.shape
+        n = int(np.prod(shape))
+        b = _apply(o, np.zeros(shape)).ravel()
+        cnt = [0]
+
+        def mv(v):
+            cnt[0] += 1
+            return v - _apply(o0, v.reshape(shape)).ravel()
+
+        def prec(v):
+            V = v.reshape(shape)
+            eps = np.zeros(o.shape)
+            eps[act] = lu.solve(V.sum(axis=0)[act])
+            return (V + w[:, None, None, None] * eps[None]).ravel()
+
+        o.init_linear()
+        x0 = o.populations().ravel()
+        r0 = b - mv(x0)
+        cnt[0] = 0
+        y, info = gmres(LinearOperator((n, n), matvec=lambda v: mv(prec(v))), r0, rtol=1e-10, restart=50,
+                        maxiter=20)
+        assert info == 0
+        counts[edge] = cnt[0]
+        x = x0 + prec(y)
+        assert np.linalg.norm(_apply(o, x.reshape(shape)).ravel() - x) <= 1e-8 * np.linalg.norm(x)
+        if edge == 16:
+            cnt[0] = 0
+            _, info = bicgstab(LinearOperator((n, n), matvec=mv), b, x0=x0, rtol=1e-10, maxiter=20000)
+            unprec = cnt[0]
+    assert counts[32] < 2 * counts[16] and counts[32] <= 150, counts
+    assert unprec >= 4 * counts[16], (unprec, counts)
