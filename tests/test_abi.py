@@ -127,6 +127,12 @@ def test_null_handle_calls(lib):
     from paper_1410_1914_gb300 import _lib
     info = _lib.cl_solve_info()
     assert lib.cl_lbm_solve(None, ctypes.byref(info)) == _lib.CL_ERR_ARG
+    it = ctypes.c_int(-1)
+    inner = ctypes.c_longlong(-1)
+    assert lib.cl_lbm_solve_krylov(None, 1e-8, 10, 0, ctypes.byref(info), ctypes.byref(it)) == _lib.CL_ERR_ARG
+    assert lib.cl_lbm_solve_krylov_dsa(None, 1e-8, 10, 0, ctypes.byref(info), ctypes.byref(it),
+                                       ctypes.byref(inner)) == _lib.CL_ERR_ARG
+    assert it.value == -1 and inner.value == -1  # outputs untouched on CL_ERR_ARG
     lib.cl_lbm_destroy(None)  # ignored
 
 
