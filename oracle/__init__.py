@@ -94,6 +94,9 @@ def lib():
                 "orc_lbm_concentration": (None, [_P, _P]),
                 "orc_lbm_populations": (None, [_P, _P]),
                 "orc_lbm_set_populations": (None, [_P, _P]),
+                "orc_lbm_set_kscale": (None, [_P, _P]),
+                "orc_lbm_set_source": (None, [_P, _P]),
+                "orc_lbm_cell_reaction": (None, [_P, _P]),
                 "orc_lbm_fluxes": (None, [_P, _P]),
                 "orc_lbm_effective_diffusivity": (None, [_P, _P]),
                 "orc_lbm_reaction_rate": (_D, [_P, _P, _P]),
@@ -300,6 +303,31 @@ class OracleLBM:
         entries of inactive cells are ignored (kept 0)."""
         g = np.ascontiguousarray(g, dtype=np.float64).reshape((self.q,) + self.shape)
         lib().orc_lbm_set_populations(self._h, _ptr(g))
+
+    def set_rate_scale(self, k):
+        """Per-cell factor on the rate constant k of the catalytic faces
+        (Eq. 17b with a non-uniform potential); None restores uniform k."""
+        if k is None:
+            self._kscale = None
+            lib().orc_lbm_set_kscale(self._h, None)
+            return
+        self._kscale = np.ascontiguousarray(k, dtype=np.float64).reshape(self.shape)
+        lib().orc_lbm_set_kscale(self._h, _ptr(self._kscale))
+
+    def set_source(self, S):
+        """Per-cell amount added to C per step in lattice units (the source
+        of Eq. 16, entering as w_i S after collision); None removes it."""
+        if S is None:
+            lib().orc_lbm_set_source(self._h, None)
+            return
+        S = np.ascontiguousarray(S, dtype=np.float64).reshape(self.shape)
+        lib().orc_lbm_set_source(self._h, _ptr(S))
+
+    def cell_reaction(self):
+        """Amount consumed per step on each cell's reactive links (lattice units)."""
+        out = np.zeros(self.shape)
+        lib().orc_lbm_cell_reaction(self._h, _ptr(out))
+        return out
 
     def fluxes(self):
         out = np.zeros(5)

@@ -383,6 +383,8 @@ typedef struct {
     double* tau;       /* per-cell relaxation time, Eq. 24 with the lattice's cs^2 */
     double* g;         /* current pre-collision populations */
     double* gn;        /* scratch for the next step */
+    double* kscale;    /* per-cell factor on k (non-uniform potential, Eq. 17b); NULL: 1 */
+    double* src;       /* per-cell amount added per step (the source of Eq. 16); NULL: none */
     double D_b, D_max, dt, k_lu;
     long step;
 } orc_lbm;
@@ -454,7 +456,7 @@ orc_lbm* orc_lbm_new(const orc_params* p, const uint8_t* phase, const uint8_t* r
                                     s->active);
     if (n_active == 0) { /* nothing percolates */
         free(s->phase); free(s->active); free(s->react); free(s->D); free(s->tau);
-        free(s->g); free(s->gn); free(s);
+        free(s->g); free(s->gn); free(s->kscale); free(s->src); free(s);
         return NULL;
     }
     if (D_override) {
@@ -508,7 +510,7 @@ void orc_lbm_free(orc_lbm* s)
 {
     if (!s) return;
     free(s->phase); free(s->active); free(s->react); free(s->D); free(s->tau);
-    free(s->g); free(s->gn); free(s);
+    free(s->g); free(s->gn); free(s->kscale); free(s->src); free(s);
 }
 
 /* g_i = w_i C  (Eq. 23 equilibrium) for a given field C (active cells only) */
@@ -532,14 +534,16 @@ void orc_lbm_init_linear(orc_lbm* s)
     free(C);
 }
 
-/* post-collision populations of Eq. 21: g* = g - (g - g_eq) / tau */
+/* post-collision populations of Eq. 21: g* = g - (g - g_eq) / tau, plus
+ * w_i S of a per-cell source S (the a_i S term of Eq. 21) where one is set */
 static void collide_cell(const orc_lbm* s, long c, double gs[QMAX])
 {
     double C = 0.0;
     for (int i = 0; i < s->L->q; ++i) C += s->g[i * s->N + c];
+    const double S = s->src ? s->src[c] : 0.0;
     for (int i = 0; i < s->L->q; ++i) {
         double gi = s->g[i * s->N + c];
-        gs[i] = gi - (gi - s->L->w[i] * C) / s->tau[c];
+        gs[i] = gi - (gi - s->L->w[i] * C) / s->tau[c] + s->L->w[i] * S;
     }
 }
 
@@ -553,7 +557,11 @@ static void collide_cell(const orc_lbm* s, long c, double gs[QMAX])
  * r = (cs^2 - k) / (cs^2 + k) for every link; on D3Q7 that is
  * (2w - k) / (2w + k).
  */
-static double reactive_factor(const orc_lbm* s) { return (s->L->cs2 - s->k_lu) / (s->L->cs2 + s->k_lu); }
+static double reactive_factor(const orc_lbm* s, long c)
+{
+    const double k = s->k_lu * (s->kscale ? s->kscale[c] : 1.0);
+    return (s->L->cs2 - k) / (s->L->cs2 + k);
+}
 
 /*
  * One time step in the order of Eq. 21: collide every active cell, then
@@ -585,7 +593,7 @@ void orc_lbm_step(orc_lbm* s, long nsteps)
                     double cb = out < 0 ? s->p.c_in : s->p.c_out;
                     s->gn[L->opp[i] * N + c] = bc == 0 ? -gs[i] + 2.0 * L->w[i] * cb : gs[i];
                 } else if (!s->active[n]) {
-                    double r = (s->react[c] >> (i - 1) & 1) ? reactive_factor(s) : 1.0;
+                    double r = (s->react[c] >> (i - 1) & 1) ? reactive_factor(s, c) : 1.0;
                     s->gn[L->opp[i] * N + c] = r * gs[i];
                 } else {
                     s->gn[i * N + n] = gs[i];
@@ -613,6 +621,43 @@ void orc_lbm_populations(const orc_lbm* s, double* out)
     memcpy(out, s->g, sizeof(double) * s->L->q * s->N);
 }
 
+/* per-cell factor on the rate constant k (NULL: uniform k); copied */
+void orc_lbm_set_kscale(orc_lbm* s, const double* k)
+{
+    free(s->kscale);
+    s->kscale = NULL;
+    if (!k) return;
+    s->kscale = (double*)malloc(sizeof(double) * s->N);
+    memcpy(s->kscale, k, sizeof(double) * s->N);
+}
+
+/* per-cell amount added to C per step, lattice units (NULL: none); copied.
+ * It enters as w_i S on the post-collision populations (Eq. 21). */
+void orc_lbm_set_source(orc_lbm* s, const double* S)
+{
+    free(s->src);
+    s->src = NULL;
+    if (!S) return;
+    s->src = (double*)malloc(sizeof(double) * s->N);
+    for (long c = 0; c < s->N; ++c) s->src[c] = s->active[c] ? S[c] : 0.0;
+}
+
+/* amount consumed per step on the reactive links of each cell, lattice units */
+void orc_lbm_cell_reaction(const orc_lbm* s, double* out)
+{
+    for (long c = 0; c < s->N; ++c) {
+        out[c] = 0.0;
+        if (!s->active[c] || !s->react[c]) continue;
+        double gs[QMAX];
+        collide_cell(s, c, gs);
+        for (int i = 1; i < s->L->q; ++i) {
+            int o;
+            long n = orc_neighbor(s, c, i, &o);
+            if (!s->active[n] && (s->react[c] >> (i - 1) & 1)) out[c] += (1.0 - reactive_factor(s, c)) * gs[i];
+        }
+    }
+}
+
 /* replace the pre-collision populations (layout [q][N]); inactive cells stay 0 */
 void orc_lbm_set_populations(orc_lbm* s, const double* g)
 {
@@ -628,7 +673,8 @@ void orc_lbm_set_populations(orc_lbm* s, const double* g)
  *   out[2] R     : amount consumed on reactive faces,
  *   out[3] sum C over active cells,
  *   out[4] number of active cells.
- * Per step: sum C(t+1) - sum C(t) = J_in - J_out - R.
+ * Per step: sum C(t+1) - sum C(t) = J_in - J_out - R (+ the sum of the
+ * per-cell sources, where set).
  */
 void orc_lbm_fluxes(const orc_lbm* s, double out[5])
 {
@@ -648,7 +694,7 @@ void orc_lbm_fluxes(const orc_lbm* s, double out[5])
             if (o < 0 && s->active[n] && s->p.bc_in == 0) jin += 2.0 * L->w[i] * s->p.c_in - 2.0 * gs[i];
             if (o > 0 && s->active[n] && s->p.bc_out == 0) jout += 2.0 * gs[i] - 2.0 * L->w[i] * s->p.c_out;
             if (!s->active[n] && (s->react[c] >> (i - 1) & 1))
-                R += (1.0 - reactive_factor(s)) * gs[i];
+                R += (1.0 - reactive_factor(s, c)) * gs[i];
         }
     }
     out[0] = jin; out[1] = jout; out[2] = R; out[3] = sc; out[4] = na;
@@ -699,7 +745,7 @@ double orc_lbm_reaction_rate(const orc_lbm* s, double* profile_R, double* profil
             int o;
             long n = orc_neighbor(s, c, i, &o);
             if (!s->active[n] && (s->react[c] >> (i - 1) & 1)) {
-                double r = (1.0 - reactive_factor(s)) * gs[i] * scale;
+                double r = (1.0 - reactive_factor(s, c)) * gs[i] * scale;
                 total += r;
                 if (profile_R) profile_R[x] += r;
             }
