@@ -20,6 +20,12 @@ What each function follows:
                        neighbours), transport / dead portions, surface area
   OracleLBM            Eq. 21, 23, 24 on D3Q7 or D3Q19 (Eq. 22); boundaries of Sec. 3.5;
                        Eq. 19 readout; Eq. 17b/18a kinetics as a surface sink
+                       (per-cell rate factor for a non-uniform potential);
+                       the a_i S source term of Eq. 21 (Eq. 16)
+  steady.solve         the exact steady state: the fixed point of one step,
+                       (I - A) x = S(0), by a sparse direct solve
+  coupled.solve        Sec. 3.3-3.4: O2 in the ionomer, protons (Eq. 16) and
+                       the potential-dependent Tafel rate (Eq. 17b, 18b)
 
 Arrays are numpy with shape (nz, ny, nx), x fastest.
 """
