@@ -20,11 +20,13 @@
 //
 // Host code must not hand the array's name to a kernel (in host code it is
 // only a stand-in symbol); it passes the device address that
-// cudaGetSymbolAddress returns.  That address is looked up once per device,
-// on the first call made while that device is current; make that first call
-// before any stream capture.
-#include <mutex>
-
+// cudaGetSymbolAddress returns for the current device.  That lookup is made
+// on every call, with the caller's device current: it allocates nothing, and
+// an address cached across calls would go stale if the host application reset
+// the device's context (cudaDeviceReset), which reloads the module.
+//
+// Both pointers must be device (or managed) memory of the current device;
+// anything else is refused before the first launch.
 #include "internal.cuh"
 
 namespace {
@@ -36,9 +38,17 @@ constexpr size_t kScratchBytes = kLabelsBytes + kFlagsBytes + 256;  // + error w
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-void* g_scratch_addr[kMaxDevices] = {};
+// true when p is device memory of device dev, or managed memory (a plain or
+// pinned host pointer gives false)
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the (non-sticky) error so that later calls do not see it
+        return false;
+    }
+    if (at.type == cudaMemoryTypeDevice) return at.device == dev;
+    return at.type == cudaMemoryTypeManaged;
+}
 
 }  // namespace
 
@@ -48,17 +58,11 @@ extern "C" cl_status cl_active_mask_noalloc(const uint8_t* phase, int nx, int ny
     const long long N = (long long)nx * ny * nz;
     if (N > kNoAllocMaxCells) return CL_ERR_ARG;  // larger boxes need the handle API
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CL_ERR_CUDA;
-    unsigned char* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mutex);
-        if (!g_scratch_addr[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CL_ERR_CUDA;
-            g_scratch_addr[dev] = p;
-        }
-        base = static_cast<unsigned char*>(g_scratch_addr[dev]);
-    }
+    if (cudaGetDevice(&dev) != cudaSuccess) return CL_ERR_CUDA;
+    if (!on_device(phase, dev) || !on_device(active, dev)) return CL_ERR_ARG;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CL_ERR_CUDA;
+    unsigned char* base = static_cast<unsigned char*>(p);
     int* labels = reinterpret_cast<int*>(base);
     uint8_t* flags = base + kLabelsBytes;
     int* err = reinterpret_cast<int*>(base + kLabelsBytes + kFlagsBytes);

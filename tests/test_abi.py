@@ -166,3 +166,24 @@ def test_ionomer_o2_argument_checks(lib):
     p.carrier = L.CL_CARRIER_PROTON
     p.D_ionomer = 1.0
     assert lib.cl_lbm_create(ctypes.byref(h), ctypes.byref(p)) == L.CL_ERR_ARG
+
+
+def test_noalloc_wrapper_checks_devices():
+    """The allocation-free wrapper runs only on CUDA tensors of one device;
+    the check answers on the host, before anything reaches the library."""
+    import torch
+
+    from paper_1410_1914_gb300 import _lib
+
+    class _Fake:
+        def __init__(self, kind, index):
+            self.device = torch.device(kind, index) if kind == "cuda" else torch.device(kind)
+
+    assert _lib._common_cuda_device(_Fake("cuda", 1), _Fake("cuda", 1)) == 1
+    with pytest.raises(ValueError, match="different CUDA devices"):
+        _lib._common_cuda_device(_Fake("cuda", 0), _Fake("cuda", 1))
+    with pytest.raises(ValueError, match="CUDA tensors"):
+        _lib._common_cuda_device(_Fake("cuda", 0), _Fake("cpu", None))
+    cpu = torch.zeros((2, 2, 2), dtype=torch.uint8)
+    with pytest.raises(ValueError):
+        _lib.cl_active_mask_noalloc(cpu, torch.zeros_like(cpu))

@@ -1,16 +1,21 @@
 """The allocation-free connectivity entry point (gpu).
 
-Callers that cannot allocate device memory when they need the answer use
-cl_active_mask_noalloc, whose scratch lives in a static device array.  This
-checks it through the C ABI against the handle-based set-up (cl_lbm_get_setup's
-active mask) on two calls in a row, bit for bit, since the mask is integer
-work; the second call reuses the scratch the first one left behind.  The file
-is collected last so that a run stopping at the first failure has already run
-every other test.
+Some callers cannot allocate device memory at the moment they need the
+inlet-connected transport mask (a host application that owns every device
+allocation, a pipeline that forbids allocation after start-up).  They call
+cl_active_mask_noalloc, whose union-find scratch lives in a static device
+array.  These tests call it through the C ABI and compare its mask bit for
+bit (the mask is integer work) with the FP64 oracle's flood fill and with the
+handle API's set-up, on two calls in a row, so that the second call runs on
+the scratch the first one left behind.  The file is collected last so that a
+run stopping at the first failure has already run every other test.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_1410_1914_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -25,33 +30,58 @@ def _handle_active(ph, params):
     return act
 
 
-def test_noalloc_matches_handle_api_on_two_calls(cuda_lib):
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+CASES = [
+    # (recipe, shape (nz, ny, nx), seed, ionomer counted as transport)
+    ("pt_cl_48", (40, 50, 61), 31, False),
+    ("npmc_cl_400", (33, 17, 129), 32, False),
+    ("pt_cl_48", (24, 37, 70), 33, True),
+]
+
+
+@pytest.mark.parametrize("recipe,shape,seed,ionomer", CASES)
+def test_noalloc_matches_oracle_on_two_calls(cuda_lib, recipe, shape, seed, ionomer):
     import torch
 
     from paper_1410_1914_gb300 import _lib
-    cases = [inputs.make_workload("pt_cl_48", shape=(40, 50, 61), seed=31, reactive=False),
-             inputs.make_workload("npmc_cl_400", shape=(33, 17, 129), seed=32, reactive=False)]
-    for ph, _, params in cases:
-        ref = _handle_active(ph, params)
-        dph = torch.from_numpy(ph).cuda()
+    ph, _, params = inputs.make_workload(recipe, shape=shape, seed=seed, reactive=False)
+    ref = oracle.active_mask(ph, ionomer_transport=ionomer)
+    if ionomer:
+        params = dict(params, D_ionomer=1e-9)  # the handle API then counts ionomer as transport
+    handle = _handle_active(ph, params)
+    np.testing.assert_array_equal(handle, ref)
+    dph = torch.from_numpy(ph).cuda()
+    for call in range(2):
         out = torch.full(ph.shape, 7, dtype=torch.uint8, device="cuda")
-        _lib.cl_active_mask_noalloc(dph, out)
+        _lib.cl_active_mask_noalloc(dph, out, ionomer_transport=ionomer)
         torch.cuda.synchronize()
         got = out.cpu().numpy()
-        np.testing.assert_array_equal(got, ref)
+        np.testing.assert_array_equal(got, ref, err_msg=f"call {call}")
         assert got.sum() > 0
 
 
-def test_noalloc_rejects_oversized_boxes(cuda_lib):
+def test_noalloc_rejects_bad_input(cuda_lib):
     import torch
 
     from paper_1410_1914_gb300 import _lib
+    # larger than the static scratch
     ph = torch.zeros((1, 1, 8), dtype=torch.uint8, device="cuda")
     out = torch.zeros_like(ph)
-    st = cuda_lib.cl_active_mask_noalloc(ctypes_ptr(ph), 2048, 2048, 2, 0, ctypes_ptr(out), None)
-    assert st == _lib.CL_ERR_ARG
-
-
-def ctypes_ptr(t):
-    import ctypes
-    return ctypes.c_void_p(t.data_ptr())
+    assert cuda_lib.cl_active_mask_noalloc(_ptr(ph), 2048, 2048, 2, 0, _ptr(out), None) == _lib.CL_ERR_ARG
+    # a phase code outside 0..3, found by the validation kernel
+    bad = torch.zeros((4, 5, 6), dtype=torch.uint8, device="cuda")
+    bad[2, 3, 4] = 5
+    out = torch.zeros_like(bad)
+    assert cuda_lib.cl_active_mask_noalloc(_ptr(bad), 6, 5, 4, 0, _ptr(out), None) == _lib.CL_ERR_ARG
+    # host memory is refused before any launch
+    host = np.zeros((4, 5, 6), dtype=np.uint8)
+    hp = host.ctypes.data_as(ctypes.c_void_p)
+    assert cuda_lib.cl_active_mask_noalloc(hp, 6, 5, 4, 0, _ptr(out), None) == _lib.CL_ERR_ARG
+    assert cuda_lib.cl_active_mask_noalloc(_ptr(bad), 6, 5, 4, 0, hp, None) == _lib.CL_ERR_ARG
+    # a valid call still works after the refusals
+    good = torch.zeros((4, 5, 6), dtype=torch.uint8, device="cuda")
+    _lib.cl_active_mask_noalloc(good, out)
+    assert int(out.sum()) == 4 * 5 * 6
