@@ -215,6 +215,18 @@ cl_status cl_lbm_step(cl_handle h, long long nsteps);
    info may be NULL. */
 cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info);
 
+/* Test hook of the step kernel's bounded waits (no counterpart in the
+   paper; D3Q7 (C, delta) storage, the only kernel with device-side waits).
+   wait_limit_clocks: SM clock cycles a consumer or producer warp waits on a
+   plane's mbarrier before it gives up (0: the default, about 1 s).
+   never_arrive (needs a limit > 0): the producer issues no plane load, so
+   the consumers' first wait runs out after the limit; the kernel then
+   returns without touching the state, and cl_lbm_solve / _solve_budget
+   report CL_ERR_TIMEOUT.  The error word is cleared once reported; set
+   (0, 0) to restore normal stepping.  Drops the captured step graphs.
+   Errors: CL_ERR_ARG. */
+cl_status cl_lbm_set_wait_test(cl_handle h, long long wait_limit_clocks, int never_arrive);
+
 /* cl_lbm_solve with an explicit step budget instead of p->max_steps (whole
    check intervals only; a budget below check_every runs no step).  Each call
    restarts the stopping rule's history, so a budget of one interval always
@@ -388,6 +400,16 @@ cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk
    from a cached autotuning result). */
 cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch);
 
+/* Test hook of the batch's bounded grid barrier (no counterpart in the
+   paper).  wait_limit_clocks: SM clock cycles a block waits at the barrier
+   before it gives up (0: the default, about 2 s).  never_arrive (needs a
+   limit > 0): every block waits for one arrival more than the grid has, so
+   the wait runs out; the launch then ends with every block returned and the
+   step reports CL_ERR_TIMEOUT.  The members' states are then partly stepped:
+   re-initialise them.  Set (0, 0) to restore normal stepping.
+   Errors: CL_ERR_ARG. */
+cl_status cl_batch_set_wait_test(cl_batch_handle b, long long wait_limit_clocks, int never_arrive);
+
 /* Resident blocks of the persistent launch, current work items, and whether
    the solve runs from a captured graph (1) or plain launches (0). */
 cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* uses_graph);
@@ -404,10 +426,14 @@ cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* 
      cuda_stream: cudaStream_t or NULL; the call synchronises it.
    Limit: nx*ny*nz <= 4,194,304 cells (CL_ERR_ARG beyond).  Scratch space is
    a static device array of about 20 MiB that every GPU loading the library
-   keeps until exit; all calls share it, so calls must not overlap on the
-   GPU.  The first call on a device looks up the array's device address
-   (make it before any stream capture).  Allocates nothing.
-   Errors: CL_ERR_ARG (NULL pointer, size, phase code > 3), CL_ERR_CUDA,
+   keeps until exit; all calls share it and it keeps the last call's
+   contents, so calls whose work overlaps on the GPU (two streams, two host
+   threads) race: serialise them.  Every call looks up the array's address on
+   the current device (no allocation; a cached address would not survive a
+   context reset).  The call copies an error word to the host and
+   synchronises its stream before it returns.  Allocates nothing.
+   Errors: CL_ERR_ARG (NULL pointer, size, a pointer that is not device or
+   managed memory of the current device, phase code > 3), CL_ERR_CUDA,
    CL_ERR_TIMEOUT (labelling iteration bound). */
 cl_status cl_active_mask_noalloc(const uint8_t* phase, int nx, int ny, int nz, int ionomer_transport,
                                  uint8_t* active, void* cuda_stream);

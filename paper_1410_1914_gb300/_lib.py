@@ -129,6 +129,8 @@ SIGNATURES = {
     "cl_batch_autotune": (_S, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
     "cl_batch_configure": (_S, [_H, _I, _I]),
     "cl_batch_info": (_S, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "cl_batch_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
+    "cl_lbm_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
 }
 
 _lock = threading.Lock()
@@ -437,17 +439,33 @@ def cl_lbm_get_info(h: int) -> cl_structure_info:
     return info
 
 
+def _common_cuda_device(*tensors):
+    """The one CUDA device that every tensor lives on; ValueError otherwise."""
+    devs = set()
+    for t in tensors:
+        dev = getattr(t, "device", None)
+        if dev is None or getattr(dev, "type", None) != "cuda":
+            raise ValueError("expected CUDA tensors")
+        devs.add(dev.index)
+    if len(devs) != 1:
+        raise ValueError(f"tensors on different CUDA devices: {sorted(devs)}")
+    return devs.pop()
+
+
 def cl_active_mask_noalloc(phase, active, ionomer_transport: bool = False, stream: int | None = None) -> None:
     """Inlet-connected transport cells without device allocation.  `phase`
-    (uint8) and `active` (uint8, written) are CUDA tensors of shape (nz, ny, nx)."""
+    (uint8) and `active` (uint8, written) are CUDA tensors of shape (nz, ny, nx)
+    on one device; the call runs with that device current, on its current
+    torch stream unless `stream` is given."""
+    import torch
+    dev = _common_cuda_device(phase, active)
     nz, ny, nx = (int(v) for v in phase.shape)
-    pp, pdev, _k1 = _arr(phase, np.uint8, nx * ny * nz)
-    ap, adev, _k2 = _arr(active, np.uint8, nx * ny * nz, writable=True)
-    if not (pdev and adev):
-        raise ValueError("phase and active must be device tensors")
-    st = current_torch_stream() if stream is None else stream
-    _check(load().cl_active_mask_noalloc(pp, nx, ny, nz, int(bool(ionomer_transport)), ap, st),
-           "cl_active_mask_noalloc")
+    pp, _p, _k1 = _arr(phase, np.uint8, nx * ny * nz)
+    ap, _a, _k2 = _arr(active, np.uint8, nx * ny * nz, writable=True)
+    with torch.cuda.device(dev):
+        st = int(torch.cuda.current_stream(dev).cuda_stream) if stream is None else stream
+        _check(load().cl_active_mask_noalloc(pp, nx, ny, nz, int(bool(ionomer_transport)), ap, st),
+               "cl_active_mask_noalloc")
 
 
 def cl_lbm_get_step(h: int) -> int:

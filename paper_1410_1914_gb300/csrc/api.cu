@@ -59,6 +59,8 @@ MarchArgs make_margs(cl_lbm* h, int dst) {
     a.Csnap = h->Csnap_p;
     a.partials = h->partials;
     a.err = h->d_err;
+    a.wait_limit = h->wait_limit;
+    a.never_arrive = h->never_arrive;
     return a;
 }
 
@@ -66,6 +68,11 @@ cl_status check_err_flag(cl_lbm* h) {
     int herr = 0;
     CK(cudaMemcpyAsync(&herr, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, h->s));
     CK(cudaStreamSynchronize(h->s));
+    if (herr) {
+        // reported once: the next call starts from a clean error word
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->s));
+        CK(cudaStreamSynchronize(h->s));
+    }
     if (herr & 1) { set_msg_txt("phase code outside 0..3"); return CL_ERR_ARG; }
     if (herr & 2) { set_msg_txt("connectivity labelling exceeded its iteration bound"); return CL_ERR_TIMEOUT; }
     if (herr & 4) { set_msg_txt("diffusivity override not positive and finite on an active cell"); return CL_ERR_ARG; }
@@ -730,6 +737,19 @@ cl_status cl_lbm_step(cl_handle h, long long nsteps) {
     h->cur = par;
     h->step += nsteps;
     CK(cudaGetLastError());
+    return CL_OK;
+}
+
+cl_status cl_lbm_set_wait_test(cl_handle h, long long wait_limit_clocks, int never_arrive) {
+    if (!h) { set_msg_txt("NULL handle"); return CL_ERR_ARG; }
+    if (wait_limit_clocks < 0) { set_msg_txt("wait_limit_clocks < 0"); return CL_ERR_ARG; }
+    if (never_arrive && wait_limit_clocks == 0) {
+        set_msg_txt("never_arrive needs a wait limit (a few hundred clocks)");
+        return CL_ERR_ARG;
+    }
+    h->wait_limit = wait_limit_clocks;
+    h->never_arrive = never_arrive ? 1 : 0;
+    drop_graphs(h);  // the wait settings are baked into captured kernel arguments
     return CL_OK;
 }
 

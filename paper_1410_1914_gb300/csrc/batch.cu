@@ -47,6 +47,8 @@ struct cl_batch {
     std::vector<char> active;
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = true;
+    long long wait_limit = 0;  // grid barrier bound (0: default)
+    int never_arrive = 0;      // test hook (cl_batch_set_wait_test)
 };
 
 namespace {
@@ -109,6 +111,8 @@ BatchLaunch launch_desc(cl_batch* b, int nsteps, bool reduce_last) {
     L.abort_flag = b->d_abort;
     L.item_partials = b->d_item_partials;
     L.err = b->d_err;
+    L.wait_limit = b->wait_limit;
+    L.never_arrive = b->never_arrive;
     return L;
 }
 
@@ -116,6 +120,10 @@ cl_status batch_err(cl_batch* b) {
     int e = 0;
     CK(cudaMemcpyAsync(&e, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, b->s));
     CK(cudaStreamSynchronize(b->s));
+    if (e) {  // reported once: the next call starts from a clean error word
+        CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->s));
+        CK(cudaStreamSynchronize(b->s));
+    }
     if (e & 32) { set_msg_txt("grid barrier of the batched step did not complete within its bound"); return CL_ERR_TIMEOUT; }
     if (e) { set_msg_txt("batched step kernel raised an error"); return CL_ERR_CUDA; }
     for (auto* h : b->m) CKS(check_err_flag(h));
@@ -380,6 +388,19 @@ cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch) {
     drop_graph(b);
     CKS(upload_insts(b));
     return upload_items(b);
+}
+
+cl_status cl_batch_set_wait_test(cl_batch_handle b, long long wait_limit_clocks, int never_arrive) {
+    if (!b) { set_msg_txt("NULL batch"); return CL_ERR_ARG; }
+    if (wait_limit_clocks < 0) { set_msg_txt("wait_limit_clocks < 0"); return CL_ERR_ARG; }
+    if (never_arrive && wait_limit_clocks == 0) {
+        set_msg_txt("never_arrive needs a wait limit (a few hundred clocks)");
+        return CL_ERR_ARG;
+    }
+    b->wait_limit = wait_limit_clocks;
+    b->never_arrive = never_arrive ? 1 : 0;
+    drop_graph(b);  // the barrier settings are baked into the captured launch
+    return CL_OK;
 }
 
 cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* uses_graph) {

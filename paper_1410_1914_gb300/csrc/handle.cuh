@@ -81,6 +81,8 @@ struct cl_lbm {
     int z_chunk = 0;
     int prefetch = cl::kPrefetchDefault;
     float s_lo = 1.f, s_d = 1.f;
+    long long wait_limit = 0;  // bounded device waits of the step kernel (0: default)
+    int never_arrive = 0;      // test hook (cl_lbm_set_wait_test)
 
     int cur = 0;
     float* fbuf = nullptr;

@@ -59,13 +59,16 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for one phase of an mbarrier; gives up after ~1 s of SM clock and
-// raises bit 8 of the error word instead of spinning forever.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err) {
+// Wait for one phase of an mbarrier; gives up after `limit` cycles of SM
+// clock (0: 2^31, about 1 s) and raises bit 8 of the error word instead of
+// spinning forever.
+constexpr long long kWaitDefault = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* err, long long limit) {
     if (mbar_try_wait(bar, parity)) return true;
+    const long long lim = limit > 0 ? limit : kWaitDefault;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > (1LL << 31)) {
+        if (clock64() - t0 > lim) {
             atomicOr(err, 8);
             return false;
         }
@@ -293,11 +296,12 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
                 for (int i = 0; i < 14; ++i) tensormap_fence_acquire(mp + i);
             }
             int k = 0;
+            if (a.never_arrive) ok = false;  // test hook: no plane is ever loaded, the consumers' wait runs out
             for (; k < nplanes && ok; ++k) {
                 const unsigned g = seq + k;
                 const int s = g % kStages;
                 const unsigned u = g / kStages;
-                if (u > 0) ok = mbar_wait_bounded(&empty[s], (u - 1) & 1, a.err);
+                if (u > 0) ok = mbar_wait_bounded(&empty[s], (u - 1) & 1, a.err, a.wait_limit);
                 if (!ok) break;
                 unsigned char* sl = slots + s * L::bytes;
                 int z = zs - 1 + k;
@@ -337,9 +341,10 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
                 }
             }
             if (!ok) {
-                // the loads still in flight land before shared memory is released
+                // the loads still in flight land before shared memory is released (they
+                // complete on their own, so this waits with the default bound)
                 for (int j = k - 1; j >= 0 && j >= k - kStages; --j)
-                    mbar_wait_bounded(&full[(seq + j) % kStages], ((seq + j) / kStages) & 1, a.err);
+                    mbar_wait_bounded(&full[(seq + j) % kStages], ((seq + j) / kStages) & 1, a.err, 0);
             }
         }
         return ok;
@@ -359,7 +364,9 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
         return S::ld(*reinterpret_cast<const T*>(sl + off), inv);
     };
     auto slot = [&](int k) { return slots + ((seq + k) % kStages) * L::bytes; };
-    auto wait = [&](int k) { return mbar_wait_bounded(&full[(seq + k) % kStages], ((seq + k) / kStages) & 1, a.err); };
+    auto wait = [&](int k) {
+        return mbar_wait_bounded(&full[(seq + k) % kStages], ((seq + k) / kStages) & 1, a.err, a.wait_limit);
+    };
     auto release = [&](int k) {
         __syncwarp();
         if (tx == 0) mbar_arrive(&empty[(seq + k) % kStages]);
@@ -566,13 +573,15 @@ __global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) =
 // ------------------------------------------------------- batched launch
 // Bounded grid-wide barrier of a cooperative launch: the counter is zeroed
 // before the launch and reaches (round + 1) * gridDim.x.  A block that gives
-// up (~2 s) raises bit 32 and the abort word so that no block waits forever.
-__device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, int* err) {
+// up (after `limit` cycles; 0: 2^32, about 2 s) raises bit 32 and the abort
+// word so that no block waits forever.
+__device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, int* err, long long limit) {
     __syncthreads();
     __shared__ int s_abort;
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         __threadfence();
         atomicAdd(counter, 1u);
+        const long long lim = limit > 0 ? limit : (1LL << 32);
         const long long t0 = clock64();
         int ab = 0;
         for (;;) {
@@ -581,7 +590,7 @@ __device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, i
             if (v >= target) break;
             ab = *(volatile int*)abort_flag;
             if (ab) break;
-            if (clock64() - t0 > (1LL << 32)) {
+            if (clock64() - t0 > lim) {
                 atomicOr(err, 32);
                 atomicExch(abort_flag, 1);
                 ab = 1;
@@ -603,7 +612,8 @@ __global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDU
                                                             const WorkItem* __restrict__ items,
                                                             const int* __restrict__ n_items_ptr, int nsteps,
                                                             int parity0, int reduce_last, unsigned* counter,
-                                                            int* abort_flag, double* item_partials, int* err) {
+                                                            int* abort_flag, double* item_partials, int* err,
+                                                            long long wait_limit, int never_arrive) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + kStages;
@@ -640,7 +650,9 @@ __global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDU
             ok = __syncthreads_and(ok);
         }
         if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(abort_flag, 1);
-        if (!grid_sync(counter, (unsigned)(step + 1) * gridDim.x, abort_flag, err)) break;
+        // test hook: one arrival more than the grid has never comes
+        const unsigned target = (unsigned)(step + 1) * gridDim.x + (never_arrive ? 1u : 0u);
+        if (!grid_sync(counter, target, abort_flag, err, wait_limit)) break;
     }
 }
 
@@ -710,7 +722,8 @@ static cudaError_t launch_batch_t(const BatchLaunch& b, int grid, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_march_batch<S, R>, b.insts, b.items, b.n_items, b.nsteps, b.parity0,
-                              b.reduce_last, b.counter, b.abort_flag, b.item_partials, b.err);
+                              b.reduce_last, b.counter, b.abort_flag, b.item_partials, b.err, b.wait_limit,
+                              b.never_arrive);
 }
 
 template <class S>

@@ -34,6 +34,11 @@ struct MarchArgs {
     float* Csnap;
     double* partials;
     int* err;
+    // bounded waits: clock cycles before a wait gives up (0: the default, about
+    // 1 s of SM clock); never_arrive (a test hook) makes the first plane wait
+    // of each work item wait for a load the producer never issues
+    long long wait_limit;
+    int never_arrive;
 };
 
 // One structure of a batch: TMA descriptors and arguments for both source
@@ -60,6 +65,11 @@ struct BatchLaunch {
     int* abort_flag;
     double* item_partials;  // [item][RED_N] when reduce_last
     int* err;
+    // grid barrier: clock cycles before a block gives up (0: the default,
+    // about 2 s of SM clock); never_arrive (a test hook) makes every block wait
+    // for one arrival more than the grid has
+    long long wait_limit;
+    int never_arrive;
 };
 
 cudaError_t launch_march_batch(const BatchLaunch& b, cudaStream_t s);
