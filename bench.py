@@ -57,17 +57,30 @@ WORKLOAD_DESC = ("256^3 Pt catalyst layer, 2 nm voxels, seeded QSGS (pore 0.45, 
 
 
 def bytes_per_cell(storage: str, lattice: str = "d3q7") -> float:
-    """Algorithmic DRAM bytes of one fused step per box cell: the cell's state
-    read once and written once, plus its relaxation rate (f32, 4 B) and link
-    mask (D3Q7: u16, 2 B; D3Q19: u32, 4 B).
-      fp32     C as two f32 + 6 f32 deviations: 32 B state -> 2*32 + 6 = 70 B
-      fp16dev  C f32 + f16 low word + 6 f16 deviations: 18 B -> 2*18 + 6 = 42 B
-      fp32pop  7 f32 populations: 28 B -> 2*28 + 6 = 62 B
-      D3Q19 (u32 link word + f32 omega = 8 B of static data; the reactive-link
-      word, read only by cells with a catalytic link, is not counted):
-        fp32pop  19 f32 populations: 76 B -> 2*76 + 8 = 160 B
-        fp32     C as two f32 + 18 f32 deviations: 80 B -> 2*80 + 8 = 168 B
-        fp16dev  C as two f32 + 18 f16 deviations: 44 B -> 2*44 + 8 = 96 B"""
+    """Algorithmic DRAM bytes of one fused step per box cell, as the method
+    needs them: every cell's populations read once and written once, plus
+    its link mask (D3Q7: 2 B; D3Q19: 4 B) and relaxation rate (f32, 4 B).
+      fp32pop, fp32   7 f32 populations: 2 * 28 + 6 = 62 B (the FP32 state
+                      carries the same information as C + 6 deviations)
+      fp16dev         C f32 + 6 f16 deviations: 2 * 16 + 6 = 38 B
+      D3Q19 (8 B of static data; the reactive-link word of the few catalytic
+      cells is not counted):
+        fp32pop, fp32   19 f32 populations: 2 * 76 + 8 = 160 B
+        fp16dev         C f32 + 18 f16 deviations: 2 * 40 + 8 = 88 B"""
+    if lattice == "d3q19":
+        return 2 * {"fp32pop": 76, "fp32": 76, "fp16dev": 40}[storage] + 8
+    state = {"fp32": 28, "fp16dev": 16, "fp32pop": 28}[storage]
+    return 2 * state + 6
+
+
+def layout_bytes_per_cell(storage: str, lattice: str = "d3q7") -> float:
+    """Bytes per cell and step that this library's layouts move (the state
+    keeps C as a double-float, whose low word the method does not need):
+      fp32     C as two f32 + 6 f32 deviations: 2 * 32 + 6 = 70 B
+      fp16dev  C f32 + f16 low word + 6 f16 deviations: 2 * 18 + 6 = 42 B
+      fp32pop  62 B, as the algorithmic figure
+      D3Q19: fp32pop 160 B; fp32 2 * (8 + 72) + 8 = 168 B; fp16dev
+      2 * (8 + 36) + 8 = 96 B"""
     if lattice == "d3q19":
         return 2 * {"fp32pop": 76, "fp32": 80, "fp16dev": 44}[storage] + 8
     state = {"fp32": 32, "fp16dev": 18, "fp32pop": 28}[storage]
@@ -159,26 +172,40 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(ph, react, params, budget_s: float = 20.0, lattice: str = "d3q7"):
+def cpu_baseline(ph, react, params, budget_s: float = 20.0, lattice: str = "d3q7", one_core_s: float = 10.0):
     """The FP64 oracle on the host cores: set-up, then as many whole steps as
-    fit the budget (at least one).  Returns MLUPS and what was sampled."""
+    fit the budget (at least one), on all cores and then on one core.
+    Returns MLUPS and what was sampled."""
     import oracle
+
+    def sample(o, budget):
+        steps = 0
+        t1 = time.perf_counter()
+        while True:
+            o.step(1)
+            steps += 1
+            el = time.perf_counter() - t1
+            if el * (steps + 1) / steps > budget:
+                return steps, el
+
     t0 = time.perf_counter()
     o = oracle.OracleLBM(ph, react=react, lattice=int(lattice == "d3q19"), **params)
     t_setup = time.perf_counter() - t0
     n = ph.size
-    steps = 0
-    t1 = time.perf_counter()
-    while True:
-        o.step(1)
-        steps += 1
-        el = time.perf_counter() - t1
-        if el * (steps + 1) / steps > budget_s:
-            break
-    mlups = n * steps / el / 1e6
-    return {"value": mlups, "unit": "MLUPS", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 steps of the full {ph.shape[2]}x{ph.shape[1]}x{ph.shape[0]} workload "
-                      f"({el:.1f} s; oracle set-up {t_setup:.1f} s not counted)"}
+    cores = oracle.num_threads()
+    steps, el = sample(o, budget_s)
+    out = {"value": n * steps / el / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+           "sample": f"{steps} FP64 steps of the full {ph.shape[2]}x{ph.shape[1]}x{ph.shape[0]} workload "
+                     f"({el:.1f} s; oracle set-up {t_setup:.1f} s not counted)"}
+    if one_core_s > 0:
+        oracle.set_num_threads(1)
+        try:
+            s1, e1 = sample(o, one_core_s)
+        finally:
+            oracle.set_num_threads(cores)
+        out["one_core"] = {"value": n * s1 / e1 / 1e6, "unit": "MLUPS", "cores": 1,
+                           "sample": f"{s1} FP64 steps of the same workload on one thread ({e1:.1f} s)"}
+    return out
 
 
 def run_reference(args):
@@ -349,6 +376,11 @@ def run_structures(args):
 
 
 def run_converge(args):
+    print(json.dumps(measure_converge(args)), flush=True)
+    return 0
+
+
+def measure_converge(args, arm_names=None):
     """Time-to-converged D_eff (Eq. 19 readout within 1e-3, and staying there)
     per storage mode, from the linear ramp and from the learned warm start,
     on a D_eff set-up of the Pt recipe.  The reference is the FP32-state
@@ -398,6 +430,8 @@ def run_converge(args):
             net = W.load_pretrained()
             net.forward(torch.zeros(1, nx, nx, nx, W.FEATURES, dtype=torch.bfloat16, device="cuda"), 1, nx)
             arms += [("fp32", True), ("fp16dev", True)]
+    if arm_names is not None:
+        arms = [(st, w) for st, w in arms if st + ("+warm" if w else "") in arm_names]
     out = {}
     for storage, warm in arms:
         torch.cuda.synchronize()
@@ -447,9 +481,9 @@ def run_converge(args):
                 "solve_s": info["seconds"], "setup_s": setup_s,
                 "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
             s.close()
-    plain = out["fp32pop"]["seconds_to_1e-3"]
-    state32 = out["fp32"]["seconds_to_1e-3"]
-    best = out.get("fp16dev+warm", out["fp16dev"])["seconds_to_1e-3"]
+    plain = out["fp32pop"]["seconds_to_1e-3"] if "fp32pop" in out else None
+    state32 = out["fp32"]["seconds_to_1e-3"] if "fp32" in out else None
+    best = out.get("fp16dev+warm", out.get("fp16dev", {})).get("seconds_to_1e-3")
     line = {"metric": "time-to-converged D_eff (rel 1e-3)" if args.carrier == "o2"
             else "time-to-converged effective proton conductivity (rel 1e-3)", "unit": "s", "higher_is_better": False,
             "workload": label, "shape_zyx": list(ph.shape), "lattice": args.lattice, "reference_D_eff_over_Db": ref,
@@ -459,8 +493,90 @@ def run_converge(args):
             "fp16_warm_vs_fp32_state_ramp": (None if state32 is None or best is None else state32 / best),
             "plain_fp32_note": "fp32pop = plain FP32 populations from the linear ramp" + (
                 "; it never came within 1e-3" if plain is None else "")}
-    print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+NPMC_DESC = ("400^3 NPMC catalyst layer, 1 nm voxels, seeded QSGS (base pore 0.45 + micropores to 0.55), "
+             "Knudsen D (353 K, M 0.032), every carbon-pore face catalytic k=1e-5 m/s, reservoir plane + "
+             "fixed C inlet, zero-flux outlet, periodic y,z")
+
+
+def measure_npmc400(stream, K: int, steps: int, peak: float, local: int):
+    """The 400^3 NPMC workload in the FP16 state: MLUPS and roofline of the
+    fused step (device-timed check intervals), the FP32 state for context,
+    and end to end through the C ABI with host buffers (structure upload,
+    set-up, 1000 steps, reaction-rate readout)."""
+    import torch
+    from paper_1410_1914_gb300 import Solver, inputs
+    from paper_1410_1914_gb300 import _lib as L
+    ph, react, params = inputs.make_workload("npmc_cl_400")
+    n_cells = ph.size
+    out = {"workload": NPMC_DESC, "shape_zyx": list(ph.shape), "storage": "fp16dev",
+           "lbm_steps_per_bench_step": K}
+    for storage in ("fp16dev", "fp32"):
+        s = Solver(ph.shape, storage=storage, stream=int(stream.cuda_stream), check_every=K, **params)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_structure(ph, react)
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        for _ in range(3):
+            s.solve_budget(K)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n = steps if storage == "fp16dev" else max(3, steps // 4)
+        with ClockSampler(local) as clocks:
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(n):
+                s.solve_budget(K)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        mlups = n_cells * K / (ms * 1e-3) / 1e6
+        launch_s = ms * 1e-3 / K
+        rec = {"mlups": mlups, "ms_per_step": ms, "setup_s": setup_s,
+               "roofline": {"bound": "hbm", "kernel": "k_march",
+                            "achieved": bytes_per_cell(storage) * n_cells / launch_s / 1e9, "peak": peak,
+                            "unit": "GB/s", "frac": bytes_per_cell(storage) * n_cells / launch_s / 1e9 / peak,
+                            "layout_frac": layout_bytes_per_cell(storage) * n_cells / launch_s / 1e9 / peak},
+               "clocks": clocks.summary()}
+        if storage == "fp16dev":
+            ph_pin = torch.from_numpy(ph).pin_memory()
+            re_pin = torch.from_numpy(react).pin_memory()
+            E = max(K, (1000 // K) * K)
+            reps = 2
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                L.cl_lbm_set_structure(s.h, ph_pin, re_pin, n_cells)
+                s.solve_budget(E)
+                s.reaction_rate()
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            rec["e2e"] = {"value": n_cells * E * reps / el / 1e6, "unit": "MLUPS",
+                          "h2d_bytes_per_step": int(ph.nbytes + react.nbytes),
+                          "d2h_bytes_per_step": int(40 * ph.shape[2] + 56 * (E // K) + 4 + 8 + 56),
+                          "lbm_steps_per_e2e_step": E,
+                          "includes": "structure upload + GPU set-up + steps + readout"}
+            out.update(rec)
+        else:
+            out["fp32_state"] = {k: rec[k] for k in ("mlups", "roofline")}
+        s.close()
+    return out
+
+
+def measure_ttc(local: int):
+    """Time to D_eff within 1e-3 on the 128^3 D_eff set-up of the Pt recipe
+    (the converge workload): plain FP32 populations and the FP32 state from
+    the linear ramp, the FP16 state from the learned warm start."""
+    ns = argparse.Namespace(shape=(128, 128, 128), carrier="o2", check_every=500, max_steps=3_000_000,
+                            lattice="d3q7", no_warm=False, krylov=False, krylov_max_iter=20000)
+    with ClockSampler(local) as clocks:
+        line = measure_converge(ns, arm_names=("fp32pop", "fp32", "fp16dev+warm"))
+    line["clocks"] = clocks.summary()
+    return line
 
 
 def run_unet(args):
@@ -600,6 +716,10 @@ def main():
                     help="converge workload: add the mixed-precision Krylov steady solves (BiCGSTAB; on D3Q7 also "
                          "the diffusion-preconditioned GMRES) on plain f32 populations")
     ap.add_argument("--krylov-max-iter", type=int, default=20000)
+    ap.add_argument("--no-ttc", action="store_true",
+                    help="default workload: skip the time-to-converged D_eff arms (128^3)")
+    ap.add_argument("--no-npmc", action="store_true",
+                    help="default workload: skip the 400^3 NPMC measurement")
     ap.add_argument("--carrier", default="o2", choices=["o2", "proton"],
                     help="converge workload: O2 in the pores (D_eff) or protons in the ionomer (sigma_eff)")
     args = ap.parse_args()
@@ -673,6 +793,8 @@ def main():
     peak, peak_kind = measured_peak_gbs()
     achieved = launch_bytes / launch_s / 1e9
     traffic, traffic_src = measured_traffic(args.storage, n_cells, args.lattice)
+    layout_frac = layout_bytes_per_cell(args.storage, args.lattice) * n_cells / launch_s / 1e9 / peak
+    dram_frac = None if traffic is None else traffic / launch_s / 1e9 / peak
 
     # the other storage modes and lattices on the same structure, for context (not the headline)
     others = {}
@@ -697,7 +819,8 @@ def main():
             ms = e0.elapsed_time(e1) / 5
             v = n_cells * K / (ms * 1e-3) / 1e6
             others[st if lat == "d3q7" else f"{lat}_{st}"] = {
-                "mlups": v, "hbm_frac": bytes_per_cell(st, lat) * n_cells / (ms * 1e-3 / K) / 1e9 / peak}
+                "mlups": v, "hbm_frac": bytes_per_cell(st, lat) * n_cells / (ms * 1e-3 / K) / 1e9 / peak,
+                "layout_frac": layout_bytes_per_cell(st, lat) * n_cells / (ms * 1e-3 / K) / 1e9 / peak}
             so.close()
 
     # ---------------------------------------------------------- end to end
@@ -733,7 +856,7 @@ def main():
                    "lattice": args.lattice,
                    "lbm_steps_per_bench_step": K, "active_fraction": info["n_active"] / n_cells,
                    "l2": "inputs larger than L2 (state buffers 2 x %.0f MB)" % (
-                       (bytes_per_cell(args.storage, args.lattice) - (8 if args.lattice == "d3q19" else 6))
+                       (layout_bytes_per_cell(args.storage, args.lattice) - (8 if args.lattice == "d3q19" else 6))
                        / 2 * n_cells / 1e6),
                    "parallelism": f"replicas x{world}", "setup_s": setup_s},
         "active_mlups": mlups * info["n_active"] / n_cells,
@@ -743,6 +866,10 @@ def main():
                      "traffic_source": traffic_src,
                      "peak_kind": f"{peak_kind} hbm_gbs",
                      "algorithmic_bytes_per_launch": launch_bytes,
+                     "algorithmic_bytes_per_cell": bytes_per_cell(args.storage, args.lattice),
+                     "layout_bytes_per_cell": layout_bytes_per_cell(args.storage, args.lattice),
+                     "layout_frac": layout_frac,
+                     "dram_frac": dram_frac,
                      "kernel": ("k_step19" if args.lattice == "d3q19" and args.storage == "fp32pop" else
                                 "k_step19s" if args.lattice == "d3q19" else
                                 "k_step_fp32" if args.storage == "fp32pop" else "k_march")},
@@ -751,9 +878,14 @@ def main():
         "e2e": e2e,
         "last_check": {k: last[k] for k in ("J_in", "J_out", "R", "flux_balance", "resid")},
     }
+    s.close()
+    if world == 1 and args.lattice == "d3q7" and args.shape is None:
+        if not args.no_npmc:
+            line["npmc_400"] = measure_npmc400(stream, K, args.steps, peak, local)
+        if not args.no_ttc:
+            line["ttc"] = measure_ttc(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ph, react, params, args.cpu_budget, args.lattice)
-    s.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -120,6 +120,7 @@ def lib():
                 "orc_lbm_get_react": (None, [_P, _P]),
                 "orc_lbm_q": (ctypes.c_int, [_P]),
                 "orc_num_threads": (ctypes.c_int, []),
+                "orc_set_num_threads": (ctypes.c_int, [ctypes.c_int]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -135,6 +136,11 @@ def _ptr(a: np.ndarray):
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> int:
+    """OpenMP threads of the oracle's later loops (n > 0); returns the count."""
+    return lib().orc_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------- formulas

@@ -815,3 +815,16 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* threads of the later parallel loops of the calling thread (timing on one
+   core); returns the new count */
+int orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
