@@ -97,7 +97,11 @@ typedef enum { CL_CARRIER_O2 = 0, CL_CARRIER_PROTON = 1 } cl_carrier;
 
 typedef enum {
     CL_REACT_GIVEN = 0,   /* reactive faces from the mask given to set_structure (NULL: none) */
-    CL_REACT_ALL_PORE_SOLID = 1 /* every face between a pore (0) and a solid (1) cell */
+    CL_REACT_ALL_PORE_SOLID = 1, /* every face between a pore (0) and a solid (1) cell */
+    /* every face between an ionomer (2) and a solid (1) cell: the reaction
+       sites of Eq. 18 (ionomer next to Pt), for O2 carried in the ionomer
+       (ionomer_o2 or D_ionomer > 0); D3Q7 only */
+    CL_REACT_IONOMER_SOLID = 2
 } cl_react_rule;
 
 /* Optional device allocator (e.g. a framework's caching allocator).  Both
@@ -321,6 +325,83 @@ cl_status cl_lbm_reaction_rate(cl_handle h, double* total, double* profile_R, do
    A_cross = ny nz dx^2 the cross-section of the layer; A/m^2.
    CL_ERR_STATE for the PROTON carrier (it has no sink). */
 cl_status cl_lbm_current_density(cl_handle h, double* i_d);
+
+/* ---------------------------------------------------------------------
+ * Non-uniform kinetics and sources: the coupled potential-reaction problem
+ * of Sec. 3.3-3.4 (Eq. 16-18).  These act on D3Q7 handles with plain f32
+ * populations (CL_STORE_FP32POP; CL_ERR_STATE otherwise), the storage of
+ * the Krylov steady solves, and are cleared by cl_lbm_set_structure.
+ * --------------------------------------------------------------------- */
+
+/* Per-cell factor s on the rate constant of the catalytic faces (Eq. 17b
+   with the local ionomer potential: k = k_ms * s, so r = (2w - k s) /
+   (2w + k s) per cell).  kscale: nx*ny*nz doubles (host or device), copied;
+   NULL restores the uniform k.  s = 0 makes a face an inert wall. */
+cl_status cl_lbm_set_rate_scale(cl_handle h, const double* kscale, int ptr_is_device);
+
+/* Per-cell source S, the amount added to C per step in lattice units
+   (Eq. 16's S_e, or Eq. 15's source, times dt): after collision each
+   population gains w_i S (the a_i S term of Eq. 21).  S: nx*ny*nz doubles
+   (host or device), copied; entries of inactive cells are ignored; NULL
+   removes the source.  The stopping rule's flux balance then reads
+   J_in - J_out - R + sum S. */
+cl_status cl_lbm_set_source(cl_handle h, const double* S, int ptr_is_device);
+
+/* Per-cell amount of the transported quantity consumed per step on the
+   catalytic faces (lattice units, C times one cell volume per step; 0 on
+   cells without a catalytic face): (1 - r) times the post-collision
+   populations that meet those faces.  out: nx*ny*nz doubles, host or
+   device.  The O2 consumption of Eq. 18 per cell is out * dx^3 / dt. */
+cl_status cl_lbm_cell_reaction(cl_handle h, double* out, int ptr_is_device);
+
+/* The coupled steady state of O2 and protons (Sec. 3.3-3.4): the reading
+   of Eq. 16-18 with a non-uniform ionomer potential phi.
+   o2: O2 carrier with the ionomer transporting O2 (ionomer_o2 = 1, or
+       D_ionomer > 0) and the reaction sites of Eq. 18 as its catalytic faces
+       (react_rule CL_REACT_IONOMER_SOLID); its k_ms is the rate constant at
+       phi_ref (Eq. 17b).
+   pr: PROTON carrier (D_ionomer = the conductivity sigma, k_ms = 0) on the
+       same voxels mirrored in x (phase[z][y][nx-1-x]), so that its inlet
+       plane is the membrane at x = L of the O2 box: bc_in Dirichlet with
+       c_in = phi_m, bc_out zero flux (no protons cross the gas side).
+   Both: D3Q7, CL_STORE_FP32POP, structures loaded.
+   Picard iteration on phi (O2 coordinates), each step in device kernels:
+   rate factor exp(alpha F (phi - phi_ref) / (R T)) on catalytic cells with
+   an ionomer path to the membrane (0 on the others, which carry no
+   current); the O2 steady state by cl_lbm_solve_krylov_dsa; the proton
+   source -4 F r_cell dt_p / dt_o2 per proton step (Eq. 18b, r_cell the
+   per-cell O2 consumption per O2 step); the proton steady state; then
+   phi += relax (phi_new - phi) until max |phi_new - phi| < tol_phi.
+   phi_out (nullable, nx*ny*nz doubles, host or device): phi on the
+   proton-conducting cells, 0 elsewhere.  Leaves both handles at their last
+   steady states (their rate scale and source set).  Allocates its scratch
+   (5 cell fields) with cudaMallocAsync and frees it before returning.
+   Returns CL_ERR_NOT_CONVERGED if max_outer iterations did not bring the
+   change of phi below tol_phi.  Errors: CL_ERR_ARG, CL_ERR_STATE and those
+   of the Krylov solve. */
+typedef struct {
+    double alpha;        /* transfer coefficient of Eq. 17b (Table 1: 0.61) */
+    double phi_m;        /* membrane potential [V], the proton handle's c_in */
+    double phi_ref;      /* potential [V] at which the O2 handle's k_ms holds */
+    double relax;        /* Picard relaxation, (0, 1] */
+    double tol_phi;      /* stop when max |phi_new - phi| < tol_phi [V] */
+    int max_outer;       /* >= 1 */
+    double krylov_tol;   /* residual reduction of each steady solve */
+    int krylov_max_iter; /* step applications per steady solve */
+} cl_coupled_params;
+
+typedef struct {
+    int outer;                  /* Picard iterations taken */
+    int converged;              /* 1 if max |phi_new - phi| fell below tol_phi */
+    double dphi;                /* max |phi_new - phi| of the last iteration [V] */
+    double current_o2_A;        /* 4 F times the O2 consumed per second [A] */
+    double current_membrane_A;  /* proton current through the membrane face [A] */
+    long long o2_iterations;    /* step applications of the O2 solves */
+    long long proton_iterations;
+} cl_coupled_info;
+
+cl_status cl_coupled_solve(cl_handle o2, cl_handle pr, const cl_coupled_params* p, double* phi_out,
+                           int phi_out_is_device, cl_coupled_info* info);
 
 /* Current concentration C = sum_i g_i (nx*ny*nz floats, host or device; 0 on
    inactive cells). */

@@ -23,7 +23,7 @@ CL_OK, CL_ERR_ARG, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_STATE = 0, 1, 2, 3, 4
 CL_ERR_DIVERGED, CL_ERR_NOT_CONVERGED, CL_ERR_NO_PATH, CL_ERR_TIMEOUT = 5, 6, 7, 8
 CL_BC_DIRICHLET, CL_BC_ZERO_FLUX = 0, 1
 CL_STORE_FP32, CL_STORE_FP16DEV, CL_STORE_FP32POP = 0, 1, 2
-CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID = 0, 1
+CL_REACT_GIVEN, CL_REACT_ALL_PORE_SOLID, CL_REACT_IONOMER_SOLID = 0, 1, 2
 CL_CARRIER_O2, CL_CARRIER_PROTON = 0, 1
 CL_LATTICE_D3Q7, CL_LATTICE_D3Q19 = 0, 1
 
@@ -70,6 +70,25 @@ class cl_solve_info(ctypes.Structure):
         ("J_in", ctypes.c_double), ("J_out", ctypes.c_double), ("R", ctypes.c_double),
         ("flux_balance", ctypes.c_double), ("rel_change", ctypes.c_double),
         ("resid", ctypes.c_double), ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cl_coupled_params(ctypes.Structure):
+    _fields_ = [
+        ("alpha", ctypes.c_double), ("phi_m", ctypes.c_double), ("phi_ref", ctypes.c_double),
+        ("relax", ctypes.c_double), ("tol_phi", ctypes.c_double), ("max_outer", ctypes.c_int),
+        ("krylov_tol", ctypes.c_double), ("krylov_max_iter", ctypes.c_int),
+    ]
+
+
+class cl_coupled_info(ctypes.Structure):
+    _fields_ = [
+        ("outer", ctypes.c_int), ("converged", ctypes.c_int), ("dphi", ctypes.c_double),
+        ("current_o2_A", ctypes.c_double), ("current_membrane_A", ctypes.c_double),
+        ("o2_iterations", ctypes.c_longlong), ("proton_iterations", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -131,6 +150,10 @@ SIGNATURES = {
     "cl_batch_info": (_S, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "cl_batch_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
     "cl_lbm_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
+    "cl_lbm_set_rate_scale": (_S, [_H, _P, _I]),
+    "cl_lbm_set_source": (_S, [_H, _P, _I]),
+    "cl_lbm_cell_reaction": (_S, [_H, _P, _I]),
+    "cl_coupled_solve": (_S, [_H, _H, ctypes.POINTER(cl_coupled_params), _P, _I, ctypes.POINTER(cl_coupled_info)]),
 }
 
 _lock = threading.Lock()
@@ -270,6 +293,31 @@ def cl_lbm_set_structure(h: int, phase, reactive_faces=None, n: int | None = Non
 def cl_lbm_set_diffusivity(h: int, D, n: int | None = None) -> None:
     p, dev, _k = _arr(D, np.float64, n)
     _check(load().cl_lbm_set_diffusivity(h, p, dev), "cl_lbm_set_diffusivity")
+
+
+def cl_lbm_set_rate_scale(h: int, kscale, n: int | None = None) -> None:
+    p, dev, _k = _arr(kscale, np.float64, n)
+    _check(load().cl_lbm_set_rate_scale(h, p, dev), "cl_lbm_set_rate_scale")
+
+
+def cl_lbm_set_source(h: int, S, n: int | None = None) -> None:
+    p, dev, _k = _arr(S, np.float64, n)
+    _check(load().cl_lbm_set_source(h, p, dev), "cl_lbm_set_source")
+
+
+def cl_lbm_cell_reaction(h: int, out, n: int | None = None) -> None:
+    p, dev, _k = _arr(out, np.float64, n, writable=True)
+    _check(load().cl_lbm_cell_reaction(h, p, dev), "cl_lbm_cell_reaction")
+
+
+def cl_coupled_solve(o2: int, pr: int, params: cl_coupled_params, phi_out=None, n: int | None = None):
+    """(status, info); phi_out (float64, nx*ny*nz) receives the ionomer potential."""
+    p, dev, _k = _arr(phi_out, np.float64, n, writable=True)
+    info = cl_coupled_info()
+    st = load().cl_coupled_solve(o2, pr, ctypes.byref(params), p, dev, ctypes.byref(info))
+    if st not in (CL_OK, CL_ERR_NOT_CONVERGED):
+        _check(st, "cl_coupled_solve")
+    return st, info
 
 
 def cl_lbm_init(h: int, C0=None, n: int | None = None) -> None:

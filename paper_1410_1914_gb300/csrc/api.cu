@@ -8,6 +8,7 @@
 #include <chrono>
 #include <vector>
 
+#include "device_util.cuh"
 #include "handle.cuh"
 
 using namespace cl;
@@ -152,6 +153,9 @@ StepArgs make_args(cl_lbm* h) {
     a.Csnap = h->Csnap;
     a.partials = h->partials;
     a.wide = h->wide;
+    a.kscale = h->kscale;
+    a.k_lu = h->k_lu;
+    a.src = h->src;
     return a;
 }
 
@@ -417,7 +421,8 @@ cl_status do_init(cl_lbm* h, const float* C0dev) {
                          h->s));
     } else {
         CK(cudaMemsetAsync(h->pop[1], 0, sizeof(float) * 7 * (size_t)h->N, h->s));
-        CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap, h->s));
+        CK(launch_init_fp32(h->pop[0], h->mask, C0dev, h->nx, h->ny, h->nz, h->p.c_in, h->p.c_out, h->Csnap,
+                            h->q == 7 ? h->src : nullptr, h->s));
     }
     h->step = 0;
     return CL_OK;
@@ -513,7 +518,12 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     if (p->D_ionomer < 0 || p->k_ms < 0) { set_msg_txt("D_ionomer and k_ms must be >= 0"); return CL_ERR_ARG; }
     if ((p->bc_in != 0 && p->bc_in != 1) || (p->bc_out != 0 && p->bc_out != 1)) { set_msg_txt("bad boundary type"); return CL_ERR_ARG; }
     if (p->storage != CL_STORE_FP32 && p->storage != CL_STORE_FP16DEV && p->storage != CL_STORE_FP32POP) { set_msg_txt("bad storage mode"); return CL_ERR_ARG; }
-    if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
+    if (p->react_rule != CL_REACT_GIVEN && p->react_rule != CL_REACT_ALL_PORE_SOLID &&
+        p->react_rule != CL_REACT_IONOMER_SOLID) { set_msg_txt("bad react_rule"); return CL_ERR_ARG; }
+    if (p->react_rule == CL_REACT_IONOMER_SOLID && p->lattice != CL_LATTICE_D3Q7) {
+        set_msg_txt("the ionomer-solid reaction rule is a D3Q7 rule");
+        return CL_ERR_ARG;
+    }
     if (p->carrier != CL_CARRIER_O2 && p->carrier != CL_CARRIER_PROTON) { set_msg_txt("bad carrier"); return CL_ERR_ARG; }
     if (p->lattice != CL_LATTICE_D3Q7 && p->lattice != CL_LATTICE_D3Q19) { set_msg_txt("bad lattice"); return CL_ERR_ARG; }
     if (p->ionomer_o2 && (p->carrier != CL_CARRIER_O2 || !(cl_ionomer_o2_diffusivity(p->T_K) > 0))) {
@@ -670,6 +680,9 @@ cl_status cl_lbm_set_structure(cl_handle h, const uint8_t* phase, const uint8_t*
     CK(launch_validate(h->phase, h->N, h->d_err, h->s));
     CKS(check_err_flag(h));
     h->have_structure = false;
+    h->kscale = nullptr;  // per-cell kinetics and sources belong to the previous structure
+    h->src = nullptr;
+    h->src_sum = 0.0;
     CK(launch_percolation(h->phase, h->nx, h->ny, h->nz, transport_phases(h->p), h->labels, h->touch, h->active,
                           h->d_err, h->s));
     CKS(check_err_flag(h));
@@ -787,7 +800,8 @@ cl_status cl_lbm_solve_budget(cl_handle h, long long max_steps, cl_solve_info* i
             set_msg_txt("non-finite concentration");
             break;
         }
-        inf.flux_balance = fabs(inf.J_in - inf.J_out - inf.R) / fmax(fabs(inf.J_in), 1e-300);
+        // per step: sum C changes by J_in - J_out - R plus the sources (zero at steady state)
+        inf.flux_balance = fabs(inf.J_in - inf.J_out - inf.R + h->src_sum) / fmax(fabs(inf.J_in), 1e-300);
         const double q = track_deff ? inf.J_out : inf.R;
         const double dq = q - q_prev;
         const double est = nchecks >= 2 ? remaining_change(dq, dq_prev) : INFINITY;
@@ -851,7 +865,7 @@ cudaError_t step_pop(cl_lbm* h, const float* src, float* dst, bool linear) {
         return launch_step19(src, dst, a, false, h->s);
     }
     StepArgs a = make_args(h);
-    if (linear) { a.abb_in = a.abb_out = 0.f; a.w_cin = a.w_cout = 0.f; }
+    if (linear) { a.abb_in = a.abb_out = 0.f; a.w_cin = a.w_cout = 0.f; a.src = nullptr; }
     return launch_step_fp32(src, dst, a, false, h->s);
 }
 
@@ -1051,6 +1065,8 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         da.mask = h->mask;
         da.rfac = reactive_factor(h);
         da.bc_in = h->p.bc_in; da.bc_out = h->p.bc_out;
+        da.kscale = h->kscale;
+        da.k_lu = h->k_lu;
         CK(launch_lap_dinv(da, dinv, nblk, h->s));
         auto host_double = [&](const double* dptr, double* out, int n) -> cl_status {
             CK(cudaMemcpyAsync(out, dptr, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
@@ -1294,12 +1310,80 @@ static cl_status state_out(cl_lbm* h, float* C, float* g, int ptr_is_device) {
     } else {
         if (C) {
             float* dstp = ptr_is_device ? C : h->fbuf;
-            CK(launch_field_fp32(h->pop[h->cur], h->mask, h->N, dstp, h->s));
+            CK(launch_field_fp32(h->pop[h->cur], h->mask, h->N, dstp, h->src, h->s));
             if (!ptr_is_device) CK(cudaMemcpyAsync(C, h->fbuf, sizeof(float) * N, cudaMemcpyDeviceToHost, h->s));
         }
         if (g) CK(cudaMemcpyAsync(g, h->pop[h->cur], sizeof(float) * 7 * N, kind_out(ptr_is_device), h->s));
     }
     CK(cudaStreamSynchronize(h->s));
+    return CL_OK;
+}
+
+namespace {
+// the per-cell arrays below act on the plain f32 population kernel of D3Q7
+cl_status need_pop7(cl_lbm* h, const char* what) {
+    CKS(need_structure(h));
+    if (h->march || h->q != 7) {
+        set_msg_txt(what);
+        return CL_ERR_STATE;
+    }
+    return CL_OK;
+}
+
+__global__ void k_active_sum(const double* __restrict__ v, const uint16_t* __restrict__ mask, long long N,
+                             double* partials) {
+    double acc[1] = {0.0};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x)
+        if (mask[c] & kActiveBit) acc[0] += v[c];
+    block_sum_store<1>(acc, partials + blockIdx.x);
+}
+}  // namespace
+
+cl_status cl_lbm_set_rate_scale(cl_handle h, const double* kscale, int ptr_is_device) {
+    CKS(need_pop7(h, "per-cell rate constants need D3Q7 plain f32 populations (CL_STORE_FP32POP)"));
+    drop_graphs(h);  // the arrays are baked into captured kernel arguments
+    if (!kscale) { h->kscale = nullptr; return CL_OK; }
+    if (!h->kscale_buf) CKS(dalloc_n(h, &h->kscale_buf, h->N));
+    CK(cudaMemcpyAsync(h->kscale_buf, kscale, sizeof(double) * (size_t)h->N, kind_in(ptr_is_device), h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->kscale = h->kscale_buf;
+    return CL_OK;
+}
+
+cl_status cl_lbm_set_source(cl_handle h, const double* S, int ptr_is_device) {
+    CKS(need_pop7(h, "per-cell sources need D3Q7 plain f32 populations (CL_STORE_FP32POP)"));
+    drop_graphs(h);
+    if (!S) { h->src = nullptr; h->src_sum = 0.0; return CL_OK; }
+    if (!h->src_buf) CKS(dalloc_n(h, &h->src_buf, h->N));
+    CK(cudaMemcpyAsync(h->src_buf, S, sizeof(double) * (size_t)h->N, kind_in(ptr_is_device), h->s));
+    // the sum over active cells enters the flux balance of the stopping rule
+    const int nb = 152 * 4;
+    CK(cudaMemsetAsync(h->d_red, 0, sizeof(double), h->s));
+    k_active_sum<<<nb, 256, 0, h->s>>>(h->src_buf, h->mask, h->N, h->partials);
+    CK(cudaGetLastError());
+    CK(launch_finalize(h->partials, nb, 1, h->d_red, h->s));
+    CK(cudaMemcpyAsync(&h->src_sum, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    CK(cudaStreamSynchronize(h->s));
+    h->src = h->src_buf;
+    return CL_OK;
+}
+
+cl_status cl_lbm_cell_reaction(cl_handle h, double* out, int ptr_is_device) {
+    CKS(need_pop7(h, "the per-cell reaction readout needs D3Q7 plain f32 populations (CL_STORE_FP32POP)"));
+    if (!out) { set_msg_txt("NULL argument"); return CL_ERR_ARG; }
+    double* d = out;
+    void* tmp = nullptr;
+    if (!ptr_is_device) {
+        CK(cudaMallocAsync(&tmp, sizeof(double) * (size_t)h->N, h->s));
+        d = (double*)tmp;
+    }
+    cudaError_t e = launch_cell_reaction_fp32(h->pop[h->cur], make_args(h), d, h->s);
+    if (e == cudaSuccess && !ptr_is_device)
+        e = cudaMemcpyAsync(out, d, sizeof(double) * (size_t)h->N, cudaMemcpyDeviceToHost, h->s);
+    if (tmp) cudaFreeAsync(tmp, h->s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+    CK(e);
     return CL_OK;
 }
 

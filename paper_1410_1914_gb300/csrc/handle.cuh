@@ -81,6 +81,10 @@ struct cl_lbm {
     int z_chunk = 0;
     int prefetch = cl::kPrefetchDefault;
     float s_lo = 1.f, s_d = 1.f;
+    double* kscale = nullptr;  // per-cell factor on k (cl_lbm_set_rate_scale), NULL: uniform
+    double* src = nullptr;     // per-cell source per step (cl_lbm_set_source), NULL: none
+    double src_sum = 0.0;      // sum of the sources over active cells (enters the flux balance)
+    double *kscale_buf = nullptr, *src_buf = nullptr;  // their storage, allocated on first use
     long long wait_limit = 0;  // bounded device waits of the step kernel (0: default)
     int never_arrive = 0;      // test hook (cl_lbm_set_wait_test)
 

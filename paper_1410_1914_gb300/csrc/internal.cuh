@@ -35,7 +35,18 @@ struct StepArgs {
     float* Csnap;        // C at the previous check (reduction)
     double* partials;    // [blocks][RED_N] (reduction)
     int wide;            // 1: 64-bit element offsets even where 32-bit ones fit
+    // non-uniform kinetics and sources (coupled problem, Eq. 16-18); NULL: uniform k, no source
+    const double* __restrict__ kscale;  // per-cell factor on k_lu (Eq. 17b with a non-uniform potential)
+    double k_lu;                        // k dt / dx
+    const double* __restrict__ src;     // per-cell amount added per step, as w_i S after collision (Eq. 21)
 };
+
+// reactive factor r = (2w - k) / (2w + k) of a cell whose rate constant is
+// k_lu times kscale (w = 1/8, so 2w = 1/4)
+__device__ __forceinline__ double cell_rfac(double k_lu, double kscale) {
+    const double k = k_lu * kscale;
+    return (0.25 - k) / (0.25 + k);
+}
 
 // ---- D3Q19 (q19.cu) ----
 constexpr int kQ19Threads = 128;
@@ -115,7 +126,7 @@ cudaError_t launch_stats(const uint8_t* phase, const uint16_t* mask, const doubl
 
 // ---- FP32 solver (kernels.cu) ----
 cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, int nx, int ny,
-                             int nz, double c_in, double c_out, float* Csnap, cudaStream_t s);
+                             int nz, double c_in, double c_out, float* Csnap, const double* src, cudaStream_t s);
 cudaError_t launch_step_fp32(const float* src, float* dst, const StepArgs& a, bool reduce,
                              cudaStream_t s);
 // the same step in FP64 on FP64 populations (no reduction)
@@ -126,9 +137,10 @@ cudaError_t launch_absmax(const float* v, long long N, double* partials, int nbl
 cudaError_t launch_finalize(const double* partials, int nblocks, int nslots, double* out,
                             cudaStream_t s);
 cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C,
-                              cudaStream_t s);
+                              const double* src, cudaStream_t s);
 // per-plane readout: out[5*nx]: sumC, count, R, J_in part, J_out part
 cudaError_t launch_readout_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s);
+cudaError_t launch_cell_reaction_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s);
 
 // ---- Krylov steady solve (krylov.cu) ----
 enum KryFin { KRY_START = 0, KRY_ALPHA, KRY_OMEGA, KRY_BETA };
@@ -171,6 +183,8 @@ struct DsaArgs {
     const uint16_t* __restrict__ mask;
     float rfac;          // reactive factor r of a catalytic face
     int bc_in, bc_out;   // cl_bc
+    const double* __restrict__ kscale;  // per-cell factor on k_lu (NULL: uniform)
+    double k_lu;
 };
 enum CgFin { CG_START = 0, CG_ALPHA, CG_BETA };
 struct CgScalars {

@@ -549,6 +549,7 @@ __global__ void k_masks(const uint8_t* __restrict__ phase, const uint8_t* __rest
                 bool react = false;
                 if (phase[n] == 1) {
                     if (rule == CL_REACT_ALL_PORE_SOLID) react = phase[c] == 0;
+                    else if (rule == CL_REACT_IONOMER_SOLID) react = phase[c] == 2;
                     else if (react_in) react = (react_in[c] >> d) & 1;
                 }
                 if (react) m |= (uint16_t)(1u << (kReactShift + d));
@@ -661,9 +662,12 @@ cudaError_t launch_finalize(const double* partials, int nblocks, int nslots, dou
 }
 
 // ====================================================== FP32 solver kernels
+// Initial post-collision state: equilibrium w_i C0, plus the w_i S of a
+// per-cell source where one is set (the stored state is the post-collision
+// populations of the current step, source included).
 __global__ void k_init_fp32(float* __restrict__ pop, const uint16_t* __restrict__ mask,
                             const float* __restrict__ C0, int nx, long long N, double c_in, double c_out,
-                            float* __restrict__ Csnap) {
+                            float* __restrict__ Csnap, const double* __restrict__ src) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         float C = 0.f;
@@ -675,17 +679,18 @@ __global__ void k_init_fp32(float* __restrict__ pop, const uint16_t* __restrict_
                 C = (float)(c_in + (c_out - c_in) * (x + 0.5) / nx);
             }
         }
-        pop[c] = act ? kW0 * C : 0.f;
+        const float S = (act && src) ? (float)src[c] : 0.f;
+        pop[c] = act ? kW0 * (C + S) : 0.f;
 #pragma unroll
-        for (int i = 1; i < 7; ++i) pop[(long long)i * N + c] = act ? kW1 * C : 0.f;
+        for (int i = 1; i < 7; ++i) pop[(long long)i * N + c] = act ? kW1 * (C + S) : 0.f;
         if (Csnap) Csnap[c] = C;
     }
 }
 
 cudaError_t launch_init_fp32(float* pop, const uint16_t* mask, const float* C0, int nx, int ny, int nz,
-                             double c_in, double c_out, float* Csnap, cudaStream_t s) {
+                             double c_in, double c_out, float* Csnap, const double* src, cudaStream_t s) {
     const long long N = (long long)nx * ny * nz;
-    k_init_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, C0, nx, N, c_in, c_out, Csnap);
+    k_init_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, C0, nx, N, c_in, c_out, Csnap, src);
     return cudaGetLastError();
 }
 
@@ -724,7 +729,9 @@ __global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T*
     T h[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     {
         if (act) {
-            const T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
+            T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
+            // a non-uniform rate constant (Eq. 17b with the local potential) on catalytic cells
+            if (a.kscale && ((m >> kReactShift) & 0x3fu)) rf = (T)cell_rfac(a.k_lu, a.kscale[c]);
             const T abb_in = kF64 ? (T)a.abb_in_d : (T)a.abb_in, abb_out = kF64 ? (T)a.abb_out_d : (T)a.abb_out;
             // source of population i (1..6 = +x, -x, +y, -y, +z, -z): x - c_i, y and z periodic
             const I sy_m = y == 0 ? (I)(ny - 1) * (I)nx : (I)0 - (I)nx;            // row y - 1
@@ -760,6 +767,12 @@ __global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T*
             h[0] = g[0] - om * (g[0] - e0);
 #pragma unroll
             for (int i = 1; i < 7; ++i) h[i] = g[i] - om * (g[i] - e1);
+            if (a.src) {  // the a_i S term of Eq. 21, added after collision
+                const T S = (T)a.src[c];
+                h[0] += (T)kW0 * S;
+#pragma unroll
+                for (int i = 1; i < 7; ++i) h[i] += (T)kW1 * S;
+            }
             if (REDUCE) {
                 if (x == 0 && a.bc_in == CL_BC_DIRICHLET) rv[RED_JIN] = 2.0 * ((double)a.w_cin - (double)h[2]);
                 if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h[1] - (double)a.w_cout);
@@ -824,22 +837,25 @@ cudaError_t launch_step_f64(const double* src, double* dst, const StepArgs& a, c
     return cudaGetLastError();
 }
 
+// C = sum of the stored post-collision populations, less the source the
+// last collision added: the concentration before collision, as Eq. 21 sees it.
 __global__ void k_field_fp32(const float* __restrict__ pop, const uint16_t* __restrict__ mask, long long N,
-                             float* __restrict__ C) {
+                             float* __restrict__ C, const double* __restrict__ src) {
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
          c += (long long)gridDim.x * blockDim.x) {
         float v = 0.f;
         if (mask[c] & kActiveBit) {
             v = pop[c];
-#pragma unroll
             for (int i = 1; i < 7; ++i) v += pop[(long long)i * N + c];
+            if (src) v = (float)((double)v - src[c]);
         }
         C[c] = v;
     }
 }
 
-cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C, cudaStream_t s) {
-    k_field_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, N, C);
+cudaError_t launch_field_fp32(const float* pop, const uint16_t* mask, long long N, float* C, const double* src,
+                              cudaStream_t s) {
+    k_field_fp32<<<152 * 8, 256, 0, s>>>(pop, mask, N, C, src);
     return cudaGetLastError();
 }
 
@@ -861,13 +877,14 @@ __global__ void k_readout_fp32(const float* __restrict__ pop, StepArgs a, double
 #pragma unroll
         for (int i = 0; i < 7; ++i) { h[i] = pop[(long long)i * N + c]; }
         C = (double)(((h[0] + h[1]) + (h[2] + h[3])) + ((h[4] + h[5]) + h[6]));
+        if (a.src) C -= a.src[c];  // the concentration before the last collision's source
         v[0] += C;
         v[1] += 1.0;
         const unsigned rb = (m >> kReactShift) & 0x3fu;
         double r = 0.0;
         for (int d = 0; d < 6; ++d)
             if (rb & (1u << d)) r += h[d + 1];
-        v[2] += sink * r;
+        v[2] += (rb && a.kscale ? 1.0 - cell_rfac(a.k_lu, a.kscale[c]) : sink) * r;
         if (x == 0 && a.bc_in == CL_BC_DIRICHLET) v[3] += 2.0 * ((double)a.w_cin - (double)h[2]);
         if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) v[4] += 2.0 * ((double)h[1] - (double)a.w_cout);
     }
@@ -876,6 +893,30 @@ __global__ void k_readout_fp32(const float* __restrict__ pop, StepArgs a, double
 
 cudaError_t launch_readout_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s) {
     k_readout_fp32<<<a.nx, 256, 0, s>>>(pop, a, out);
+    return cudaGetLastError();
+}
+
+// Per-cell amount consumed per step on the catalytic links, from the stored
+// post-collision populations: (1 - r) times the populations that meet a
+// catalytic face (lattice units; 0 on cells without one).
+__global__ void k_cell_reaction_fp32(const float* __restrict__ pop, StepArgs a, double* __restrict__ out) {
+    const long long N = a.N;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint16_t m = a.mask[c];
+        const unsigned rb = (m >> kReactShift) & 0x3fu;
+        double r = 0.0;
+        if ((m & kActiveBit) && rb) {
+            for (int d = 0; d < 6; ++d)
+                if (rb & (1u << d)) r += (double)pop[(long long)(d + 1) * N + c];
+            r *= a.kscale ? 1.0 - cell_rfac(a.k_lu, a.kscale[c]) : 1.0 - (double)a.rfac_d;
+        }
+        out[c] = r;
+    }
+}
+
+cudaError_t launch_cell_reaction_fp32(const float* pop, const StepArgs& a, double* out, cudaStream_t s) {
+    k_cell_reaction_fp32<<<152 * 8, 256, 0, s>>>(pop, a, out);
     return cudaGetLastError();
 }
 

@@ -61,6 +61,20 @@ class Solver:
     def set_diffusivity(self, D):
         L.cl_lbm_set_diffusivity(self.h, D, self.n)
 
+    def set_rate_scale(self, kscale):
+        """Per-cell factor on k (Eq. 17b with a non-uniform potential); None: uniform."""
+        L.cl_lbm_set_rate_scale(self.h, kscale, self.n)
+
+    def set_source(self, S):
+        """Per-cell source per step, lattice units (the a_i S term of Eq. 21); None: none."""
+        L.cl_lbm_set_source(self.h, S, self.n)
+
+    def cell_reaction(self):
+        """Per-cell amount consumed per step on catalytic faces (lattice units)."""
+        out = np.zeros(self.shape, dtype=np.float64)
+        L.cl_lbm_cell_reaction(self.h, out, self.n)
+        return out
+
     def init(self, C0=None):
         L.cl_lbm_init(self.h, C0, self.n)
 
