@@ -56,7 +56,7 @@ def ionomer_solid_faces(phase: np.ndarray) -> np.ndarray:
 
 
 def solve(phase, params, sigma, phi_m, k_ref, alpha=0.61, phi_ref=None, relax=0.5, tol_phi=1e-9,
-          max_outer=200):
+          max_outer=200, ionomer_D=None):
     """Coupled O2 / proton steady state on `phase` (nz, ny, nx).
 
     params: the O2 set-up (dx_m, T_K, knudsen, c_in in mol/m^3, bc_in, bc_out,
@@ -65,12 +65,20 @@ def solve(phase, params, sigma, phi_m, k_ref, alpha=0.61, phi_ref=None, relax=0.
     Returns a dict: phi (V, NaN outside the proton-conducting ionomer), C,
     site (cells that carry current), R_cell (mol/s per cell), current_A from
     the O2 side (4 F sum R_cell) and from the proton side (the membrane
-    flux), the proton solve's source sum, the outer iterations, converged."""
+    flux), the proton solve's source sum, the outer iterations, converged.
+
+    ionomer_D: None carries O2 in the ionomer as Eq. 10-15 (D_e RT/H,
+    ``ionomer_o2 = 1``); a value [m^2/s] gives the ionomer that diffusivity
+    instead.  The coupling of Sec. 3.3-3.4 (Eq. 16-18) is the same for any
+    ionomer diffusivity; a larger one keeps the O2 problem within reach of
+    an iterative steady solver at the ~1e5 pore/ionomer contrast of Eq. 13."""
     phase = np.ascontiguousarray(phase, dtype=np.uint8)
     phi_ref = phi_m if phi_ref is None else phi_ref
     T = params.get("T_K", 353.0)
     faces = ionomer_solid_faces(phase)
-    o2 = OracleLBM(phase, react=faces, **dict(params, ionomer_o2=1, k_ms=k_ref, carrier=0))
+    o2_params = dict(params, ionomer_o2=1, k_ms=k_ref, carrier=0) if ionomer_D is None else \
+        dict(params, ionomer_o2=0, D_ionomer=ionomer_D, k_ms=k_ref, carrier=0)
+    o2 = OracleLBM(phase, react=faces, **o2_params)
     pr_params = dict(dx_m=params["dx_m"], T_K=T, knudsen=0, carrier=1, D_ionomer=sigma, k_ms=0.0,
                      bc_in=0, bc_out=1, c_in=phi_m, c_out=phi_m, tau_ref=1.0)
     pr = OracleLBM(phase[:, :, ::-1], **pr_params)

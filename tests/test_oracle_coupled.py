@@ -119,3 +119,20 @@ def test_coupling_conserves_current_and_lowers_the_rate():
     assert np.nanmax(phi) <= 0.6 + 1e-12 and np.nanmin(phi) < 0.6 - 1e-3
     # Eq. 17b: a lower potential means a lower rate
     assert r["current_A_o2"] < weak["current_A_o2"]
+
+
+def test_given_ionomer_diffusivity_keeps_the_coupling_pins():
+    """With the ionomer's O2 diffusivity given instead of Eq. 10-13 (a lower
+    contrast to the pores), the same conservation holds: the membrane passes
+    what the sources draw, 4 F times the O2 consumed, and the potential falls
+    away from the membrane; a very large conductivity keeps phi uniform."""
+    ph, params = _layer()
+    r = coupled.solve(ph, params, sigma=1e-4, phi_m=0.6, k_ref=1e-2, ionomer_D=2e-7)
+    assert r["converged"] and r["site"].sum() > 0
+    assert r["o2"].D()[ph == 2].max() == pytest.approx(2e-7, rel=1e-12)
+    assert r["membrane_flux_lu"] == pytest.approx(-r["source_sum_lu"], rel=1e-10)
+    assert r["current_A_membrane"] == pytest.approx(r["current_A_o2"], rel=1e-10)
+    assert np.nanmax(r["phi"]) <= 0.6 + 1e-12 and np.nanmin(r["phi"]) < 0.6 - 1e-4
+    flat = coupled.solve(ph, params, sigma=1e4, phi_m=0.6, k_ref=1e-2, ionomer_D=2e-7)
+    assert np.nanmax(np.abs(flat["phi"] - 0.6)) < 1e-6
+    assert r["current_A_o2"] < flat["current_A_o2"]
