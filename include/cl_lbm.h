@@ -296,6 +296,49 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
 cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
                                   int* iterations, long long* inner_iterations);
 
+/* The steady state with the populations eliminated along lines (no
+   counterpart in the paper, which marches Eq. 21 in time).  At steady state
+   the populations of each axis obey, along every run of open faces, a
+   two-stream recursion driven by C (g_i(x + c_i) = (1 - omega) g_i(x) +
+   omega w C(x) + w S(x), with the wall, catalytic, fixed-value and
+   zero-flux rules at the run's ends), which one sweep per direction solves
+   exactly; summing them gives C = F(C), an affine map of C alone whose fixed
+   point is exactly the steady state of the march.  (I - M) C = F(0) (M the
+   linear part of F) is solved by flexible GMRES(restart) in FP64,
+   preconditioned by the finite-volume operator with the scheme's link
+   conductances (2 D_a D_b / (D_a + D_b), D = cs^2 (tau - 1/2); 2 D on a
+   fixed-value face; 2 k D / (2 D + k) on a catalytic face), whose systems
+   diagonal-preconditioned FP64 conjugate gradients solve to cg_tol.
+   Relaxation rates are formed in FP64 from the stored D (Eq. 24).  This
+   reaches the steady state of O2 dissolved in the ionomer (Eq. 10-15,
+   relaxation times within 1e-5 of 1/2 there), where the march and the
+   population-space Krylov solves stall; per-cell rate factors and sources
+   (cl_lbm_set_rate_scale / _set_source) are honoured.
+     tol:      stop when |F(C) - C| falls to tol times |F(0)| (the right-hand
+               side; a warm start close to the answer stops at once).
+     max_iter: GMRES iterations (applications of F) in all.
+     restart:  Krylov vectors kept; the call allocates 2 * restart + 8
+               FP64 cell fields (restart 1000 at 32^3: 0.5 GB), freed
+               before returning.
+     cg_tol:   relative residual of each preconditioner solve, in (0, 1).
+   Starts from the current state's C; on return the state holds the
+   post-collision populations of the result, so every readout applies.
+   Needs D3Q7 and CL_STORE_FP32POP, else CL_ERR_STATE.  Returns
+   CL_ERR_NOT_CONVERGED at max_iter, CL_ERR_DIVERGED on a non-finite
+   residual or a breakdown of the inner solve, CL_ERR_OOM / CL_ERR_CUDA. */
+typedef struct {
+    int iterations;              /* GMRES iterations (applications of F) */
+    int cycles;                  /* GMRES cycles */
+    long long inner_iterations;  /* conjugate-gradient iterations of the preconditioner */
+    double residual;             /* |F(C) - C| / |F(0)| at the end */
+    double seconds;              /* wall time of the call */
+    double J_in, J_out, R;       /* fluxes of the result in FP64, lattice units per step (as
+                                    cl_lbm_fluxes, which reads the f32 populations) */
+} cl_steady_info;
+
+cl_status cl_lbm_solve_steady_lines(cl_handle h, double tol, int max_iter, int restart, double cg_tol,
+                                    cl_steady_info* info);
+
 /* Lattice-unit fluxes of the current state, FP64 sums:
    out[0] J_in  net amount entering through x = 0 per step,
    out[1] J_out net amount leaving through x = L per step,
@@ -368,7 +411,8 @@ cl_status cl_lbm_cell_reaction(cl_handle h, double* out, int ptr_is_device);
    Picard iteration on phi (O2 coordinates), each step in device kernels:
    rate factor exp(alpha F (phi - phi_ref) / (R T)) on catalytic cells with
    an ionomer path to the membrane (0 on the others, which carry no
-   current); the O2 steady state by cl_lbm_solve_krylov_dsa; the proton
+   current); the O2 steady state (cl_lbm_solve_krylov_dsa, or
+   cl_lbm_solve_steady_lines with steady_solver = 1); the proton
    source -4 F r_cell dt_p / dt_o2 per proton step (Eq. 18b, r_cell the
    per-cell O2 consumption per O2 step); the proton steady state; then
    phi += relax (phi_new - phi) until max |phi_new - phi| < tol_phi.
@@ -387,7 +431,9 @@ typedef struct {
     double tol_phi;      /* stop when max |phi_new - phi| < tol_phi [V] */
     int max_outer;       /* >= 1 */
     double krylov_tol;   /* residual reduction of each steady solve */
-    int krylov_max_iter; /* step applications per steady solve */
+    int krylov_max_iter; /* iterations per steady solve */
+    int steady_solver;   /* 0: cl_lbm_solve_krylov_dsa; 1: cl_lbm_solve_steady_lines, which
+                            also reaches the dissolved-O2 contrast of Eq. 10-15 (ionomer_o2) */
 } cl_coupled_params;
 
 typedef struct {

@@ -80,7 +80,7 @@ class cl_coupled_params(ctypes.Structure):
     _fields_ = [
         ("alpha", ctypes.c_double), ("phi_m", ctypes.c_double), ("phi_ref", ctypes.c_double),
         ("relax", ctypes.c_double), ("tol_phi", ctypes.c_double), ("max_outer", ctypes.c_int),
-        ("krylov_tol", ctypes.c_double), ("krylov_max_iter", ctypes.c_int),
+        ("krylov_tol", ctypes.c_double), ("krylov_max_iter", ctypes.c_int), ("steady_solver", ctypes.c_int),
     ]
 
 
@@ -89,6 +89,17 @@ class cl_coupled_info(ctypes.Structure):
         ("outer", ctypes.c_int), ("converged", ctypes.c_int), ("dphi", ctypes.c_double),
         ("current_o2_A", ctypes.c_double), ("current_membrane_A", ctypes.c_double),
         ("o2_iterations", ctypes.c_longlong), ("proton_iterations", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class cl_steady_info(ctypes.Structure):
+    _fields_ = [
+        ("iterations", ctypes.c_int), ("cycles", ctypes.c_int), ("inner_iterations", ctypes.c_longlong),
+        ("residual", ctypes.c_double), ("seconds", ctypes.c_double),
+        ("J_in", ctypes.c_double), ("J_out", ctypes.c_double), ("R", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -153,6 +164,8 @@ SIGNATURES = {
     "cl_lbm_set_rate_scale": (_S, [_H, _P, _I]),
     "cl_lbm_set_source": (_S, [_H, _P, _I]),
     "cl_lbm_cell_reaction": (_S, [_H, _P, _I]),
+    "cl_lbm_solve_steady_lines": (_S, [_H, ctypes.c_double, _I, _I, ctypes.c_double,
+                                       ctypes.POINTER(cl_steady_info)]),
     "cl_coupled_solve": (_S, [_H, _H, ctypes.POINTER(cl_coupled_params), _P, _I, ctypes.POINTER(cl_coupled_info)]),
 }
 
@@ -317,6 +330,16 @@ def cl_coupled_solve(o2: int, pr: int, params: cl_coupled_params, phi_out=None, 
     st = load().cl_coupled_solve(o2, pr, ctypes.byref(params), p, dev, ctypes.byref(info))
     if st not in (CL_OK, CL_ERR_NOT_CONVERGED):
         _check(st, "cl_coupled_solve")
+    return st, info
+
+
+def cl_lbm_solve_steady_lines(h: int, tol: float, max_iter: int, restart: int, cg_tol: float):
+    """(status, cl_steady_info); raises on errors other than CL_ERR_NOT_CONVERGED."""
+    info = cl_steady_info()
+    st = load().cl_lbm_solve_steady_lines(h, float(tol), int(max_iter), int(restart), float(cg_tol),
+                                          ctypes.byref(info))
+    if st not in (CL_OK, CL_ERR_NOT_CONVERGED):
+        _check(st, "cl_lbm_solve_steady_lines")
     return st, info
 
 

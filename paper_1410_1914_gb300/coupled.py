@@ -12,7 +12,8 @@ from .solver import Solver
 
 
 def solve(phase, params, sigma, phi_m, k_ref, alpha=0.61, phi_ref=None, relax=0.5, tol_phi=1e-7,
-          max_outer=200, ionomer_D=None, krylov_tol=1e-10, krylov_max_iter=20000, stream=None):
+          max_outer=200, ionomer_D=None, krylov_tol=None, krylov_max_iter=20000, steady_solver=None,
+          stream=None):
     """Coupled steady state on `phase` (nz, ny, nx).
 
     params: the O2 set-up (dx_m, T_K, knudsen, c_in in mol/m^3, bc_in,
@@ -20,6 +21,11 @@ def solve(phase, params, sigma, phi_m, k_ref, alpha=0.61, phi_ref=None, relax=0.
     potential [V] at x = L; k_ref: rate constant [m/s] at phi_ref (default
     phi_m); ionomer_D: None carries O2 in the ionomer by Eq. 10-13
     (ionomer_o2), a value [m^2/s] gives the ionomer that diffusivity.
+    steady_solver: "krylov" (population-space GMRES with the diffusion
+    preconditioner) or "lines" (populations eliminated along lines; it also
+    reaches the contrast of Eq. 13); default "lines" when ionomer_D is None.
+    krylov_tol: residual of each steady solve (default 1e-12 for "lines",
+    1e-10 for "krylov").
     Returns a dict: phi (V, 0 outside the proton-conducting ionomer), C
     (O2 field), current_A_o2, current_A_membrane, outer, converged, dphi,
     and the Krylov step applications of both carriers."""
@@ -38,8 +44,15 @@ def solve(phase, params, sigma, phi_m, k_ref, alpha=0.61, phi_ref=None, relax=0.
                c_out=phi_m, tau_ref=1.0)
     pr = Solver(shape, storage="fp32pop", stream=stream, **prp)
     pr.set_structure(np.ascontiguousarray(phase[:, :, ::-1]), None)
+    if steady_solver is None:
+        steady_solver = "lines" if ionomer_D is None else "krylov"
+    if krylov_tol is None:
+        # the line-eliminated residual is taken against |F(0)|: 1e-12 leaves the ionomer's slow
+        # modes at about 1e-7 of C, where 1e-10 left them at 1e-5
+        krylov_tol = 1e-12 if steady_solver == "lines" else 1e-10
     cp = L.cl_coupled_params(alpha=alpha, phi_m=phi_m, phi_ref=phi_ref, relax=relax, tol_phi=tol_phi,
-                             max_outer=max_outer, krylov_tol=krylov_tol, krylov_max_iter=krylov_max_iter)
+                             max_outer=max_outer, krylov_tol=krylov_tol, krylov_max_iter=krylov_max_iter,
+                             steady_solver={"krylov": 0, "lines": 1}[steady_solver])
     phi = np.zeros(shape, dtype=np.float64)
     st, info = L.cl_coupled_solve(o2.h, pr.h, cp, phi, phi.size)
     out = dict(info.as_dict())

@@ -147,7 +147,7 @@ extern "C" cl_status cl_coupled_solve(cl_handle o2, cl_handle pr, const cl_coupl
         return CL_ERR_ARG;
     }
     if (!(cp->relax > 0.0 && cp->relax <= 1.0) || !(cp->tol_phi > 0.0) || cp->max_outer < 1 ||
-        !(cp->krylov_tol > 0.0) || cp->krylov_max_iter < 1) {
+        !(cp->krylov_tol > 0.0) || cp->krylov_max_iter < 1 || (cp->steady_solver != 0 && cp->steady_solver != 1)) {
         set_msg_txt("relax in (0, 1], tol_phi > 0, max_outer >= 1, krylov_tol > 0, krylov_max_iter >= 1 required");
         return CL_ERR_ARG;
     }
@@ -167,6 +167,20 @@ extern "C" cl_status cl_coupled_solve(cl_handle o2, cl_handle pr, const cl_coupl
     CK(b.get(&scal, 2));
     k_phi_init<<<kCBlocks, kCB, 0, s>>>(pr->active, nx, N, cp->phi_m, phi);
     CK(cudaGetLastError());
+    // the steady state of one carrier: the population-space Krylov solve (max_steps 0: no march
+    // after it, which reports CL_ERR_NOT_CONVERGED) or the line-eliminated one
+    auto steady = [&](cl_lbm* h, int* iters) -> cl_status {
+        if (cp->steady_solver == 1) {
+            cl_steady_info li;
+            const int restart = cp->krylov_max_iter < 1500 ? cp->krylov_max_iter : 1500;
+            cl_status e = cl_lbm_solve_steady_lines(h, cp->krylov_tol, cp->krylov_max_iter, restart, 1e-10, &li);
+            *iters = li.iterations;
+            return e;
+        }
+        cl_solve_info si;
+        long long inner = 0;
+        return cl_lbm_solve_krylov_dsa(h, cp->krylov_tol, cp->krylov_max_iter, 0, &si, iters, &inner);
+    };
     const double a_over_rt = cp->alpha * kFaraday / (kRgas * o2->p.T_K);
     // S_e = 4 F r_cell dx^3 / dt_o2 per cell volume dx^3; a sink of Eq. 16 per proton step
     const double factor = 4.0 * kFaraday * pr->dt / o2->dt;
@@ -178,11 +192,8 @@ extern "C" cl_status cl_coupled_solve(cl_handle o2, cl_handle pr, const cl_coupl
         k_rate_scale<<<kCBlocks, kCB, 0, s>>>(o2->mask, pr->active, phi, nx, N, a_over_rt, cp->phi_ref, ks);
         CK(cudaGetLastError());
         CKS(cl_lbm_set_rate_scale(o2, ks, 1));
-        cl_solve_info si;
         int it = 0;
-        long long inner = 0;
-        // max_steps 0: the steady state alone (no march after it), which reports CL_ERR_NOT_CONVERGED
-        cl_status e = cl_lbm_solve_krylov_dsa(o2, cp->krylov_tol, cp->krylov_max_iter, 0, &si, &it, &inner);
+        cl_status e = steady(o2, &it);
         if (e != CL_OK && e != CL_ERR_NOT_CONVERGED) return e;
         inf.o2_iterations += it;
         CKS(cl_lbm_cell_reaction(o2, rc, 1));
@@ -193,7 +204,7 @@ extern "C" cl_status cl_coupled_solve(cl_handle o2, cl_handle pr, const cl_coupl
         CK(cudaGetLastError());
         CK(cudaStreamSynchronize(s));
         CKS(cl_lbm_set_source(pr, src, 1));
-        e = cl_lbm_solve_krylov_dsa(pr, cp->krylov_tol, cp->krylov_max_iter, 0, &si, &it, &inner);
+        e = steady(pr, &it);
         if (e != CL_OK && e != CL_ERR_NOT_CONVERGED) return e;
         inf.proton_iterations += it;
         CKS(cl_lbm_get_field(pr, fpr, 1));

@@ -122,6 +122,16 @@ class Solver:
         d["inner_iterations"] = inner
         return d
 
+    def solve_steady_lines(self, tol: float = 1e-12, max_iter: int = 4000, restart: int = 1500,
+                           cg_tol: float = 1e-10):
+        """Steady state as the fixed point of the line-eliminated map C = F(C)
+        (D3Q7, plain f32 populations), flexible GMRES in FP64 with the
+        finite-volume preconditioner.  Returns the call's info and status."""
+        st, info = L.cl_lbm_solve_steady_lines(self.h, tol, max_iter, restart, cg_tol)
+        d = info.as_dict()
+        d["status"] = L.status_str(st)
+        return d
+
     # ------------------------------------------------------------ readouts
     def fluxes(self):
         f = L.cl_lbm_fluxes(self.h)

@@ -73,7 +73,7 @@ def test_struct_layouts_match_c(tmp_path):
     from paper_1410_1914_gb300 import _lib
     structs = {"cl_params": _lib.cl_params, "cl_structure_info": _lib.cl_structure_info,
                "cl_solve_info": _lib.cl_solve_info, "cl_coupled_params": _lib.cl_coupled_params,
-               "cl_coupled_info": _lib.cl_coupled_info}
+               "cl_coupled_info": _lib.cl_coupled_info, "cl_steady_info": _lib.cl_steady_info}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cl_lbm.h"', '#include "cl_nn.h"', "int main(void){"]
     for sname, cls in structs.items():
         lines.append(f'printf("{sname} sizeof %zu\\n", sizeof({sname}));')

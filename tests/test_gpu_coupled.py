@@ -5,11 +5,12 @@
   sources (the a_i S term of Eq. 21) in the plain-population step kernel:
   a trajectory and the per-cell consumption readout, element by element.
 * The coupled solve (cl_coupled_solve: Picard on the ionomer potential,
-  Krylov steady states of both carriers in the library's kernels) against
+  steady states of both carriers in the library's kernels) against
   oracle/coupled.py (exact steady states by a sparse direct solve) on a
-  small Pt layer, with the ionomer's O2 diffusivity given (the iterative
-  solver does not reach the ~1e5 contrast of Eq. 13): potential, O2 field,
-  current from both sides.
+  small Pt layer: potential, O2 field, current from both sides.  With the
+  population-space Krylov solve the ionomer's O2 diffusivity is given (that
+  solve does not reach the ~1e5 contrast of Eq. 13); with the
+  line-eliminated solve also at the physical contrast of Eq. 10-13.
 """
 import numpy as np
 import pytest
@@ -74,12 +75,17 @@ def _layer(seed=2):
     return ph, params
 
 
-@pytest.mark.parametrize("sigma", [1e-4, 1e4])
-def test_coupled_against_oracle(cuda_lib, sigma):
+@pytest.mark.parametrize("sigma,ionomer_D,solver", [(1e-4, 2e-7, "krylov"), (1e4, 2e-7, "krylov"),
+                                                    (1e-4, 2e-7, "lines"), (1e-4, None, "lines"),
+                                                    (1e4, None, "lines")])
+def test_coupled_against_oracle(cuda_lib, sigma, ionomer_D, solver):
+    """ionomer_D None: O2 dissolved in the ionomer by Eq. 10-13 (the physical
+    contrast), reached by the line-eliminated steady solve."""
     from paper_1410_1914_gb300 import coupled
     ph, params = _layer()
-    ref = ocoupled.solve(ph, params, sigma=sigma, phi_m=0.6, k_ref=1e-2, ionomer_D=2e-7)
-    got = coupled.solve(ph, params, sigma=sigma, phi_m=0.6, k_ref=1e-2, ionomer_D=2e-7, tol_phi=1e-7)
+    ref = ocoupled.solve(ph, params, sigma=sigma, phi_m=0.6, k_ref=1e-2, ionomer_D=ionomer_D)
+    got = coupled.solve(ph, params, sigma=sigma, phi_m=0.6, k_ref=1e-2, ionomer_D=ionomer_D, tol_phi=1e-7,
+                        steady_solver=solver, krylov_max_iter=3000)
     assert ref["converged"] and got["converged"], got["status"]
     site = ref["site"]
     assert site.sum() > 0
@@ -112,13 +118,16 @@ def test_coupled_arguments(cuda_lib):
                dx_m=5e-9, bc_in=0, bc_out=1, c_in=0.6, c_out=0.6)
     b.set_structure(np.ascontiguousarray(ph[:, :, ::-1]))
     cp = L.cl_coupled_params(alpha=0.61, phi_m=0.6, phi_ref=0.6, relax=0.5, tol_phi=1e-7, max_outer=5,
-                             krylov_tol=1e-10, krylov_max_iter=100)
+                             krylov_tol=1e-10, krylov_max_iter=100, steady_solver=0)
     lib = L.load()
     import ctypes
     info = L.cl_coupled_info()
     assert lib.cl_coupled_solve(a.h, b.h, ctypes.byref(cp), None, 0, ctypes.byref(info)) == L.CL_ERR_STATE
     assert lib.cl_coupled_solve(a.h, a.h, ctypes.byref(cp), None, 0, ctypes.byref(info)) == L.CL_ERR_ARG
     cp.relax = 0.0
+    assert lib.cl_coupled_solve(a.h, a.h, ctypes.byref(cp), None, 0, ctypes.byref(info)) == L.CL_ERR_ARG
+    cp.relax = 0.5
+    cp.steady_solver = 2
     assert lib.cl_coupled_solve(a.h, a.h, ctypes.byref(cp), None, 0, ctypes.byref(info)) == L.CL_ERR_ARG
     a.close()
     b.close()
