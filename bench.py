@@ -481,6 +481,19 @@ def measure_converge(args, arm_names=None):
                 "solve_s": info["seconds"], "setup_s": setup_s,
                 "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
             s.close()
+            # the same fixed point in C alone, the populations eliminated along lines (FGMRES in FP64)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s = solver("fp32pop")
+            torch.cuda.synchronize()
+            setup_s = time.perf_counter() - t0
+            info = s.solve_steady_lines(tol=1e-10, max_iter=args.krylov_max_iter, restart=200)
+            err = abs(s.effective_diffusivity()[1] - ref) / abs(ref)
+            out["fp32pop+lines"] = {
+                "iterations": info["iterations"], "inner_iterations": info["inner_iterations"],
+                "solve_s": info["seconds"], "setup_s": setup_s, "status": info["status"],
+                "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
+            s.close()
     plain = out["fp32pop"]["seconds_to_1e-3"] if "fp32pop" in out else None
     state32 = out["fp32"]["seconds_to_1e-3"] if "fp32" in out else None
     best = out.get("fp16dev+warm", out.get("fp16dev", {})).get("seconds_to_1e-3")
@@ -714,7 +727,7 @@ def main():
     ap.add_argument("--no-warm", action="store_true", help="converge workload: skip the learned warm-start arms")
     ap.add_argument("--krylov", action="store_true",
                     help="converge workload: add the mixed-precision Krylov steady solves (BiCGSTAB; on D3Q7 also "
-                         "the diffusion-preconditioned GMRES) on plain f32 populations")
+                         "the diffusion-preconditioned GMRES and the line-eliminated FGMRES) on plain f32 populations")
     ap.add_argument("--krylov-max-iter", type=int, default=20000)
     ap.add_argument("--no-ttc", action="store_true",
                     help="default workload: skip the time-to-converged D_eff arms (128^3)")

@@ -55,12 +55,17 @@ struct SchurArgs {
     const double* __restrict__ src;     // per-cell source per step (nullable)
     double c_in, c_out;
     int bc_in, bc_out;
+    // formed once per call (k_schur_setup): omega in FP64, and the finite-volume
+    // operator as the conductances of the +x, +y, +z links and the diagonal (4 N)
+    const double* __restrict__ om64;
+    const double* __restrict__ G;
 };
 
 // relaxation rate in FP64 from the cell's D (Eq. 24), as the FP64 oracle forms it
-__device__ __forceinline__ double cell_omega(const SchurArgs& a, long long c) {
+__device__ __forceinline__ double omega_from_D(const SchurArgs& a, long long c) {
     return 1.0 / (0.5 + a.D[c] * a.dt_cs2dx2);
 }
+__device__ __forceinline__ double cell_omega(const SchurArgs& a, long long c) { return a.om64[c]; }
 
 __device__ __forceinline__ double cat_factor(const SchurArgs& a, long long c) {
     return a.kscale ? cell_rfac(a.k_lu, a.kscale[c]) : a.rfac;
@@ -220,49 +225,73 @@ __device__ __forceinline__ double cell_D(const SchurArgs& a, long long c) {
     return 0.25 * a.D[c] * a.dt_cs2dx2;
 }
 
-// q = L_D p on active cells (and its diagonal when q == nullptr and dg != nullptr)
-__device__ __forceinline__ void ld_row(const SchurArgs& a, long long c, const double* __restrict__ p, double& diag,
-                                       double& off) {
+// neighbour of c across face d (0 +x, 1 -x, 2 +y, 3 -y, 4 +z, 5 -z), y and z periodic
+__device__ __forceinline__ long long face_nb(const SchurArgs& a, long long c, int d, int y, int z) {
     const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const uint16_t m = a.mask[c];
-    const int x = (int)(c % nx);
-    const long long r = c / nx;
-    const int y = (int)(r % ny), z = (int)(r / ny);
     const long long plane = (long long)nx * ny;
-    const double Dc = cell_D(a, c);
-    diag = 0.0;
-    off = 0.0;
-    for (int d = 0; d < 6; ++d) {
-        if ((m >> d) & 1u) {
-            if (d == 1 && x == 0) { if (a.bc_in == CL_BC_DIRICHLET) diag += 2.0 * Dc; }
-            else if (d == 0 && x == nx - 1) { if (a.bc_out == CL_BC_DIRICHLET) diag += 2.0 * Dc; }
-            else if ((m >> (kReactShift + d)) & 1u) {
-                const double k = a.k_lu * (a.kscale ? a.kscale[c] : 1.0);
-                diag += 2.0 * k * Dc / (2.0 * Dc + k);
+    if (d == 0) return c + 1;
+    if (d == 1) return c - 1;
+    if (d == 2) return y == ny - 1 ? c - (long long)(ny - 1) * nx : c + nx;
+    if (d == 3) return y == 0 ? c + (long long)(ny - 1) * nx : c - nx;
+    if (d == 4) return z == nz - 1 ? c - (long long)(nz - 1) * plane : c + plane;
+    return z == 0 ? c + (long long)(nz - 1) * plane : c - plane;
+}
+
+// once per call: omega (FP64) and the finite-volume operator L_D (link conductance
+// 2 D_a D_b / (D_a + D_b); 2 D on a fixed-value face; 2 k D / (2 D + k) on a catalytic
+// face) as G[0..2] = conductances of the +x, +y, +z links (0 where closed), G[3] = the
+// diagonal, and dinv = 1 / diagonal (0 off the active set)
+__global__ void k_schur_setup(SchurArgs a, double* __restrict__ om64, double* __restrict__ G,
+                              double* __restrict__ dinv) {
+    const int nx = a.nx, ny = a.ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint16_t m = a.mask[c];
+        double g[3] = {0.0, 0.0, 0.0}, diag = 0.0;
+        double om = 1.0;
+        if (m & kActiveBit) {
+            om = omega_from_D(a, c);
+            const int x = (int)(c % nx);
+            const long long r = c / nx;
+            const int y = (int)(r % ny), z = (int)(r / ny);
+            const double Dc = cell_D(a, c);
+            for (int d = 0; d < 6; ++d) {
+                if ((m >> d) & 1u) {
+                    if (d == 1 && x == 0) { if (a.bc_in == CL_BC_DIRICHLET) diag += 2.0 * Dc; }
+                    else if (d == 0 && x == nx - 1) { if (a.bc_out == CL_BC_DIRICHLET) diag += 2.0 * Dc; }
+                    else if ((m >> (kReactShift + d)) & 1u) {
+                        const double k = a.k_lu * (a.kscale ? a.kscale[c] : 1.0);
+                        diag += 2.0 * k * Dc / (2.0 * Dc + k);
+                    }
+                    continue;
+                }
+                const double Dn = cell_D(a, face_nb(a, c, d, y, z));
+                const double Gl = 2.0 * Dc * Dn / (Dc + Dn);
+                diag += Gl;
+                if ((d & 1) == 0) g[d >> 1] = Gl;
             }
-            continue;
         }
-        long long nb;
-        if (d == 0) nb = c + 1;
-        else if (d == 1) nb = c - 1;
-        else if (d == 2) nb = y == ny - 1 ? c - (long long)(ny - 1) * nx : c + nx;
-        else if (d == 3) nb = y == 0 ? c + (long long)(ny - 1) * nx : c - nx;
-        else if (d == 4) nb = z == nz - 1 ? c - (long long)(nz - 1) * plane : c + plane;
-        else nb = z == 0 ? c + (long long)(nz - 1) * plane : c - plane;
-        const double Dn = cell_D(a, nb);
-        const double G = 2.0 * Dc * Dn / (Dc + Dn);
-        diag += G;
-        if (p) off += G * p[nb];
+        om64[c] = om;
+        for (int k = 0; k < 3; ++k) G[(long long)k * a.N + c] = g[k];
+        G[3 * a.N + c] = diag;
+        dinv[c] = diag > 0.0 ? 1.0 / diag : 0.0;
     }
 }
 
-__global__ void k_ld_dinv(SchurArgs a, double* __restrict__ dinv) {
-    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
-         c += (long long)gridDim.x * blockDim.x) {
-        double d = 0.0, o;
-        if (a.mask[c] & kActiveBit) ld_row(a, c, nullptr, d, o);
-        dinv[c] = d > 0.0 ? 1.0 / d : 0.0;
+// (L_D p)(c) from the stored conductances
+__device__ __forceinline__ double ld_apply(const SchurArgs& a, long long c, const double* __restrict__ p) {
+    const int nx = a.nx, ny = a.ny;
+    const uint16_t m = a.mask[c];
+    const int y = (int)((c / nx) % ny), z = (int)(c / ((long long)nx * ny));
+    const long long N = a.N;
+    double q = a.G[3 * N + c] * p[c];
+    for (int d = 0; d < 6; ++d) {
+        if ((m >> d) & 1u) continue;
+        const long long nb = face_nb(a, c, d, y, z);
+        const double Gl = (d & 1) == 0 ? a.G[(long long)(d >> 1) * N + c] : a.G[(long long)(d >> 1) * N + nb];
+        q -= Gl * p[nb];
     }
+    return q;
 }
 
 struct Cg64 {
@@ -294,12 +323,7 @@ __global__ void k_cg_q64(SchurArgs a, const double* __restrict__ p, double* __re
     double acc[1] = {0.0};
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
          c += (long long)gridDim.x * blockDim.x) {
-        double out = 0.0;
-        if (a.mask[c] & kActiveBit) {
-            double d, o;
-            ld_row(a, c, p, d, o);
-            out = d * p[c] - o;
-        }
+        const double out = (a.mask[c] & kActiveBit) ? ld_apply(a, c, p) : 0.0;
         q[c] = out;
         acc[0] += p[c] * out;
     }
@@ -353,7 +377,11 @@ __global__ void k_cg_fin64(const double* __restrict__ part, int nblk, int stage,
     } else if (stage == 1) {
         if (cs->bad) return;
         cs->pq = out[0];
-        if (!(out[0] > 0.0) || !isfinite(out[0])) { cs->bad = 1; return; }
+        if (!(out[0] > 0.0) || !isfinite(out[0])) {
+            // p.q = 0 after the residual has vanished is convergence, not a breakdown
+            cs->bad = (isfinite(out[0]) && cs->rr <= 1e-28 * cs->rr0) ? 2 : 1;
+            return;
+        }
         cs->alpha = cs->rz / out[0];
     } else {
         if (cs->bad) return;
@@ -529,6 +557,11 @@ extern "C" cl_status cl_lbm_solve_steady_lines(cl_handle h, double tol, int max_
         CK(mem.get(&cp, N));
         CK(mem.get(&cq, N));
         CK(mem.get(&cpart, 2 * kSBlk));
+        double *om64 = nullptr, *G = nullptr;
+        CK(mem.get(&om64, N));
+        CK(mem.get(&G, 4 * N));
+        a.om64 = om64;
+        a.G = G;
         Cg64* cs = nullptr;
         {
             void* v = nullptr;
@@ -557,30 +590,62 @@ extern "C" cl_status cl_lbm_solve_steady_lines(cl_handle h, double tol, int max_
             return CL_OK;
         };
         // z = L_D^{-1} v to cg_tol (diagonal-preconditioned CG, FP64)
+        // 16 CG iterations on fixed buffers (solution cx), replayed as one CUDA graph
+        double* cx = nullptr;
+        CK(mem.get(&cx, N));
+        constexpr int kCgBatch = 16;
+        cudaGraphExec_t cg_graph = nullptr;
+        struct GraphGuard {
+            cudaGraphExec_t* g;
+            ~GraphGuard() { if (*g) cudaGraphExecDestroy(*g); }
+        } guard{&cg_graph};
+        auto enqueue_cg = [&](cudaStream_t st) {
+            for (int k = 0; k < kCgBatch; ++k) {
+                k_cg_q64<<<kSBlk, kSB, 0, st>>>(a, cp, cq, cpart, cs);
+                k_cg_fin64<<<1, kSB, 0, st>>>(cpart, kSBlk, 1, cs);
+                k_cg_upd64<<<kSBlk, kSB, 0, st>>>(N, dinv, cp, cq, cx, cr, cpart, cs);
+                k_cg_fin64<<<1, kSB, 0, st>>>(cpart, kSBlk, 2, cs);
+                k_cg_p64<<<kSBlk, kSB, 0, st>>>(N, dinv, cr, cp, cs);
+            }
+        };
+        {
+            cudaStream_t cap = nullptr;
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                enqueue_cg(cap);
+                ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && g;
+            }
+            if (ok) ok = cudaGraphInstantiate(&cg_graph, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (cap) cudaStreamDestroy(cap);
+            if (!ok) {
+                cg_graph = nullptr;
+                cudaGetLastError();  // the same kernels then run as plain launches
+            }
+        }
+        // z = L_D^{-1} v to cg_tol (diagonal-preconditioned CG, FP64)
         auto precondition = [&](const double* v, double* z) -> cl_status {
-            k_cg_start64<<<kSBlk, kSB, 0, s>>>(N, v, dinv, z, cr, cp, cpart);
+            k_cg_start64<<<kSBlk, kSB, 0, s>>>(N, v, dinv, cx, cr, cp, cpart);
             k_cg_fin64<<<1, kSB, 0, s>>>(cpart, kSBlk, 0, cs);
             CK(cudaGetLastError());
             Cg64 hc;
             CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, s));
             CK(cudaStreamSynchronize(s));
             while (!hc.bad && hc.rr > cg_tol * cg_tol * hc.rr0 && hc.iters < 100000) {
-                for (int k = 0; k < 16; ++k) {
-                    k_cg_q64<<<kSBlk, kSB, 0, s>>>(a, cp, cq, cpart, cs);
-                    k_cg_fin64<<<1, kSB, 0, s>>>(cpart, kSBlk, 1, cs);
-                    k_cg_upd64<<<kSBlk, kSB, 0, s>>>(N, dinv, cp, cq, z, cr, cpart, cs);
-                    k_cg_fin64<<<1, kSB, 0, s>>>(cpart, kSBlk, 2, cs);
-                    k_cg_p64<<<kSBlk, kSB, 0, s>>>(N, dinv, cr, cp, cs);
-                }
+                if (cg_graph) CK(cudaGraphLaunch(cg_graph, s));
+                else enqueue_cg(s);
                 CK(cudaGetLastError());
                 CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, s));
                 CK(cudaStreamSynchronize(s));
             }
             if (hc.bad == 1) { set_msg_txt("inner conjugate gradients broke down"); return CL_ERR_DIVERGED; }
+            CK(cudaMemcpyAsync(z, cx, sizeof(double) * (size_t)N, cudaMemcpyDeviceToDevice, s));
             inf.inner_iterations += hc.iters;
             return CL_OK;
         };
-        k_ld_dinv<<<kSBlk, kSB, 0, s>>>(a, dinv);
+        k_schur_setup<<<kSBlk, kSB, 0, s>>>(a, om64, G, dinv);
         // start from the current state's concentration
         k_field_to_f64<<<kSBlk, kSB, 0, s>>>(N, h->pop[h->cur], h->mask, h->src, x);
         CK(cudaGetLastError());
