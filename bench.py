@@ -430,6 +430,8 @@ def measure_converge(args, arm_names=None):
             net = W.load_pretrained()
             net.forward(torch.zeros(1, nx, nx, nx, W.FEATURES, dtype=torch.bfloat16, device="cuda"), 1, nx)
             arms += [("fp32", True), ("fp16dev", True)]
+    if arm_names is None and getattr(args, "arms", None):
+        arm_names = tuple(a.strip() for a in args.arms.split(","))
     if arm_names is not None:
         arms = [(st, w) for st, w in arms if st + ("+warm" if w else "") in arm_names]
     out = {}
@@ -453,47 +455,36 @@ def measure_converge(args, arm_names=None):
             "seconds_to_1e-3": None if t is None else setup_s + inf_s + t,
             "final_rel_err": abs(float(val[-1]) - ref) / abs(ref), "steps_run": int(st[-1])}
         s.close()
-    if args.krylov:
+    def want(name):
+        return (arm_names is None and args.krylov) or (arm_names is not None and name in arm_names)
+
+    def steady_arm(name, run):
         # the steady state as the fixed point of the step map; the arm's time covers the set-up and the
-        # whole Krylov solve (residual 1e-8 of its initial value, or its stall), no march afterwards
+        # whole steady solve (to its residual, or its stall), no march afterwards
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s = solver("fp32pop")
         torch.cuda.synchronize()
         setup_s = time.perf_counter() - t0
-        info = s.solve_krylov(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0)
+        info = run(s)
         err = abs(s.effective_diffusivity()[1] - ref) / abs(ref)
-        out["fp32pop+krylov"] = {
-            "iterations": info["iterations"], "solve_s": info["seconds"], "setup_s": setup_s,
-            "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
+        rec = {k: info[k] for k in ("iterations", "inner_iterations", "status") if k in info}
+        rec.update({"solve_s": info["seconds"], "setup_s": setup_s,
+                    "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err})
+        out[name] = rec
         s.close()
-        if args.lattice == "d3q7":
-            # the same fixed point by flexible GMRES with the diffusion preconditioner
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s = solver("fp32pop")
-            torch.cuda.synchronize()
-            setup_s = time.perf_counter() - t0
-            info = s.solve_krylov_dsa(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0)
-            err = abs(s.effective_diffusivity()[1] - ref) / abs(ref)
-            out["fp32pop+krylov_dsa"] = {
-                "iterations": info["iterations"], "inner_iterations": info["inner_iterations"],
-                "solve_s": info["seconds"], "setup_s": setup_s,
-                "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
-            s.close()
+
+    if want("fp32pop+krylov"):
+        steady_arm("fp32pop+krylov", lambda s: s.solve_krylov(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0))
+    if args.lattice == "d3q7":
+        if want("fp32pop+krylov_dsa"):
+            # flexible GMRES with the diffusion preconditioner
+            steady_arm("fp32pop+krylov_dsa",
+                       lambda s: s.solve_krylov_dsa(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0))
+        if want("fp32pop+lines"):
             # the same fixed point in C alone, the populations eliminated along lines (FGMRES in FP64)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            s = solver("fp32pop")
-            torch.cuda.synchronize()
-            setup_s = time.perf_counter() - t0
-            info = s.solve_steady_lines(tol=1e-10, max_iter=args.krylov_max_iter, restart=200)
-            err = abs(s.effective_diffusivity()[1] - ref) / abs(ref)
-            out["fp32pop+lines"] = {
-                "iterations": info["iterations"], "inner_iterations": info["inner_iterations"],
-                "solve_s": info["seconds"], "setup_s": setup_s, "status": info["status"],
-                "seconds_to_1e-3": setup_s + info["seconds"] if err <= 1e-3 else None, "final_rel_err": err}
-            s.close()
+            steady_arm("fp32pop+lines",
+                       lambda s: s.solve_steady_lines(tol=1e-10, max_iter=args.krylov_max_iter, restart=200))
     plain = out["fp32pop"]["seconds_to_1e-3"] if "fp32pop" in out else None
     state32 = out["fp32"]["seconds_to_1e-3"] if "fp32" in out else None
     best = out.get("fp16dev+warm", out.get("fp16dev", {})).get("seconds_to_1e-3")
@@ -583,11 +574,12 @@ def measure_npmc400(stream, K: int, steps: int, peak: float, local: int):
 def measure_ttc(local: int):
     """Time to D_eff within 1e-3 on the 128^3 D_eff set-up of the Pt recipe
     (the converge workload): plain FP32 populations and the FP32 state from
-    the linear ramp, the FP16 state from the learned warm start."""
+    the linear ramp, the FP16 state from the learned warm start, and the
+    steady state found directly by the diffusion-preconditioned Krylov solve."""
     ns = argparse.Namespace(shape=(128, 128, 128), carrier="o2", check_every=500, max_steps=3_000_000,
-                            lattice="d3q7", no_warm=False, krylov=False, krylov_max_iter=20000)
+                            lattice="d3q7", no_warm=False, krylov=False, krylov_max_iter=20000, arms=None)
     with ClockSampler(local) as clocks:
-        line = measure_converge(ns, arm_names=("fp32pop", "fp32", "fp16dev+warm"))
+        line = measure_converge(ns, arm_names=("fp32pop", "fp32", "fp16dev+warm", "fp32pop+krylov_dsa"))
     line["clocks"] = clocks.summary()
     return line
 
@@ -729,6 +721,9 @@ def main():
                     help="converge workload: add the mixed-precision Krylov steady solves (BiCGSTAB; on D3Q7 also "
                          "the diffusion-preconditioned GMRES and the line-eliminated FGMRES) on plain f32 populations")
     ap.add_argument("--krylov-max-iter", type=int, default=20000)
+    ap.add_argument("--arms", default=None,
+                    help="converge workload: comma-separated arms to run (e.g. fp16dev+warm,fp32pop+krylov_dsa); "
+                         "default: all storage arms, and the steady-solve arms with --krylov")
     ap.add_argument("--no-ttc", action="store_true",
                     help="default workload: skip the time-to-converged D_eff arms (128^3)")
     ap.add_argument("--no-npmc", action="store_true",
