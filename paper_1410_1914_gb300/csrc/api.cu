@@ -39,6 +39,12 @@ double reactive_factor_d(const cl_lbm* h) {
     return (cs2 - h->k_lu) / (cs2 + h->k_lu);
 }
 float reactive_factor(const cl_lbm* h) { return (float)reactive_factor_d(h); }
+// 1 - r = 2k / (cs^2 + k), formed directly: at nm voxels k_lu is ~1e-8..1e-10 of cs^2,
+// and 1 - r taken from a rounded r would lose most of its digits (all of them in FP32)
+double reactive_sink_d(const cl_lbm* h) {
+    const double cs2 = h->q == 19 ? 1.0 / 3.0 : 0.25;
+    return 2.0 * h->k_lu / (cs2 + h->k_lu);
+}
 
 MarchArgs make_margs(cl_lbm* h, int dst) {
     MarchArgs a;
@@ -49,6 +55,8 @@ MarchArgs make_margs(cl_lbm* h, int dst) {
     a.clo = h->st[dst].clo;
     for (int i = 0; i < 6; ++i) a.d[i] = h->st[dst].d[i];
     a.rfac = reactive_factor(h);
+    a.rsink = (float)reactive_sink_d(h);
+    a.rsink_d = reactive_sink_d(h);
     a.c_in = (float)h->p.c_in;
     a.c_out = (float)h->p.c_out;
     a.bc_in = h->p.bc_in;
@@ -142,6 +150,8 @@ StepArgs make_args(cl_lbm* h) {
     const double w = 0.125;
     a.rfac = reactive_factor(h);
     a.rfac_d = reactive_factor_d(h);
+    a.rsink = (float)reactive_sink_d(h);
+    a.rsink_d = reactive_sink_d(h);
     a.abb_in = (float)(2.0 * w * h->p.c_in);
     a.abb_out = (float)(2.0 * w * h->p.c_out);
     a.abb_in_d = 2.0 * w * h->p.c_in;
@@ -169,6 +179,8 @@ Q19Args make_args19(cl_lbm* h) {
     a.omega = h->omega19;
     a.rfac = reactive_factor(h);
     a.rfac_d = reactive_factor_d(h);
+    a.rsink = (float)reactive_sink_d(h);
+    a.rsink_d = reactive_sink_d(h);
     a.c_in = (float)h->p.c_in;
     a.c_out = (float)h->p.c_out;
     a.c_in_d = h->p.c_in;
@@ -1064,6 +1076,7 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         da.nx = h->nx; da.ny = h->ny; da.nz = h->nz; da.N = N;
         da.mask = h->mask;
         da.rfac = reactive_factor(h);
+        da.rsink = (float)reactive_sink_d(h);
         da.bc_in = h->p.bc_in; da.bc_out = h->p.bc_out;
         da.kscale = h->kscale;
         da.k_lu = h->k_lu;

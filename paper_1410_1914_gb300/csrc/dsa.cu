@@ -38,7 +38,7 @@ __device__ __forceinline__ void lap_row(uint16_t m, int x, int y, int z, long lo
             if (k == 2 && x == 0) d += a.bc_in == CL_BC_DIRICHLET ? 2.f * kW1 : 0.f;
             else if (k == 1 && x == a.nx - 1) d += a.bc_out == CL_BC_DIRICHLET ? 2.f * kW1 : 0.f;
             else if ((m >> (kReactShift + k - 1)) & 1u)
-                d += (a.kscale ? (float)(1.0 - cell_rfac(a.k_lu, a.kscale[c])) : 1.f - a.rfac) * kW1;
+                d += (a.kscale ? (float)cell_sink(a.k_lu, a.kscale[c]) : a.rsink) * kW1;
         } else if (v) {
             long long nb;
             if (k == 1) nb = c + 1;

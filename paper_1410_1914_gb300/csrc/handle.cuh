@@ -112,6 +112,7 @@ cl_status from_cuda(cudaError_t e);
 int transport_phases(const cl_params& p);
 float reactive_factor(const cl_lbm* h);
 double reactive_factor_d(const cl_lbm* h);
+double reactive_sink_d(const cl_lbm* h);
 MarchArgs make_margs(cl_lbm* h, int dst);
 cl_status check_err_flag(cl_lbm* h);
 

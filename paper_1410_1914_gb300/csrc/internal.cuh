@@ -27,6 +27,8 @@ struct StepArgs {
     const uint16_t* __restrict__ mask;
     const float* __restrict__ omega;
     float rfac;          // (2w - k_lu) / (2w + k_lu), w = 1/8 on every axis link
+    float rsink;         // 1 - rfac = 2 k_lu / (2w + k_lu), formed without the cancellation of 1 - rfac
+    double rsink_d;      // the same in FP64
     float abb_in;        // 2 w C_in
     float abb_out;       // 2 w C_out
     float w_cin, w_cout; // w C_in, w C_out (reduction)
@@ -47,6 +49,13 @@ __device__ __forceinline__ double cell_rfac(double k_lu, double kscale) {
     const double k = k_lu * kscale;
     return (0.25 - k) / (0.25 + k);
 }
+// its complement 1 - r = 2k / (2w + k): the fraction a catalytic face keeps.
+// Formed directly, because k is often ~1e-8 of 2w at nm-scale voxels, where
+// 1 - r taken from a rounded r loses most (FP32: all) of its digits.
+__device__ __forceinline__ double cell_sink(double k_lu, double kscale) {
+    const double k = k_lu * kscale;
+    return 2.0 * k / (0.25 + k);
+}
 
 // ---- D3Q19 (q19.cu) ----
 constexpr int kQ19Threads = 128;
@@ -62,6 +71,8 @@ struct Q19Args {
     const float* __restrict__ omega;
     float rfac;           // (cs^2 - k_lu) / (cs^2 + k_lu), cs^2 = 1/3
     double rfac_d;        // the same in FP64 (FP64 step)
+    float rsink;          // 1 - rfac = 2 k_lu / (cs^2 + k_lu), without cancellation
+    double rsink_d;
     float c_in, c_out;
     double c_in_d, c_out_d;
     int bc_in, bc_out;
@@ -182,6 +193,7 @@ struct DsaArgs {
     long long N;
     const uint16_t* __restrict__ mask;
     float rfac;          // reactive factor r of a catalytic face
+    float rsink;         // 1 - r, without cancellation
     int bc_in, bc_out;   // cl_bc
     const double* __restrict__ kscale;  // per-cell factor on k_lu (NULL: uniform)
     double k_lu;

@@ -729,9 +729,11 @@ __global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T*
     T h[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
     {
         if (act) {
-            T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
-            // a non-uniform rate constant (Eq. 17b with the local potential) on catalytic cells
-            if (a.kscale && ((m >> kReactShift) & 0x3fu)) rf = (T)cell_rfac(a.k_lu, a.kscale[c]);
+            // 1 - r of the catalytic faces; a non-uniform rate constant (Eq. 17b with the local
+            // potential) on catalytic cells
+            double sink_d = a.rsink_d;
+            if (a.kscale && ((m >> kReactShift) & 0x3fu)) sink_d = cell_sink(a.k_lu, a.kscale[c]);
+            const T rs = kF64 ? (T)sink_d : (T)(float)sink_d;
             const T abb_in = kF64 ? (T)a.abb_in_d : (T)a.abb_in, abb_out = kF64 ? (T)a.abb_out_d : (T)a.abb_out;
             // source of population i (1..6 = +x, -x, +y, -y, +z, -z): x - c_i, y and z periodic
             const I sy_m = y == 0 ? (I)(ny - 1) * (I)nx : (I)0 - (I)nx;            // row y - 1
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T*
                 if ((m >> (o - 1)) & 1u) {
                     if (i == 1 && x == 0) gi = a.bc_in == CL_BC_DIRICHLET ? abb_in - gi : gi;
                     else if (i == 2 && x == nx - 1) gi = a.bc_out == CL_BC_DIRICHLET ? abb_out - gi : gi;
-                    else if (m & (1u << (kReactShift + o - 1))) gi = rf * gi;
+                    else if (m & (1u << (kReactShift + o - 1))) gi = gi - rs * gi;
                 }
                 g[i] = gi;
             }
@@ -778,7 +780,7 @@ __global__ void __launch_bounds__(128) k_step_fp32(const T* __restrict__ src, T*
                 if (x == nx - 1 && a.bc_out == CL_BC_DIRICHLET) rv[RED_JOUT] = 2.0 * ((double)h[1] - (double)a.w_cout);
                 const unsigned rb = (m >> kReactShift) & 0x3fu;
                 if (rb) {
-                    const double sink = 1.0 - (double)rf;
+                    const double sink = sink_d;
                     double r = 0.0;
 #pragma unroll
                     for (int d = 0; d < 6; ++d)
@@ -867,7 +869,7 @@ __global__ void k_readout_fp32(const float* __restrict__ pop, StepArgs a, double
     const long long N = a.N;
     const long long nyz = (long long)a.ny * a.nz;
     double v[5] = {0, 0, 0, 0, 0};
-    const double sink = 1.0 - (double)a.rfac;
+    const double sink = a.rsink_d;
     for (long long j = threadIdx.x; j < nyz; j += blockDim.x) {
         const long long c = x + (long long)a.nx * j;
         const uint16_t m = a.mask[c];
@@ -884,7 +886,7 @@ __global__ void k_readout_fp32(const float* __restrict__ pop, StepArgs a, double
         double r = 0.0;
         for (int d = 0; d < 6; ++d)
             if (rb & (1u << d)) r += h[d + 1];
-        v[2] += (rb && a.kscale ? 1.0 - cell_rfac(a.k_lu, a.kscale[c]) : sink) * r;
+        v[2] += (rb && a.kscale ? cell_sink(a.k_lu, a.kscale[c]) : sink) * r;
         if (x == 0 && a.bc_in == CL_BC_DIRICHLET) v[3] += 2.0 * ((double)a.w_cin - (double)h[2]);
         if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) v[4] += 2.0 * ((double)h[1] - (double)a.w_cout);
     }
@@ -909,7 +911,7 @@ __global__ void k_cell_reaction_fp32(const float* __restrict__ pop, StepArgs a, 
         if ((m & kActiveBit) && rb) {
             for (int d = 0; d < 6; ++d)
                 if (rb & (1u << d)) r += (double)pop[(long long)(d + 1) * N + c];
-            r *= a.kscale ? 1.0 - cell_rfac(a.k_lu, a.kscale[c]) : 1.0 - (double)a.rfac_d;
+            r *= a.kscale ? cell_sink(a.k_lu, a.kscale[c]) : a.rsink_d;
         }
         out[c] = r;
     }

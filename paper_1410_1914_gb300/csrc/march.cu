@@ -186,18 +186,18 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
     const float s_d = HALF ? a.s_d : 1.0f, inv_d = HALF ? a.inv_d : 1.0f;
     const float w = kW1;
     const float ws = w * s_d;
-    const float rf = a.rfac;
+    const float sink = a.rsink;  // 1 - r
     const float lx = lxs * inv_lo;
     const float Cx = hx + lx;
-    // catalytic face: r dopp - (1 - r) w C (the half-way first-order sink)
-    const float q_cat = (1.0f - rf) * ws * Cx;
+    // catalytic face: r dopp - (1 - r) w C = dopp - (1 - r)(dopp + w C) (the half-way first-order sink)
+    const float wsC = ws * Cx;
     float av[6];
 #pragma unroll
     for (int i = 0; i < 6; ++i) {
         const int fb = i ^ 1;
         const float dopp = dds[fb];
         const float a_open = ws * ((nh[i] - hx) + (nls[i] - lxs) * inv_lo) + nds[i];
-        float a_closed = (m & (1u << (kReactShift + fb))) ? fmaf(rf, dopp, -q_cat) : dopp;
+        float a_closed = (m & (1u << (kReactShift + fb))) ? fmaf(-sink, dopp + wsC, dopp) : dopp;
         if (i == 0 && x == 0)
             a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_in - hx) - lx) - dopp : dopp;
         if (i == 1 && x == a.nx - 1)
@@ -231,7 +231,7 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
 #pragma unroll
             for (int d = 0; d < 6; ++d)
                 if (rb & (1u << d)) r += (double)w * Cn + (double)dns[d] * id;
-            rv[RED_R] += (1.0 - (double)rf) * r;
+            rv[RED_R] += a.rsink_d * r;
         }
         const float Cf = hnew + lnew;  // the f32 rounding of the double-float C
         rs[0] += Cf;
@@ -874,7 +874,7 @@ __global__ void k_state_readout(MarchArgs a, const uint16_t* __restrict__ mask_p
         double r = 0.0;
         for (int dd = 0; dd < 6; ++dd)
             if (rb & (1u << dd)) r += w * C + d[dd];
-        v[2] += (1.0 - (double)a.rfac) * r;
+        v[2] += a.rsink_d * r;
         if (x == 0 && a.bc_in == CL_BC_DIRICHLET) v[3] += 2.0 * w * ((double)a.c_in - C) - 2.0 * d[1];
         if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) v[4] += 2.0 * w * (C - (double)a.c_out) + 2.0 * d[0];
     }

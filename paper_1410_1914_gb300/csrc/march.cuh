@@ -28,6 +28,8 @@ struct MarchArgs {
     void* clo;
     void* d[6];
     float rfac;
+    float rsink;     // 1 - rfac = 2 k_lu / (2w + k_lu), without the cancellation of 1 - rfac
+    double rsink_d;
     float c_in, c_out;
     int bc_in, bc_out;
     float s_lo, inv_lo, s_d, inv_d;  // FP16 scales (1 for FP32 storage)

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const T* __restrict__ sr
             const I e = own[i] ? (I)j * NP + c : (I)i * NP + s;
             v[i] = src[e];
         }
-        const T rf = kF64 ? (T)a.rfac_d : (T)a.rfac;
+        const T rs = kF64 ? (T)a.rsink_d : (T)a.rsink;  // 1 - r
         const T cin = kF64 ? (T)a.c_in_d : (T)a.c_in, cout = kF64 ? (T)a.c_out_d : (T)a.c_out;
         T g[19];
         g[0] = v[0];
@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const T* __restrict__ sr
             const T wi = q19_wt<T>(i);
             T o = v[i];
             if (own[i]) {
-                if ((m >> (j - 1)) & 1u) o = ((rb >> (j - 1)) & 1u) ? rf * o : o;
+                if ((m >> (j - 1)) & 1u) o = ((rb >> (j - 1)) & 1u) ? o - rs * o : o;
                 else if (cx > 0) o = a.bc_in == CL_BC_DIRICHLET ? T(2) * wi * cin - o : o;
                 else o = a.bc_out == CL_BC_DIRICHLET ? T(2) * wi * cout - o : o;
             }
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(kQ19Threads) k_step19(const T* __restrict__ sr
             }
             rv[RED_JIN] = jin;
             rv[RED_JOUT] = jout;
-            rv[RED_R] = (1.0 - (double)a.rfac) * r;
+            rv[RED_R] = a.rsink_d * r;
             rv[RED_SUMC] = C;
             rv[RED_DC] = fabs((double)C - (double)a.Csnap[c]);
             rv[RED_ABSC] = fabs((double)C);
@@ -319,7 +319,7 @@ __global__ void k_readout19(const float* __restrict__ pop, Q19Args a, double* ou
     const int x = blockIdx.x;
     const long long nyz = (long long)a.ny * a.nz;
     double v[5] = {0, 0, 0, 0, 0};
-    const double sink = 1.0 - (double)a.rfac;
+    const double sink = a.rsink_d;
     for (long long j = threadIdx.x; j < nyz; j += blockDim.x) {
         const long long c = x + (long long)a.px * j;
         const uint32_t m = a.mask[c];

@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
         const float2 own_hl = shl[c];
         const float hx = own_hl.x, lx = own_hl.y;
         const float Cx = hx + lx;
-        const float rf = a.rfac;
+        const float rs = a.rsink;  // 1 - r
         // own deviations: their sum is -delta_0
         float sdd = 0.f;
 #pragma unroll
@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
             float ei = ws * ((nhl.x - hx) + (nhl.y - lx)) + nd;
             if (own) {
                 if (wall) {
-                    if ((rb >> (j - 1)) & 1u) ei = fmaf(rf, nd, -(1.0f - rf) * ws * Cx);
+                    if ((rb >> (j - 1)) & 1u) ei = fmaf(-rs, nd + ws * Cx, nd);
                 } else if (cx > 0) {
                     if (a.bc_in == CL_BC_DIRICHLET) ei = 2.0f * ws * ((a.c_in - hx) - lx) - nd;
                 } else {
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(kS19X * kS19Y) k_step19s(Q19State src, Q19Stat
             }
             rv[RED_JIN] = jin;
             rv[RED_JOUT] = jout;
-            rv[RED_R] = (1.0 - (double)rf) * r;
+            rv[RED_R] = a.rsink_d * r;
             const float Cf = hnew + lnew;
             rv[RED_SUMC] = Cf;
             rv[RED_DC] = fabs((double)Cf - (double)a.Csnap[c]);
@@ -238,7 +238,7 @@ __global__ void k_readout19s(Q19State st, Q19Args a, double* out) {
     const int x = blockIdx.x;
     const long long nyz = (long long)a.ny * a.nz;
     double v[5] = {0, 0, 0, 0, 0};
-    const double sink = 1.0 - (double)a.rfac;
+    const double sink = a.rsink_d;
     for (long long j = threadIdx.x; j < nyz; j += blockDim.x) {
         const long long p = x + (long long)a.px * j;
         const uint32_t m = a.mask[p];

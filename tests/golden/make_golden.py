@@ -94,11 +94,40 @@ def converged(name, edge=64, chunk=1000, rel=1e-10, max_steps=3_000_000):
                 f"two checks of {chunk} steps in a row", threads=oracle.num_threads())
 
 
+# converged reactive instances by the oracle's exact steady state (oracle/steady.py: the
+# fixed point of one step by a sparse direct solve; the march approaches it too slowly
+# with a zero-flux outlet): y and z extents multiples of 3
+EXACT = {
+    "c2_react_48": ("pt_cl_256", 43, True),
+    "c3_react_48": ("npmc_cl_400", 44, True),
+}
+
+
+def exact(name, edge=48):
+    """The exact steady state of a reactive 48^3 instance: readouts of the
+    oracle's populations at the fixed point of its step."""
+    from oracle import steady
+    recipe, seed, reactive = EXACT[name]
+    ph, react, params = inputs.make_workload(recipe, shape=(edge, edge, edge), seed=seed, reactive=reactive)
+    o = oracle.OracleLBM(ph, react=react, **params)
+    t0 = time.time()
+    steady.solve(o)
+    f = o.fluxes()
+    R, _, _ = o.reaction_rate()
+    return dict(workload=recipe, shape=[edge, edge, edge], seed=seed, reactive=reactive, lattice="D3Q7",
+                method="exact fixed point of the oracle's step (oracle/steady.py)", converged=True,
+                seconds=time.time() - t0, R=R, J_in=f["J_in"], J_out=f["J_out"], R_lu=f["R"],
+                flux_balance=abs(f["J_in"] - f["J_out"] - f["R"]) / abs(f["J_in"]), n_active=f["n_active"],
+                threads=oracle.num_threads())
+
+
 if __name__ == "__main__":
     which = sys.argv[1:] or ["c1_deff", "c1_deff_d3q19"]
     for name in which:
         if name in CONVERGED:
             out = converged(name)
+        elif name in EXACT:
+            out = exact(name)
         else:
             out = c1_deff(lattice=1 if name.endswith("d3q19") else 0)
         print(name, out)

@@ -44,6 +44,10 @@ CASES = {
     "pt_deff": ("pt_cl_48", (19, 23, 37), 22, {}),
     "npmc": ("npmc_cl_400", (24, 20, 150), 23, dict(k_ms=5e3)),
     "thin": ("pt_cl_256", (3, 5, 40), 24, dict(k_ms=2e4)),
+    # the workloads' own rate constants: at nm voxels k dt / dx is ~1e-8 (Pt, 1e-3 m/s) and
+    # ~1e-10 (NPMC, 1e-5 m/s) of 2w, where 1 - r must be formed without cancellation
+    "pt_physical_k": ("pt_cl_256", (13, 17, 291), 25, {}),
+    "npmc_physical_k": ("npmc_cl_400", (24, 20, 150), 26, {}),
 }
 
 
@@ -116,7 +120,7 @@ def test_trajectory(cuda_lib, storage, name, steps):
     assert fg["n_active"] == fo["n_active"]
     assert abs(fg["J_in"] - fo["J_in"]) <= ftol * scale + floor
     assert abs(fg["J_out"] - fo["J_out"]) <= ftol * scale + floor
-    assert abs(fg["R"] - fo["R"]) <= ftol * max(abs(fo["R"]), 1e-30) + floor
+    assert abs(fg["R"] - fo["R"]) <= ftol * max(abs(fo["R"]), 1e-30) + min(floor, 1e-3 * abs(fo["R"]))
     assert fg["sum_C"] == pytest.approx(fo["sum_C"], rel=max(ftol, 1e-6))
     tg, pRg, pCg = s.reaction_rate()
     to, pRo, pCo = o.reaction_rate()
