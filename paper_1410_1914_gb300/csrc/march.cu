@@ -197,13 +197,14 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
         const int fb = i ^ 1;
         const float dopp = dds[fb];
         const float a_open = ws * ((nh[i] - hx) + (nls[i] - lxs) * inv_lo) + nds[i];
-        float a_closed = (m & (1u << (kReactShift + fb))) ? fmaf(-sink, dopp + wsC, dopp) : dopp;
-        if (i == 0 && x == 0)
-            a_closed = a.bc_in == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_in - hx) - lx) - dopp : dopp;
-        if (i == 1 && x == a.nx - 1)
-            a_closed = a.bc_out == CL_BC_DIRICHLET ? 2.0f * ws * ((a.c_out - hx) - lx) - dopp : dopp;
+        const float a_closed = (m & (1u << (kReactShift + fb))) ? fmaf(-sink, dopp + wsC, dopp) : dopp;
         av[i] = (m & (1u << fb)) ? a_closed : a_open;
     }
+    // the x faces of the box (closed, never catalytic, so the loop gave the wall value dopp):
+    // anti-bounce-back at a fixed value, bounce-back at zero flux.  Only the first and last
+    // lanes of a row's end tiles take these branches; every other warp passes them uniformly.
+    if (x == 0 && a.bc_in == CL_BC_DIRICHLET) av[0] = 2.0f * ws * ((a.c_in - hx) - lx) - dds[1];
+    if (x == a.nx - 1 && a.bc_out == CL_BC_DIRICHLET) av[1] = 2.0f * ws * ((a.c_out - hx) - lx) - dds[0];
     const float dCs = ((av[0] + av[1]) + (av[2] + av[3]) + (av[4] + av[5])) -
                       ((dds[0] + dds[1]) + (dds[2] + dds[3]) + (dds[4] + dds[5]));
     float lnew;
