@@ -211,8 +211,9 @@ __device__ __forceinline__ void cell_update(const MarchArgs& a, uint32_t m, floa
     df_add(hx, lx, dCs * inv_d, hnew, lnew);
     lnew_s = lnew * s_lo;
     const float om1 = 1.0f - om;
+    const float t = om1 * w * dCs;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) dns[i] = om1 * (av[i] - w * dCs);
+    for (int i = 0; i < 6; ++i) dns[i] = fmaf(om1, av[i], -t);  // (1 - omega)(a_i - w dC)
     if (REDUCE) {
         // Fluxes and reaction in FP64 (boundary and catalytic cells only:
         // the stopping rule resolves their changes down to 1e-9); the
