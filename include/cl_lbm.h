@@ -506,8 +506,8 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
 void cl_batch_destroy(cl_batch_handle b);
 
 /* Advance every member by exactly nsteps steps in one cooperative launch
-   (the same arithmetic as cl_lbm_step).  CL_ERR_TIMEOUT if the bounded grid
-   barrier gave up. */
+   (the same arithmetic as cl_lbm_step).  CL_ERR_TIMEOUT if a bounded wait
+   for a member's previous step gave up. */
 cl_status cl_batch_step(cl_batch_handle b, long long nsteps);
 
 /* Advance all members, check_every steps per launch (a captured CUDA graph
@@ -529,11 +529,12 @@ cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk
    from a cached autotuning result). */
 cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch);
 
-/* Test hook of the batch's bounded grid barrier (no counterpart in the
-   paper).  wait_limit_clocks: SM clock cycles a block waits at the barrier
-   before it gives up (0: the default, about 2 s).  never_arrive (needs a
-   limit > 0): every block waits for one arrival more than the grid has, so
-   the wait runs out; the launch then ends with every block returned and the
+/* Test hook of the batch's bounded step-dependency waits (no counterpart in
+   the paper).  wait_limit_clocks: SM clock cycles a block waits for a member's
+   previous step to finish before it gives up (0: the default, about 2 s).
+   never_arrive (needs a limit > 0): every such wait asks for one finished
+   item more than the member has, so the first wait of a launch of two or more
+   steps runs out; the launch then ends with every block returned and the
    step reports CL_ERR_TIMEOUT.  The members' states are then partly stepped:
    re-initialise them.  Set (0, 0) to restore normal stepping.
    Errors: CL_ERR_ARG. */

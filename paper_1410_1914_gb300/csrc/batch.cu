@@ -2,9 +2,11 @@
 //
 // A batch groups existing solver handles (each with its structure loaded).
 // One cooperative launch of k_march_batch advances every structure that is
-// still running by K steps: the blocks (one or two per SM, all resident) walk
-// a work list of (structure, 64x8 tile column, z range) items, then meet at a
-// bounded grid barrier before the next step.  The last step of a launch also
+// still running by K steps: the blocks (up to three per SM, all resident) take
+// (step, item) pairs from one queue, an item being a (structure, 64x8 tile
+// column, z range); an item of step t waits only until its own structure's
+// step t - 1 is done (a bounded wait on a per-structure count), so structures
+// pipeline across steps with no grid-wide barrier.  The last step of a launch also
 // reduces each structure's fluxes; the host applies each structure's stopping
 // rule and drops converged structures from the work list, whose length is
 // read on the device, so the captured graph stays valid as the batch shrinks.
@@ -38,7 +40,8 @@ struct cl_batch {
     int* d_n_items = nullptr;
     int* d_inst_first = nullptr;
     int* d_inst_count = nullptr;
-    unsigned* d_counter = nullptr;
+    unsigned long long* d_next = nullptr;  // queue position
+    unsigned long long* d_done = nullptr;  // [n] finished items per member
     int* d_abort = nullptr;
     int* d_err = nullptr;
     double* d_item_partials = nullptr;
@@ -47,7 +50,7 @@ struct cl_batch {
     std::vector<char> active;
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = true;
-    long long wait_limit = 0;  // grid barrier bound (0: default)
+    long long wait_limit = 0;  // step-dependency wait bound (0: default)
     int never_arrive = 0;      // test hook (cl_batch_set_wait_test)
 };
 
@@ -57,7 +60,9 @@ int items_of(const cl_lbm* h, int zc) {
     return ((h->px + kBX - 1) / kBX) * ((h->ny + kBY - 1) / kBY) * ((h->nz + zc - 1) / zc);
 }
 
-// Work list over the running structures, z ranges of z_chunk planes.
+// Work list over the running structures: each column's planes split into
+// ceil(nz / z_chunk) ranges of nearly equal length (no short remainder range,
+// whose two halo planes and pipeline fill would cost as much as its work).
 cl_status upload_items(cl_batch* b) {
     std::vector<WorkItem> items;
     std::vector<int> first(b->n, 0), count(b->n, 0);
@@ -65,10 +70,12 @@ cl_status upload_items(cl_batch* b) {
         first[i] = (int)items.size();
         if (!b->active[i]) continue;
         const cl_lbm* h = b->m[i];
-        for (int zs = 0; zs < h->nz; zs += b->z_chunk)
+        const int g = (h->nz + b->z_chunk - 1) / b->z_chunk;
+        for (int j = 0; j < g; ++j) {
+            const int zs = (int)((long long)h->nz * j / g), ze = (int)((long long)h->nz * (j + 1) / g);
             for (int y0 = 0; y0 < h->ny; y0 += kBY)
-                for (int x0 = 0; x0 < h->px; x0 += kBX)
-                    items.push_back(WorkItem{i, x0, y0, zs, std::min(h->nz, zs + b->z_chunk)});
+                for (int x0 = 0; x0 < h->px; x0 += kBX) items.push_back(WorkItem{i, x0, y0, zs, ze});
+        }
         count[i] = (int)items.size() - first[i];
     }
     b->n_items = (int)items.size();
@@ -101,13 +108,16 @@ BatchLaunch launch_desc(cl_batch* b, int nsteps, bool reduce_last) {
     L.storage = b->storage;
     L.grid = b->grid;
     L.grid_reduce = b->grid_reduce;
+    L.n_inst = b->n;
     L.insts = b->d_insts;
     L.items = b->d_items;
     L.n_items = b->d_n_items;
+    L.inst_count = b->d_inst_count;
     L.nsteps = nsteps;
     L.parity0 = b->parity;
     L.reduce_last = reduce_last ? 1 : 0;
-    L.counter = b->d_counter;
+    L.next = b->d_next;
+    L.done = b->d_done;
     L.abort_flag = b->d_abort;
     L.item_partials = b->d_item_partials;
     L.err = b->d_err;
@@ -124,7 +134,10 @@ cl_status batch_err(cl_batch* b) {
         CK(cudaMemsetAsync(b->d_err, 0, sizeof(int), b->s));
         CK(cudaStreamSynchronize(b->s));
     }
-    if (e & 32) { set_msg_txt("grid barrier of the batched step did not complete within its bound"); return CL_ERR_TIMEOUT; }
+    if (e & 32) {
+        set_msg_txt("a step-dependency wait of the batched step did not complete within its bound");
+        return CL_ERR_TIMEOUT;
+    }
     if (e) { set_msg_txt("batched step kernel raised an error"); return CL_ERR_CUDA; }
     for (auto* h : b->m) CKS(check_err_flag(h));
     return CL_OK;
@@ -214,7 +227,8 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_n_items, sizeof(int), b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_inst_first, sizeof(int) * n, b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_inst_count, sizeof(int) * n, b->s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&b->d_counter, sizeof(unsigned), b->s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&b->d_next, sizeof(unsigned long long), b->s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&b->d_done, sizeof(unsigned long long) * n, b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_abort, sizeof(int), b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_err, sizeof(int), b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_item_partials, sizeof(double) * RED_N * b->max_items, b->s);
@@ -233,8 +247,8 @@ void cl_batch_destroy(cl_batch_handle b) {
     if (!b) return;
     drop_graph(b);
     if (b->s || true) cudaStreamSynchronize(b->s);
-    void* ptrs[] = {b->d_insts, b->d_items, b->d_n_items, b->d_inst_first, b->d_inst_count, b->d_counter,
-                    b->d_abort, b->d_err, b->d_item_partials, b->d_inst_red};
+    void* ptrs[] = {b->d_insts, b->d_items, b->d_n_items, b->d_inst_first, b->d_inst_count, b->d_next,
+                    b->d_done, b->d_abort, b->d_err, b->d_item_partials, b->d_inst_red};
     for (void* p : ptrs)
         if (p) cudaFreeAsync(p, b->s);
     cudaStreamSynchronize(b->s);
@@ -399,7 +413,7 @@ cl_status cl_batch_set_wait_test(cl_batch_handle b, long long wait_limit_clocks,
     }
     b->wait_limit = wait_limit_clocks;
     b->never_arrive = never_arrive ? 1 : 0;
-    drop_graph(b);  // the barrier settings are baked into the captured launch
+    drop_graph(b);  // the wait settings are baked into the captured launch
     return CL_OK;
 }
 

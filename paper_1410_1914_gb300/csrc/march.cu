@@ -573,88 +573,127 @@ __global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) =
 }
 
 // ------------------------------------------------------- batched launch
-// Bounded grid-wide barrier of a cooperative launch: the counter is zeroed
-// before the launch and reaches (round + 1) * gridDim.x.  A block that gives
-// up (after `limit` cycles; 0: 2^32, about 2 s) raises bit 32 and the abort
-// word so that no block waits forever.
-__device__ bool grid_sync(unsigned* counter, unsigned target, int* abort_flag, int* err, long long limit) {
-    __syncthreads();
-    __shared__ int s_abort;
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        __threadfence();
-        atomicAdd(counter, 1u);
-        const long long lim = limit > 0 ? limit : (1LL << 32);
-        const long long t0 = clock64();
-        int ab = 0;
-        for (;;) {
-            unsigned v;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(counter) : "memory");
-            if (v >= target) break;
-            ab = *(volatile int*)abort_flag;
-            if (ab) break;
-            if (clock64() - t0 > lim) {
-                atomicOr(err, 32);
-                atomicExch(abort_flag, 1);
-                ab = 1;
-                break;
-            }
+// The work of a launch is one queue of (step, item) pairs, step-major and,
+// within a step, member-major.  A block takes the next pair from a global
+// counter; before it marches an item of step t >= 1 it waits until every item
+// of the same member at step t - 1 is done (a per-member count of finished
+// items), which is all the lattice step needs: a member's step t reads only
+// what its own step t - 1 wrote.  Members never wait on one another, so the
+// blocks that finish a step early go on with the next step of the members that
+// are ready instead of idling at a grid-wide barrier.  A wait only ever
+// depends on items taken from the queue before the waiting one, whose blocks
+// are running, so it cannot deadlock.
+//
+// Bounded wait for a member's count of finished items: gives up after `limit`
+// cycles (0: 2^32, about 2 s) and raises bit 32 and the abort word, so that no
+// block waits forever; another block's abort ends the wait at once.
+__device__ bool wait_done(const unsigned long long* done, unsigned long long target, int* abort_flag, int* err,
+                          long long limit) {
+    const long long lim = limit > 0 ? limit : (1LL << 32);
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned long long v;
+        asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(done) : "memory");
+        if (v >= target) return true;
+        if (*(volatile int*)abort_flag) return false;
+        if (clock64() - t0 > lim) {
+            atomicOr(err, 32);
+            atomicExch(abort_flag, 1);
+            return false;
         }
-        __threadfence();
-        s_abort = ab;
+        __nanosleep(64);
     }
-    __syncthreads();
-    return s_abort == 0;
 }
+
+constexpr int kFenceBits = 2048;  // (member, parity) pairs whose descriptors a block has fenced
 
 // FP16 plain steps fit three resident blocks per SM; the others keep the
 // registers they need
 template <class S, bool REDUCE>
 __global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 3 : 1)
-    k_march_batch(const BatchInst* __restrict__ insts,
-                                                            const WorkItem* __restrict__ items,
-                                                            const int* __restrict__ n_items_ptr, int nsteps,
-                                                            int parity0, int reduce_last, unsigned* counter,
-                                                            int* abort_flag, double* item_partials, int* err,
-                                                            long long wait_limit, int never_arrive) {
+    k_march_batch(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items,
+                  const int* __restrict__ n_items_ptr, const int* __restrict__ inst_count, int nsteps, int parity0,
+                  unsigned long long* next, unsigned long long* done, int* abort_flag, double* item_partials,
+                  int* err, long long wait_limit, int never_arrive) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + kStages;
     unsigned char* slots = smem_raw + 128;
+    __shared__ MarchArgs s_args;
+    __shared__ WorkItem s_it;
+    __shared__ int s_w;      // its index in the work list
+    __shared__ int s_step;   // step of the taken item, -1: no more work
+    __shared__ int s_fence;  // first use of the item's descriptors by this block
+    __shared__ unsigned s_fenced[kFenceBits / 32];
     if (!smem_ok(smem_raw, err)) { atomicExch(abort_flag, 1); return; }
-    init_ring(full, empty);
-    const int n_items = *n_items_ptr;
+    for (int i = threadIdx.y * 32 + threadIdx.x; i < kFenceBits / 32; i += kThreads) s_fenced[i] = 0u;
+    init_ring(full, empty);  // ends with a block barrier
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    const long long n_items = *n_items_ptr;
+    const unsigned long long total = (unsigned long long)n_items * (unsigned long long)nsteps;
     unsigned seq = 0;
-    for (int step = 0; step < nsteps; ++step) {
-        const int par = parity0 ^ (step & 1);
-        const bool red = REDUCE && step == nsteps - 1;
-        bool ok = true;
-        for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
-            const WorkItem it = items[w];
-            const BatchInst* in = insts + it.inst;
-            // per-instance arguments staged once per item in shared memory
-            __shared__ MarchArgs s_args;
-            __syncthreads();
-            if (threadIdx.x == 0 && threadIdx.y == 0) s_args = in->args[par];
-            __syncthreads();
-            const MarchArgs& a = s_args;
-            double rv[RED_N];
-#pragma unroll
-            for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
-            if (REDUCE && red) {
-                ok = march_item<S, true>(&in->maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq,
-                                         step < 2, rv);
-                block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
-            } else {
-                ok = march_item<S, false>(&in->maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq,
-                                          step < 2, rv);
+    for (;;) {
+        if (lead) {
+            int step = -1;
+            const unsigned long long q = atomicAdd(next, 1ull);
+            if (q < total && *(volatile int*)abort_flag == 0) {
+                step = (int)(q / (unsigned long long)n_items);
+                const int w = (int)(q - (unsigned long long)step * n_items);
+                const WorkItem it = items[w];
+                // test hook: one finished item more than the member has never comes
+                if (step > 0 &&
+                    !wait_done(done + it.inst,
+                               (unsigned long long)step * (unsigned long long)inst_count[it.inst] +
+                                   (never_arrive ? 1ull : 0ull),
+                               abort_flag, err, wait_limit))
+                    step = -1;
+                if (step >= 0) {
+                    const int par = parity0 ^ (step & 1);
+                    s_it = it;
+                    s_w = w;
+                    s_args = insts[it.inst].args[par];
+                    const int fb = 2 * it.inst + par;
+                    int fence = 1;
+                    if (fb < kFenceBits) {
+                        fence = !((s_fenced[fb >> 5] >> (fb & 31)) & 1u);
+                        s_fenced[fb >> 5] |= 1u << (fb & 31);
+                    }
+                    s_fence = fence;
+                }
             }
-            seq += (unsigned)(it.ze - it.zs + 2);
-            ok = __syncthreads_and(ok);
+            s_step = step;
         }
-        if (!ok && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(abort_flag, 1);
-        // test hook: one arrival more than the grid has never comes
-        const unsigned target = (unsigned)(step + 1) * gridDim.x + (never_arrive ? 1u : 0u);
-        if (!grid_sync(counter, target, abort_flag, err, wait_limit)) break;
+        __syncthreads();
+        const int step = s_step;
+        if (step < 0) break;
+        const WorkItem it = s_it;
+        const int w = s_w;
+        const int par = parity0 ^ (step & 1);
+        const MarchArgs& a = s_args;
+        // the producer's loads (async proxy) come after the other members' writes it waited for
+        if (threadIdx.y == kBY && threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
+        double rv[RED_N];
+#pragma unroll
+        for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+        bool ok;
+        if (REDUCE) {
+            ok = march_item<S, true>(&insts[it.inst].maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty,
+                                     seq, s_fence != 0, rv);
+            block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
+        } else {
+            ok = march_item<S, false>(&insts[it.inst].maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full,
+                                      empty, seq, s_fence != 0, rv);
+        }
+        seq += (unsigned)(it.ze - it.zs + 2);
+        ok = __syncthreads_and(ok);
+        if (!ok) {
+            if (lead) atomicExch(abort_flag, 1);
+            break;
+        }
+        if (lead) {
+            __threadfence();  // this item's stores before its count
+            atomicAdd(done + it.inst, 1ull);
+        }
     }
 }
 
@@ -719,13 +758,21 @@ static cudaError_t launch_batch_t(const BatchLaunch& b, int grid, cudaStream_t s
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;  // blocks wait on one another at the step barrier
+    attr[0].id = cudaLaunchAttributeCooperative;  // every block resident: one persistent block per slot
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_march_batch<S, R>, b.insts, b.items, b.n_items, b.nsteps, b.parity0,
-                              b.reduce_last, b.counter, b.abort_flag, b.item_partials, b.err, b.wait_limit,
+    return cudaLaunchKernelEx(&cfg, k_march_batch<S, R>, b.insts, b.items, b.n_items, b.inst_count, b.nsteps,
+                              b.parity0, b.next, b.done, b.abort_flag, b.item_partials, b.err, b.wait_limit,
                               b.never_arrive);
+}
+
+// queue counter, per-member counts and abort word start from zero in each launch
+static cudaError_t reset_queue(const BatchLaunch& b, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(b.next, 0, sizeof(unsigned long long), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.done, 0, sizeof(unsigned long long) * b.n_inst, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+    return e;
 }
 
 template <class S>
@@ -736,16 +783,14 @@ static cudaError_t launch_batch_s(const BatchLaunch& b, cudaStream_t s) {
     BatchLaunch p = b;
     if (plain > 0) {
         p.nsteps = plain;
-        e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+        e = reset_queue(b, s);
         if (e == cudaSuccess) e = launch_batch_t<S, false>(p, b.grid, s);
         if (e != cudaSuccess) return e;
     }
     if (b.reduce_last) {
         p.nsteps = 1;
         p.parity0 = b.parity0 ^ (plain & 1);
-        e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(b.abort_flag, 0, sizeof(int), s);
+        e = reset_queue(b, s);
         if (e == cudaSuccess) e = launch_batch_t<S, true>(p, b.grid_reduce, s);
     }
     return e;

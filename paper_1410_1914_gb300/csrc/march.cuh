@@ -59,17 +59,20 @@ struct BatchLaunch {
     int storage;
     int grid;         // co-resident blocks of the plain-step launch (cooperative)
     int grid_reduce;  // co-resident blocks of the reducing-step launch
+    int n_inst;
     const BatchInst* insts;
     const WorkItem* items;
-    const int* n_items;  // device count, so the list can shrink between graph replays
+    const int* n_items;     // device count, so the list can shrink between graph replays
+    const int* inst_count;  // items of each member in the list (0 for a member that stopped)
     int nsteps, parity0, reduce_last;
-    unsigned* counter;   // grid barrier counter (zeroed before each launch)
+    unsigned long long* next;  // queue position (zeroed before each launch)
+    unsigned long long* done;  // [n_inst] finished items per member (zeroed before each launch)
     int* abort_flag;
     double* item_partials;  // [item][RED_N] when reduce_last
     int* err;
-    // grid barrier: clock cycles before a block gives up (0: the default,
-    // about 2 s of SM clock); never_arrive (a test hook) makes every block wait
-    // for one arrival more than the grid has
+    // step-dependency waits: clock cycles before a block gives up (0: the
+    // default, about 2 s of SM clock); never_arrive (a test hook) makes every
+    // wait ask for one finished item more than the member has
     long long wait_limit;
     int never_arrive;
 };

@@ -1,11 +1,12 @@
 """Bounded device-side waits that run out (gpu), made to do so on purpose.
 
-The step kernel's plane loads are guarded by mbarrier waits and the batched
-launch meets at a grid barrier after every lattice step; each wait gives up
+The step kernel's plane loads are guarded by mbarrier waits, and in the
+batched launch an item of step t waits until its member's step t - 1 is
+done (a per-member count of finished items); each wait gives up
 after a bound and raises an error bit that the host maps to CL_ERR_TIMEOUT.
 The test hooks shorten the bound to a few hundred SM clock cycles and make
 the awaited event one that never happens (a plane load the producer never
-issues; one barrier arrival more than the grid has).  The call must return
+issues; one finished item more than the member has).  The call must return
 CL_ERR_TIMEOUT, the kernel must not touch the state it would have written,
 and the handle or batch must step normally again once the hook is reset --
 no fault, no trap, no hang.
@@ -66,7 +67,7 @@ def test_wait_hook_arguments(cuda_lib):
 
 
 @pytest.mark.parametrize("storage", ["fp32", "fp16dev"])
-def test_batch_grid_barrier_runs_out(cuda_lib, storage):
+def test_batch_step_wait_runs_out(cuda_lib, storage):
     from paper_1410_1914_gb300 import _lib as L
     from paper_1410_1914_gb300.batch import Batch
     members = []
