@@ -258,7 +258,7 @@ def run_batch(args):
         solvers.append(s)
     cells = sum(ph.size for ph, _, _ in work)
     b = Batch(solvers)
-    zc, pf, ms_tune, cached = b.autotune(steps_per_trial=4, cache=None)
+    zc, pf, tr, ms_tune, cached = b.autotune(steps_per_trial=4, cache=None)
     bi = b.info()
     for _ in range(args.warmup):
         b.step(K)
@@ -299,7 +299,7 @@ def run_batch(args):
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": "64 cubes, edge uniform 32-160, Pt/NPMC alternating, porosity 0.35-0.65, "
                                "Knudsen D, D_eff set-up", "cells": cells, "storage": args.storage,
-                   "lbm_steps_per_bench_step": K, "autotuned": {"z_chunk": zc, "prefetch": pf},
+                   "lbm_steps_per_bench_step": K, "autotuned": {"z_chunk": zc, "prefetch": pf, "tile_rows": tr},
                    "grid_blocks": bi["grid_blocks"], "work_items": bi["n_items"]},
         "sequential_mlups": seq_mlups,
         "batch_over_sequential": mlups / seq_mlups,

@@ -231,6 +231,19 @@ cl_status cl_lbm_solve(cl_handle h, cl_solve_info* info);
    Errors: CL_ERR_ARG. */
 cl_status cl_lbm_set_wait_test(cl_handle h, long long wait_limit_clocks, int never_arrive);
 
+/* Tile shape of the plane-marching step kernel ((C, delta) storage; a
+   layout choice with no counterpart in the paper).  A thread block steps a
+   column of 512 cells, rows x of 64 / rows cells by 8 * rows (rows = 1, 2 or
+   4: 64 x 8, 32 x 16, 16 x 32 cells) through its planes; a narrow tile leaves
+   fewer lanes idle where nx is not a multiple of 64.  rows = 0 restores the
+   default, the shape with the fewest cell slots along x (ties to the wider
+   tile).  The arithmetic is the same for every shape (the results are
+   bit-identical).  rows_out (may be NULL) receives the shape in use.  Drops
+   the captured step graphs.  A batch takes each member's shape when it is
+   created.  Errors: CL_ERR_ARG (rows), CL_ERR_STATE (population storage),
+   CL_ERR_CUDA. */
+cl_status cl_lbm_set_tile_rows(cl_handle h, int rows, int* rows_out);
+
 /* cl_lbm_solve with an explicit step budget instead of p->max_steps (whole
    check intervals only; a budget below check_every runs no step).  Each call
    restarts the stopping rule's history, so a budget of one interval always
@@ -519,15 +532,22 @@ cl_status cl_batch_step(cl_batch_handle b, long long nsteps);
    non-finite member. */
 cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* infos, int* n_converged);
 
-/* Time steps_per_trial (even) steps for each z_chunk in {8, 16, 32, 64} and
-   L2 prefetch distance in {0, 2}, keep the fastest and report it (ms per
-   step in best_ms).  The trial steps are real steps of every member. */
-cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk, int* prefetch,
+/* Time steps_per_trial (even) steps for each tile shape in {1, 2, 4} rows
+   per warp (one shape for every member; cl_lbm_set_tile_rows), z_chunk in
+   {8, 16, 32, 64} and L2 prefetch distance in {0, 2}, keep the fastest and
+   report it (ms per step in best_ms).  The trial steps are real steps of
+   every member.  Any out pointer may be NULL. */
+cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk, int* prefetch, int* tile_rows,
                             double* best_ms);
 
-/* Set the work-item z length (>= 8) and prefetch distance directly (e.g.
-   from a cached autotuning result). */
-cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch);
+/* Set the work-item z length (>= 8), prefetch distance and tile shape
+   directly (e.g. from a cached autotuning result).  tile_rows: 1, 2 or 4
+   rows per warp for every member, or 0 for each member's own shape (its
+   handle's at batch creation).  A new batch starts with the single shape of
+   least modelled cost over its members (idle lanes and rows against each
+   shape's per-cell cost); members of different shapes in one launch run
+   slower than any single shape.  Errors: CL_ERR_ARG. */
+cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch, int tile_rows);
 
 /* Test hook of the batch's bounded step-dependency waits (no counterpart in
    the paper).  wait_limit_clocks: SM clock cycles a block waits for a member's

@@ -156,11 +156,13 @@ SIGNATURES = {
     "cl_batch_destroy": (None, [_H]),
     "cl_batch_step": (_S, [_H, ctypes.c_longlong]),
     "cl_batch_solve": (_S, [_H, ctypes.c_longlong, _P, ctypes.POINTER(_I)]),
-    "cl_batch_autotune": (_S, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_double)]),
-    "cl_batch_configure": (_S, [_H, _I, _I]),
+    "cl_batch_autotune": (_S, [_H, _I, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "cl_batch_configure": (_S, [_H, _I, _I, _I]),
     "cl_batch_info": (_S, [_H, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "cl_batch_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
     "cl_lbm_set_wait_test": (_S, [_H, ctypes.c_longlong, _I]),
+    "cl_lbm_set_tile_rows": (_S, [_H, _I, ctypes.POINTER(_I)]),
     "cl_lbm_set_rate_scale": (_S, [_H, _P, _I]),
     "cl_lbm_set_source": (_S, [_H, _P, _I]),
     "cl_lbm_cell_reaction": (_S, [_H, _P, _I]),
@@ -341,6 +343,12 @@ def cl_lbm_solve_steady_lines(h: int, tol: float, max_iter: int, restart: int, c
     if st not in (CL_OK, CL_ERR_NOT_CONVERGED):
         _check(st, "cl_lbm_solve_steady_lines")
     return st, info
+
+
+def cl_lbm_set_tile_rows(h: int, rows: int) -> int:
+    out = ctypes.c_int(0)
+    _check(load().cl_lbm_set_tile_rows(h, rows, ctypes.byref(out)), "cl_lbm_set_tile_rows")
+    return out.value
 
 
 def cl_lbm_init(h: int, C0=None, n: int | None = None) -> None:
@@ -571,14 +579,14 @@ def cl_batch_solve(b: int, n: int, max_steps: int):
 
 
 def cl_batch_autotune(b: int, steps_per_trial: int = 20):
-    zc, pf, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-    _check(load().cl_batch_autotune(b, int(steps_per_trial), ctypes.byref(zc), ctypes.byref(pf), ctypes.byref(ms)),
-           "cl_batch_autotune")
-    return zc.value, pf.value, ms.value
+    zc, pf, tr, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(load().cl_batch_autotune(b, int(steps_per_trial), ctypes.byref(zc), ctypes.byref(pf), ctypes.byref(tr),
+                                    ctypes.byref(ms)), "cl_batch_autotune")
+    return zc.value, pf.value, tr.value, ms.value
 
 
-def cl_batch_configure(b: int, z_chunk: int, prefetch: int) -> None:
-    _check(load().cl_batch_configure(b, int(z_chunk), int(prefetch)), "cl_batch_configure")
+def cl_batch_configure(b: int, z_chunk: int, prefetch: int, tile_rows: int) -> None:
+    _check(load().cl_batch_configure(b, int(z_chunk), int(prefetch), int(tile_rows)), "cl_batch_configure")
 
 
 def cl_batch_info(b: int):

@@ -2,9 +2,9 @@
 
 ``Batch`` groups ``Solver`` objects (each with its structure loaded) and
 drives the batch entry points of the C ABI.  ``Batch.autotune`` times the
-work-item z length and L2 prefetch distance on the GPU and caches the result
-in a JSON file keyed by storage mode and the members' box sizes, so the next
-batch of the same shape skips the trials.
+tile shape, work-item z length and L2 prefetch distance on the GPU and caches
+the result in a JSON file keyed by storage mode and the members' box sizes,
+so the next batch of the same shape skips the trials.
 """
 from __future__ import annotations
 
@@ -37,8 +37,9 @@ class Batch:
         status, infos, nconv = L.cl_batch_solve(self.b, len(self.solvers), max_steps)
         return L.status_str(status), infos, nconv
 
-    def configure(self, z_chunk: int, prefetch: int):
-        L.cl_batch_configure(self.b, z_chunk, prefetch)
+    def configure(self, z_chunk: int, prefetch: int, tile_rows: int):
+        """tile_rows: 1, 2, 4 rows per warp for every member, 0: each member's own shape."""
+        L.cl_batch_configure(self.b, z_chunk, prefetch, tile_rows)
 
     def info(self):
         return L.cl_batch_info(self.b)
@@ -49,7 +50,7 @@ class Batch:
         return hashlib.sha256(json.dumps([storage, sizes]).encode()).hexdigest()[:16]
 
     def autotune(self, steps_per_trial: int = 20, cache: str | None = DEFAULT_CACHE):
-        """(z_chunk, prefetch, ms_per_step, from_cache)."""
+        """(z_chunk, prefetch, tile_rows, ms_per_step, from_cache)."""
         key = self.signature()
         table = {}
         if cache and os.path.exists(cache):
@@ -58,16 +59,16 @@ class Batch:
                     table = json.load(fh)
             except (OSError, ValueError):
                 table = {}
-        if key in table:
-            zc, pf, ms = table[key]
-            self.configure(zc, pf)
-            return zc, pf, ms, True
-        zc, pf, ms = L.cl_batch_autotune(self.b, steps_per_trial)
+        if key in table and len(table[key]) == 4:
+            zc, pf, tr, ms = table[key]
+            self.configure(zc, pf, tr)
+            return zc, pf, tr, ms, True
+        zc, pf, tr, ms = L.cl_batch_autotune(self.b, steps_per_trial)
         if cache:
-            table[key] = [zc, pf, ms]
+            table[key] = [zc, pf, tr, ms]
             os.makedirs(os.path.dirname(cache), exist_ok=True)
             tmp = cache + f".tmp{os.getpid()}"
             with open(tmp, "w") as fh:
                 json.dump(table, fh)
             os.replace(tmp, cache)
-        return zc, pf, ms, False
+        return zc, pf, tr, ms, False

@@ -215,40 +215,54 @@ cl_status make_map(CUtensorMap* m, CUtensorMapDataType dt, int el, void* ptr, in
     return CL_OK;
 }
 
-cl_status build_maps(cl_lbm* h) {
+// TMA descriptors of both time levels for tiles of rw rows per warp
+cl_status build_maps_rw(const cl_lbm* h, int rw, MarchMaps* maps) {
     const CUtensorMapDataType tT = h->el == 2 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const CUtensorMapDataType tF = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const int R = h->ny + 2, px = h->px, nz = h->nz, el = h->el;
     const int hxl = 16 / el;
+    const int bx = kBX / rw, by = kBY * rw;  // the tile of the march
     for (int b = 0; b < 2; ++b) {
-        MarchMaps& m = h->maps[b];
-        MState& s = h->st[b];
-        CKS(make_map(&m.chi, tF, 4, s.chi, px, R, nz, kBX, kBY + 2));
-        CKS(make_map(&m.clo, tT, el, s.clo, px, R, nz, kBX, kBY + 2));
-        CKS(make_map(&m.d3, tT, el, s.d[2], px, R, nz, kBX, kBY + 2));
-        CKS(make_map(&m.d4, tT, el, s.d[3], px, R, nz, kBX, kBY + 2));
-        CKS(make_map(&m.d1, tT, el, s.d[0], px, R, nz, kBX, kBY));
-        CKS(make_map(&m.d2, tT, el, s.d[1], px, R, nz, kBX, kBY));
-        CKS(make_map(&m.d5, tT, el, s.d[4], px, R, nz, kBX, kBY));
-        CKS(make_map(&m.d6, tT, el, s.d[5], px, R, nz, kBX, kBY));
-        CKS(make_map(&m.om, tF, 4, h->omega_p, px, R, nz, kBX, kBY));
-        CKS(make_map(&m.mk, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->mask_p, px, R, nz, kBX, kBY));
-        CKS(make_map(&m.chi_h, tF, 4, s.chi, px, R, nz, 4, kBY));
-        CKS(make_map(&m.clo_h, tT, el, s.clo, px, R, nz, hxl, kBY));
-        CKS(make_map(&m.d1_h, tT, el, s.d[0], px, R, nz, hxl, kBY));
-        CKS(make_map(&m.d2_h, tT, el, s.d[1], px, R, nz, hxl, kBY));
+        MarchMaps& m = maps[b];
+        const MState& s = h->st[b];
+        CKS(make_map(&m.chi, tF, 4, s.chi, px, R, nz, bx, by + 2));
+        CKS(make_map(&m.clo, tT, el, s.clo, px, R, nz, bx, by + 2));
+        CKS(make_map(&m.d3, tT, el, s.d[2], px, R, nz, bx, by + 2));
+        CKS(make_map(&m.d4, tT, el, s.d[3], px, R, nz, bx, by + 2));
+        CKS(make_map(&m.d1, tT, el, s.d[0], px, R, nz, bx, by));
+        CKS(make_map(&m.d2, tT, el, s.d[1], px, R, nz, bx, by));
+        CKS(make_map(&m.d5, tT, el, s.d[4], px, R, nz, bx, by));
+        CKS(make_map(&m.d6, tT, el, s.d[5], px, R, nz, bx, by));
+        CKS(make_map(&m.om, tF, 4, h->omega_p, px, R, nz, bx, by));
+        CKS(make_map(&m.mk, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, h->mask_p, px, R, nz, bx, by));
+        CKS(make_map(&m.chi_h, tF, 4, s.chi, px, R, nz, 4, by));
+        CKS(make_map(&m.clo_h, tT, el, s.clo, px, R, nz, hxl, by));
+        CKS(make_map(&m.d1_h, tT, el, s.d[0], px, R, nz, hxl, by));
+        CKS(make_map(&m.d2_h, tT, el, s.d[1], px, R, nz, hxl, by));
     }
     return CL_OK;
 }
 
+cl_status build_maps(cl_lbm* h) { return build_maps_rw(h, h->tile_rw, h->maps); }
+
+// Tiles of rw rows per warp over the box: (columns along x, rows along y).
+// Columns cover the nx cells (the pitch beyond nx holds only inactive cells).
+static void march_tiles(const cl_lbm* h, int rw, int& tx, int& ty) {
+    const int bx = kBX / rw, by = kBY * rw;
+    tx = (h->nx + bx - 1) / bx;
+    ty = (h->ny + by - 1) / by;
+}
+
 // Blocks per z-column chosen so that the grid fills whole waves of resident
 // blocks while keeping at least 8 planes per block.
-void choose_march_grid(cl_lbm* h) {
+static dim3 march_grid(cl_lbm* h, int rw, int* z_chunk) {
     int dev = 0, nsm = 152;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int resident = nsm * march_blocks_per_sm(h->p.storage);
-    const int tiles = ((h->px + kBX - 1) / kBX) * ((h->ny + kBY - 1) / kBY);
+    const int resident = nsm * march_blocks_per_sm(h->p.storage, rw);
+    int tx = 1, ty = 1;
+    march_tiles(h, rw, tx, ty);
+    const int tiles = tx * ty;
     int best_gz = 1;
     double best = 1e30;
     const int gz_max = h->nz < 8 ? 1 : h->nz / 8;
@@ -261,9 +275,12 @@ void choose_march_grid(cl_lbm* h) {
         const double cost = waves * (zc + 2.0);
         if (cost < best - 1e-9) { best = cost; best_gz = g; }
     }
-    h->z_chunk = (h->nz + best_gz - 1) / best_gz;
-    h->mgrid = dim3((h->px + kBX - 1) / kBX, (h->ny + kBY - 1) / kBY, (h->nz + h->z_chunk - 1) / h->z_chunk);
+    const int zc = (h->nz + best_gz - 1) / best_gz;
+    if (z_chunk) *z_chunk = zc;
+    return dim3(tx, ty, (h->nz + zc - 1) / zc);
 }
+
+void choose_march_grid(cl_lbm* h) { h->mgrid = march_grid(h, h->tile_rw, &h->z_chunk); }
 
 void drop_graphs(cl_lbm* h) {
     for (auto& g : h->graphs) {
@@ -278,7 +295,7 @@ cl_status enqueue_steps(cl_lbm* h, long long n, bool reduce, cudaStream_t s, int
         for (long long i = 0; i < n; ++i) {
             const bool red = reduce && i == n - 1;
             MarchArgs a = make_margs(h, *parity ^ 1);
-            CK(launch_march(h->p.storage, red, h->maps[*parity], a, h->mgrid, s));
+            CK(launch_march(h->p.storage, red, h->tile_rw, h->maps[*parity], a, h->mgrid, s));
             *parity ^= 1;
         }
     } else if (h->q19s) {
@@ -465,6 +482,10 @@ cl_status plane_readout(cl_lbm* h, double* tot /* [5] */) {
 
 }  // namespace
 
+namespace cl {
+cl_status build_march_maps(const cl_lbm* h, int rw, MarchMaps* maps) { return build_maps_rw(h, rw, maps); }
+}  // namespace cl
+
 extern "C" {
 
 void cl_params_default(cl_params* p) {
@@ -568,6 +589,7 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
     cudaError_t e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
 
+    int nblk_alloc = 0;
     if (h->march) {
         // row pitch: a multiple of 16 cells, so that every row starts on a
         // 32-byte sector of the f16 arrays and the lanes that store a sector
@@ -580,8 +602,14 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         h->prefetch = p->storage == CL_STORE_FP32 ? 2 : 0;
         if (const char* e = getenv("CL_LBM_PREFETCH")) h->prefetch = atoi(e);  // tuning override
         h->NP = (long long)h->px * (h->ny + 2) * h->nz;
+        h->tile_rw = march_auto_rows(h->nx, h->ny, h->p.storage);
         choose_march_grid(h);
         h->nblk_step = (int)(h->mgrid.x * h->mgrid.y * h->mgrid.z);
+        // reduction partials for the largest grid of any tile shape (cl_lbm_set_tile_rows)
+        for (int rw = 1; rw <= kRowsMax; rw *= 2) {
+            const dim3 g = march_grid(h, rw, nullptr);
+            nblk_alloc = std::max(nblk_alloc, (int)(g.x * g.y * g.z));
+        }
     } else if (h->q == 19) {
         // row pitch a multiple of 32 cells: every row starts on a 128-byte
         // line, and the 8 lanes of each 32-byte sector hold one row's cells
@@ -596,8 +624,9 @@ cl_status cl_lbm_create(cl_handle* out, const cl_params* p) {
         h->nblk_step = step_fp32_blocks(a);
     }
     h->nblk_stats = 152 * 4;
-    const long long npart = (long long)h->nblk_step * RED_N > (long long)h->nblk_stats * 8
-                                ? (long long)h->nblk_step * RED_N : (long long)h->nblk_stats * 8;
+    nblk_alloc = std::max(nblk_alloc, h->nblk_step);
+    const long long npart = (long long)nblk_alloc * RED_N > (long long)h->nblk_stats * 8
+                                ? (long long)nblk_alloc * RED_N : (long long)h->nblk_stats * 8;
     if ((st = dalloc_n(h, &h->phase, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->react, N)) != CL_OK) return fail(st);
     if ((st = dalloc_n(h, &h->active, N)) != CL_OK) return fail(st);
@@ -775,6 +804,23 @@ cl_status cl_lbm_set_wait_test(cl_handle h, long long wait_limit_clocks, int nev
     h->wait_limit = wait_limit_clocks;
     h->never_arrive = never_arrive ? 1 : 0;
     drop_graphs(h);  // the wait settings are baked into captured kernel arguments
+    return CL_OK;
+}
+
+cl_status cl_lbm_set_tile_rows(cl_handle h, int rows, int* rows_out) {
+    if (!h) { set_msg_txt("NULL handle"); return CL_ERR_ARG; }
+    if (!h->march) { set_msg_txt("tile shapes apply to the (C, delta) storage modes"); return CL_ERR_STATE; }
+    if (rows != 0 && rows != 1 && rows != 2 && rows != 4) { set_msg_txt("rows must be 0, 1, 2 or 4"); return CL_ERR_ARG; }
+    const int rw = rows ? rows : march_auto_rows(h->nx, h->ny, h->p.storage);
+    if (rw != h->tile_rw) {
+        // queued launches carry their own copies of the descriptors and grid
+        h->tile_rw = rw;
+        CKS(build_maps(h));
+        choose_march_grid(h);
+        h->nblk_step = (int)(h->mgrid.x * h->mgrid.y * h->mgrid.z);
+        drop_graphs(h);
+    }
+    if (rows_out) *rows_out = h->tile_rw;
     return CL_OK;
 }
 

@@ -3,8 +3,9 @@
 // A batch groups existing solver handles (each with its structure loaded).
 // One cooperative launch of k_march_batch advances every structure that is
 // still running by K steps: the blocks (up to three per SM, all resident) take
-// (step, item) pairs from one queue, an item being a (structure, 64x8 tile
-// column, z range); an item of step t waits only until its own structure's
+// (step, item) pairs from one queue, an item being a (structure, 512-cell
+// tile column -- 64 x 8, 32 x 16 or 16 x 32, the member's shape -- z range);
+// an item of step t waits only until its own structure's
 // step t - 1 is done (a bounded wait on a per-structure count), so structures
 // pipeline across steps with no grid-wide barrier.  The last step of a launch also
 // reduces each structure's fluxes; the host applies each structure's stopping
@@ -48,6 +49,9 @@ struct cl_batch {
     double* d_inst_red = nullptr;
     double* h_inst_red = nullptr;  // pinned [n][RED_N]
     std::vector<char> active;
+    std::vector<int> own_rw;  // each member's handle's tile shape at creation
+    std::vector<int> rw;      // tile rows per warp in use for each member
+    int tile_rows = 0;        // 1, 2, 4: one shape for every member; 0: the members' own
     cudaGraphExec_t graph = nullptr;
     bool graph_ok = true;
     long long wait_limit = 0;  // step-dependency wait bound (0: default)
@@ -56,8 +60,28 @@ struct cl_batch {
 
 namespace {
 
-int items_of(const cl_lbm* h, int zc) {
-    return ((h->px + kBX - 1) / kBX) * ((h->ny + kBY - 1) / kBY) * ((h->nz + zc - 1) / zc);
+int items_of(const cl_lbm* h, int rw, int zc) {
+    const int bx = kBX / rw, by = kBY * rw;
+    return ((h->nx + bx - 1) / bx) * ((h->ny + by - 1) / by) * ((h->nz + zc - 1) / zc);
+}
+
+// One tile shape for every member unless the policy is 0 (the members' own
+// shapes): blocks that march different shapes at once on one SM run three
+// copies of the march code, which measured slower than any single shape.
+void apply_tile_policy(cl_batch* b) {
+    for (int i = 0; i < b->n; ++i) b->rw[i] = b->tile_rows ? b->tile_rows : b->own_rw[i];
+}
+
+// the uniform shape of least summed cost over the members
+int batch_auto_rows(const cl_batch* b) {
+    int best = 1;
+    double best_cost = 0.0;
+    for (int rw = 1; rw <= kRowsMax; rw *= 2) {
+        double c = 0.0;
+        for (const cl_lbm* h : b->m) c += march_tile_cost(h->nx, h->ny, b->storage, rw) * h->nz;
+        if (rw == 1 || c < best_cost * (1.0 - 1e-9)) { best = rw; best_cost = c; }
+    }
+    return best;
 }
 
 // Work list over the running structures: each column's planes split into
@@ -70,11 +94,12 @@ cl_status upload_items(cl_batch* b) {
         first[i] = (int)items.size();
         if (!b->active[i]) continue;
         const cl_lbm* h = b->m[i];
+        const int rw = b->rw[i], bx = kBX / rw, by = kBY * rw;
         const int g = (h->nz + b->z_chunk - 1) / b->z_chunk;
         for (int j = 0; j < g; ++j) {
             const int zs = (int)((long long)h->nz * j / g), ze = (int)((long long)h->nz * (j + 1) / g);
-            for (int y0 = 0; y0 < h->ny; y0 += kBY)
-                for (int x0 = 0; x0 < h->px; x0 += kBX) items.push_back(WorkItem{i, x0, y0, zs, ze});
+            for (int y0 = 0; y0 < h->ny; y0 += by)
+                for (int x0 = 0; x0 < h->nx; x0 += bx) items.push_back(WorkItem{i, x0, y0, zs, ze, rw});
         }
         count[i] = (int)items.size() - first[i];
     }
@@ -92,8 +117,8 @@ cl_status upload_insts(cl_batch* b) {
     std::vector<BatchInst> insts(b->n);
     for (int i = 0; i < b->n; ++i) {
         cl_lbm* h = b->m[i];
+        CKS(build_march_maps(h, b->rw[i], insts[i].maps));
         for (int par = 0; par < 2; ++par) {
-            insts[i].maps[par] = h->maps[par];
             insts[i].args[par] = make_margs(h, par ^ 1);
             insts[i].args[par].prefetch = b->prefetch;
         }
@@ -209,6 +234,10 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
     b->z_chunk = z_chunk > 0 ? z_chunk : 32;
     b->prefetch = h0->prefetch;
     b->active.assign(n, 1);
+    for (int i = 0; i < n; ++i) b->own_rw.push_back(members[i]->tile_rw);
+    b->rw = b->own_rw;
+    b->tile_rows = batch_auto_rows(b);
+    apply_tile_policy(b);
     auto fail = [&](cl_status st) { cl_batch_destroy(b); return st; };
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) { set_msg("cudaStreamCreate", e); return fail(from_cuda(e)); }
@@ -220,8 +249,12 @@ cl_status cl_batch_create(cl_batch_handle* out, const cl_handle* members, int n,
     if (per_sm < 1 || per_sm_r < 1) { set_msg_txt("batched step kernel does not fit on an SM"); return fail(CL_ERR_CUDA); }
     b->grid = nsm * per_sm;
     b->grid_reduce = nsm * per_sm_r;
-    // the work list is largest at the smallest z chunk the autotuner tries
-    for (int i = 0; i < n; ++i) b->max_items += items_of(b->m[i], std::min(8, b->z_chunk));
+    // the work list is largest at the smallest z chunk the autotuner tries, in the member's largest tiling
+    for (int i = 0; i < n; ++i) {
+        int most = 0;
+        for (int rw = 1; rw <= kRowsMax; rw *= 2) most = std::max(most, items_of(b->m[i], rw, std::min(8, b->z_chunk)));
+        b->max_items += most;
+    }
     e = cudaMallocAsync(&b->d_insts, sizeof(BatchInst) * n, b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_items, sizeof(WorkItem) * b->max_items, b->s);
     if (e == cudaSuccess) e = cudaMallocAsync(&b->d_n_items, sizeof(int), b->s);
@@ -350,7 +383,7 @@ cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* 
 }
 
 cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk_out, int* prefetch_out,
-                            double* best_ms_out) {
+                            int* tile_rows_out, double* best_ms_out) {
     if (!b || steps_per_trial < 2 || (steps_per_trial & 1)) { set_msg_txt("steps_per_trial must be even, >= 2"); return CL_ERR_ARG; }
     for (auto* h : b->m)
         if (h->cur != b->parity) { set_msg_txt("a member was stepped outside the batch"); return CL_ERR_STATE; }
@@ -358,47 +391,61 @@ cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk
     for (auto* h : b->m) nz_max = std::max(nz_max, h->nz);
     const int zcs[] = {8, 16, 32, 64};
     const int pfs[] = {0, 2};
+    const int tiles[] = {1, 2, 4};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = INFINITY;
-    int bz = b->z_chunk, bp = b->prefetch;
+    int bz = b->z_chunk, bp = b->prefetch, bt = b->tile_rows;
     std::fill(b->active.begin(), b->active.end(), 1);
-    for (int zc : zcs) {
-        if (zc > std::max(8, nz_max)) continue;
-        for (int pf : pfs) {
-            b->z_chunk = zc;
-            b->prefetch = pf;
-            CKS(upload_insts(b));
-            CKS(upload_items(b));
-            CK(cudaEventRecord(e0, b->s));
-            CK(launch_march_batch(launch_desc(b, steps_per_trial, false), b->s));
-            CK(cudaEventRecord(e1, b->s));
-            CK(cudaEventSynchronize(e1));
-            CKS(batch_err(b));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            for (auto* h : b->m) h->step += steps_per_trial;  // the trials are real steps
-            if (ms < best) { best = ms; bz = zc; bp = pf; }
+    for (int tr : tiles) {
+        b->tile_rows = tr;
+        apply_tile_policy(b);
+        for (int zc : zcs) {
+            if (zc > std::max(8, nz_max)) continue;
+            for (int pf : pfs) {
+                b->z_chunk = zc;
+                b->prefetch = pf;
+                CKS(upload_insts(b));
+                CKS(upload_items(b));
+                CK(cudaEventRecord(e0, b->s));
+                CK(launch_march_batch(launch_desc(b, steps_per_trial, false), b->s));
+                CK(cudaEventRecord(e1, b->s));
+                CK(cudaEventSynchronize(e1));
+                CKS(batch_err(b));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                for (auto* h : b->m) h->step += steps_per_trial;  // the trials are real steps
+                if (ms < best) { best = ms; bz = zc; bp = pf; bt = tr; }
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->z_chunk = bz;
     b->prefetch = bp;
+    b->tile_rows = bt;
+    apply_tile_policy(b);
     drop_graph(b);
     CKS(upload_insts(b));
     CKS(upload_items(b));
     if (z_chunk_out) *z_chunk_out = bz;
     if (prefetch_out) *prefetch_out = bp;
+    if (tile_rows_out) *tile_rows_out = bt;
     if (best_ms_out) *best_ms_out = best / steps_per_trial;
     return CL_OK;
 }
 
-cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch) {
+cl_status cl_batch_configure(cl_batch_handle b, int z_chunk, int prefetch, int tile_rows) {
     if (!b || z_chunk < 8 || prefetch < 0) { set_msg_txt("z_chunk >= 8 and prefetch >= 0 required"); return CL_ERR_ARG; }
+    if (tile_rows != 0 && tile_rows != 1 && tile_rows != 2 && tile_rows != 4) {
+        set_msg_txt("tile_rows must be 0, 1, 2 or 4");
+        return CL_ERR_ARG;
+    }
     b->z_chunk = z_chunk;
     b->prefetch = prefetch;
+    b->tile_rows = tile_rows;
+    apply_tile_policy(b);
     drop_graph(b);
     CKS(upload_insts(b));
     return upload_items(b);

@@ -79,6 +79,7 @@ struct cl_lbm {
     cl::MarchMaps maps[2];
     dim3 mgrid;
     int z_chunk = 0;
+    int tile_rw = 1;  // tile rows per consumer warp of the plane march (1, 2, 4)
     int prefetch = cl::kPrefetchDefault;
     float s_lo = 1.f, s_d = 1.f;
     double* kscale = nullptr;  // per-cell factor on k (cl_lbm_set_rate_scale), NULL: uniform
@@ -114,6 +115,8 @@ float reactive_factor(const cl_lbm* h);
 double reactive_factor_d(const cl_lbm* h);
 double reactive_sink_d(const cl_lbm* h);
 MarchArgs make_margs(cl_lbm* h, int dst);
+// TMA descriptors of both time levels of the (C, delta) state for tiles of rw rows per warp
+cl_status build_march_maps(const cl_lbm* h, int rw, MarchMaps* maps);
 cl_status check_err_flag(cl_lbm* h);
 
 }  // namespace cl

@@ -18,7 +18,10 @@
 // double-float so that increments far below ulp(C) are not lost.
 //
 // Each thread block owns a BX x BY column of cells and marches along z
-// through a chunk of planes.  Planes are staged into shared memory by TMA
+// through a chunk of planes.  A tile always holds 512 cells, as RW rows of
+// 64 / RW cells per consumer warp (RW = 1, 2 or 4: tiles of 64 x 8, 32 x 16 or
+// 16 x 32): narrow tiles fit boxes whose rows are not a multiple of 64 cells
+// without idle lanes.  Planes are staged into shared memory by TMA
 // (cp.async.bulk.tensor.3d) into a ring of S slots guarded by mbarriers;
 // the producer thread keeps S - 2 planes in flight.  Arrays carry two ghost
 // rows (copies of rows ny-1 and 0 above and below) so the y-halo of a tile
@@ -128,41 +131,82 @@ __device__ __forceinline__ void df_add(float hi, float lo, float d, float& ho, f
 }
 
 // ------------------------------------------------------- shared layout
-template <class S>
+template <class S, int RW>
 struct SlotLayout {
     using T = typename S::T;
+    static constexpr int BX = kBX / RW;  // tile width (cells)
+    static constexpr int BY = kBY * RW;  // tile height (rows)
     static constexpr int EL = sizeof(T);
     static constexpr int HXL = 16 / EL;  // width of a 16-byte x-halo box in elements of T
     static constexpr int HXF = 4;        // same for f32 arrays
-    static constexpr int R2 = kBY + 2;
+    static constexpr int R2 = BY + 2;
     static constexpr int al(int b) { return (b + 127) & ~127; }
     static constexpr int o_chi = 0;
-    static constexpr int o_clo = o_chi + al(R2 * kBX * 4);
-    static constexpr int o_d3 = o_clo + al(R2 * kBX * EL);
-    static constexpr int o_d4 = o_d3 + al(R2 * kBX * EL);
-    static constexpr int o_d1 = o_d4 + al(R2 * kBX * EL);
-    static constexpr int o_d2 = o_d1 + al(kBY * kBX * EL);
-    static constexpr int o_d5 = o_d2 + al(kBY * kBX * EL);
-    static constexpr int o_d6 = o_d5 + al(kBY * kBX * EL);
-    static constexpr int o_om = o_d6 + al(kBY * kBX * EL);
-    static constexpr int o_mk = o_om + al(kBY * kBX * 4);
-    static constexpr int o_chiL = o_mk + al(kBY * kBX * 2);
-    static constexpr int o_chiR = o_chiL + al(kBY * HXF * 4);
-    static constexpr int o_cloL = o_chiR + al(kBY * HXF * 4);
-    static constexpr int o_cloR = o_cloL + al(kBY * HXL * EL);
-    static constexpr int o_d1L = o_cloR + al(kBY * HXL * EL);
-    static constexpr int o_d2R = o_d1L + al(kBY * HXL * EL);
-    static constexpr int bytes = o_d2R + al(kBY * HXL * EL);
+    static constexpr int o_clo = o_chi + al(R2 * BX * 4);
+    static constexpr int o_d3 = o_clo + al(R2 * BX * EL);
+    static constexpr int o_d4 = o_d3 + al(R2 * BX * EL);
+    static constexpr int o_d1 = o_d4 + al(R2 * BX * EL);
+    static constexpr int o_d2 = o_d1 + al(BY * BX * EL);
+    static constexpr int o_d5 = o_d2 + al(BY * BX * EL);
+    static constexpr int o_d6 = o_d5 + al(BY * BX * EL);
+    static constexpr int o_om = o_d6 + al(BY * BX * EL);
+    static constexpr int o_mk = o_om + al(BY * BX * 4);
+    static constexpr int o_chiL = o_mk + al(BY * BX * 2);
+    static constexpr int o_chiR = o_chiL + al(BY * HXF * 4);
+    static constexpr int o_cloL = o_chiR + al(BY * HXF * 4);
+    static constexpr int o_cloR = o_cloL + al(BY * HXL * EL);
+    static constexpr int o_d1L = o_cloR + al(BY * HXL * EL);
+    static constexpr int o_d2R = o_d1L + al(BY * HXL * EL);
+    static constexpr int bytes = o_d2R + al(BY * HXL * EL);
     // bytes delivered by the TMA loads of one plane (full boxes)
-    static constexpr uint32_t tx = R2 * kBX * 4 + 3 * R2 * kBX * EL + 4 * kBY * kBX * EL + kBY * kBX * 4 +
-                                   kBY * kBX * 2 + 2 * kBY * HXF * 4 + 4 * kBY * HXL * EL;
+    static constexpr uint32_t tx = R2 * BX * 4 + 3 * R2 * BX * EL + 4 * BY * BX * EL + BY * BX * 4 +
+                                   BY * BX * 2 + 2 * BY * HXF * 4 + 4 * BY * HXL * EL;
 };
 
-int march_slot_bytes(int storage) {
-    return storage == CL_STORE_FP16DEV ? SlotLayout<StoreF16>::bytes : SlotLayout<StoreF32>::bytes;
+template <class S>
+static int slot_bytes_rw(int rw) {
+    return rw == 4 ? SlotLayout<S, 4>::bytes : (rw == 2 ? SlotLayout<S, 2>::bytes : SlotLayout<S, 1>::bytes);
 }
 
-int march_smem_bytes(int storage) { return 128 + kStages * march_slot_bytes(storage); }
+int march_slot_bytes(int storage, int rw) {
+    return storage == CL_STORE_FP16DEV ? slot_bytes_rw<StoreF16>(rw) : slot_bytes_rw<StoreF32>(rw);
+}
+
+int march_smem_bytes(int storage, int rw) { return 128 + kStages * march_slot_bytes(storage, rw); }
+
+// the batched kernel marches tiles of every shape
+static int batch_smem_bytes(int storage) {
+    int m = 0;
+    for (int rw = 1; rw <= kRowsMax; rw *= 2) m = m > march_smem_bytes(storage, rw) ? m : march_smem_bytes(storage, rw);
+    return m;
+}
+
+// Relative cost of a tile shape for a box: the tile slots it steps (the idle
+// lanes of a row's last tile count in full; rows past ny count half, their
+// warps issue no arithmetic but their planes are still loaded), times the
+// per-cell cost of the shape on full tiles.  Per-cell costs measured on one
+// GB300 for the 256^3 Pt box (plain steps, all tiles full): FP16 state 1 :
+// 1 : 1.027 (1 and 2 rows within 0.5 %) and FP32 state 1 : 1.027 : 1.155
+// for 1, 2, 4 rows per warp (narrow tiles issue more TMA rows and x-halo
+// boxes per cell).
+double march_tile_cost(int nx, int ny, int storage, int rw) {
+    static const double f16[3] = {1.0, 1.0, 1.027}, f32[3] = {1.0, 1.027, 1.155};
+    const int bx = kBX / rw, by = kBY * rw;
+    const double xs = (double)((nx + bx - 1) / bx) * bx;
+    const double ys = (double)((ny + by - 1) / by) * by;
+    const int k = rw == 4 ? 2 : rw - 1;
+    return xs * (ny + 0.5 * (ys - ny)) * (storage == CL_STORE_FP16DEV ? f16[k] : f32[k]);
+}
+
+int march_auto_rows(int nx, int ny, int storage) {
+    int best = 1;
+    double best_cost = 0.0;
+    for (int rw = 1; rw <= kRowsMax; rw *= 2) {
+        const double c = march_tile_cost(nx, ny, storage, rw);
+        if (rw == 1 || c < best_cost * (1.0 - 1e-9)) { best = rw; best_cost = c; }  // ties to the wider tile
+    }
+    return best;
+}
 
 // ------------------------------------------------------------- the kernel
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -266,23 +310,26 @@ struct Pair<StoreF16> {
     }
 };
 
-// Warp roles: warps 0..kBY-1 each own one row of the tile (two cells per
-// lane) and compute; warp kBY is the producer and issues the TMA loads of
-// one plane per slot.  full[s] completes when a plane has landed in slot s,
-// empty[s] when every consumer warp has released it.  A consumer keeps the
-// z-1 values it needs (its own cells one plane below) in registers, so a
-// slot is live only while its plane is the current or the next one.
-// One work item: the kBX x kBY column at (x0, y0), planes [zs, ze).  Planes
+// Warp roles: warps 0..kBY-1 each own RW rows of the tile (32 / RW lanes
+// per row, two cells per lane) and compute; warp kBY is the producer and
+// issues the TMA loads of one plane per slot.  full[s] completes when a plane
+// has landed in slot s, empty[s] when every consumer warp has released it.  A
+// consumer keeps the z-1 values it needs (its own cells one plane below) in
+// registers, so a slot is live only while its plane is the current or the
+// next one.
+// One work item: the BX x BY column at (x0, y0), planes [zs, ze).  Planes
 // zs-1 .. ze stream through the ring; `seq` is the block's running plane
 // count before this item (it fixes each plane's slot and mbarrier phase, so
 // items can follow each other in one block).  Every plane is released after
 // use, including the last one.  Returns false if a bounded wait expired.
-template <class S, bool REDUCE>
+template <class S, bool REDUCE, int RW>
 __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArgs& a, int x0, int y0, int zs,
                                            int ze, unsigned char* slots, uint64_t* full, uint64_t* empty,
                                            unsigned seq, bool fence_maps, double (&rv)[RED_N]) {
     using T = typename S::T;
-    using L = SlotLayout<S>;
+    using L = SlotLayout<S, RW>;
+    constexpr int BX = L::BX;
+    constexpr int LPR = BX / 2;  // lanes per tile row (two cells each)
     using P = Pair<S>;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int nx = a.nx, ny = a.ny, nz = a.nz, px = a.px;
@@ -322,11 +369,11 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
                 tma_load_3d(sl + L::o_om, &maps->om, bar, x0, y0 + 1, z);
                 tma_load_3d(sl + L::o_mk, &maps->mk, bar, x0, y0 + 1, z);
                 tma_load_3d(sl + L::o_chiL, &maps->chi_h, bar, x0 - L::HXF, y0 + 1, z);
-                tma_load_3d(sl + L::o_chiR, &maps->chi_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_chiR, &maps->chi_h, bar, x0 + BX, y0 + 1, z);
                 tma_load_3d(sl + L::o_cloL, &maps->clo_h, bar, x0 - L::HXL, y0 + 1, z);
-                tma_load_3d(sl + L::o_cloR, &maps->clo_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_cloR, &maps->clo_h, bar, x0 + BX, y0 + 1, z);
                 tma_load_3d(sl + L::o_d1L, &maps->d1_h, bar, x0 - L::HXL, y0 + 1, z);
-                tma_load_3d(sl + L::o_d2R, &maps->d2_h, bar, x0 + kBX, y0 + 1, z);
+                tma_load_3d(sl + L::o_d2R, &maps->d2_h, bar, x0 + BX, y0 + 1, z);
                 if (a.prefetch > 0 && k + a.prefetch < nplanes) {
                     int zp = zs - 1 + k + a.prefetch;
                     zp = zp >= nz ? zp - nz : zp;
@@ -353,11 +400,13 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
     }
     // ---------------------------------------------------------- consumers
     float rs[4] = {0.f, 0.f, 0.f, 0.f};  // FP32 partials of sum C, sum |dC|, sum |C|, non-finite
-    const int xa = x0 + 2 * tx;  // this lane's cells: xa, xa + 1
-    const int y = y0 + ty;
+    const int xl = tx & (LPR - 1);        // lane within its tile row
+    const int row = ty * RW + tx / LPR;   // tile row of this lane
+    const int xa = x0 + 2 * xl;  // this lane's cells: xa, xa + 1
+    const int y = y0 + row;
     const bool row_ok = y < ny;
-    const int c_own = (ty + 1) * kBX + 2 * tx;  // element index, ghosted arrays
-    const int c_pl = ty * kBX + 2 * tx;         // element index, plain arrays
+    const int c_own = (row + 1) * BX + 2 * xl;  // element index, ghosted arrays
+    const int c_pl = row * BX + 2 * xl;         // element index, plain arrays
     // values stay in storage units; cell_update applies the scales
     const float inv_lo = 1.0f, inv_d = 1.0f, s_lo = 1.0f, s_d = 1.0f;
     constexpr int EL = L::EL;
@@ -374,13 +423,13 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
         if (tx == 0) mbar_arrive(&empty[(seq + k) % kStages]);
     };
     // x-halo neighbours: left of xa, right of xa + 1
-    const bool lane_l = tx == 0, lane_r = tx == 31;
-    const int xl_f = lane_l ? L::o_chiL + 4 * (ty * L::HXF + L::HXF - 1) : L::o_chi + 4 * (c_own - 1);
-    const int xr_f = lane_r ? L::o_chiR + 4 * (ty * L::HXF) : L::o_chi + 4 * (c_own + 2);
-    const int xl_lo = lane_l ? L::o_cloL + EL * (ty * L::HXL + L::HXL - 1) : L::o_clo + EL * (c_own - 1);
-    const int xr_lo = lane_r ? L::o_cloR + EL * (ty * L::HXL) : L::o_clo + EL * (c_own + 2);
-    const int xl_d1 = lane_l ? L::o_d1L + EL * (ty * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
-    const int xr_d2 = lane_r ? L::o_d2R + EL * (ty * L::HXL) : L::o_d2 + EL * (c_pl + 2);
+    const bool lane_l = xl == 0, lane_r = xl == LPR - 1;
+    const int xl_f = lane_l ? L::o_chiL + 4 * (row * L::HXF + L::HXF - 1) : L::o_chi + 4 * (c_own - 1);
+    const int xr_f = lane_r ? L::o_chiR + 4 * (row * L::HXF) : L::o_chi + 4 * (c_own + 2);
+    const int xl_lo = lane_l ? L::o_cloL + EL * (row * L::HXL + L::HXL - 1) : L::o_clo + EL * (c_own - 1);
+    const int xr_lo = lane_r ? L::o_cloR + EL * (row * L::HXL) : L::o_clo + EL * (c_own + 2);
+    const int xl_d1 = lane_l ? L::o_d1L + EL * (row * L::HXL + L::HXL - 1) : L::o_d1 + EL * (c_pl - 1);
+    const int xr_d2 = lane_r ? L::o_d2R + EL * (row * L::HXL) : L::o_d2 + EL * (c_pl + 2);
 
     // every lane of a warp leaves the plane loop together (warp votes below)
     ok = __all_sync(0xffffffffu, wait(0));  // plane zs-1
@@ -404,8 +453,9 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
         // in its sector is active, so that no sector is written in part --
         // a partial sector costs a DRAM read to fill it -- and sectors of
         // inactive cells only are not written at all.  Rows start on
-        // 16-cell boundaries (px is a multiple of 16), so 4 lanes cover an
-        // f32 sector and 8 lanes an f16 sector.
+        // 16-cell boundaries (px and every tile width are multiples of 16),
+        // so 4 lanes of one tile row cover an f32 sector and 8 lanes an f16
+        // sector.
         const bool pact = ((ma | mb) & kActiveBit) != 0;
         const unsigned vote = __ballot_sync(0xffffffffu, pact);
         const bool st_f32 = ((vote >> (tx & ~3)) & 0xFu) != 0;
@@ -428,12 +478,12 @@ __device__ __forceinline__ bool march_item(const MarchMaps* maps, const MarchArg
             dp[5] = P::ld(sc + L::o_d6 + EL * c_pl, inv_d);
             const float2 om = *reinterpret_cast<const float2*>(sc + L::o_om + 4 * c_pl);
             // y and z neighbours of both cells
-            const float2 hym = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own - kBX));
-            const float2 lym = P::ld(sc + L::o_clo + EL * (c_own - kBX), inv_lo);
-            const float2 dym = P::ld(sc + L::o_d3 + EL * (c_own - kBX), inv_d);
-            const float2 hyp = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own + kBX));
-            const float2 lyp = P::ld(sc + L::o_clo + EL * (c_own + kBX), inv_lo);
-            const float2 dyp = P::ld(sc + L::o_d4 + EL * (c_own + kBX), inv_d);
+            const float2 hym = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own - BX));
+            const float2 lym = P::ld(sc + L::o_clo + EL * (c_own - BX), inv_lo);
+            const float2 dym = P::ld(sc + L::o_d3 + EL * (c_own - BX), inv_d);
+            const float2 hyp = *reinterpret_cast<const float2*>(sc + L::o_chi + 4 * (c_own + BX));
+            const float2 lyp = P::ld(sc + L::o_clo + EL * (c_own + BX), inv_lo);
+            const float2 dyp = P::ld(sc + L::o_d4 + EL * (c_own + BX), inv_d);
             const float2 hzp = *reinterpret_cast<const float2*>(sp + L::o_chi + 4 * c_own);
             const float2 lzp = P::ld(sp + L::o_clo + EL * c_own, inv_lo);
             const float2 dzp = P::ld(sp + L::o_d6 + EL * c_pl, inv_d);
@@ -539,17 +589,11 @@ __device__ __forceinline__ void init_ring(uint64_t* full, uint64_t* empty) {
     __syncthreads();
 }
 
-// Warp roles: warps 0..kBY-1 each own one row of the tile (two cells per
-// lane) and compute; warp kBY is the producer and issues the TMA loads of
-// one plane per slot.  full[s] completes when a plane has landed in slot s,
-// empty[s] when every consumer warp has released it.  A consumer keeps the
-// z-1 values it needs (its own cells one plane below) in registers, so a
-// slot is live only while its plane is the current or the next one.
 // FP16 plain steps: 72 registers, which still fits three resident blocks per
 // SM (3 x 288 x 72 <= 65536) without the recomputation a tighter bound
 // forces; FP32 plain steps need fewer than 112; the reducing steps (one per
 // check) are capped at 112 so that two blocks fit per SM.
-template <class S, bool REDUCE>
+template <class S, bool REDUCE, int RW>
 __global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) == 2 && !REDUCE) ? 72 : 112)
     k_march(const __grid_constant__ MarchMaps maps, const MarchArgs a) {
     // Addressed directly (no integer round trip) so that every slot access
@@ -565,7 +609,8 @@ __global__ void __launch_bounds__(kThreads) __maxnreg__((sizeof(typename S::T) =
     init_ring(full, empty);
     const int zs = blockIdx.z * a.z_chunk;
     const int ze = min(a.nz, zs + a.z_chunk);
-    march_item<S, REDUCE>(&maps, a, blockIdx.x * kBX, blockIdx.y * kBY, zs, ze, slots, full, empty, 0u, false, rv);
+    march_item<S, REDUCE, RW>(&maps, a, blockIdx.x * (kBX / RW), blockIdx.y * (kBY * RW), zs, ze, slots, full, empty,
+                              0u, false, rv);
     if (REDUCE) {
         const long long blk = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         block_sum_store<RED_N>(rv, a.partials + blk * RED_N);
@@ -607,10 +652,10 @@ __device__ bool wait_done(const unsigned long long* done, unsigned long long tar
 
 constexpr int kFenceBits = 2048;  // (member, parity) pairs whose descriptors a block has fenced
 
-// FP16 plain steps fit three resident blocks per SM; the others keep the
-// registers they need
+// Plain steps fit three (FP16) or two (FP32) resident blocks per SM; the
+// reducing step keeps the registers it needs
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDUCE) ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, REDUCE ? 1 : (sizeof(typename S::T) == 2 ? 3 : 2))
     k_march_batch(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items,
                   const int* __restrict__ n_items_ptr, const int* __restrict__ inst_count, int nsteps, int parity0,
                   unsigned long long* next, unsigned long long* done, int* abort_flag, double* item_partials,
@@ -675,15 +720,16 @@ __global__ void __launch_bounds__(kThreads, (sizeof(typename S::T) == 2 && !REDU
         double rv[RED_N];
 #pragma unroll
         for (int k = 0; k < RED_N; ++k) rv[k] = 0.0;
+        const MarchMaps* mp = &insts[it.inst].maps[par];
+        const bool fm = s_fence != 0;
         bool ok;
-        if (REDUCE) {
-            ok = march_item<S, true>(&insts[it.inst].maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full, empty,
-                                     seq, s_fence != 0, rv);
-            block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
-        } else {
-            ok = march_item<S, false>(&insts[it.inst].maps[par], a, it.x0, it.y0, it.zs, it.ze, slots, full,
-                                      empty, seq, s_fence != 0, rv);
-        }
+        if (it.rw == 4)
+            ok = march_item<S, REDUCE, 4>(mp, a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq, fm, rv);
+        else if (it.rw == 2)
+            ok = march_item<S, REDUCE, 2>(mp, a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq, fm, rv);
+        else
+            ok = march_item<S, REDUCE, 1>(mp, a, it.x0, it.y0, it.zs, it.ze, slots, full, empty, seq, fm, rv);
+        if (REDUCE) block_sum_store<RED_N>(rv, item_partials + (long long)w * RED_N);
         seq += (unsigned)(it.ze - it.zs + 2);
         ok = __syncthreads_and(ok);
         if (!ok) {
@@ -715,34 +761,46 @@ __global__ void k_batch_finalize(const double* __restrict__ item_partials, const
 }
 
 // ----------------------------------------------------------- host launch
-template <class S, bool R>
+template <class S, bool R, int RW>
 static cudaError_t launch_one(const MarchMaps& maps, const MarchArgs& a, dim3 grid, int smem, cudaStream_t s) {
     static bool attr_set = false;  // per template instance
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_march<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(k_march<S, R, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_march<S, R>, cudaFuncAttributePreferredSharedMemoryCarveout,
+            e = cudaFuncSetAttribute(k_march<S, R, RW>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                      cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    k_march<S, R><<<grid, dim3(32, kBY + 1, 1), smem, s>>>(maps, a);
+    k_march<S, R, RW><<<grid, dim3(32, kBY + 1, 1), smem, s>>>(maps, a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
+template <class S, int RW>
+static cudaError_t launch_rw(bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid, int smem,
+                             cudaStream_t s) {
+    return reduce ? launch_one<S, true, RW>(maps, a, grid, smem, s) : launch_one<S, false, RW>(maps, a, grid, smem, s);
+}
+
+template <class S>
+static cudaError_t launch_s(int rw, bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid, int smem,
+                            cudaStream_t s) {
+    if (rw == 4) return launch_rw<S, 4>(reduce, maps, a, grid, smem, s);
+    if (rw == 2) return launch_rw<S, 2>(reduce, maps, a, grid, smem, s);
+    return launch_rw<S, 1>(reduce, maps, a, grid, smem, s);
+}
+
+cudaError_t launch_march(int storage, bool reduce, int rw, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
                          cudaStream_t s) {
-    const int smem = march_smem_bytes(storage);
-    if (storage == CL_STORE_FP16DEV)
-        return reduce ? launch_one<StoreF16, true>(maps, a, grid, smem, s)
-                      : launch_one<StoreF16, false>(maps, a, grid, smem, s);
-    return reduce ? launch_one<StoreF32, true>(maps, a, grid, smem, s)
-                  : launch_one<StoreF32, false>(maps, a, grid, smem, s);
+    if (rw != 1 && rw != 2 && rw != 4) return cudaErrorInvalidValue;
+    const int smem = march_smem_bytes(storage, rw);
+    if (storage == CL_STORE_FP16DEV) return launch_s<StoreF16>(rw, reduce, maps, a, grid, smem, s);
+    return launch_s<StoreF32>(rw, reduce, maps, a, grid, smem, s);
 }
 
 template <class S, bool R>
 static cudaError_t launch_batch_t(const BatchLaunch& b, int grid, cudaStream_t s) {
-    const int smem = march_smem_bytes(b.storage);
+    const int smem = batch_smem_bytes(b.storage);
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_march_batch<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -817,27 +875,32 @@ static int batch_occupancy(int smem) {
 }
 
 int march_batch_blocks_per_sm(int storage, bool reduce) {
-    const int smem = march_smem_bytes(storage);
+    const int smem = batch_smem_bytes(storage);
     if (storage == CL_STORE_FP16DEV)
         return reduce ? batch_occupancy<StoreF16, true>(smem) : batch_occupancy<StoreF16, false>(smem);
     return reduce ? batch_occupancy<StoreF32, true>(smem) : batch_occupancy<StoreF32, false>(smem);
 }
 
-int march_blocks_per_sm(int storage) {
-    const int smem = march_smem_bytes(storage);
-    int nb = 0;
+template <class S, int RW>
+static int march_occupancy(int smem) {
     // the plain step variant sets the grid; the reduction variant runs once per check
-    if (storage == CL_STORE_FP16DEV) {
-        cudaFuncSetAttribute(k_march<StoreF16, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_march<StoreF16, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF16, false>, kThreads, smem);
-    } else {
-        cudaFuncSetAttribute(k_march<StoreF32, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        cudaFuncSetAttribute(k_march<StoreF32, false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<StoreF32, false>, kThreads, smem);
-    }
+    int nb = 0;
+    cudaFuncSetAttribute(k_march<S, false, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_march<S, false, RW>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_march<S, false, RW>, kThreads, smem);
+    return nb;
+}
+
+template <class S>
+static int march_occupancy_s(int rw, int smem) {
+    return rw == 4 ? march_occupancy<S, 4>(smem) : (rw == 2 ? march_occupancy<S, 2>(smem) : march_occupancy<S, 1>(smem));
+}
+
+int march_blocks_per_sm(int storage, int rw) {
+    const int smem = march_smem_bytes(storage, rw);
+    const int nb = storage == CL_STORE_FP16DEV ? march_occupancy_s<StoreF16>(rw, smem)
+                                               : march_occupancy_s<StoreF32>(rw, smem);
     return nb > 0 ? nb : 1;
 }
 

@@ -7,8 +7,9 @@
 
 namespace cl {
 
-constexpr int kBX = 64;     // tile width in x (cells; two per lane of a warp)
-constexpr int kBY = 8;      // tile height in y (consumer warps per block)
+constexpr int kBX = 64;     // widest tile in x (cells; two per lane of a warp)
+constexpr int kBY = 8;      // consumer warps per block (tile rows of the widest tile)
+constexpr int kRowsMax = 4;  // tile shapes: RW = 1, 2, 4 rows per warp, tiles (kBX / RW) x (kBY * RW)
 constexpr int kStages = 4;  // plane slots per block: z, z+1 in use, two in flight
 constexpr int kPrefetchDefault = 0;  // planes beyond the TMA load pulled into L2
 constexpr int kThreads = 32 * (kBY + 1);  // one warp per row plus one producer warp
@@ -50,9 +51,9 @@ struct BatchInst {
     MarchArgs args[2];
 };
 
-// A tile column of one instance over planes [zs, ze)
+// A tile column of one instance over planes [zs, ze), tiles of rw rows per warp
 struct WorkItem {
-    int inst, x0, y0, zs, ze;
+    int inst, x0, y0, zs, ze, rw;
 };
 
 struct BatchLaunch {
@@ -82,10 +83,14 @@ cudaError_t launch_batch_finalize(const double* item_partials, const int* inst_f
                                   int n_inst, double* out, cudaStream_t s);
 int march_batch_blocks_per_sm(int storage, bool reduce);
 
-int march_slot_bytes(int storage);
-int march_smem_bytes(int storage);
-int march_blocks_per_sm(int storage);
-cudaError_t launch_march(int storage, bool reduce, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
+int march_slot_bytes(int storage, int rw);
+int march_smem_bytes(int storage, int rw);
+int march_blocks_per_sm(int storage, int rw);
+// relative cost of stepping one nx x ny plane in tiles of rw rows per warp
+double march_tile_cost(int nx, int ny, int storage, int rw);
+// tile rows per warp of least cost for an nx x ny plane
+int march_auto_rows(int nx, int ny, int storage);
+cudaError_t launch_march(int storage, bool reduce, int rw, const MarchMaps& maps, const MarchArgs& a, dim3 grid,
                          cudaStream_t s);
 cudaError_t launch_state_init(int storage, const MarchArgs& a, const uint16_t* mask_p, const float* C0,
                               cudaStream_t s);

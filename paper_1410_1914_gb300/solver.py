@@ -61,6 +61,13 @@ class Solver:
     def set_diffusivity(self, D):
         L.cl_lbm_set_diffusivity(self.h, D, self.n)
 
+    def set_tile_rows(self, rows: int = 0) -> int:
+        """Tile shape of the plane march ((C, delta) storage): rows of the
+        512-cell tile per warp, 1 (64 x 8), 2 (32 x 16) or 4 (16 x 32); 0
+        picks the shape with the fewest idle lanes along x.  Returns the
+        shape in use."""
+        return L.cl_lbm_set_tile_rows(self.h, rows)
+
     def set_rate_scale(self, kscale):
         """Per-cell factor on k (Eq. 17b with a non-uniform potential); None: uniform."""
         L.cl_lbm_set_rate_scale(self.h, kscale, self.n)

@@ -85,12 +85,12 @@ def test_batch_autotune_and_cache(cuda_lib, tmp_path):
     members = _make("fp16dev", check_every=20)
     b = Batch([s for s, *_ in members])
     cache = str(tmp_path / "tune.json")
-    zc, pf, ms, cached = b.autotune(steps_per_trial=4, cache=cache)
-    assert zc in (8, 16, 32, 64) and pf in (0, 2) and ms > 0 and not cached
-    zc2, pf2, ms2, cached2 = b.autotune(steps_per_trial=4, cache=cache)
-    assert cached2 and (zc2, pf2) == (zc, pf)
+    zc, pf, tr, ms, cached = b.autotune(steps_per_trial=4, cache=cache)
+    assert zc in (8, 16, 32, 64) and pf in (0, 2) and tr in (1, 2, 4) and ms > 0 and not cached
+    zc2, pf2, tr2, ms2, cached2 = b.autotune(steps_per_trial=4, cache=cache)
+    assert cached2 and (zc2, pf2, tr2) == (zc, pf, tr)
     steps = members[0][0].steps
-    assert steps == 8 * 4 or steps == 6 * 4  # every trial is a real step
+    assert steps == 3 * 6 * 4  # every trial is a real step: 3 shapes x z chunks 8, 16, 32 x 2 prefetch
     b.step(2)
     b.close()
 
