@@ -534,7 +534,8 @@ cl_status cl_batch_solve(cl_batch_handle b, long long max_steps, cl_solve_info* 
 
 /* Time steps_per_trial (even) steps for each tile shape in {1, 2, 4} rows
    per warp (one shape for every member; cl_lbm_set_tile_rows), z_chunk in
-   {8, 16, 32, 64} and L2 prefetch distance in {0, 2}, keep the fastest and
+   {8, 16, 32, 64, 128} (up to the deepest member) and L2 prefetch distance in
+   {0, 2}, keep the fastest and
    report it (ms per step in best_ms).  The trial steps are real steps of
    every member.  Any out pointer may be NULL. */
 cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk, int* prefetch, int* tile_rows,

@@ -389,7 +389,7 @@ cl_status cl_batch_autotune(cl_batch_handle b, int steps_per_trial, int* z_chunk
         if (h->cur != b->parity) { set_msg_txt("a member was stepped outside the batch"); return CL_ERR_STATE; }
     int nz_max = 0;
     for (auto* h : b->m) nz_max = std::max(nz_max, h->nz);
-    const int zcs[] = {8, 16, 32, 64};
+    const int zcs[] = {8, 16, 32, 64, 128};
     const int pfs[] = {0, 2};
     const int tiles[] = {1, 2, 4};
     cudaEvent_t e0, e1;

@@ -652,10 +652,10 @@ __device__ bool wait_done(const unsigned long long* done, unsigned long long tar
 
 constexpr int kFenceBits = 2048;  // (member, parity) pairs whose descriptors a block has fenced
 
-// Plain steps fit three (FP16) or two (FP32) resident blocks per SM; the
-// reducing step keeps the registers it needs
+// Plain steps fit three (FP16) or two (FP32) resident blocks per SM, the
+// reducing step (one per check interval) two
 template <class S, bool REDUCE>
-__global__ void __launch_bounds__(kThreads, REDUCE ? 1 : (sizeof(typename S::T) == 2 ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, REDUCE ? 2 : (sizeof(typename S::T) == 2 ? 3 : 2))
     k_march_batch(const BatchInst* __restrict__ insts, const WorkItem* __restrict__ items,
                   const int* __restrict__ n_items_ptr, const int* __restrict__ inst_count, int nsteps, int parity0,
                   unsigned long long* next, unsigned long long* done, int* abort_flag, double* item_partials,
