@@ -520,7 +520,10 @@ void cl_batch_destroy(cl_batch_handle b);
 
 /* Advance every member by exactly nsteps steps in one cooperative launch
    (the same arithmetic as cl_lbm_step).  CL_ERR_TIMEOUT if a bounded wait
-   for a member's previous step gave up. */
+   for a member's previous step, or a member's own plane wait, gave up (the
+   members' states are then partly stepped: re-initialise them).  A member's
+   wait settings (cl_lbm_set_wait_test) reach the batch when it is created
+   or configured. */
 cl_status cl_batch_step(cl_batch_handle b, long long nsteps);
 
 /* Advance all members, check_every steps per launch (a captured CUDA graph

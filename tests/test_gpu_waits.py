@@ -98,3 +98,44 @@ def test_batch_step_wait_runs_out(cuda_lib, storage):
     b.close()
     for s in members:
         s.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16dev"])
+def test_member_plane_wait_runs_out_inside_batch(cuda_lib, storage):
+    """A member's own plane wait gives up inside the batched launch: its
+    block raises the abort word, every other block leaves its queue or its
+    step wait, and the step reports CL_ERR_TIMEOUT through the member's
+    error word.  A member's wait settings reach the batch when the batch is
+    created or configured."""
+    from paper_1410_1914_gb300 import Solver
+    from paper_1410_1914_gb300 import _lib as L
+    from paper_1410_1914_gb300.batch import Batch
+    spec = (("pt_cl_256", (20, 30, 70), 43), ("npmc_cl_400", (33, 17, 45), 44))
+
+    def make():
+        out = []
+        for wl, shape, seed in spec:
+            ph, react, params = inputs.make_workload(wl, shape=shape, seed=seed)
+            s = Solver(ph.shape, storage=storage, check_every=20, **params)
+            s.set_structure(ph, react)
+            out.append(s)
+        return out
+
+    members = make()
+    lib = L.load()
+    assert lib.cl_lbm_set_wait_test(members[1].h, SHORT, 1) == L.CL_OK
+    b = Batch(members, z_chunk=8)
+    assert lib.cl_batch_step(b.b, 4) == L.CL_ERR_TIMEOUT
+    assert lib.cl_lbm_set_wait_test(members[1].h, 0, 0) == L.CL_OK
+    b.configure(8, 0, 0)  # the members' arguments again, without the hook
+    for s in members:
+        s.init()
+    b.step(30)
+    refs = make()
+    for s, r in zip(members, refs):
+        r.step(30)
+        np.testing.assert_array_equal(s.populations(), r.populations())
+        r.close()
+    b.close()
+    for s in members:
+        s.close()
