@@ -1132,6 +1132,38 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
             CK(cudaStreamSynchronize(h->s));
             return CL_OK;
         };
+        // kCgBatch CG iterations on the fixed cell buffers, captured once and
+        // replayed as one CUDA graph (five launches per iteration otherwise
+        // cost more than the iteration's own memory traffic on small boxes)
+        auto enqueue_cg = [&](cudaStream_t st) -> cudaError_t {
+            for (int k = 0; k < kCgBatch; ++k) {
+                const cudaError_t ce = launch_cg_iter(da, dinv, eps, rc, zc, pc, qc, nblk, part, cs, st);
+                if (ce != cudaSuccess) return ce;
+            }
+            return cudaSuccess;
+        };
+        cudaGraphExec_t cg_graph = nullptr;
+        struct GraphGuard {
+            cudaGraphExec_t* g;
+            ~GraphGuard() { if (*g) cudaGraphExecDestroy(*g); }
+        } guard{&cg_graph};
+        {
+            cudaStream_t cap = nullptr;
+            cudaGraph_t g = nullptr;
+            bool ok = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess;
+            if (ok) ok = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const cudaError_t ce = enqueue_cg(cap);
+                ok = cudaStreamEndCapture(cap, &g) == cudaSuccess && g && ce == cudaSuccess;
+            }
+            if (ok) ok = cudaGraphInstantiate(&cg_graph, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (cap) cudaStreamDestroy(cap);
+            if (!ok) {
+                cg_graph = nullptr;
+                cudaGetLastError();  // the same kernels then run as plain launches
+            }
+        }
         // P v = v + w_i eps, L eps = sum_i v_i to kCgTol by diagonal-preconditioned CG
         auto precondition = [&](const float* v, float* zout) -> cl_status {
             CK(launch_cg_start(da, v, dinv, eps, rc, zc, pc, nblk, part, cs, h->s));
@@ -1139,7 +1171,8 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
             CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, h->s));
             CK(cudaStreamSynchronize(h->s));
             while (!hc.bad && hc.iters < kMaxCg && hc.rr > kCgTol * kCgTol * hc.rr0) {
-                for (int k = 0; k < kCgBatch; ++k) CK(launch_cg_iter(da, dinv, eps, rc, zc, pc, qc, nblk, part, cs, h->s));
+                if (cg_graph) CK(cudaGraphLaunch(cg_graph, h->s));
+                else CK(enqueue_cg(h->s));
                 CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, h->s));
                 CK(cudaStreamSynchronize(h->s));
             }
