@@ -14,8 +14,11 @@
 // positive definite (with a fixed-concentration face or a sink) and is
 // solved by conjugate gradients with its diagonal as preconditioner.
 //
-// Every vector kernel is a grid-stride loop; dot products accumulate in
-// FP64 per block and one block sums the block partials in a fixed order.
+// Every vector kernel is a grid-stride loop.  The inner CG's dot products
+// accumulate per thread in FP32 (a few dozen terms each: ample for a solve
+// to 1e-2, and FP64 arithmetic runs at a small fraction of the FP32 rate on
+// this GPU), then per block in FP64; the GMRES dot products accumulate in
+// FP64.  One block sums the block partials in a fixed order.
 // The CG scalars live in device memory, so a batch of iterations runs
 // without a host round trip.
 #include "internal.cuh"
@@ -57,7 +60,17 @@ __device__ __forceinline__ void lap_row(uint16_t m, int x, int y, int z, long lo
     *off = o;
 }
 
+// (x, y, z) of cell c: 32-bit division while the box's cell count fits (a
+// 64-bit division is a long emulated sequence on the GPU)
 __device__ __forceinline__ void cell_xyz(long long c, const DsaArgs& a, int* x, int* y, int* z) {
+    if (a.N < (1LL << 31)) {
+        const unsigned cc = (unsigned)c, nx = (unsigned)a.nx, ny = (unsigned)a.ny;
+        const unsigned r = cc / nx;
+        *x = (int)(cc - r * nx);
+        *y = (int)(r % ny);
+        *z = (int)(r / ny);
+        return;
+    }
     *x = (int)(c % a.nx);
     const long long r = c / a.nx;
     *y = (int)(r % a.ny);
@@ -86,7 +99,7 @@ __global__ void __launch_bounds__(kDT) k_cg_start(DsaArgs a, const float* __rest
                                                   float* __restrict__ eps, float* __restrict__ r,
                                                   float* __restrict__ zc, float* __restrict__ p,
                                                   double* __restrict__ part) {
-    double acc[2] = {0.0, 0.0};
+    float af[2] = {0.f, 0.f};  // per-thread FP32 partials (FP64 is a small fraction of the FP32 rate here)
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
          c += (long long)gridDim.x * blockDim.x) {
         float rho = 0.f;
@@ -99,9 +112,10 @@ __global__ void __launch_bounds__(kDT) k_cg_start(DsaArgs a, const float* __rest
         r[c] = rho;
         zc[c] = zz;
         p[c] = zz;
-        acc[0] += (double)rho * zz;
-        acc[1] += (double)rho * rho;
+        af[0] = fmaf(rho, zz, af[0]);
+        af[1] = fmaf(rho, rho, af[1]);
     }
+    double acc[2] = {(double)af[0], (double)af[1]};
     block_sum_store<2>(acc, part + 2 * blockIdx.x);
 }
 
@@ -109,7 +123,7 @@ __global__ void __launch_bounds__(kDT) k_cg_start(DsaArgs a, const float* __rest
 __global__ void __launch_bounds__(kDT) k_cg_lap(DsaArgs a, const float* __restrict__ p, float* __restrict__ q,
                                                 double* __restrict__ part, const CgScalars* __restrict__ cs) {
     if (cs->bad) return;
-    double acc[1] = {0.0};
+    float af = 0.f;  // per-thread FP32 partial
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
          c += (long long)gridDim.x * blockDim.x) {
         const uint16_t m = a.mask[c];
@@ -122,8 +136,9 @@ __global__ void __launch_bounds__(kDT) k_cg_lap(DsaArgs a, const float* __restri
             out = d * p[c] - o;
         }
         q[c] = out;
-        acc[0] += (double)p[c] * out;
+        af = fmaf(p[c], out, af);
     }
+    double acc[1] = {(double)af};
     block_sum_store<1>(acc, part + 2 * blockIdx.x);
 }
 
@@ -134,16 +149,17 @@ __global__ void __launch_bounds__(kDT) k_cg_update(long long N, const float* __r
                                                    double* __restrict__ part, const CgScalars* __restrict__ cs) {
     if (cs->bad) return;
     const float al = (float)cs->alpha;
-    double acc[2] = {0.0, 0.0};
+    float af[2] = {0.f, 0.f};  // per-thread FP32 partials
     for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
         eps[c] = fmaf(al, p[c], eps[c]);
         const float rr = fmaf(-al, q[c], r[c]);
         r[c] = rr;
         const float zz = dinv[c] * rr;
         zc[c] = zz;
-        acc[0] += (double)rr * zz;
-        acc[1] += (double)rr * rr;
+        af[0] = fmaf(rr, zz, af[0]);
+        af[1] = fmaf(rr, rr, af[1]);
     }
+    double acc[2] = {(double)af[0], (double)af[1]};
     block_sum_store<2>(acc, part + 2 * blockIdx.x);
 }
 
