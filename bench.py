@@ -29,6 +29,7 @@ import threading
 import time
 
 import hashlib
+import re
 
 import numpy as np
 
@@ -40,12 +41,21 @@ KERNEL_SRCS_Q19S = [os.path.join(_CSRC, f) for f in ("q19s.cu", "internal.cuh", 
 KERNEL_SRCS_POP = [os.path.join(_CSRC, f) for f in ("kernels.cu", "internal.cuh", "device_util.cuh")]
 
 
+def code_only(text: str) -> str:
+    """C/CUDA source without its comments and with whitespace collapsed, so
+    that editing a comment does not read as a kernel change."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_src_sha256(srcs=None) -> str:
-    """sha256 over the step kernel's sources (the key of profiles/traffic.json)."""
+    """sha256 over the step kernel's sources, comments and whitespace aside
+    (the key of profiles/traffic.json)."""
     h = hashlib.sha256()
     for f in srcs or KERNEL_SRCS:
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(code_only(fh.read()).encode())
     return h.hexdigest()
 TRAFFIC_JSON = os.path.join(ROOT, "profiles", "traffic.json")
 sys.path.insert(0, ROOT)

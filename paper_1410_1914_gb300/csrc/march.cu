@@ -715,7 +715,8 @@ __global__ void __launch_bounds__(kThreads, REDUCE ? 2 : (sizeof(typename S::T) 
         const int w = s_w;
         const int par = parity0 ^ (step & 1);
         const MarchArgs& a = s_args;
-        // the producer's loads (async proxy) come after the other members' writes it waited for
+        // the producer's TMA loads (async proxy) come after the stores of the member's previous
+        // step by other blocks (generic proxy), which the lead thread's wait acquired
         if (threadIdx.y == kBY && threadIdx.x == 0) asm volatile("fence.proxy.async.global;" ::: "memory");
         double rv[RED_N];
 #pragma unroll

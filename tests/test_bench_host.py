@@ -51,7 +51,13 @@ def test_source_hash_covers_the_kernel_files(tmp_path):
     b.write_text("header B")
     h1 = bench.kernel_src_sha256([str(a), str(b)])
     b.write_text("header B changed")
-    assert bench.kernel_src_sha256([str(a), str(b)]) != h1
+    h2 = bench.kernel_src_sha256([str(a), str(b)])
+    assert h2 != h1
+    # comments and layout are not the kernel: editing them keeps the key
+    b.write_text("header   B /* a note */ changed // another note\n")
+    assert bench.kernel_src_sha256([str(a), str(b)]) == h2
+    a.write_text("kernel A // x\n/* y\n z */")
+    assert bench.kernel_src_sha256([str(a), str(b)]) == h2
 
 
 def test_peak_bandwidth_measured_or_fallback(tmp_path, monkeypatch):
