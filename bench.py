@@ -251,38 +251,36 @@ def run_reference(args):
     return 0
 
 
-def run_batch(args):
-    """Batched persistent launch: 64 structures of edge 32-160 in one launch
-    per check interval, against the same structures stepped one by one."""
+def measure_batch64(storage: str, K: int, steps: int, warmup: int, stream):
+    """The batch of 64 structures (edges 32-160, Pt/NPMC alternating) in one
+    persistent launch per check interval, after the autotuner; against the
+    same structures stepped one by one."""
     import torch
     from paper_1410_1914_gb300 import Solver, inputs
     from paper_1410_1914_gb300.batch import Batch
-    torch.cuda.set_device(0)
-    stream = torch.cuda.current_stream()
-    K = args.check_every
     work = inputs.batch_workloads(64)
     solvers = []
     for ph, react, params in work:
-        s = Solver(ph.shape, storage=args.storage, stream=int(stream.cuda_stream), check_every=K, **params)
+        s = Solver(ph.shape, storage=storage, stream=int(stream.cuda_stream), check_every=K, **params)
         s.set_structure(ph, react)
         solvers.append(s)
     cells = sum(ph.size for ph, _, _ in work)
     b = Batch(solvers)
     zc, pf, tr, ms_tune, cached = b.autotune(steps_per_trial=4, cache=None)
     bi = b.info()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.step(K)
     torch.cuda.synchronize()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clocks:
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.step(K)
         ev1.record(stream)
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
-    mlups = cells * K * args.steps / (ms * 1e-3) / 1e6
+    mlups = cells * K * steps / (ms * 1e-3) / 1e6
     # one solve interval through the per-structure stopping rule, for its overhead
     t0 = time.perf_counter()
     b.solve(K)
@@ -301,28 +299,50 @@ def run_batch(args):
     torch.cuda.synchronize()
     seq_mlups = cells * K / (e0.elapsed_time(e1) * 1e-3) / 1e6
     peak, peak_kind = measured_peak_gbs()
-    achieved = bytes_per_cell(args.storage) * cells * K * args.steps / (ms * 1e-3) / 1e9
-    line = {
-        "metric": "MLUPS (batch of 64 structures, one persistent launch per check interval)",
-        "value": mlups, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "64 cubes, edge uniform 32-160, Pt/NPMC alternating, porosity 0.35-0.65, "
-                               "Knudsen D, D_eff set-up", "cells": cells, "storage": args.storage,
-                   "lbm_steps_per_bench_step": K, "autotuned": {"z_chunk": zc, "prefetch": pf, "tile_rows": tr},
-                   "grid_blocks": bi["grid_blocks"], "work_items": bi["n_items"]},
-        "sequential_mlups": seq_mlups,
-        "batch_over_sequential": mlups / seq_mlups,
-        "solve_interval_s": interval_s,
-        "solve_uses_graph": b.info()["uses_graph"],
+    achieved = bytes_per_cell(storage) * cells * K * steps / (ms * 1e-3) / 1e9
+    out = {
+        "workload": "64 cubes, edge uniform 32-160, Pt/NPMC alternating, porosity 0.35-0.65, Knudsen D, "
+                    "D_eff set-up", "cells": cells, "storage": storage, "lbm_steps_per_bench_step": K,
+        "steps": steps, "warmup": warmup, "mlups": mlups, "ms_per_step": ms / steps,
+        "autotuned": {"z_chunk": zc, "prefetch": pf, "tile_rows": tr},
+        "grid_blocks": bi["grid_blocks"], "work_items": bi["n_items"],
+        "sequential_mlups": seq_mlups, "batch_over_sequential": mlups / seq_mlups,
+        "solve_interval_s": interval_s, "solve_uses_graph": b.info()["uses_graph"],
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "layout_frac": layout_bytes_per_cell(storage) * cells * K * steps / (ms * 1e-3) / 1e9 / peak,
                      "traffic": None, "peak_kind": f"{peak_kind} hbm_gbs", "kernel": "k_march_batch"},
-        "gpu_launches": args.steps,
+        "gpu_launches": steps,
         "clocks": clocks.summary(),
     }
     b.close()
     for s in solvers:
         s.close()
+    return out
+
+
+def run_batch(args):
+    """Batched persistent launch: 64 structures of edge 32-160 in one launch
+    per check interval, against the same structures stepped one by one."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    r = measure_batch64(args.storage, args.check_every, args.steps, args.warmup, stream)
+    line = {
+        "metric": "MLUPS (batch of 64 structures, one persistent launch per check interval)",
+        "value": r["mlups"], "unit": "MLUPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "cells": r["cells"], "storage": args.storage,
+                   "lbm_steps_per_bench_step": args.check_every, "autotuned": r["autotuned"],
+                   "grid_blocks": r["grid_blocks"], "work_items": r["work_items"]},
+        "sequential_mlups": r["sequential_mlups"],
+        "batch_over_sequential": r["batch_over_sequential"],
+        "solve_interval_s": r["solve_interval_s"],
+        "solve_uses_graph": r["solve_uses_graph"],
+        "roofline": r["roofline"],
+        "gpu_launches": r["gpu_launches"],
+        "clocks": r["clocks"],
+    }
     print(json.dumps(line), flush=True)
     return 0
 
@@ -738,6 +758,8 @@ def main():
                     help="default workload: skip the time-to-converged D_eff arms (128^3)")
     ap.add_argument("--no-npmc", action="store_true",
                     help="default workload: skip the 400^3 NPMC measurement")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="default workload: skip the batch of 64 structures (FP16 state, 5 intervals)")
     ap.add_argument("--carrier", default="o2", choices=["o2", "proton"],
                     help="converge workload: O2 in the pores (D_eff) or protons in the ionomer (sigma_eff)")
     args = ap.parse_args()
@@ -902,6 +924,11 @@ def main():
             line["npmc_400"] = measure_npmc400(stream, K, args.steps, peak, local)
         if not args.no_ttc:
             line["ttc"] = measure_ttc(local)
+        if not args.no_batch:
+            try:
+                line["batch64"] = measure_batch64("fp16dev", K, 5, 3, stream)
+            except Exception as e:  # reported in the line, which is printed either way
+                line["batch64"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(ph, react, params, args.cpu_budget, args.lattice)
     if rank == 0:
