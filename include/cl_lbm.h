@@ -585,7 +585,8 @@ cl_status cl_batch_info(cl_batch_handle b, int* grid_blocks, int* n_items, int* 
    threads) race: serialise them.  Every call looks up the array's address on
    the current device (no allocation; a cached address would not survive a
    context reset).  The call copies an error word to the host and
-   synchronises its stream before it returns.  Allocates nothing.
+   synchronises its stream before it returns, so it cannot be made inside a
+   stream capture (CUDA graph).  Allocates nothing.
    Errors: CL_ERR_ARG (NULL pointer, size, a pointer that is not device or
    managed memory of the current device, phase code > 3), CL_ERR_CUDA,
    CL_ERR_TIMEOUT (labelling iteration bound). */
