@@ -286,10 +286,11 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
                               int* iterations);
 
 /* cl_lbm_solve_krylov with each f32 correction found by flexible GMRES(30)
-   with a diffusion preconditioner, for D3Q7 only.  The slow modes of the
+   with a diffusion preconditioner, on either lattice.  The slow modes of the
    step map are diffusive: a correction of equilibrium shape w_i eps changes
    the cell sums by L eps in one step, L being the Laplacian of the active
-   cells with link weight 1/8 (2/8 on a fixed-concentration face, (1 - r)/8
+   cells with the lattice weight w_i on each link (D3Q7: 1/8; D3Q19: 1/18
+   axial, 1/36 diagonal; 2 w_i on a fixed-concentration face, (1 - r) w_i
    on a catalytic face, 0 on a bounce-back face).  The preconditioner
    P v = v + w_i eps with L eps = sum_i v_i (diagonal-preconditioned
    conjugate gradients to 1e-2) keeps the number of step applications
@@ -302,7 +303,7 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
    cl_lbm_solve_krylov.
      iterations:       nullable; GMRES iterations (step applications).
      inner_iterations: nullable; conjugate-gradient iterations in all.
-   Needs D3Q7 and CL_STORAGE_FP32POP, else CL_ERR_STATE.  Allocates 64 f32
+   Needs CL_STORAGE_FP32POP, else CL_ERR_STATE.  Allocates 64 f32
    and 2 FP64 population-sized vectors plus 6 f32 cell fields for the call
    (through p->alloc if given) and frees them before returning.
    Errors: as cl_lbm_solve_krylov. */

@@ -10,6 +10,7 @@
 
 #include "device_util.cuh"
 #include "handle.cuh"
+#include "dsa.cuh"
 
 using namespace cl;
 
@@ -1068,8 +1069,8 @@ cl_status cl_lbm_solve_krylov(cl_handle h, double tol, int max_iter, long long m
 cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long long max_steps, cl_solve_info* info,
                                   int* iterations, long long* inner_iterations) {
     CKS(need_structure(h));
-    if (h->march || h->q19s || h->q != 7) {
-        set_msg_txt("the preconditioned Krylov solve needs D3Q7 with the plain f32 population storage");
+    if (h->march || h->q19s) {
+        set_msg_txt("the preconditioned Krylov solve needs the plain f32 population storage");
         return CL_ERR_STATE;
     }
     if (!(tol > 0.0) || max_iter < 0 || max_steps < 0) {
@@ -1077,7 +1078,8 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         return CL_ERR_ARG;
     }
     auto t0 = std::chrono::steady_clock::now();
-    const long long N = h->N, L = 7 * h->N;
+    const bool q19 = h->q == 19;  // D3Q19: the padded population layout (pitch px19)
+    const long long N = q19 ? h->NP19 : h->N, L = (q19 ? 19 : 7) * N;
     const int nblk = kry_blocks();
     constexpr int kM = 30;           // Krylov vectors per GMRES cycle
     constexpr int kMaxCycles = 10;   // cycles per correction
@@ -1126,7 +1128,11 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         da.bc_in = h->p.bc_in; da.bc_out = h->p.bc_out;
         da.kscale = h->kscale;
         da.k_lu = h->k_lu;
-        CK(launch_lap_dinv(da, dinv, nblk, h->s));
+        Dsa19 d19;
+        d19.px = h->px19;
+        d19.mask = h->mask19;
+        d19.react = h->react19;
+        CK(q19 ? launch_lap_dinv19(da, d19, dinv, nblk, h->s) : launch_lap_dinv(da, dinv, nblk, h->s));
         auto host_double = [&](const double* dptr, double* out, int n) -> cl_status {
             CK(cudaMemcpyAsync(out, dptr, sizeof(double) * n, cudaMemcpyDeviceToHost, h->s));
             CK(cudaStreamSynchronize(h->s));
@@ -1137,7 +1143,8 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         // cost more than the iteration's own memory traffic on small boxes)
         auto enqueue_cg = [&](cudaStream_t st) -> cudaError_t {
             for (int k = 0; k < kCgBatch; ++k) {
-                const cudaError_t ce = launch_cg_iter(da, dinv, eps, rc, zc, pc, qc, nblk, part, cs, st);
+                const cudaError_t ce = q19 ? launch_cg_iter19(da, d19, dinv, eps, rc, zc, pc, qc, nblk, part, cs, st)
+                                           : launch_cg_iter(da, dinv, eps, rc, zc, pc, qc, nblk, part, cs, st);
                 if (ce != cudaSuccess) return ce;
             }
             return cudaSuccess;
@@ -1166,7 +1173,8 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
         }
         // P v = v + w_i eps, L eps = sum_i v_i to kCgTol by diagonal-preconditioned CG
         auto precondition = [&](const float* v, float* zout) -> cl_status {
-            CK(launch_cg_start(da, v, dinv, eps, rc, zc, pc, nblk, part, cs, h->s));
+            CK(q19 ? launch_cg_start19(da, d19, v, dinv, eps, rc, zc, pc, nblk, part, cs, h->s)
+                   : launch_cg_start(da, v, dinv, eps, rc, zc, pc, nblk, part, cs, h->s));
             CgScalars hc;
             CK(cudaMemcpyAsync(&hc, cs, sizeof(hc), cudaMemcpyDeviceToHost, h->s));
             CK(cudaStreamSynchronize(h->s));
@@ -1177,7 +1185,7 @@ cl_status cl_lbm_solve_krylov_dsa(cl_handle h, double tol, int max_iter, long lo
                 CK(cudaStreamSynchronize(h->s));
             }
             cg_total += hc.iters;
-            CK(launch_prec_out(N, v, eps, zout, nblk, h->s));
+            CK(q19 ? launch_prec_out19(N, v, eps, zout, nblk, h->s) : launch_prec_out(N, v, eps, zout, nblk, h->s));
             return CL_OK;
         };
         // flexible GMRES(kM) in f32 on (I - A) e = c from e = 0, to tol_in times |c|

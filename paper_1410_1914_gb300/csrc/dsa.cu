@@ -23,6 +23,7 @@
 // without a host round trip.
 #include "internal.cuh"
 #include "device_util.cuh"
+#include "dsa.cuh"
 
 namespace cl {
 
@@ -262,6 +263,134 @@ __global__ void __launch_bounds__(kDT) k_comb(const float* __restrict__ a, const
         out[i] = c ? (a[i] - b[i]) + c[i] : a[i] - b[i];
 }
 
+// ---- D3Q19 (Eq. 22-24): link weights 1/18 (axial), 1/36 (diagonal), 1/3 (rest)
+// velocities of Eq. 22 in the order of the step kernels: 1-6 axial (+x, -x,
+// +y, -y, +z, -z), 7-18 the face diagonals
+__device__ __forceinline__ int d19_cx(int i) {
+    constexpr int t[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+    return t[i];
+}
+__device__ __forceinline__ int d19_cy(int i) {
+    constexpr int t[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+    return t[i];
+}
+__device__ __forceinline__ int d19_cz(int i) {
+    constexpr int t[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+    return t[i];
+}
+__device__ __forceinline__ float d19_w(int i) { return i == 0 ? 1.f / 3.f : (i <= 6 ? 1.f / 18.f : 1.f / 36.f); }
+
+__device__ __forceinline__ void cell_xyz19(long long c, const DsaArgs& a, const Dsa19& b, int* x, int* y, int* z) {
+    const long long r = c / b.px;
+    *x = (int)(c - r * b.px);
+    *y = (int)(r % a.ny);
+    *z = (int)(r / a.ny);
+}
+
+// Row of L at cell c on D3Q19: for each link toward x + c_i, weight w_i to an
+// open neighbour; a closed link is a wall (nothing) or catalytic ((1 - r)
+// w_i on the diagonal); a link that leaves the box in x meets the inlet or
+// outlet face (2 w_i at a fixed value, nothing at zero flux).  A closed link
+// takes precedence over the face, as in the step kernel.
+__device__ __forceinline__ void lap_row19(uint32_t m, uint32_t rb, int x, int y, int z, const DsaArgs& a,
+                                          const Dsa19& b, const float* __restrict__ v, float* diag, float* off) {
+    float d = 0.f, o = 0.f;
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const float w = d19_w(i);
+        const int cx = d19_cx(i), cy = d19_cy(i), cz = d19_cz(i);
+        if ((m >> (i - 1)) & 1u) {
+            if ((rb >> (i - 1)) & 1u) d += a.rsink * w;
+        } else if ((cx < 0 && x == 0) || (cx > 0 && x == a.nx - 1)) {
+            if ((cx < 0 ? a.bc_in : a.bc_out) == CL_BC_DIRICHLET) d += 2.f * w;
+        } else {
+            d += w;
+            if (v) {
+                const int yy = y + cy < 0 ? a.ny - 1 : (y + cy >= a.ny ? 0 : y + cy);
+                const int zz = z + cz < 0 ? a.nz - 1 : (z + cz >= a.nz ? 0 : z + cz);
+                o += w * v[(long long)(x + cx) + (long long)b.px * (yy + (long long)a.ny * zz)];
+            }
+        }
+    }
+    *diag = d;
+    *off = o;
+}
+
+__global__ void __launch_bounds__(kDT) k_lap_dinv19(DsaArgs a, Dsa19 b, float* __restrict__ dinv) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = b.mask[c];
+        float out = 0.f;
+        if (m & kQ19Active) {
+            int x, y, z;
+            cell_xyz19(c, a, b, &x, &y, &z);
+            const uint32_t rb = (m & kQ19HasReact) ? b.react[c] : 0u;
+            float d, o;
+            lap_row19(m, rb, x, y, z, a, b, nullptr, &d, &o);
+            out = d > 0.f ? 1.f / d : 0.f;
+        }
+        dinv[c] = out;
+    }
+}
+
+__global__ void __launch_bounds__(kDT) k_cg_start19(DsaArgs a, Dsa19 b, const float* __restrict__ v,
+                                                    const float* __restrict__ dinv, float* __restrict__ eps,
+                                                    float* __restrict__ r, float* __restrict__ zc,
+                                                    float* __restrict__ p, double* __restrict__ part) {
+    float af[2] = {0.f, 0.f};
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        float rho = 0.f;
+        if (b.mask[c] & kQ19Active) {
+#pragma unroll
+            for (int i = 0; i < 19; ++i) rho += v[(long long)i * a.N + c];
+        }
+        const float zz = dinv[c] * rho;
+        eps[c] = 0.f;
+        r[c] = rho;
+        zc[c] = zz;
+        p[c] = zz;
+        af[0] = fmaf(rho, zz, af[0]);
+        af[1] = fmaf(rho, rho, af[1]);
+    }
+    double acc[2] = {(double)af[0], (double)af[1]};
+    block_sum_store<2>(acc, part + 2 * blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kDT) k_cg_lap19(DsaArgs a, Dsa19 b, const float* __restrict__ p,
+                                                  float* __restrict__ q, double* __restrict__ part,
+                                                  const CgScalars* __restrict__ cs) {
+    if (cs->bad) return;
+    float af = 0.f;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < a.N;
+         c += (long long)gridDim.x * blockDim.x) {
+        const uint32_t m = b.mask[c];
+        float out = 0.f;
+        if (m & kQ19Active) {
+            int x, y, z;
+            cell_xyz19(c, a, b, &x, &y, &z);
+            const uint32_t rb = (m & kQ19HasReact) ? b.react[c] : 0u;
+            float d, o;
+            lap_row19(m, rb, x, y, z, a, b, p, &d, &o);
+            out = d * p[c] - o;
+        }
+        q[c] = out;
+        af = fmaf(p[c], out, af);
+    }
+    double acc[1] = {(double)af};
+    block_sum_store<1>(acc, part + 2 * blockIdx.x);
+}
+
+// zout_i = v_i + w_i eps over the 19 planes
+__global__ void __launch_bounds__(kDT) k_prec_out19(long long N, const float* __restrict__ v,
+                                                    const float* __restrict__ eps, float* __restrict__ zout) {
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < N; c += (long long)gridDim.x * blockDim.x) {
+        const float e = eps[c];
+#pragma unroll
+        for (int i = 0; i < 19; ++i) zout[(long long)i * N + c] = fmaf(d19_w(i), e, v[(long long)i * N + c]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_lap_dinv(const DsaArgs& a, float* dinv, int nblk, cudaStream_t s) {
@@ -312,6 +441,33 @@ cudaError_t launch_scale_dev(float* y, const float* x, const double* nrm, long l
 cudaError_t launch_comb(const float* a, const float* b, const float* c, float* out, long long L, int nblk,
                         cudaStream_t s) {
     k_comb<<<nblk, kDT, 0, s>>>(a, b, c, out, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lap_dinv19(const DsaArgs& a, const Dsa19& b, float* dinv, int nblk, cudaStream_t s) {
+    k_lap_dinv19<<<nblk, kDT, 0, s>>>(a, b, dinv);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_start19(const DsaArgs& a, const Dsa19& b, const float* v, const float* dinv, float* eps,
+                              float* r, float* zc, float* p, int nblk, double* part, CgScalars* cs, cudaStream_t s) {
+    k_cg_start19<<<nblk, kDT, 0, s>>>(a, b, v, dinv, eps, r, zc, p, part);
+    k_cg_fin<CG_START><<<1, kDT, 0, s>>>(part, nblk, cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cg_iter19(const DsaArgs& a, const Dsa19& b, const float* dinv, float* eps, float* r, float* zc,
+                             float* p, float* q, int nblk, double* part, CgScalars* cs, cudaStream_t s) {
+    k_cg_lap19<<<nblk, kDT, 0, s>>>(a, b, p, q, part, cs);
+    k_cg_fin<CG_ALPHA><<<1, kDT, 0, s>>>(part, nblk, cs);
+    k_cg_update<<<nblk, kDT, 0, s>>>(a.N, p, q, dinv, eps, r, zc, part, cs);
+    k_cg_fin<CG_BETA><<<1, kDT, 0, s>>>(part, nblk, cs);
+    k_cg_p<<<nblk, kDT, 0, s>>>(a.N, zc, p, cs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prec_out19(long long N, const float* v, const float* eps, float* zout, int nblk, cudaStream_t s) {
+    k_prec_out19<<<nblk, kDT, 0, s>>>(N, v, eps, zout);
     return cudaGetLastError();
 }
 

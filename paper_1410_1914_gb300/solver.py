@@ -117,7 +117,7 @@ class Solver:
 
     def solve_krylov_dsa(self, tol: float = 1e-8, max_iter: int = 20000, max_steps: int | None = None):
         """solve_krylov with flexible GMRES and the diffusion preconditioner
-        (D3Q7, plain f32 populations).  Adds "iterations" (step
+        (either lattice, plain f32 populations).  Adds "iterations" (step
         applications) and "inner_iterations" (conjugate-gradient
         iterations) to the solve info."""
         if max_steps is None:
