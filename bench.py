@@ -506,11 +506,11 @@ def measure_converge(args, arm_names=None):
 
     if want("fp32pop+krylov"):
         steady_arm("fp32pop+krylov", lambda s: s.solve_krylov(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0))
+    if want("fp32pop+krylov_dsa"):
+        # flexible GMRES with the diffusion preconditioner (either lattice)
+        steady_arm("fp32pop+krylov_dsa",
+                   lambda s: s.solve_krylov_dsa(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0))
     if args.lattice == "d3q7":
-        if want("fp32pop+krylov_dsa"):
-            # flexible GMRES with the diffusion preconditioner
-            steady_arm("fp32pop+krylov_dsa",
-                       lambda s: s.solve_krylov_dsa(tol=1e-8, max_iter=args.krylov_max_iter, max_steps=0))
         if want("fp32pop+lines"):
             # the same fixed point in C alone, the populations eliminated along lines (FGMRES in FP64)
             steady_arm("fp32pop+lines",
